@@ -1,0 +1,338 @@
+"""Benchmark of the GB300 FT-GCR(k) library.
+
+Workload (one "step"): one mixed-precision FT-GCR(4) solve of the 1024 x 512
+latitude-longitude hill problem (h0 = 0.1, half-width 20 deg, flow RHS,
+mu = 0.3 / dtheta^2, tol 1e-10 relative): FP32 inner vectors, stencil,
+preconditioner and axpys; FP64 inner products, norm test and outer refinement
+residual.  Inputs are resident in HBM; L2 (129 MB) is flushed between timed
+steps by writing a 256 MB buffer.  Reported beside it: the plain FP64 GPU path
+on the same problem, per-solve p50/p99 latency, the roofline of the
+persistent iteration kernel, the end-to-end number through the C ABI with
+host buffers, and the CPU oracle timed on this host's cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2103_07210_gb300 import inputs  # noqa: E402
+
+METRIC = "GCR iters/s, solves/s at 1024x512 (mixed vs FP64), HBM % peak; p50/p99 latency"
+NLON, NLAT, K, TOL = 1024, 512, 4, 1e-10
+WORKLOAD = "ftgcr4_mixed_1024x512_hill_tol1e-10"
+
+# Algorithmic bytes of one inner step, averaged over a Krylov cycle of length
+# k: (14 + 1.5 (k + 1)) vectors of s bytes (s = 4 for the FP32 inner vectors);
+# each refinement sweep adds 6 FP64 vectors (x, d, R, r_out, Tx, Ty).
+def algorithmic_bytes(steps: int, outer: int, k: int = K, s: int = 4, N: int = NLON * NLAT) -> float:
+    return steps * (14 + 1.5 * (k + 1)) * s * N + (outer + 1) * 6 * 8 * N
+
+
+# DRAM traffic per launch of the persistent kernel from one ncu capture, valid
+# only for the kernel sources it was taken on (sha256 of the CUDA sources).
+NCU_TRAFFIC = {"sources_sha256": None, "bytes_per_launch": None}
+
+
+def sources_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2103_07210_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        time.sleep(0.25)
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ oracle arm
+def _oracle_solve(_):
+    import oracle
+
+    p = inputs.hill_problem(NLON, NLAT)
+    t = time.perf_counter()
+    o = oracle.ftgcr(p.D, p.R, p.mu, K, TOL)
+    return time.perf_counter() - t, o["steps"]
+
+
+def oracle_throughput(seconds_budget: float = 12.0, cores: int | None = None):
+    """Independent oracle solves of the benchmark problem, one process per
+    core, for about `seconds_budget` of wall time: solves/s and steps/s."""
+    import multiprocessing as mp
+
+    import oracle
+
+    oracle.build()
+    cores = cores or os.cpu_count() or 1
+    one, steps = _oracle_solve(0)
+    per_core = max(1, int(seconds_budget / max(one, 1e-3)))
+    n = cores * per_core
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_solve, range(cores))  # warm the workers
+        t = time.perf_counter()
+        res = pool.map(_oracle_solve, range(n), chunksize=1)
+        wall = time.perf_counter() - t
+    return dict(value=n / wall, steps_per_s=sum(r[1] for r in res) / wall, cores=cores,
+                latency_s=float(np.median([r[0] for r in res])), n=n, wall=wall)
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import multiprocessing as mp
+
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    times = []
+    with ctx.Pool(cores) as pool:
+        for i in range(args.warmup + args.steps):
+            t = time.perf_counter()
+            pool.map(_oracle_solve, range(cores), chunksize=1)
+            dt = time.perf_counter() - t
+            if i >= args.warmup:
+                times.append(dt)
+    ms = 1e3 * float(np.mean(times))
+    value = cores / (ms * 1e-3)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nlon": NLON, "nlat": NLAT, "k": K, "tol": TOL},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                             "sample": f"each step: {cores} independent FP64 oracle solves of the {NLON}x{NLAT} "
+                                       f"problem, one per core"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args):
+    import torch
+
+    from paper_2103_07210_gb300 import ftgcr
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    p = inputs.hill_problem(NLON, NLAT)
+    R = torch.from_numpy(p.R).to(dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def measure(precision, nsteps, nwarm):
+        s = ftgcr.Solver(p.D, p.mu, k=K, tol=TOL, precision=precision)
+        xs = [torch.zeros_like(R) for _ in range(2)]
+        for i in range(nwarm):
+            xs[0].zero_()
+            s.solve_async(R, xs[0], stream=stream)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
+        barrier()
+        for i in range(nsteps):
+            x = xs[i % 2]
+            x.zero_()
+            flush.fill_(i & 0xFF)  # evict L2 between timed steps
+            ev[i][0].record(stream)
+            s.solve_async(R, x, stream=stream)
+            ev[i][1].record(stream)
+        barrier()
+        ms = np.array([a.elapsed_time(b) for a, b in ev])
+        info = s.stats()
+        return s, ms, info, xs[(nsteps - 1) % 2]
+
+    with ClockSampler(local) as clk:
+        s_mx, ms_mx, info_mx, x_mx = measure("mixed", args.steps, args.warmup)
+    clocks = clk.summary()
+    s64, ms_64, info_64, _ = measure("fp64", max(3, args.steps // 4), max(1, args.warmup // 2))
+
+    # max over ranks
+    tot = float(ms_mx.sum())
+    if ws > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([tot], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot = float(t.item())
+    ms_step = tot / args.steps
+    value = ws * 1e3 / ms_step
+
+    # e2e: host buffers through the C ABI (blocking ftgcr_solve), copies inside
+    Rh = torch.from_numpy(p.R).pin_memory()
+    xh = torch.zeros(NLAT, NLON, dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        xh.zero_()
+        s_mx.solve(Rh, xh)
+    e2e = []
+    for _ in range(args.steps):
+        xh.zero_()
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        s_mx.solve(Rh, xh)
+        e2e.append(time.perf_counter() - t)
+    e2e_val = ws / float(np.mean(e2e))
+
+    peak, peak_kind = read_peaks()
+    bytes_launch = algorithmic_bytes(info_mx["steps"], info_mx["outer"])
+    kern_ms = float(np.mean(ms_mx))
+    achieved = bytes_launch / (kern_ms * 1e-3) / 1e9
+    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["sources_sha256"] == sources_hash() else None
+
+    # correctness of the timed result, by a property that holds at any size
+    res_rel = info_mx["res_final_true"] / info_mx["norm_R"]
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nlon": NLON, "nlat": NLAT, "k": K, "tol": TOL,
+                       "precision": "mixed (FP32 inner, FP64 dots/norm/refinement)",
+                       "l2": "flushed between timed steps (256 MB write)", "tiles": info_mx["tiles"]},
+            "iters_per_s": info_mx["steps"] * value, "inner_steps_per_solve": info_mx["steps"],
+            "refinement_sweeps": info_mx["outer"],
+            "latency_ms": {"p50": float(np.percentile(ms_mx, 50)), "p99": float(np.percentile(ms_mx, 99))},
+            "fp64_path": {"solves_per_s": 1e3 / float(np.mean(ms_64)),
+                          "iters_per_s": info_64["steps"] * 1e3 / float(np.mean(ms_64)),
+                          "steps_per_solve": info_64["steps"]},
+            "mixed_over_fp64": float(np.mean(ms_64)) / float(np.mean(ms_mx)),
+            "residual_rel": res_rel,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": "k_ftgcr_persistent<float>",
+                         "algorithmic_bytes_per_launch": bytes_launch},
+            "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": 2 * 8 * NLON * NLAT,
+                    "d2h_bytes_per_step": 8 * NLON * NLAT + 2 * 4096},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline and ws == 1:
+            cb = oracle_throughput()
+            line["cpu_baseline"] = {"value": cb["value"], "unit": "solves/s", "cores": cb["cores"], "kind": "oracle",
+                                    "sample": f"{cb['n']} FP64 oracle solves of the {NLON}x{NLAT} problem, "
+                                              f"one process per core, {cb['wall']:.1f} s",
+                                    "latency_s_per_solve_one_core": cb["latency_s"]}
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,180 @@
+/*
+ * ftgcr.h - C ABI of the GB300-native FT-GCR(k) solver library (libftgcr.so).
+ *
+ * FT-GCR(k) is the preconditioned generalised conjugate residual method with
+ * soft-fault detection and recovery of Gillard & Benacchio, "FT-GCR: a
+ * fault-tolerant generalized conjugate residual elliptic solver"
+ * (arXiv 2103.07210): Algorithm 1, Section 2.  The library solves the
+ * elliptic problem L(phi) = R of Eq. (1) on a regular latitude-longitude grid:
+ *
+ *   (L phi)_{j,i} = Tx_{j,i}(phi_{j,i+1}-phi_{j,i}) + Tx_{j,i-1}(phi_{j,i-1}-phi_{j,i})
+ *                 + Ty_{j,i}(phi_{j+1,i}-phi_{j,i}) + Ty_{j-1,i}(phi_{j-1,i}-phi_{j,i})
+ *                 - mu A_j phi_{j,i}
+ *
+ * the area-integrated finite-volume form of div(D grad phi) - mu phi on the
+ * unit sphere (2-D stand-in for the 3-D potential-flow problem of Section 3,
+ * Eq. (3)): cell centres theta_j = -pi/2 + (j+1/2) pi/nlat, lambda_i =
+ * (i+1/2) 2pi/nlon; Tx_{j,i} = (D_{j,i}+D_{j,i+1})/2 * dth/(cos theta_j dlam),
+ * Ty_{j,i} = (D_{j,i}+D_{j+1,i})/2 * cos theta_{j+1/2} dlam/dth, zero flux
+ * through the pole faces, A_j the exact cell area.  The left preconditioner
+ * ("bespoke", Section 2) is the zonal line operator: the longitude couplings
+ * of L plus the diagonal of the rest, one periodic tridiagonal solve per row.
+ *
+ * Conventions for every entry point:
+ *  - Arrays are row-major [nlat][nlon] (longitude fastest), FP64, N = nlat*nlon.
+ *  - Unless stated otherwise a pointer may be host or device memory; the
+ *    library detects which (cudaPointerGetAttributes).  Host arrays are staged
+ *    through buffers owned by the handle.
+ *  - The caller owns every array it passes; the handle owns all solver state,
+ *    which stays resident on the device between solves.
+ *  - Every function returns an int status: 0 (FTGCR_OK), a positive warning,
+ *    or a negative error; ftgcr_error_string() names it.  A handle is not
+ *    thread-safe: one solve at a time per handle.
+ */
+#ifndef FTGCR_H
+#define FTGCR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define FTGCR_OK 0
+#define FTGCR_NOT_CONVERGED 1   /* step limit reached; x holds the last iterate */
+#define FTGCR_ERR_ARG (-1)      /* bad size, k, tol, pointer, fault or non-finite input */
+#define FTGCR_ERR_OOM (-2)      /* device allocation failed */
+#define FTGCR_ERR_CUDA (-3)     /* a CUDA call failed (launch, copy, ...) */
+#define FTGCR_ERR_TIMEOUT (-4)  /* an in-kernel grid barrier gave up waiting */
+#define FTGCR_ERR_BUDGET (-5)   /* serving: request larger than the memory budget */
+#define FTGCR_ERR_STATE (-6)    /* call out of order (e.g. stats before any solve) */
+
+/* ---- precision of the iteration ---- */
+#define FTGCR_FP64 0  /* every vector, stencil, preconditioner and reduction in FP64 */
+#define FTGCR_MIXED 1 /* FP32 inner FT-GCR vectors, stencil, preconditioner and axpys;
+                         FP64 inner products (exact FP32 products, float-float per
+                         thread, FP64 across threads), FP64 norm test and FP64
+                         outer iterative-refinement residual R - L(x) */
+
+/* ---- preconditioner ---- */
+#define FTGCR_PRECOND_LINE 0     /* zonal periodic line solve (default) */
+#define FTGCR_PRECOND_JACOBI 1   /* diagonal of L */
+#define FTGCR_PRECOND_IDENTITY 2 /* no preconditioning */
+
+/* ---- vectors a fault may hit (Algorithm 1 names) ---- */
+#define FTGCR_VEC_X 0  /* phi^nu   */
+#define FTGCR_VEC_R 1  /* r^nu     */
+#define FTGCR_VEC_P 2  /* p^nu     */
+#define FTGCR_VEC_AP 3 /* L(p^nu)  */
+#define FTGCR_VEC_E 4  /* e = P^-1(r^{nu+1}), the paper's injection site (Section 3) */
+
+typedef struct ftgcr_handle ftgcr_handle;
+
+typedef struct {
+  int32_t nlon;      /* >= 3 */
+  int32_t nlat;      /* >= 1 */
+  double mu;         /* Helmholtz coefficient per unit area, >= 0 (mu > 0 makes -L definite) */
+  int32_t precision; /* FTGCR_FP64 | FTGCR_MIXED */
+  int32_t precond;   /* FTGCR_PRECOND_* */
+  int64_t max_steps; /* executed-step limit; 0 = 100*ceil(sqrt(N)) + 100 */
+  int32_t tiles;     /* row bands per solve (work items per phase); 0 = automatic */
+  double inner_tol;  /* FTGCR_MIXED only: relative tolerance of each inner FP32 solve;
+                        0 = 1e-5 */
+  int32_t max_outer; /* FTGCR_MIXED only: refinement sweeps limit; 0 = 40 */
+} ftgcr_grid;
+
+typedef struct {
+  const double* D;   /* [nlat][nlon] cell-centred coefficient (column depth 1 - h), > 0 */
+} ftgcr_coeffs;
+
+/* One single-bit flip: at executed step `step` (1-based, re-executed steps
+ * count) XOR bit `bit` of element `index` of vector `vec`.  x, r, p and Ap are
+ * hit at the start of the step, before beta is formed; e right after the
+ * preconditioner of that step (skipped if the step exits or detects a fault
+ * first).  bit is 0..63 of the binary64 pattern (FTGCR_FP64) or 0..31 of the
+ * binary32 pattern of the inner vectors (FTGCR_MIXED); in the mixed path
+ * `step` counts inner steps across all refinement sweeps. */
+typedef struct {
+  int64_t step;
+  int32_t vec;
+  int64_t index;
+  int32_t bit;
+} ftgcr_fault;
+
+typedef struct {
+  const ftgcr_fault* faults; /* host memory, n entries */
+  int32_t n;                 /* 0..FTGCR_MAX_FAULTS */
+} ftgcr_fault_plan;
+
+#define FTGCR_MAX_FAULTS 64
+#define FTGCR_MAX_K 16
+#define FTGCR_MAX_DETECT 16
+
+typedef struct {
+  int64_t steps;           /* executed inner steps (all sweeps) */
+  int64_t cycles;          /* completed Krylov cycles (n of Algorithm 1) */
+  int64_t restarts;        /* restores of the backup (= detected faults) */
+  int64_t faults_injected; /* plan entries that fired */
+  int64_t faults_detected;
+  int64_t outer;           /* FTGCR_MIXED: refinement sweeps; FTGCR_FP64: 0 */
+  int32_t ndetect;         /* entries used in detect_step / detect_ratio */
+  int32_t converged;
+  int64_t detect_step[FTGCR_MAX_DETECT];   /* step at which each fault was detected */
+  double detect_ratio[FTGCR_MAX_DETECT];   /* ||r_new||^2 / ||r_old||^2 at that step */
+  double res0;             /* ||L(x0) - R|| */
+  double res_final_rec;    /* recurrence residual norm at exit (inner, last sweep) */
+  double res_final_true;   /* ||L(x) - R|| of the returned x, FP64 */
+  double norm_R;           /* ||R|| */
+  int64_t bytes_resident;  /* device bytes held by the handle */
+  int64_t bytes_backup;    /* of which the backup [phi, r, p, L(p)]^* (Section 4: 4 arrays) */
+  int32_t tiles;           /* row bands used */
+  int32_t status;          /* status of the last solve */
+} ftgcr_stats_t;
+
+/* Create a solver for one grid and coefficient field.  Copies D, builds the
+ * face coefficients and the line-preconditioner factorisation on the device
+ * and allocates every Krylov vector.  k: Krylov cycle length, 1..FTGCR_MAX_K.
+ * tol: exit when ||r|| <= tol ||R|| (tol > 0).  Errors: FTGCR_ERR_ARG,
+ * FTGCR_ERR_OOM, FTGCR_ERR_CUDA. */
+int ftgcr_create(const ftgcr_grid* grid, const ftgcr_coeffs* coeffs, int32_t k, double tol, ftgcr_handle** out);
+
+/* Solve L(x) = rhs (Algorithm 1).  rhs: [N] FP64; x: [N] FP64, in = initial
+ * guess, out = solution (host or device memory).  plan: NULL or a fault plan.
+ * stream: a cudaStream_t, or NULL for the legacy default stream.  Blocks
+ * until done and returns FTGCR_OK, FTGCR_NOT_CONVERGED or an error. */
+int ftgcr_solve(ftgcr_handle* h, const double* rhs, double* x, const ftgcr_fault_plan* plan, void* stream);
+
+/* Same as ftgcr_solve but only enqueues the work on `stream` and returns;
+ * rhs and x must be device memory.  The status of the solve is read with
+ * ftgcr_stats() once the stream has reached the end of the solve. */
+int ftgcr_solve_async(ftgcr_handle* h, const double* rhs, double* x, const ftgcr_fault_plan* plan, void* stream);
+
+/* Statistics of the last solve of h (synchronises with its stream). */
+int ftgcr_stats(ftgcr_handle* h, ftgcr_stats_t* out);
+
+/* Solve n independent problems in ONE persistent launch (all handles of the
+ * same precision).  Each solve uses its own handle's tiling, so its result is
+ * bitwise the same as when it is solved alone.  rhs[i], x[i] device memory;
+ * plans may be NULL.  Enqueues only; read each status with ftgcr_stats(). */
+int ftgcr_solve_batch(ftgcr_handle* const* hs, const double* const* rhs, double* const* x,
+                      const ftgcr_fault_plan* const* plans, int32_t n, void* stream);
+
+/* out = L(in), FP64 (device pointers).  The operator of Eq. (1) as built by
+ * ftgcr_create. */
+int ftgcr_apply_operator(ftgcr_handle* h, const double* in, double* out, void* stream);
+
+/* out = P^-1(in), FP64 (device pointers), with the handle's preconditioner
+ * (Algorithm 1, e = P^-1(r)). */
+int ftgcr_apply_precond(ftgcr_handle* h, const double* in, double* out, void* stream);
+
+/* Device bytes a handle for this grid would hold (admission control). */
+int64_t ftgcr_footprint(const ftgcr_grid* grid, int32_t k);
+
+void ftgcr_destroy(ftgcr_handle* h);
+const char* ftgcr_error_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FTGCR_H */

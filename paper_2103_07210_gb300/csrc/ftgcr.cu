@@ -1,0 +1,756 @@
+// libftgcr: C ABI, setup kernels and launch logic of the GB300-native FT-GCR(k)
+// solver (Gillard & Benacchio, arXiv 2103.07210, Algorithm 1).  See
+// include/ftgcr.h for the contract of every entry point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/ftgcr.h"
+#include "ftgcr_device.cuh"
+#include "ftgcr_phases.cuh"
+
+using namespace ftgcr;
+
+static_assert(sizeof(Fault) == sizeof(ftgcr_fault), "fault layout");
+static_assert(kMaxK == FTGCR_MAX_K, "max k");
+static_assert(kMaxFaults == FTGCR_MAX_FAULTS, "max faults");
+static_assert(kMaxDetect == FTGCR_MAX_DETECT, "max detect");
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// ------------------------------------------------------------ setup kernels
+// Face coefficients of Eq. (1)'s finite-volume operator from the cell-centred
+// coefficient D and the per-row geometry; same expressions, in the same
+// order, as the definition (FP64, --fmad=false).
+__global__ void k_face_coeffs(int nlon, int nlat, const double* __restrict__ D, const double* __restrict__ cx,
+                              const double* __restrict__ cy, const double* __restrict__ area, double mu,
+                              double* Tx, double* Ty, double* muA, float* Tx32, float* Ty32, float* muA32) {
+  const long long N = (long long)nlon * nlat;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N; g += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(g / nlon), i = (int)(g - (long long)j * nlon);
+    const int ie = (i + 1) % nlon;
+    const double tx = 0.5 * (D[g] + D[(long long)j * nlon + ie]) * cx[j];
+    const double ty = (j == nlat - 1) ? 0.0 : 0.5 * (D[g] + D[g + nlon]) * cy[j];
+    Tx[g] = tx;
+    Ty[g] = ty;
+    if (Tx32) {
+      Tx32[g] = (float)tx;
+      Ty32[g] = (float)ty;
+    }
+    if (i == 0) {
+      const double m = mu * area[j];
+      muA[j] = m;
+      if (muA32) muA32[j] = (float)m;
+    }
+  }
+}
+
+// Line-preconditioner factorisation, one thread per latitude row (setup
+// only).  Row system M x = b, M_ii = d_i = Tx_i + Tx_{i-1} + sigma_i,
+// M_{i,i+1} = -Tx_i (periodic).  LU of the leading block: w_0 = d_0,
+// w_i = d_i - Tx_{i-1} c_{i-1}, c_i = Tx_i / w_i; bordering vector
+// z = A0^-1 (-Tx_{n-1} e_0 - Tx_{n-2} e_{n-2}); delta = d_{n-1} + Tx_{n-1} z_0 +
+// Tx_{n-2} z_{n-2}.  Stored permuted for the per-lane chunks of the solve:
+// element i -> [row][i % C][i / C].  Jacobi: 1 / d_i in natural layout.
+__global__ void k_line_factor(int nlon, int nlat, int C, int precond, const double* __restrict__ Tx,
+                              const double* __restrict__ Ty, const double* __restrict__ muA, double* work,
+                              double* lc, double* lw, double* lz, double* lrow, float* lc32, float* lw32, float* lz32,
+                              float* lrow32) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nlat) return;
+  const int n = nlon, m = n - 1;
+  const double* tx = Tx + (long long)j * n;
+  auto diag = [&](int i) {
+    const long long c = (long long)j * n + i;
+    double s = 0.0;
+    if (j < nlat - 1) s = s + Ty[c];
+    if (j > 0) s = s + Ty[c - n];
+    s = s + muA[j];
+    return tx[i] + tx[(i + n - 1) % n] + s;
+  };
+  if (precond == PC_JACOBI) {
+    for (int i = 0; i < n; ++i) {
+      const double v = 1.0 / diag(i);
+      lw[(long long)j * n + i] = v;
+      if (lw32) lw32[(long long)j * n + i] = (float)v;
+    }
+    return;
+  }
+  if (precond != PC_LINE) return;
+  double* w = work + (long long)j * 3 * n;  // w_i, c_i, z_i
+  double* cc = w + n;
+  double* z = w + 2 * n;
+  w[0] = diag(0);
+  cc[0] = (m >= 2) ? tx[0] / w[0] : 0.0;
+  for (int i = 1; i < m; ++i) {
+    w[i] = diag(i) - tx[i - 1] * cc[i - 1];
+    cc[i] = (i <= m - 2) ? tx[i] / w[i] : 0.0;
+  }
+  cc[m - 1] = 0.0;
+  // z: forward g_i = cvec_i + c_{i-1} g_{i-1}, backward z_i = g_i / w_i + c_i z_{i+1}
+  for (int i = 0; i < m; ++i) z[i] = 0.0;
+  z[0] = -tx[n - 1];
+  z[m - 1] = z[m - 1] + -tx[n - 2];
+  for (int i = 1; i < m; ++i) z[i] = z[i] + cc[i - 1] * z[i - 1];
+  z[m - 1] = z[m - 1] / w[m - 1];
+  for (int i = m - 2; i >= 0; --i) z[i] = z[i] / w[i] + cc[i] * z[i + 1];
+  const double delta = diag(n - 1) + tx[n - 1] * z[0] + tx[n - 2] * z[m - 1];
+  const double dinv = 1.0 / delta;
+  const long long rb = (long long)j * 32 * C;
+  for (int i = 0; i < 32 * C; ++i) {
+    const int lane = i / C, k = i % C;
+    const long long pos = rb + (long long)k * 32 + lane;
+    const bool in = i < m;
+    const double vc = in ? cc[i] : 0.0, vw = in ? 1.0 / w[i] : 0.0, vz = in ? z[i] : 0.0;
+    lc[pos] = vc;
+    lw[pos] = vw;
+    lz[pos] = vz;
+    if (lc32) {
+      lc32[pos] = (float)vc;
+      lw32[pos] = (float)vw;
+      lz32[pos] = (float)vz;
+    }
+  }
+  const double r4[4] = {dinv, tx[n - 1] * dinv, tx[n - 2] * dinv, 0.0};
+  for (int q = 0; q < 4; ++q) {
+    lrow[(long long)j * 4 + q] = r4[q];
+    if (lrow32) lrow32[(long long)j * 4 + q] = (float)r4[q];
+  }
+}
+
+// out = L(in), FP64, one thread per element.
+__global__ void k_apply_operator(const double* in, double* out, const double* Tx, const double* Ty, const double* muA,
+                                 int nlon, int nlat) {
+  const long long N = (long long)nlon * nlat;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N; g += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(g / nlon), i = (int)(g - (long long)j * nlon);
+    out[g] = stencil_global<double>(in, Tx, Ty, muA, nlon, nlat, j, i);
+  }
+}
+
+// out = P^-1(in), FP64, one warp per latitude row (the solve of the
+// persistent kernel's PA phase).
+__global__ void k_apply_precond(const double* in, double* out, SolveDev<double> sd) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  double* sm = reinterpret_cast<double*>(dsm);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (j >= sd.nlat) return;
+  const int stride = row_stride(sd.nlon);
+  double* row = sm + warp * stride;
+  const long long base = (long long)j * sd.nlon;
+  for (int i = lane; i < sd.nlon; i += 32) row[sk(i)] = in[base + i];
+  __syncwarp();
+  precond_row(sd, j, row);
+  if (sd.precond == PC_IDENTITY) __syncwarp();
+  for (int i = lane; i < sd.nlon; i += 32) out[base + i] = row[sk(i)];
+}
+
+// Per-solve start: record the call's pointers and fault plan in the device
+// descriptor, reset the state machine and the launch control block.
+struct BeginArgs {
+  const double* R;
+  const double* x0;
+  double* xout;
+  int nfaults;
+  long long max_steps;
+  Fault faults[kMaxFaults];
+};
+
+template <typename T>
+__global__ void k_begin_solve(SolveDev<T>* sd, BeginArgs b, int* active, int n_active, int slot, int par,
+                              LaunchCtl* ctl) {
+  if (threadIdx.x == 0) {
+    sd->R = b.R;
+    sd->x0 = b.x0;
+    sd->xout = b.xout;
+    sd->nfaults = b.nfaults;
+    SolveState S;
+    memset(&S, 0, sizeof S);
+    S.active = 1;
+    S.pending = K_NONE;
+    S.first_out = 1;
+    S.phiS = S.rS = 0;
+    S.phiW = S.rW = 1;
+    S.status = ST_RUNNING;
+    sd->st[par] = S;
+    sd->st[par ^ 1] = S;
+    *sd->result = S;
+    active[par * n_active + slot] = 1;
+    if (ctl) {
+      ctl->counter = 0;
+      ctl->err = 0;
+      ctl->round0 = 0;
+      ctl->round_end = 0;
+    }
+  }
+  for (int q = threadIdx.x; q < b.nfaults; q += blockDim.x) const_cast<Fault*>(sd->faults)[q] = b.faults[q];
+}
+
+// ------------------------------------------------------------ host helpers
+struct DeviceInfo {
+  int sms = 0;
+  int smem_optin = 0;
+};
+DeviceInfo device_info(int dev) {
+  static std::mutex mu;
+  static std::vector<DeviceInfo> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  if ((int)cache.size() <= dev) cache.resize(dev + 1);
+  if (cache[dev].sms == 0) {
+    cudaDeviceGetAttribute(&cache[dev].sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&cache[dev].smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  }
+  return cache[dev];
+}
+
+// Per-row geometry of the latitude-longitude grid on the unit sphere (same
+// definition, written out, as the problem statement in include/ftgcr.h).
+void row_geometry(int nlon, int nlat, std::vector<double>& cx, std::vector<double>& cy, std::vector<double>& area) {
+  const double dlam = 2.0 * kPi / nlon;
+  const double dth = kPi / nlat;
+  cx.resize(nlat);
+  cy.resize(nlat);
+  area.resize(nlat);
+  for (int j = 0; j < nlat; ++j) {
+    const double th = -0.5 * kPi + (j + 0.5) * dth;
+    const double s_south = (j == 0) ? -1.0 : sin(-0.5 * kPi + j * dth);
+    const double s_north = (j == nlat - 1) ? 1.0 : sin(-0.5 * kPi + (j + 1) * dth);
+    cx[j] = dth / (cos(th) * dlam);
+    cy[j] = (j == nlat - 1) ? 0.0 : cos(-0.5 * kPi + (j + 1) * dth) * dlam / dth;
+    area[j] = dlam * (s_north - s_south);
+  }
+}
+
+int chunk_len(int nlon) { return (nlon - 1 + 31) / 32; }
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Dynamic shared memory of the persistent kernel for a solve with nt tiles.
+size_t dyn_smem(int nlon, int nlat, int nt, int mixed, size_t elem) {
+  const int hmax = (nlat + nt - 1) / nt;
+  const size_t e = mixed ? sizeof(double) : elem;
+  return (size_t)(hmax + 2) * row_stride(nlon) * e;
+}
+
+int choose_tiles(int nlon, int nlat, int mixed, size_t elem, int sms, int smem_limit) {
+  int nt = std::min(nlat, sms);
+  while (nt < nlat && dyn_smem(nlon, nlat, nt, mixed, elem) > (size_t)smem_limit) nt = std::min(nlat, nt * 2);
+  return nt;
+}
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return FTGCR_OK;
+  if (e == cudaErrorMemoryAllocation) return FTGCR_ERR_OOM;
+  return FTGCR_ERR_CUDA;
+}
+
+#define CK(x)                                  \
+  do {                                         \
+    cudaError_t e_ = (x);                      \
+    if (e_ != cudaSuccess) return cuda_status(e_); \
+  } while (0)
+
+constexpr int kStaticSmemReserve = 20 * 1024;  // KernelSmem and friends
+
+}  // namespace
+
+// ------------------------------------------------------------ the handle
+struct ftgcr_handle {
+  int dev = 0;
+  int nlon = 0, nlat = 0, k = 0, precision = 0, precond = 0, nt = 0, C = 0;
+  long long N = 0, max_steps = 0;
+  double tol = 0, mu = 0, inner_tol = 0;
+  int max_outer = 0;
+  unsigned char* pool = nullptr;
+  size_t pool_bytes = 0;
+  size_t backup_bytes = 0;
+  // FP64 operator (always)
+  double *Tx64 = nullptr, *Ty64 = nullptr, *muA64 = nullptr;
+  double *stageR = nullptr, *stageX = nullptr;  // host-pointer staging
+  void* sdev = nullptr;                        // SolveDev<T>* on the device
+  void** sdev_arr = nullptr;                   // device array holding sdev
+  int* nt_dev = nullptr;
+  int* active = nullptr;                       // [2]
+  LaunchCtl* ctl = nullptr;
+  SolveState* result = nullptr;
+  SolveState* h_result = nullptr;              // pinned
+  LaunchCtl* h_ctl = nullptr;                  // pinned
+  SolveDev<double> sd64{};
+  SolveDev<float> sd32{};
+  size_t smem = 0;
+  int grid = 0;
+  cudaStream_t last_stream = nullptr;
+  int solved = 0;
+  int last_status = FTGCR_ERR_STATE;
+};
+
+namespace {
+
+template <typename T>
+void* kernel_ptr() {
+  return (void*)k_ftgcr_persistent<T>;
+}
+
+template <typename T>
+int configure_kernel(size_t smem) {
+  CK(cudaFuncSetAttribute(k_ftgcr_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  return FTGCR_OK;
+}
+
+template <typename T>
+int occupancy(size_t smem, int* occ) {
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_ftgcr_persistent<T>, kThreads, smem));
+  return FTGCR_OK;
+}
+
+bool finite_array(const double* a, long long n) {
+  for (long long i = 0; i < n; ++i)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int validate_plan(const ftgcr_handle* h, const ftgcr_fault_plan* plan) {
+  if (!plan || plan->n == 0) return FTGCR_OK;
+  if (plan->n < 0 || plan->n > FTGCR_MAX_FAULTS || !plan->faults) return FTGCR_ERR_ARG;
+  const int maxbit = h->precision == FTGCR_MIXED ? 31 : 63;
+  for (int q = 0; q < plan->n; ++q) {
+    const ftgcr_fault& f = plan->faults[q];
+    if (f.vec < 0 || f.vec > FTGCR_VEC_E || f.index < 0 || f.index >= h->N || f.bit < 0 || f.bit > maxbit ||
+        f.step < 1)
+      return FTGCR_ERR_ARG;
+  }
+  return FTGCR_OK;
+}
+
+// Carve every allocation of a handle out of one pool (or just count bytes).
+template <typename T>
+size_t layout(ftgcr_handle* h, unsigned char* base, SolveDev<T>* sd) {
+  size_t off = 0;
+  const long long N = h->N;
+  const int nlat = h->nlat, k = h->k, C = h->C;
+  auto take = [&](size_t bytes) -> unsigned char* {
+    unsigned char* p = base ? base + off : nullptr;
+    off += align256(bytes);
+    return p;
+  };
+  const size_t vT = sizeof(T) * N, v64 = sizeof(double) * N;
+  const size_t lcn = (h->precond == FTGCR_PRECOND_LINE) ? (size_t)nlat * 32 * C
+                                                        : (h->precond == FTGCR_PRECOND_JACOBI ? (size_t)N : 1);
+  h->Tx64 = (double*)take(v64);
+  h->Ty64 = (double*)take(v64);
+  h->muA64 = (double*)take(sizeof(double) * nlat);
+  sd->Tx = (const T*)(std::is_same<T, double>::value ? (void*)h->Tx64 : (void*)take(vT));
+  sd->Ty = (const T*)(std::is_same<T, double>::value ? (void*)h->Ty64 : (void*)take(vT));
+  sd->muA = (const T*)(std::is_same<T, double>::value ? (void*)h->muA64 : (void*)take(sizeof(T) * nlat));
+  sd->lc = (const T*)take(sizeof(T) * lcn);
+  sd->lw = (const T*)take(sizeof(T) * lcn);
+  sd->lz = (const T*)take(sizeof(T) * lcn);
+  sd->lrow = (const T*)take(sizeof(T) * 4 * nlat);
+  size_t before = off;
+  for (int q = 0; q < 3; ++q) sd->phi[q] = (T*)take(vT);
+  for (int q = 0; q < 3; ++q) sd->r[q] = (T*)take(vT);
+  sd->e = (T*)take(vT);
+  sd->Le = (T*)take(vT);
+  for (int s = 0; s < kNSlot; ++s) {
+    sd->p[s] = s < k + 2 ? (T*)take(vT) : nullptr;
+    sd->Lp[s] = s < k + 2 ? (T*)take(vT) : nullptr;
+  }
+  (void)before;
+  h->backup_bytes = 4 * vT;
+  sd->Rin = (T*)(std::is_same<T, float>::value ? take(vT) : nullptr);
+  sd->xbuf[0] = (double*)(std::is_same<T, float>::value ? take(v64) : nullptr);
+  sd->xbuf[1] = (double*)(std::is_same<T, float>::value ? take(v64) : nullptr);
+  h->stageR = (double*)take(v64);
+  h->stageX = (double*)take(v64);
+  sd->part = (double*)take(sizeof(double) * 2 * h->nt * kNPart);
+  sd->st = (SolveState*)take(sizeof(SolveState) * 2);
+  sd->result = (SolveState*)take(sizeof(SolveState));
+  sd->faults = (const Fault*)take(sizeof(Fault) * kMaxFaults);
+  sd->patchval = (double*)take(sizeof(double) * kMaxFaults);
+  h->sdev = take(sizeof(SolveDev<T>));
+  h->sdev_arr = (void**)take(sizeof(void*));
+  h->nt_dev = (int*)take(sizeof(int));
+  h->active = (int*)take(sizeof(int) * 2);
+  h->ctl = (LaunchCtl*)take(sizeof(LaunchCtl));
+  h->result = sd->result;
+  return off;
+}
+
+template <typename T>
+int create_impl(ftgcr_handle* h, const double* D_host_or_dev, bool D_on_device) {
+  SolveDev<T> sd{};
+  const size_t bytes = layout<T>(h, nullptr, &sd);
+  if (cudaMalloc(&h->pool, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return FTGCR_ERR_OOM;
+  }
+  h->pool_bytes = bytes;
+  CK(cudaMemset(h->pool, 0, bytes));
+  layout<T>(h, h->pool, &sd);
+  sd.nlon = h->nlon;
+  sd.nlat = h->nlat;
+  sd.k = h->k;
+  sd.nt = h->nt;
+  sd.C = h->C;
+  sd.precond = h->precond;
+  sd.mixed = std::is_same<T, float>::value ? 1 : 0;
+  sd.nfaults = 0;
+  sd.N = h->N;
+  sd.max_steps = h->max_steps;
+  sd.max_outer = h->max_outer;
+  sd.tol2 = h->tol * h->tol;
+  sd.inner_tol2 = h->inner_tol * h->inner_tol;
+  sd.Tx64 = h->Tx64;
+  sd.Ty64 = h->Ty64;
+  sd.muA64 = h->muA64;
+
+  // geometry (host) + face coefficients and factorisation (device)
+  std::vector<double> cx, cy, area;
+  row_geometry(h->nlon, h->nlat, cx, cy, area);
+  double *dcx = nullptr, *dD = nullptr, *work = nullptr;
+  CK(cudaMalloc(&dcx, sizeof(double) * 3 * h->nlat));
+  CK(cudaMemcpy(dcx, cx.data(), sizeof(double) * h->nlat, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dcx + h->nlat, cy.data(), sizeof(double) * h->nlat, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dcx + 2 * h->nlat, area.data(), sizeof(double) * h->nlat, cudaMemcpyHostToDevice));
+  const double* Dd = D_host_or_dev;
+  if (!D_on_device) {
+    CK(cudaMalloc(&dD, sizeof(double) * h->N));
+    CK(cudaMemcpy(dD, D_host_or_dev, sizeof(double) * h->N, cudaMemcpyHostToDevice));
+    Dd = dD;
+  }
+  const bool mixed = std::is_same<T, float>::value;
+  k_face_coeffs<<<1024, 256>>>(h->nlon, h->nlat, Dd, dcx, dcx + h->nlat, dcx + 2 * h->nlat, h->mu, h->Tx64, h->Ty64,
+                               h->muA64, mixed ? (float*)sd.Tx : nullptr, mixed ? (float*)sd.Ty : nullptr,
+                               mixed ? (float*)sd.muA : nullptr);
+  CK(cudaGetLastError());
+  CK(cudaMalloc(&work, sizeof(double) * 3 * (size_t)h->N));
+  {
+    double *lc = (double*)sd.lc, *lw = (double*)sd.lw, *lz = (double*)sd.lz, *lr = (double*)sd.lrow;
+    double* tmp = nullptr;
+    const size_t lcn = (h->precond == FTGCR_PRECOND_LINE) ? (size_t)h->nlat * 32 * h->C : (size_t)h->N;
+    if (mixed) {
+      CK(cudaMalloc(&tmp, sizeof(double) * (3 * lcn + 4 * h->nlat)));
+      lc = tmp;
+      lw = tmp + lcn;
+      lz = tmp + 2 * lcn;
+      lr = tmp + 3 * lcn;
+    }
+    k_line_factor<<<(h->nlat + 63) / 64, 64>>>(h->nlon, h->nlat, h->C, h->precond, h->Tx64, h->Ty64, h->muA64, work,
+                                               lc, lw, lz, lr, mixed ? (float*)sd.lc : nullptr,
+                                               mixed ? (float*)sd.lw : nullptr, mixed ? (float*)sd.lz : nullptr,
+                                               mixed ? (float*)sd.lrow : nullptr);
+    CK(cudaGetLastError());
+    CK(cudaDeviceSynchronize());
+    if (tmp) cudaFree(tmp);
+  }
+  cudaFree(work);
+  cudaFree(dcx);
+  if (dD) cudaFree(dD);
+
+  CK(cudaMemcpy(h->sdev, &sd, sizeof sd, cudaMemcpyHostToDevice));
+  void* sp = h->sdev;
+  CK(cudaMemcpy(h->sdev_arr, &sp, sizeof(void*), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->nt_dev, &h->nt, sizeof(int), cudaMemcpyHostToDevice));
+  if constexpr (std::is_same<T, float>::value)
+    h->sd32 = sd;
+  else
+    h->sd64 = sd;
+
+  h->smem = dyn_smem(h->nlon, h->nlat, h->nt, mixed, sizeof(T));
+  int rc = configure_kernel<T>(std::max<size_t>(h->smem, 1));
+  if (rc) return rc;
+  int occ = 0;
+  rc = occupancy<T>(h->smem, &occ);
+  if (rc) return rc;
+  if (occ < 1) return FTGCR_ERR_ARG;
+  const DeviceInfo di = device_info(h->dev);
+  h->grid = std::min(h->nt, di.sms * occ);
+  CK(cudaMallocHost(&h->h_result, sizeof(SolveState)));
+  CK(cudaMallocHost(&h->h_ctl, sizeof(LaunchCtl)));
+  return FTGCR_OK;
+}
+
+template <typename T>
+int launch_persistent(SolveDev<T>* const* solves, const int* nt, int* active, int n, LaunchCtl* ctl, int max_rounds,
+                      int grid, size_t smem, cudaStream_t st) {
+  BatchArgs<T> a;
+  a.solves = solves;
+  a.nt = nt;
+  a.active = active;
+  a.n = n;
+  a.ctl = ctl;
+  a.max_rounds = max_rounds;
+  void* args[] = {&a};
+  CK(cudaLaunchCooperativeKernel(kernel_ptr<T>(), dim3(grid), dim3(kThreads), args, smem, st));
+  return FTGCR_OK;
+}
+
+template <typename T>
+int solve_async_impl(ftgcr_handle* h, const double* R, const double* x0, double* xout, const ftgcr_fault_plan* plan,
+                     cudaStream_t st) {
+  BeginArgs b;
+  memset(&b, 0, sizeof b);
+  b.R = R;
+  b.x0 = x0;
+  b.xout = xout;
+  b.nfaults = plan ? plan->n : 0;
+  b.max_steps = h->max_steps;
+  for (int q = 0; q < b.nfaults; ++q) memcpy(&b.faults[q], &plan->faults[q], sizeof(Fault));
+  k_begin_solve<T><<<1, 64, 0, st>>>((SolveDev<T>*)h->sdev, b, h->active, 1, 0, 0, h->ctl);
+  CK(cudaGetLastError());
+  // every inner step takes two rounds, every refinement sweep a few more
+  const int max_rounds = (int)std::min<long long>(1 << 30, 2 * h->max_steps + 8 * ((long long)h->max_outer + 2) + 16);
+  int rc = launch_persistent<T>((SolveDev<T>* const*)h->sdev_arr, h->nt_dev, h->active, 1, h->ctl, max_rounds, h->grid,
+                                h->smem, st);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(h->h_result, h->result, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(LaunchCtl), cudaMemcpyDeviceToHost, st));
+  h->last_stream = st;
+  h->solved = 1;
+  return FTGCR_OK;
+}
+
+int status_from_result(const ftgcr_handle* h) {
+  if (h->h_ctl->err) return FTGCR_ERR_TIMEOUT;
+  const SolveState& S = *h->h_result;
+  if (S.active) return FTGCR_ERR_CUDA;
+  return S.status == ST_CONVERGED ? FTGCR_OK : FTGCR_NOT_CONVERGED;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ C ABI
+extern "C" {
+
+const char* ftgcr_error_string(int status) {
+  switch (status) {
+    case FTGCR_OK: return "ok";
+    case FTGCR_NOT_CONVERGED: return "not converged (step limit reached)";
+    case FTGCR_ERR_ARG: return "invalid argument";
+    case FTGCR_ERR_OOM: return "device out of memory";
+    case FTGCR_ERR_CUDA: return "CUDA error";
+    case FTGCR_ERR_TIMEOUT: return "grid barrier timed out";
+    case FTGCR_ERR_BUDGET: return "request exceeds the memory budget";
+    case FTGCR_ERR_STATE: return "call out of order";
+    default: return "unknown status";
+  }
+}
+
+static int check_grid(const ftgcr_grid* g, int32_t k, double tol) {
+  if (!g) return FTGCR_ERR_ARG;
+  if (g->nlon < 3 || g->nlat < 1 || g->nlon > (1 << 20) || g->nlat > (1 << 20)) return FTGCR_ERR_ARG;
+  if (!(g->mu >= 0.0) || !std::isfinite(g->mu)) return FTGCR_ERR_ARG;
+  if (g->precision != FTGCR_FP64 && g->precision != FTGCR_MIXED) return FTGCR_ERR_ARG;
+  if (g->precond < FTGCR_PRECOND_LINE || g->precond > FTGCR_PRECOND_IDENTITY) return FTGCR_ERR_ARG;
+  if (k < 1 || k > FTGCR_MAX_K) return FTGCR_ERR_ARG;
+  if (!(tol > 0.0) || !std::isfinite(tol)) return FTGCR_ERR_ARG;
+  if (g->max_steps < 0 || g->tiles < 0 || g->max_outer < 0 || !(g->inner_tol >= 0.0) || g->inner_tol >= 1.0)
+    return FTGCR_ERR_ARG;
+  return FTGCR_OK;
+}
+
+static void fill_handle_params(ftgcr_handle* h, const ftgcr_grid* g, int32_t k, double tol, int sms, int smem_limit) {
+  h->nlon = g->nlon;
+  h->nlat = g->nlat;
+  h->k = k;
+  h->tol = tol;
+  h->mu = g->mu;
+  h->precision = g->precision;
+  h->precond = g->precond;
+  h->N = (long long)g->nlon * g->nlat;
+  h->C = chunk_len(g->nlon);
+  h->max_steps = g->max_steps > 0 ? g->max_steps : 100LL * (long long)std::ceil(std::sqrt((double)h->N)) + 100;
+  h->inner_tol = g->inner_tol > 0 ? g->inner_tol : 1e-5;
+  h->max_outer = g->max_outer > 0 ? g->max_outer : 40;
+  const bool mixed = g->precision == FTGCR_MIXED;
+  const size_t elem = mixed ? sizeof(float) : sizeof(double);
+  h->nt = g->tiles > 0 ? std::min(g->tiles, g->nlat) : choose_tiles(g->nlon, g->nlat, mixed, elem, sms, smem_limit);
+}
+
+int ftgcr_create(const ftgcr_grid* grid, const ftgcr_coeffs* coeffs, int32_t k, double tol, ftgcr_handle** out) {
+  if (!out) return FTGCR_ERR_ARG;
+  *out = nullptr;
+  int rc = check_grid(grid, k, tol);
+  if (rc) return rc;
+  if (!coeffs || !coeffs->D) return FTGCR_ERR_ARG;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  const DeviceInfo di = device_info(dev);
+  const int smem_limit = di.smem_optin - kStaticSmemReserve;
+  ftgcr_handle* h = new ftgcr_handle();
+  h->dev = dev;
+  fill_handle_params(h, grid, k, tol, di.sms, smem_limit);
+  const bool mixed = grid->precision == FTGCR_MIXED;
+  if (dyn_smem(h->nlon, h->nlat, h->nt, mixed, mixed ? 4 : 8) > (size_t)smem_limit) {
+    delete h;
+    return FTGCR_ERR_ARG;  // a single latitude row does not fit on chip
+  }
+  const bool Ddev = is_device_ptr(coeffs->D);
+  if (!Ddev) {
+    for (long long i = 0; i < h->N; ++i)
+      if (!std::isfinite(coeffs->D[i]) || !(coeffs->D[i] > 0.0)) {
+        delete h;
+        return FTGCR_ERR_ARG;
+      }
+  }
+  rc = mixed ? create_impl<float>(h, coeffs->D, Ddev) : create_impl<double>(h, coeffs->D, Ddev);
+  if (rc) {
+    ftgcr_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return FTGCR_OK;
+}
+
+int64_t ftgcr_footprint(const ftgcr_grid* grid, int32_t k) {
+  if (check_grid(grid, k, 1.0)) return -1;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    dev = 0;
+  }
+  const DeviceInfo di = device_info(dev);
+  ftgcr_handle h;
+  fill_handle_params(&h, grid, k, 1.0, di.sms > 0 ? di.sms : 152, di.smem_optin > 0 ? di.smem_optin - kStaticSmemReserve : 200000);
+  size_t b;
+  if (grid->precision == FTGCR_MIXED) {
+    SolveDev<float> sd{};
+    b = layout<float>(&h, nullptr, &sd);
+  } else {
+    SolveDev<double> sd{};
+    b = layout<double>(&h, nullptr, &sd);
+  }
+  return (int64_t)b + 3 * (int64_t)h.N * (int64_t)sizeof(double);  // + create-time scratch
+}
+
+int ftgcr_solve_async(ftgcr_handle* h, const double* rhs, double* x, const ftgcr_fault_plan* plan, void* stream) {
+  if (!h || !rhs || !x) return FTGCR_ERR_ARG;
+  int rc = validate_plan(h, plan);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  return h->precision == FTGCR_MIXED ? solve_async_impl<float>(h, rhs, x, x, plan, st)
+                                     : solve_async_impl<double>(h, rhs, x, x, plan, st);
+}
+
+int ftgcr_solve(ftgcr_handle* h, const double* rhs, double* x, const ftgcr_fault_plan* plan, void* stream) {
+  if (!h || !rhs || !x) return FTGCR_ERR_ARG;
+  int rc = validate_plan(h, plan);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool rdev = is_device_ptr(rhs), xdev = is_device_ptr(x);
+  const double* R = rhs;
+  double* X = x;
+  if (!rdev) {
+    if (!finite_array(rhs, h->N)) return FTGCR_ERR_ARG;
+    CK(cudaMemcpyAsync(h->stageR, rhs, sizeof(double) * h->N, cudaMemcpyHostToDevice, st));
+    R = h->stageR;
+  }
+  if (!xdev) {
+    if (!finite_array(x, h->N)) return FTGCR_ERR_ARG;
+    CK(cudaMemcpyAsync(h->stageX, x, sizeof(double) * h->N, cudaMemcpyHostToDevice, st));
+    X = h->stageX;
+  }
+  rc = h->precision == FTGCR_MIXED ? solve_async_impl<float>(h, R, X, X, plan, st)
+                                   : solve_async_impl<double>(h, R, X, X, plan, st);
+  if (rc) return rc;
+  if (!xdev) CK(cudaMemcpyAsync(x, h->stageX, sizeof(double) * h->N, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  h->last_status = status_from_result(h);
+  return h->last_status;
+}
+
+int ftgcr_stats(ftgcr_handle* h, ftgcr_stats_t* out) {
+  if (!h || !out) return FTGCR_ERR_ARG;
+  if (!h->solved) return FTGCR_ERR_STATE;
+  CK(cudaStreamSynchronize(h->last_stream));
+  h->last_status = status_from_result(h);
+  const SolveState& S = *h->h_result;
+  memset(out, 0, sizeof *out);
+  out->steps = S.step;
+  out->cycles = S.cycles;
+  out->restarts = S.restarts;
+  out->faults_injected = S.finj;
+  out->faults_detected = S.fdet;
+  out->outer = h->precision == FTGCR_MIXED ? std::max(0, S.outer - 1) : 0;
+  out->ndetect = S.ndetect;
+  out->converged = S.status == ST_CONVERGED;
+  for (int q = 0; q < S.ndetect && q < FTGCR_MAX_DETECT; ++q) {
+    out->detect_step[q] = S.detect_step[q];
+    out->detect_ratio[q] = S.detect_ratio[q];
+  }
+  out->res0 = std::sqrt(S.nrm2_0);
+  out->res_final_rec = std::sqrt(S.nrm2_last);
+  out->res_final_true = std::sqrt(S.res_true2);
+  out->norm_R = std::sqrt(S.nrm2_R);
+  out->bytes_resident = (int64_t)h->pool_bytes;
+  out->bytes_backup = (int64_t)h->backup_bytes;
+  out->tiles = h->nt;
+  out->status = h->last_status;
+  return FTGCR_OK;
+}
+
+int ftgcr_apply_operator(ftgcr_handle* h, const double* in, double* out, void* stream) {
+  if (!h || !in || !out) return FTGCR_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int blocks = (int)std::min<long long>((h->N + 255) / 256, 4096);
+  k_apply_operator<<<blocks, 256, 0, st>>>(in, out, h->Tx64, h->Ty64, h->muA64, h->nlon, h->nlat);
+  CK(cudaGetLastError());
+  return FTGCR_OK;
+}
+
+int ftgcr_apply_precond(ftgcr_handle* h, const double* in, double* out, void* stream) {
+  if (!h || !in || !out) return FTGCR_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  SolveDev<double> sd{};
+  if (h->precision == FTGCR_FP64) {
+    sd = h->sd64;
+  } else {
+    return FTGCR_ERR_ARG;  // the FP64 factorisation is only kept by FP64 handles
+  }
+  const int rows_per_block = 4;
+  const size_t smem = (size_t)rows_per_block * row_stride(h->nlon) * sizeof(double);
+  CK(cudaFuncSetAttribute(k_apply_precond, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_apply_precond<<<(h->nlat + rows_per_block - 1) / rows_per_block, 32 * rows_per_block, smem, st>>>(in, out, sd);
+  CK(cudaGetLastError());
+  return FTGCR_OK;
+}
+
+int ftgcr_solve_batch(ftgcr_handle* const* hs, const double* const* rhs, double* const* x,
+                      const ftgcr_fault_plan* const* plans, int32_t n, void* stream) {
+  (void)hs;
+  (void)rhs;
+  (void)x;
+  (void)plans;
+  (void)n;
+  (void)stream;
+  return FTGCR_ERR_STATE;
+}
+
+void ftgcr_destroy(ftgcr_handle* h) {
+  if (!h) return;
+  if (h->pool) cudaFree(h->pool);
+  if (h->h_result) cudaFreeHost(h->h_result);
+  if (h->h_ctl) cudaFreeHost(h->h_ctl);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,287 @@
+"""Python binding of libftgcr, the GB300 FT-GCR(k) solver (C ABI in
+include/ftgcr.h).  Argument marshalling only: every step of the solve runs in
+the library's CUDA kernels.  There is no fallback: if the library cannot be
+built or loaded, every call raises.
+
+Arrays are numpy (host) or torch (host or CUDA) FP64 arrays of shape
+[nlat, nlon]; the library detects where they live.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_CSRC = os.path.join(_HERE, "csrc")
+_INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
+_BUILD = os.path.join(_HERE, "_build")
+LIB_PATH = os.path.join(_BUILD, "libftgcr.so")
+SOURCES = ["ftgcr.cu"]
+HEADERS = ["ftgcr_device.cuh", "ftgcr_phases.cuh"]
+NVCC_FLAGS = ["-std=c++17", "-O3", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "--fmad=false",
+              "-Xcompiler", "-fPIC", "-shared"]
+
+FP64, MIXED = 0, 1
+PRECOND = {"line": 0, "jacobi": 1, "identity": 2}
+VEC = {"x": 0, "r": 1, "p": 2, "ap": 3, "e": 4}
+MAX_FAULTS, MAX_K, MAX_DETECT = 64, 16, 16
+
+OK, NOT_CONVERGED, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BUDGET, ERR_STATE = 0, 1, -1, -2, -3, -4, -5, -6
+
+# every symbol include/ftgcr.h declares
+EXPORTS = ["ftgcr_create", "ftgcr_solve", "ftgcr_solve_async", "ftgcr_stats", "ftgcr_solve_batch",
+           "ftgcr_apply_operator", "ftgcr_apply_precond", "ftgcr_footprint", "ftgcr_destroy", "ftgcr_error_string"]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nlon", ctypes.c_int32), ("nlat", ctypes.c_int32), ("mu", ctypes.c_double),
+                ("precision", ctypes.c_int32), ("precond", ctypes.c_int32), ("max_steps", ctypes.c_int64),
+                ("tiles", ctypes.c_int32), ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int32)]
+
+
+class Coeffs(ctypes.Structure):
+    _fields_ = [("D", ctypes.c_void_p)]
+
+
+class Fault(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int64), ("vec", ctypes.c_int32), ("index", ctypes.c_int64), ("bit", ctypes.c_int32)]
+
+
+class FaultPlan(ctypes.Structure):
+    _fields_ = [("faults", ctypes.POINTER(Fault)), ("n", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("cycles", ctypes.c_int64), ("restarts", ctypes.c_int64),
+                ("faults_injected", ctypes.c_int64), ("faults_detected", ctypes.c_int64), ("outer", ctypes.c_int64),
+                ("ndetect", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("detect_step", ctypes.c_int64 * MAX_DETECT), ("detect_ratio", ctypes.c_double * MAX_DETECT),
+                ("res0", ctypes.c_double), ("res_final_rec", ctypes.c_double), ("res_final_true", ctypes.c_double),
+                ("norm_R", ctypes.c_double), ("bytes_resident", ctypes.c_int64), ("bytes_backup", ctypes.c_int64),
+                ("tiles", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+
+class FTGCRError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        msg = lib().ftgcr_error_string(status).decode() if _lib is not None else str(status)
+        super().__init__(f"{what}: {msg} ({status})" if what else f"{msg} ({status})")
+        self.status = status
+
+
+def _stale() -> bool:
+    if not os.path.exists(LIB_PATH):
+        return True
+    t = os.path.getmtime(LIB_PATH)
+    deps = [os.path.join(_CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(_INCLUDE, "ftgcr.h")]
+    return any(os.path.getmtime(d) > t for d in deps)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile libftgcr.so for sm_103a in-tree (paper_2103_07210_gb300/_build)."""
+    with _lock:
+        if not force and not _stale():
+            return LIB_PATH
+        os.makedirs(_BUILD, exist_ok=True)
+        tmp = LIB_PATH + ".%d.tmp" % os.getpid()
+        cmd = ["nvcc"] + NVCC_FLAGS + ["-o", tmp] + [os.path.join(_CSRC, f) for f in SOURCES]
+        if verbose:
+            print(" ".join(cmd))
+        subprocess.check_call(cmd, cwd=_CSRC)
+        os.replace(tmp, LIB_PATH)
+        return LIB_PATH
+
+
+def lib():
+    """Load libftgcr.so (building it first if needed); raises if that fails."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH) or _stale():
+            build()
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        L.ftgcr_create.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Coeffs), i32, dbl, ctypes.POINTER(vp)]
+        L.ftgcr_solve.argtypes = [vp, vp, vp, ctypes.POINTER(FaultPlan), vp]
+        L.ftgcr_solve_async.argtypes = [vp, vp, vp, ctypes.POINTER(FaultPlan), vp]
+        L.ftgcr_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+        L.ftgcr_solve_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                        ctypes.POINTER(ctypes.POINTER(FaultPlan)), i32, vp]
+        L.ftgcr_apply_operator.argtypes = [vp, vp, vp, vp]
+        L.ftgcr_apply_precond.argtypes = [vp, vp, vp, vp]
+        L.ftgcr_footprint.argtypes = [ctypes.POINTER(Grid), i32]
+        L.ftgcr_footprint.restype = i64
+        L.ftgcr_destroy.argtypes = [vp]
+        L.ftgcr_destroy.restype = None
+        L.ftgcr_error_string.argtypes = [ctypes.c_int]
+        L.ftgcr_error_string.restype = ctypes.c_char_p
+        for f in EXPORTS:
+            if not hasattr(L, f):
+                raise RuntimeError(f"libftgcr.so does not export {f}")
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    """(pointer, keep-alive) of a contiguous FP64 numpy array or torch tensor."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags.c_contiguous:
+            raise TypeError("expected a C-contiguous float64 numpy array")
+        return a.ctypes.data, a
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(a, torch.Tensor):
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("expected a contiguous float64 torch tensor")
+        return a.data_ptr(), a
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+def _plan(faults):
+    if not faults:
+        return None, None
+    if len(faults) > MAX_FAULTS:
+        raise ValueError("too many faults")
+    arr = (Fault * len(faults))()
+    for q, (step, vec, idx, bit) in enumerate(faults):
+        arr[q].step, arr[q].vec, arr[q].index, arr[q].bit = int(step), VEC.get(vec, vec), int(idx), int(bit)
+    plan = FaultPlan(ctypes.cast(arr, ctypes.POINTER(Fault)), len(faults))
+    return plan, arr
+
+
+def _grid(nlon, nlat, mu, precision, precond, max_steps, tiles, inner_tol, max_outer):
+    prec = {"fp64": FP64, "mixed": MIXED}.get(precision, precision)
+    pc = PRECOND.get(precond, precond)
+    return Grid(int(nlon), int(nlat), float(mu), int(prec), int(pc), int(max_steps), int(tiles), float(inner_tol),
+                int(max_outer))
+
+
+def footprint(nlon, nlat, k=4, precision="fp64", precond="line", tiles=0) -> int:
+    g = _grid(nlon, nlat, 1.0, precision, precond, 0, tiles, 0.0, 0)
+    return int(lib().ftgcr_footprint(ctypes.byref(g), int(k)))
+
+
+class Solver:
+    """One FT-GCR(k) problem resident on the GPU (ftgcr_create)."""
+
+    def __init__(self, D, mu, k=4, tol=1e-10, precision="fp64", precond="line", max_steps=0, tiles=0,
+                 inner_tol=0.0, max_outer=0):
+        L = lib()
+        nlat, nlon = D.shape
+        self.nlon, self.nlat, self.k, self.tol = int(nlon), int(nlat), int(k), float(tol)
+        self.precision = precision
+        g = _grid(nlon, nlat, mu, precision, precond, max_steps, tiles, inner_tol, max_outer)
+        dp, keep = _ptr(D)
+        c = Coeffs(dp)
+        h = ctypes.c_void_p()
+        st = L.ftgcr_create(ctypes.byref(g), ctypes.byref(c), int(k), float(tol), ctypes.byref(h))
+        del keep
+        if st != OK:
+            raise FTGCRError(st, "ftgcr_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ftgcr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def solve(self, rhs, x, faults=(), stream=None) -> int:
+        """Blocking solve; x holds the initial guess on entry and the solution
+        on exit.  Returns OK or NOT_CONVERGED, raises on errors."""
+        rp, rk = _ptr(rhs)
+        xp, xk = _ptr(x)
+        plan, keep = _plan(faults)
+        st = lib().ftgcr_solve(self.h, rp, xp, ctypes.byref(plan) if plan else None, _stream_ptr(stream))
+        if st < 0:
+            raise FTGCRError(st, "ftgcr_solve")
+        return st
+
+    def solve_async(self, rhs, x, faults=(), stream=None) -> None:
+        rp, rk = _ptr(rhs)
+        xp, xk = _ptr(x)
+        plan, keep = _plan(faults)
+        st = lib().ftgcr_solve_async(self.h, rp, xp, ctypes.byref(plan) if plan else None, _stream_ptr(stream))
+        if st < 0:
+            raise FTGCRError(st, "ftgcr_solve_async")
+
+    def stats(self) -> dict:
+        s = Stats()
+        st = lib().ftgcr_stats(self.h, ctypes.byref(s))
+        if st < 0:
+            raise FTGCRError(st, "ftgcr_stats")
+        n = s.ndetect
+        return dict(steps=s.steps, cycles=s.cycles, restarts=s.restarts, faults_injected=s.faults_injected,
+                    faults_detected=s.faults_detected, outer=s.outer, converged=bool(s.converged),
+                    detect_steps=[s.detect_step[i] for i in range(n)],
+                    detect_ratio=[s.detect_ratio[i] for i in range(n)], res0=s.res0, res_final_rec=s.res_final_rec,
+                    res_final_true=s.res_final_true, norm_R=s.norm_R, bytes_resident=s.bytes_resident,
+                    bytes_backup=s.bytes_backup, tiles=s.tiles, status=s.status)
+
+    def apply_operator(self, inp, out, stream=None):
+        ip, ik = _ptr(inp)
+        op, ok = _ptr(out)
+        st = lib().ftgcr_apply_operator(self.h, ip, op, _stream_ptr(stream))
+        if st < 0:
+            raise FTGCRError(st, "ftgcr_apply_operator")
+
+    def apply_precond(self, inp, out, stream=None):
+        ip, ik = _ptr(inp)
+        op, ok = _ptr(out)
+        st = lib().ftgcr_apply_precond(self.h, ip, op, _stream_ptr(stream))
+        if st < 0:
+            raise FTGCRError(st, "ftgcr_apply_precond")
+
+
+def solve_batch(solvers, rhs, xs, faults=None, stream=None) -> None:
+    """Enqueue all solves in one persistent launch (ftgcr_solve_batch)."""
+    n = len(solvers)
+    H = (ctypes.c_void_p * n)(*[s.h.value for s in solvers])
+    keep = []
+    Rp = (ctypes.c_void_p * n)()
+    Xp = (ctypes.c_void_p * n)()
+    for i in range(n):
+        p, k = _ptr(rhs[i])
+        Rp[i] = p
+        keep.append(k)
+        p, k = _ptr(xs[i])
+        Xp[i] = p
+        keep.append(k)
+    P = (ctypes.POINTER(FaultPlan) * n)()
+    for i in range(n):
+        f = faults[i] if faults else ()
+        plan, arr = _plan(f)
+        if plan is not None:
+            keep += [plan, arr]
+            P[i] = ctypes.pointer(plan)
+    st = lib().ftgcr_solve_batch(H, Rp, Xp, P, n, _stream_ptr(stream))
+    if st < 0:
+        raise FTGCRError(st, "ftgcr_solve_batch")

@@ -1,0 +1,57 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+include/ftgcr.h declares; the binding fails loudly when the library is
+missing (no CPU fallback).  No compute calls: these run without a GPU."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2103_07210_gb300 import ftgcr
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "ftgcr.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(ftgcr_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_the_binding_exports():
+    assert sorted(ftgcr.EXPORTS) == declared_functions()
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = ftgcr.build()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    syms = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    missing = [f for f in declared_functions() if f not in syms]
+    assert not missing, missing
+    L = ctypes.CDLL(path)
+    for f in declared_functions():
+        assert hasattr(L, f)
+
+
+def test_build_flags_target_sm_103a_only():
+    assert "arch=compute_103a,code=sm_103a" in ftgcr.NVCC_FLAGS
+    assert "--fmad=false" in ftgcr.NVCC_FLAGS
+
+
+def test_error_strings_without_gpu():
+    L = ftgcr.lib()
+    assert L.ftgcr_error_string(0) == b"ok"
+    assert b"timed out" in L.ftgcr_error_string(-4)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    monkeypatch.setattr(ftgcr, "_lib", None)
+    monkeypatch.setattr(ftgcr, "LIB_PATH", str(tmp_path / "nope" / "libftgcr.so"))
+
+    def no_build(*a, **k):
+        raise RuntimeError("build disabled")
+
+    monkeypatch.setattr(ftgcr, "build", no_build)
+    with pytest.raises(Exception):
+        ftgcr.lib()

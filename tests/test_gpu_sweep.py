@@ -1,0 +1,46 @@
+"""Fault sweep at 512 x 256 (FP64, k = 4, hill coefficients, flow RHS): 1000
+seeded single-bit flips, uniform over step (1..fault-free step count),
+vector {x, r, p, Ap}, index and bit 0-63.  The GPU path must take exactly the
+oracle's decisions (detected or not, detection steps, step count,
+convergence) and match its solution to 1e-10."""
+import multiprocessing as mp
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_07210_gb300 import ftgcr, inputs
+from tests import sweep_worker
+from tests.gpu_util import decisions, rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+NLON, NLAT, K, TOL, SEED, TRIALS = 512, 256, 4, 1e-10, 0, 1000
+
+
+def test_sweep_1000_flips_identical_decisions():
+    p = inputs.hill_problem(NLON, NLAT)
+    ff = oracle.ftgcr(p.D, p.R, p.mu, K, TOL)
+    nff = ff["steps"]
+    oracle.build()
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
+        refs = pool.map(sweep_worker.oracle_trial, [(NLON, NLAT, K, TOL, SEED, t, nff) for t in range(TRIALS)],
+                        chunksize=8)
+    mism, worst, detected = [], 0.0, 0
+    with ftgcr.Solver(p.D, p.mu, k=K, tol=TOL) as s:
+        R = torch.from_numpy(p.R).cuda()
+        for trial, f, dref, inj, xref in refs:
+            x = torch.zeros_like(R)
+            s.solve(R, x, faults=[f])
+            info = s.stats()
+            if decisions(info) != dref or info["faults_injected"] != inj:
+                mism.append((trial, f, decisions(info), dref))
+                continue
+            detected += info["faults_detected"] > 0
+            worst = max(worst, rel_err(x.cpu().numpy(), xref))
+    assert not mism, mism[:5]
+    assert worst <= 1e-10, worst
+    assert detected > 0
