@@ -32,10 +32,11 @@
  *               of executed step `step` (x, r, p, Ap: before beta is formed)
  *               or right after the preconditioner of that step (e).
  *
- * Every reduction is a plain sequential sum in index order.  Every pointwise
- * update is written as an explicit fma where the method multiplies and adds
- * (axpy, recurrences); everything else uses separately rounded operations
- * (compile with -ffp-contract=off).
+ * Every reduction is a sequential sum in index order accumulated in twice the
+ * working precision and rounded once (Dot2).  Every pointwise update is
+ * written as an explicit fma where the method multiplies and adds (axpy,
+ * recurrences, line-solve substitution); everything else uses separately
+ * rounded operations (compile with -ffp-contract=off).
  */
 #include <math.h>
 #include <stdint.h>
@@ -164,43 +165,51 @@ void orc_apply_P(int nlon, int nlat, double mu, const double* Tx, const double* 
 
 /* Solve one periodic symmetric tridiagonal system M x = b of order n >= 3,
  * M_ii = d_i, M_{i,i+1} = M_{i+1,i} = -o_i (o_{n-1} couples x_{n-1} and x_0).
- * Textbook method: Thomas elimination on the leading (n-1) x (n-1) block A0,
- * with the periodic coupling of the last unknown eliminated by bordering:
- * x' = A0^-1 b' - x_{n-1} A0^-1 c, c = (-o_{n-1}, 0, ..., 0, -o_{n-2}), and
- * x_{n-1} from the last equation. */
-static void orc_thomas(int m, const double* sub, const double* diag, const double* sup, const double* rhs,
-                       double* x, double* w) {
-  /* A0 x = rhs for a non-periodic tridiagonal of order m: sub[i] couples i to
-   * i-1, sup[i] couples i to i+1.  w is scratch of length m. */
-  w[0] = diag[0];
-  x[0] = rhs[0];
+ * Textbook method: LU (Thomas) elimination of the leading (n-1) x (n-1) block
+ * A0, with the periodic coupling of the last unknown eliminated by
+ * bordering: x' = A0^-1 b' - x_{n-1} A0^-1 c, c = (-o_{n-1}, 0, ..., 0, -o_{n-2}),
+ * and x_{n-1} from the last equation.
+ *
+ * Factorisation of A0 (sub_i = -o_{i-1}, sup_i = -o_i): w_0 = d_0,
+ * l_i = sub_i / w_{i-1}, w_i = d_i - l_i sup_{i-1}; the pivots are kept as
+ * reciprocals winv_i = 1 / w_i and u_i = sup_i winv_i.  Substitution:
+ * forward y_i = b_i - l_i y_{i-1}, backward y_i = winv_i y_i - u_i y_{i+1},
+ * each step one fused multiply-add. */
+static void orc_thomas_factor(int m, const double* d, const double* o, double* l, double* winv, double* u) {
+  double w = d[0];
+  winv[0] = 1.0 / w;
+  l[0] = 0.0;
   for (int i = 1; i < m; ++i) {
-    double l = sub[i] / w[i - 1];
-    w[i] = diag[i] - l * sup[i - 1];
-    x[i] = rhs[i] - l * x[i - 1];
+    l[i] = -o[i - 1] / w;
+    w = d[i] - l[i] * -o[i - 1];
+    winv[i] = 1.0 / w;
   }
-  x[m - 1] = x[m - 1] / w[m - 1];
-  for (int i = m - 2; i >= 0; --i) x[i] = (x[i] - sup[i] * x[i + 1]) / w[i];
+  for (int i = 0; i < m; ++i) u[i] = (i < m - 1) ? -o[i] * winv[i] : 0.0;
+}
+
+static void orc_thomas_solve(int m, const double* l, const double* winv, const double* u, const double* rhs,
+                             double* y) {
+  y[0] = rhs[0];
+  for (int i = 1; i < m; ++i) y[i] = fma(-l[i], y[i - 1], rhs[i]);
+  y[m - 1] = y[m - 1] * winv[m - 1];
+  for (int i = m - 2; i >= 0; --i) y[i] = fma(-u[i], y[i + 1], y[i] * winv[i]);
 }
 
 static void orc_periodic_tridiag(int n, const double* d, const double* o, const double* b, double* x,
                                  double* work) {
   int m = n - 1;
-  double* sub = work;
-  double* sup = work + n;
-  double* c = work + 2 * n;
-  double* y = work + 3 * n;
-  double* z = work + 4 * n;
-  double* w = work + 5 * n;
-  for (int i = 0; i < m; ++i) {
-    sub[i] = (i > 0) ? -o[i - 1] : 0.0;
-    sup[i] = (i < m - 1) ? -o[i] : 0.0;
-    c[i] = 0.0;
-  }
+  double* l = work;
+  double* winv = work + n;
+  double* u = work + 2 * n;
+  double* c = work + 3 * n;
+  double* y = work + 4 * n;
+  double* z = work + 5 * n;
+  orc_thomas_factor(m, d, o, l, winv, u);
+  for (int i = 0; i < m; ++i) c[i] = 0.0;
   c[0] = -o[n - 1];
   c[m - 1] = c[m - 1] + -o[n - 2];
-  orc_thomas(m, sub, d, sup, b, y, w);
-  orc_thomas(m, sub, d, sup, c, z, w);
+  orc_thomas_solve(m, l, winv, u, b, y);
+  orc_thomas_solve(m, l, winv, u, c, z);
   /* last row: -o_{n-1} x_0 - o_{n-2} x_{n-2} + d_{n-1} x_{n-1} = b_{n-1} */
   double num = b[n - 1] + o[n - 1] * y[0] + o[n - 2] * y[m - 1];
   double den = d[n - 1] + o[n - 1] * z[0] + o[n - 2] * z[m - 1];
@@ -242,7 +251,7 @@ void orc_solve_P(int nlon, int nlat, double mu, const double* Tx, const double* 
   double* d = (double*)malloc(sizeof(double) * nlon);
   double* o = (double*)malloc(sizeof(double) * nlon);
   double* b = (double*)malloc(sizeof(double) * nlon);
-  double* work = (double*)malloc(sizeof(double) * 6 * nlon);
+  double* work = (double*)malloc(sizeof(double) * 6 * nlon);  /* l, winv, u, c, y, z */
   for (int j = 0; j < nlat; ++j) {
     double muA = mu * area[j];
     for (int i = 0; i < nlon; ++i) {
@@ -261,10 +270,23 @@ void orc_solve_P(int nlon, int nlat, double mu, const double* Tx, const double* 
 }
 
 /* ------------------------------------------------------------ reductions */
+/* Inner product accumulated in twice the working precision and rounded once
+ * (Dot2 of Ogita, Rump and Oishi, 2005): each product split exactly into
+ * h + r by one fma (TwoProduct), the running sum p advanced by Knuth's
+ * TwoSum with its rounding error q, the low parts q + r collected in s,
+ * result p + s. */
 double orc_dot(long n, const double* a, const double* b) {
-  double s = 0.0;
-  for (long i = 0; i < n; ++i) s = s + a[i] * b[i];
-  return s;
+  double p = 0.0, s = 0.0;
+  for (long i = 0; i < n; ++i) {
+    double h = a[i] * b[i];
+    double r = fma(a[i], b[i], -h);
+    double t = p + h;
+    double z = t - p;
+    double q = (p - (t - z)) + (h - z);
+    p = t;
+    s = s + (q + r);
+  }
+  return p + s;
 }
 
 /* Flip one bit of the IEEE-754 binary64 pattern of v. */

@@ -15,6 +15,7 @@
 #include "../../include/ftgcr.h"
 #include "ftgcr_device.cuh"
 #include "ftgcr_phases.cuh"
+#include "ftgcr_instances.h"
 
 using namespace ftgcr;
 
@@ -56,21 +57,26 @@ __global__ void k_face_coeffs(int nlon, int nlat, const double* __restrict__ D, 
 
 // Line-preconditioner factorisation, one thread per latitude row (setup
 // only).  Row system M x = b, M_ii = d_i = Tx_i + Tx_{i-1} + sigma_i,
-// M_{i,i+1} = -Tx_i (periodic).  LU of the leading block: w_0 = d_0,
-// w_i = d_i - Tx_{i-1} c_{i-1}, c_i = Tx_i / w_i; bordering vector
-// z = A0^-1 (-Tx_{n-1} e_0 - Tx_{n-2} e_{n-2}); delta = d_{n-1} + Tx_{n-1} z_0 +
-// Tx_{n-2} z_{n-2}.  Stored permuted for the per-lane chunks of the solve:
-// element i -> [row][i % C][i / C].  Jacobi: 1 / d_i in natural layout.
+// M_{i,i+1} = -Tx_i (periodic).  Thomas factorisation of the leading
+// (n-1) x (n-1) block, operation for operation the CPU oracle's:
+// w_0 = d_0, l_i = -Tx_{i-1} / w_{i-1}, w_i = d_i - l_i (-Tx_{i-1}),
+// winv_i = 1 / w_i, u_i = -Tx_i winv_i; bordering vector z = A0^-1 c,
+// c = (-Tx_{n-1}, 0, ..., 0, -Tx_{n-2}) by the same substitution; delta =
+// d_{n-1} + Tx_{n-1} z_0 + Tx_{n-2} z_{n-2}.
+// FP64 outputs (natural layout): l, winv, u, z, delta.  FP32 outputs (chunk
+// layout, element i -> [row][i % C][i / C]): c = -u, winv, z, and per row
+// 1/delta, Tx_{n-1}/delta, Tx_{n-2}/delta.  Jacobi: d_i (FP64) or 1/d_i (FP32).
 __global__ void k_line_factor(int nlon, int nlat, int C, int precond, const double* __restrict__ Tx,
-                              const double* __restrict__ Ty, const double* __restrict__ muA, double* work,
-                              double* lc, double* lw, double* lz, double* lrow, float* lc32, float* lw32, float* lz32,
-                              float* lrow32) {
+                              const double* __restrict__ Ty, const double* __restrict__ muA, double* l64,
+                              double* w64, double* u64, double* z64, double* lrow64, float* lc32, float* lw32,
+                              float* lz32, float* lrow32) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nlat) return;
   const int n = nlon, m = n - 1;
-  const double* tx = Tx + (long long)j * n;
+  const long long rb = (long long)j * n;
+  const double* tx = Tx + rb;
   auto diag = [&](int i) {
-    const long long c = (long long)j * n + i;
+    const long long c = rb + i;
     double s = 0.0;
     if (j < nlat - 1) s = s + Ty[c];
     if (j > 0) s = s + Ty[c - n];
@@ -79,51 +85,57 @@ __global__ void k_line_factor(int nlon, int nlat, int C, int precond, const doub
   };
   if (precond == PC_JACOBI) {
     for (int i = 0; i < n; ++i) {
-      const double v = 1.0 / diag(i);
-      lw[(long long)j * n + i] = v;
-      if (lw32) lw32[(long long)j * n + i] = (float)v;
+      const double d = diag(i);
+      if (w64) w64[rb + i] = d;
+      if (lw32) lw32[rb + i] = (float)(1.0 / d);
     }
     return;
   }
   if (precond != PC_LINE) return;
-  double* w = work + (long long)j * 3 * n;  // w_i, c_i, z_i
-  double* cc = w + n;
-  double* z = w + 2 * n;
-  w[0] = diag(0);
-  cc[0] = (m >= 2) ? tx[0] / w[0] : 0.0;
+  double* l = l64 + rb;
+  double* winv = w64 + rb;
+  double* u = u64 + rb;
+  double* z = z64 + rb;
+  double w = diag(0);
+  winv[0] = 1.0 / w;
+  l[0] = 0.0;
   for (int i = 1; i < m; ++i) {
-    w[i] = diag(i) - tx[i - 1] * cc[i - 1];
-    cc[i] = (i <= m - 2) ? tx[i] / w[i] : 0.0;
+    l[i] = -tx[i - 1] / w;
+    w = diag(i) - l[i] * -tx[i - 1];
+    winv[i] = 1.0 / w;
   }
-  cc[m - 1] = 0.0;
-  // z: forward g_i = cvec_i + c_{i-1} g_{i-1}, backward z_i = g_i / w_i + c_i z_{i+1}
+  for (int i = 0; i < m; ++i) u[i] = (i < m - 1) ? -tx[i] * winv[i] : 0.0;
+  u[m] = 0.0;
+  l[m] = 0.0;
+  winv[m] = 0.0;
+  // z = A0^-1 c
   for (int i = 0; i < m; ++i) z[i] = 0.0;
   z[0] = -tx[n - 1];
   z[m - 1] = z[m - 1] + -tx[n - 2];
-  for (int i = 1; i < m; ++i) z[i] = z[i] + cc[i - 1] * z[i - 1];
-  z[m - 1] = z[m - 1] / w[m - 1];
-  for (int i = m - 2; i >= 0; --i) z[i] = z[i] / w[i] + cc[i] * z[i + 1];
+  for (int i = 1; i < m; ++i) z[i] = fma(-l[i], z[i - 1], z[i]);
+  z[m - 1] = z[m - 1] * winv[m - 1];
+  for (int i = m - 2; i >= 0; --i) z[i] = fma(-u[i], z[i + 1], z[i] * winv[i]);
+  z[m] = 0.0;
   const double delta = diag(n - 1) + tx[n - 1] * z[0] + tx[n - 2] * z[m - 1];
-  const double dinv = 1.0 / delta;
-  const long long rb = (long long)j * 32 * C;
-  for (int i = 0; i < 32 * C; ++i) {
-    const int lane = i / C, k = i % C;
-    const long long pos = rb + (long long)k * 32 + lane;
-    const bool in = i < m;
-    const double vc = in ? cc[i] : 0.0, vw = in ? 1.0 / w[i] : 0.0, vz = in ? z[i] : 0.0;
-    lc[pos] = vc;
-    lw[pos] = vw;
-    lz[pos] = vz;
-    if (lc32) {
-      lc32[pos] = (float)vc;
-      lw32[pos] = (float)vw;
-      lz32[pos] = (float)vz;
+  lrow64[(long long)j * 4 + 0] = delta;
+  lrow64[(long long)j * 4 + 1] = 0.0;
+  lrow64[(long long)j * 4 + 2] = 0.0;
+  lrow64[(long long)j * 4 + 3] = 0.0;
+  if (lc32) {
+    const long long cb = (long long)j * 32 * C;
+    for (int i = 0; i < 32 * C; ++i) {
+      const int lane = i / C, k = i % C;
+      const long long pos = cb + (long long)k * 32 + lane;
+      const bool in = i < m;
+      lc32[pos] = in ? (float)(-u[i]) : 0.f;
+      lw32[pos] = in ? (float)winv[i] : 0.f;
+      lz32[pos] = in ? (float)z[i] : 0.f;
     }
-  }
-  const double r4[4] = {dinv, tx[n - 1] * dinv, tx[n - 2] * dinv, 0.0};
-  for (int q = 0; q < 4; ++q) {
-    lrow[(long long)j * 4 + q] = r4[q];
-    if (lrow32) lrow32[(long long)j * 4 + q] = (float)r4[q];
+    const double dinv = 1.0 / delta;
+    lrow32[(long long)j * 4 + 0] = (float)dinv;
+    lrow32[(long long)j * 4 + 1] = (float)(tx[n - 1] * dinv);
+    lrow32[(long long)j * 4 + 2] = (float)(tx[n - 2] * dinv);
+    lrow32[(long long)j * 4 + 3] = 0.f;
   }
 }
 
@@ -150,8 +162,8 @@ __global__ void k_apply_precond(const double* in, double* out, SolveDev<double> 
   const long long base = (long long)j * sd.nlon;
   for (int i = lane; i < sd.nlon; i += 32) row[sk(i)] = in[base + i];
   __syncwarp();
-  precond_row(sd, j, row);
-  if (sd.precond == PC_IDENTITY) __syncwarp();
+  precond_row(sd, j, row, row_consts_global(sd, j));
+  __syncwarp();
   for (int i = lane; i < sd.nlon; i += 32) out[base + i] = row[sk(i)];
 }
 
@@ -235,16 +247,23 @@ int chunk_len(int nlon) { return (nlon - 1 + 31) / 32; }
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-// Dynamic shared memory of the persistent kernel for a solve with nt tiles.
-size_t dyn_smem(int nlon, int nlat, int nt, int mixed, size_t elem) {
-  const int hmax = (nlat + nt - 1) / nt;
-  const size_t e = mixed ? sizeof(double) : elem;
-  return (size_t)(hmax + 2) * row_stride(nlon) * e;
+// Dynamic shared memory of the persistent kernel for a solve with nt tiles:
+// the tile's rows plus halo (inner precision) and, for the line
+// preconditioner, the three staged constant arrays of those rows; the mixed
+// path's refinement phase holds the same rows in FP64.
+size_t dyn_smem(int nlon, int nlat, int nt, int mixed, size_t elem, int precond) {
+  const size_t hmax = (size_t)((nlat + nt - 1) / nt);
+  const size_t rows = (hmax + 2) * row_stride(nlon) * elem;
+  const size_t per_row = mixed ? 32 * (size_t)chunk_len(nlon) : (size_t)nlon;  // chunk vs natural layout
+  const size_t consts = precond == FTGCR_PRECOND_LINE ? 3 * (hmax + 2) * per_row * elem : 0;
+  const size_t out = mixed ? (hmax + 2) * row_stride(nlon) * sizeof(double) : 0;
+  return std::max(rows + consts, out);
 }
 
-int choose_tiles(int nlon, int nlat, int mixed, size_t elem, int sms, int smem_limit) {
+int choose_tiles(int nlon, int nlat, int mixed, size_t elem, int precond, int sms, int smem_limit) {
   int nt = std::min(nlat, sms);
-  while (nt < nlat && dyn_smem(nlon, nlat, nt, mixed, elem) > (size_t)smem_limit) nt = std::min(nlat, nt * 2);
+  while (nt < nlat && dyn_smem(nlon, nlat, nt, mixed, elem, precond) > (size_t)smem_limit)
+    nt = std::min(nlat, nt + sms);
   return nt;
 }
 
@@ -281,6 +300,7 @@ struct ftgcr_handle {
   void** sdev_arr = nullptr;                   // device array holding sdev
   int* nt_dev = nullptr;
   int* active = nullptr;                       // [2]
+  int* diag = nullptr;                         // [grid][4] per-CTA progress (timeout report)
   LaunchCtl* ctl = nullptr;
   SolveState* result = nullptr;
   SolveState* h_result = nullptr;              // pinned
@@ -296,20 +316,40 @@ struct ftgcr_handle {
 
 namespace {
 
+// Compile-time bound on the Krylov directions of the kernel instance.
+int kbound(int k) { return k <= 4 ? 4 : (k <= 8 ? 8 : 16); }
+
+// The persistent kernel instances live in their own translation units
+// (ftgcr_k4.cu, ftgcr_k8.cu, ftgcr_k16.cu) so that they compile in parallel.
 template <typename T>
-void* kernel_ptr() {
-  return (void*)k_ftgcr_persistent<T>;
+const void* kernel_ptr(int kb) {
+  return ftgcr::persistent_kernel_ptr(kb, sizeof(T) == 8);
 }
 
+// The dynamic shared memory attribute of a kernel is process-wide: only ever
+// raise it, so that a handle created later never shrinks what an earlier one
+// needs.
 template <typename T>
-int configure_kernel(size_t smem) {
-  CK(cudaFuncSetAttribute(k_ftgcr_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+int configure_kernel(int kb, size_t smem) {
+  static std::mutex mu;
+  static std::vector<std::pair<const void*, size_t>> set;
+  std::lock_guard<std::mutex> lk(mu);
+  const void* f = kernel_ptr<T>(kb);
+  for (auto& e : set)
+    if (e.first == f) {
+      if (e.second >= smem) return FTGCR_OK;
+      CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      e.second = smem;
+      return FTGCR_OK;
+    }
+  CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  set.emplace_back(f, smem);
   return FTGCR_OK;
 }
 
 template <typename T>
-int occupancy(size_t smem, int* occ) {
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_ftgcr_persistent<T>, kThreads, smem));
+int occupancy(int kb, size_t smem, int* occ) {
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kernel_ptr<T>(kb), kThreads, smem));
   return FTGCR_OK;
 }
 
@@ -353,7 +393,9 @@ size_t layout(ftgcr_handle* h, unsigned char* base, SolveDev<T>* sd) {
     return p;
   };
   const size_t vT = sizeof(T) * N, v64 = sizeof(double) * N;
-  const size_t lcn = (h->precond == FTGCR_PRECOND_LINE) ? (size_t)nlat * 32 * C
+  const bool fp64 = std::is_same<T, double>::value;
+  // preconditioner arrays: FP64 natural [N] (+ u), FP32 chunk layout [nlat][32 C]
+  const size_t lcn = (h->precond == FTGCR_PRECOND_LINE) ? (fp64 ? (size_t)N : (size_t)nlat * 32 * C)
                                                         : (h->precond == FTGCR_PRECOND_JACOBI ? (size_t)N : 1);
   h->Tx64 = (double*)take(v64);
   h->Ty64 = (double*)take(v64);
@@ -364,6 +406,7 @@ size_t layout(ftgcr_handle* h, unsigned char* base, SolveDev<T>* sd) {
   sd->lc = (const T*)take(sizeof(T) * lcn);
   sd->lw = (const T*)take(sizeof(T) * lcn);
   sd->lz = (const T*)take(sizeof(T) * lcn);
+  sd->lu = (const T*)(fp64 && h->precond == FTGCR_PRECOND_LINE ? take(sizeof(T) * lcn) : nullptr);
   sd->lrow = (const T*)take(sizeof(T) * 4 * nlat);
   size_t before = off;
   for (int q = 0; q < 3; ++q) sd->phi[q] = (T*)take(vT);
@@ -381,7 +424,7 @@ size_t layout(ftgcr_handle* h, unsigned char* base, SolveDev<T>* sd) {
   sd->xbuf[1] = (double*)(std::is_same<T, float>::value ? take(v64) : nullptr);
   h->stageR = (double*)take(v64);
   h->stageX = (double*)take(v64);
-  sd->part = (double*)take(sizeof(double) * 2 * h->nt * kNPart);
+  sd->part = (double*)take(sizeof(double) * 2 * h->nt * kPartStride);  // [2 parities][nt][kNPart pairs]
   sd->st = (SolveState*)take(sizeof(SolveState) * 2);
   sd->result = (SolveState*)take(sizeof(SolveState));
   sd->faults = (const Fault*)take(sizeof(Fault) * kMaxFaults);
@@ -390,6 +433,7 @@ size_t layout(ftgcr_handle* h, unsigned char* base, SolveDev<T>* sd) {
   h->sdev_arr = (void**)take(sizeof(void*));
   h->nt_dev = (int*)take(sizeof(int));
   h->active = (int*)take(sizeof(int) * 2);
+  h->diag = (int*)take(sizeof(int) * 4 * 4096);
   h->ctl = (LaunchCtl*)take(sizeof(LaunchCtl));
   h->result = sd->result;
   return off;
@@ -410,6 +454,7 @@ int create_impl(ftgcr_handle* h, const double* D_host_or_dev, bool D_on_device) 
   sd.nlat = h->nlat;
   sd.k = h->k;
   sd.nt = h->nt;
+  sd.nt_hmax = (h->nlat + h->nt - 1) / h->nt;
   sd.C = h->C;
   sd.precond = h->precond;
   sd.mixed = std::is_same<T, float>::value ? 1 : 0;
@@ -426,7 +471,7 @@ int create_impl(ftgcr_handle* h, const double* D_host_or_dev, bool D_on_device) 
   // geometry (host) + face coefficients and factorisation (device)
   std::vector<double> cx, cy, area;
   row_geometry(h->nlon, h->nlat, cx, cy, area);
-  double *dcx = nullptr, *dD = nullptr, *work = nullptr;
+  double *dcx = nullptr, *dD = nullptr;
   CK(cudaMalloc(&dcx, sizeof(double) * 3 * h->nlat));
   CK(cudaMemcpy(dcx, cx.data(), sizeof(double) * h->nlat, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(dcx + h->nlat, cy.data(), sizeof(double) * h->nlat, cudaMemcpyHostToDevice));
@@ -442,27 +487,31 @@ int create_impl(ftgcr_handle* h, const double* D_host_or_dev, bool D_on_device) 
                                h->muA64, mixed ? (float*)sd.Tx : nullptr, mixed ? (float*)sd.Ty : nullptr,
                                mixed ? (float*)sd.muA : nullptr);
   CK(cudaGetLastError());
-  CK(cudaMalloc(&work, sizeof(double) * 3 * (size_t)h->N));
   {
-    double *lc = (double*)sd.lc, *lw = (double*)sd.lw, *lz = (double*)sd.lz, *lr = (double*)sd.lrow;
-    double* tmp = nullptr;
-    const size_t lcn = (h->precond == FTGCR_PRECOND_LINE) ? (size_t)h->nlat * 32 * h->C : (size_t)h->N;
-    if (mixed) {
-      CK(cudaMalloc(&tmp, sizeof(double) * (3 * lcn + 4 * h->nlat)));
-      lc = tmp;
-      lw = tmp + lcn;
-      lz = tmp + 2 * lcn;
-      lr = tmp + 3 * lcn;
+    // FP64 factors: into the handle (FP64 path) or scratch (mixed path)
+    double *l64 = nullptr, *w64 = nullptr, *u64 = nullptr, *z64 = nullptr, *r64 = nullptr, *tmp = nullptr;
+    if (!mixed) {
+      l64 = (double*)sd.lc;
+      w64 = (double*)sd.lw;
+      u64 = (double*)sd.lu;
+      z64 = (double*)sd.lz;
+      r64 = (double*)sd.lrow;
+    } else {
+      CK(cudaMalloc(&tmp, sizeof(double) * (4 * (size_t)h->N + 4 * h->nlat)));
+      l64 = tmp;
+      w64 = tmp + h->N;
+      u64 = tmp + 2 * h->N;
+      z64 = tmp + 3 * h->N;
+      r64 = tmp + 4 * h->N;
     }
-    k_line_factor<<<(h->nlat + 63) / 64, 64>>>(h->nlon, h->nlat, h->C, h->precond, h->Tx64, h->Ty64, h->muA64, work,
-                                               lc, lw, lz, lr, mixed ? (float*)sd.lc : nullptr,
+    k_line_factor<<<(h->nlat + 63) / 64, 64>>>(h->nlon, h->nlat, h->C, h->precond, h->Tx64, h->Ty64, h->muA64, l64,
+                                               w64, u64, z64, r64, mixed ? (float*)sd.lc : nullptr,
                                                mixed ? (float*)sd.lw : nullptr, mixed ? (float*)sd.lz : nullptr,
                                                mixed ? (float*)sd.lrow : nullptr);
     CK(cudaGetLastError());
     CK(cudaDeviceSynchronize());
     if (tmp) cudaFree(tmp);
   }
-  cudaFree(work);
   cudaFree(dcx);
   if (dD) cudaFree(dD);
 
@@ -475,13 +524,21 @@ int create_impl(ftgcr_handle* h, const double* D_host_or_dev, bool D_on_device) 
   else
     h->sd64 = sd;
 
-  h->smem = dyn_smem(h->nlon, h->nlat, h->nt, mixed, sizeof(T));
-  int rc = configure_kernel<T>(std::max<size_t>(h->smem, 1));
+  h->smem = dyn_smem(h->nlon, h->nlat, h->nt, mixed, sizeof(T), h->precond);
+  int rc = configure_kernel<T>(kbound(h->k), std::max<size_t>(h->smem, 1));
   if (rc) return rc;
   int occ = 0;
-  rc = occupancy<T>(h->smem, &occ);
+  rc = occupancy<T>(kbound(h->k), h->smem, &occ);
   if (rc) return rc;
   if (occ < 1) return FTGCR_ERR_ARG;
+  {
+    // the per-thread stack must hold the kernel's spill frame
+    cudaFuncAttributes fa;
+    CK(cudaFuncGetAttributes(&fa, kernel_ptr<T>(kbound(h->k))));
+    size_t cur = 0;
+    CK(cudaDeviceGetLimit(&cur, cudaLimitStackSize));
+    if (fa.localSizeBytes + 256 > cur) CK(cudaDeviceSetLimit(cudaLimitStackSize, fa.localSizeBytes + 256));
+  }
   const DeviceInfo di = device_info(h->dev);
   h->grid = std::min(h->nt, di.sms * occ);
   CK(cudaMallocHost(&h->h_result, sizeof(SolveState)));
@@ -489,9 +546,56 @@ int create_impl(ftgcr_handle* h, const double* D_host_or_dev, bool D_on_device) 
   return FTGCR_OK;
 }
 
+// Developer trace (FTGCR_TRACE=<csv path>): per-round timestamps of every
+// CTA of the next launches, written after each blocking solve.
+struct TraceBuf {
+  TraceEnt* d = nullptr;
+  int rounds = 0, grid = 0;
+  const char* path = nullptr;
+};
+TraceBuf& trace_buf() {
+  static TraceBuf t;
+  return t;
+}
+TraceEnt* trace_ptr(int grid, int* rounds) {
+  TraceBuf& t = trace_buf();
+  t.path = getenv("FTGCR_TRACE");
+  if (!t.path || !*t.path) return nullptr;
+  const int want = 4096;
+  if (!t.d || t.grid < grid) {
+    if (t.d) cudaFree(t.d);
+    if (cudaMalloc(&t.d, sizeof(TraceEnt) * (size_t)want * grid) != cudaSuccess) {
+      cudaGetLastError();
+      t.d = nullptr;
+      return nullptr;
+    }
+    t.rounds = want;
+    t.grid = grid;
+  }
+  cudaMemset(t.d, 0, sizeof(TraceEnt) * (size_t)t.rounds * t.grid);
+  *rounds = t.rounds;
+  return t.d;
+}
+void trace_dump(int grid) {
+  TraceBuf& t = trace_buf();
+  if (!t.d || !t.path || !*t.path) return;
+  std::vector<TraceEnt> h((size_t)t.rounds * t.grid);
+  cudaMemcpy(h.data(), t.d, h.size() * sizeof(TraceEnt), cudaMemcpyDeviceToHost);
+  FILE* f = fopen(t.path, "w");
+  if (!f) return;
+  fprintf(f, "round,cta,kind,items,t0,t1,t2,t3\n");
+  for (int r = 0; r < t.rounds; ++r)
+    for (int b = 0; b < grid; ++b) {
+      const TraceEnt& e = h[(size_t)r * t.grid + b];
+      if (e.t3 == 0) continue;
+      fprintf(f, "%d,%d,%d,%d,%llu,%llu,%llu,%llu\n", r, b, e.kind, e.items, e.t0, e.t1, e.t2, e.t3);
+    }
+  fclose(f);
+}
+
 template <typename T>
-int launch_persistent(SolveDev<T>* const* solves, const int* nt, int* active, int n, LaunchCtl* ctl, int max_rounds,
-                      int grid, size_t smem, cudaStream_t st) {
+int launch_persistent(int kb, SolveDev<T>* const* solves, const int* nt, int* active, int n, LaunchCtl* ctl,
+                      int* diag, int max_rounds, int grid, size_t smem, cudaStream_t st) {
   BatchArgs<T> a;
   a.solves = solves;
   a.nt = nt;
@@ -499,14 +603,15 @@ int launch_persistent(SolveDev<T>* const* solves, const int* nt, int* active, in
   a.n = n;
   a.ctl = ctl;
   a.max_rounds = max_rounds;
+  a.trace = trace_ptr(grid, &a.trace_rounds);
+  a.diag = diag;
   void* args[] = {&a};
-  CK(cudaLaunchCooperativeKernel(kernel_ptr<T>(), dim3(grid), dim3(kThreads), args, smem, st));
+  CK(cudaLaunchCooperativeKernel(kernel_ptr<T>(kb), dim3(grid), dim3(kThreads), args, smem, st));
   return FTGCR_OK;
 }
 
-template <typename T>
-int solve_async_impl(ftgcr_handle* h, const double* R, const double* x0, double* xout, const ftgcr_fault_plan* plan,
-                     cudaStream_t st) {
+BeginArgs begin_args(const ftgcr_handle* h, const double* R, const double* x0, double* xout,
+                     const ftgcr_fault_plan* plan) {
   BeginArgs b;
   memset(&b, 0, sizeof b);
   b.R = R;
@@ -515,12 +620,19 @@ int solve_async_impl(ftgcr_handle* h, const double* R, const double* x0, double*
   b.nfaults = plan ? plan->n : 0;
   b.max_steps = h->max_steps;
   for (int q = 0; q < b.nfaults; ++q) memcpy(&b.faults[q], &plan->faults[q], sizeof(Fault));
+  return b;
+}
+
+template <typename T>
+int solve_async_impl(ftgcr_handle* h, const double* R, const double* x0, double* xout, const ftgcr_fault_plan* plan,
+                     cudaStream_t st) {
+  const BeginArgs b = begin_args(h, R, x0, xout, plan);
   k_begin_solve<T><<<1, 64, 0, st>>>((SolveDev<T>*)h->sdev, b, h->active, 1, 0, 0, h->ctl);
   CK(cudaGetLastError());
   // every inner step takes two rounds, every refinement sweep a few more
   const int max_rounds = (int)std::min<long long>(1 << 30, 2 * h->max_steps + 8 * ((long long)h->max_outer + 2) + 16);
-  int rc = launch_persistent<T>((SolveDev<T>* const*)h->sdev_arr, h->nt_dev, h->active, 1, h->ctl, max_rounds, h->grid,
-                                h->smem, st);
+  int rc = launch_persistent<T>(kbound(h->k), (SolveDev<T>* const*)h->sdev_arr, h->nt_dev, h->active, 1, h->ctl,
+                                h->diag, max_rounds, h->grid, h->smem, st);
   if (rc) return rc;
   CK(cudaMemcpyAsync(h->h_result, h->result, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(LaunchCtl), cudaMemcpyDeviceToHost, st));
@@ -529,8 +641,89 @@ int solve_async_impl(ftgcr_handle* h, const double* R, const double* x0, double*
   return FTGCR_OK;
 }
 
+// Several independent solves in one persistent launch.  Each solve keeps its
+// own handle's tiling and reduction order, so its arithmetic is bitwise that
+// of a lone solve; the launch only interleaves the solves' tiles over the
+// CTAs.  The launch's own arrays (solve pointers, tile counts, active flags,
+// control block, progress record) are stream-ordered allocations freed after
+// the launch.
+template <typename T>
+int solve_batch_impl(ftgcr_handle* const* hs, const double* const* rhs, double* const* x,
+                     const ftgcr_fault_plan* const* plans, int n, cudaStream_t st) {
+  int kb = 4;
+  size_t smem = 1;
+  long long max_steps = 0, total_tiles = 0;
+  int max_outer = 0;
+  for (int i = 0; i < n; ++i) {
+    kb = std::max(kb, kbound(hs[i]->k));
+    smem = std::max(smem, hs[i]->smem);
+    max_steps = std::max(max_steps, hs[i]->max_steps);
+    max_outer = std::max(max_outer, hs[i]->max_outer);
+    total_tiles += hs[i]->nt;
+  }
+  int rc = configure_kernel<T>(kb, smem);
+  if (rc) return rc;
+  int occ = 0;
+  rc = occupancy<T>(kb, smem, &occ);
+  if (rc) return rc;
+  if (occ < 1) return FTGCR_ERR_ARG;
+  const DeviceInfo di = device_info(hs[0]->dev);
+  const int grid = (int)std::min<long long>(total_tiles, (long long)di.sms * occ);
+  const size_t b_solves = align256(sizeof(void*) * n), b_nt = align256(sizeof(int) * n),
+               b_act = align256(sizeof(int) * 2 * n), b_ctl = align256(sizeof(LaunchCtl)),
+               b_diag = align256(sizeof(int) * 4 * grid);
+  unsigned char* buf = nullptr;
+  CK(cudaMallocAsync((void**)&buf, b_solves + b_nt + b_act + b_ctl + b_diag, st));
+  void** d_solves = (void**)buf;
+  int* d_nt = (int*)(buf + b_solves);
+  int* d_act = (int*)(buf + b_solves + b_nt);
+  LaunchCtl* d_ctl = (LaunchCtl*)(buf + b_solves + b_nt + b_act);
+  int* d_diag = (int*)(buf + b_solves + b_nt + b_act + b_ctl);
+  std::vector<void*> hp(n);
+  std::vector<int> hnt(n);
+  for (int i = 0; i < n; ++i) {
+    hp[i] = hs[i]->sdev;
+    hnt[i] = hs[i]->nt;
+  }
+  CK(cudaMemcpyAsync(d_solves, hp.data(), sizeof(void*) * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_nt, hnt.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(d_act, 0, sizeof(int) * 2 * n, st));
+  for (int i = 0; i < n; ++i) {
+    const BeginArgs b = begin_args(hs[i], rhs[i], x[i], x[i], plans ? plans[i] : nullptr);
+    k_begin_solve<T><<<1, 64, 0, st>>>((SolveDev<T>*)hs[i]->sdev, b, d_act, n, i, 0, i == 0 ? d_ctl : nullptr);
+    CK(cudaGetLastError());
+  }
+  const int max_rounds = (int)std::min<long long>(1 << 30, 2 * max_steps + 8 * ((long long)max_outer + 2) + 16);
+  rc = launch_persistent<T>(kb, (SolveDev<T>* const*)d_solves, d_nt, d_act, n, d_ctl, d_diag, max_rounds, grid, smem,
+                            st);
+  if (rc) {
+    cudaFreeAsync(buf, st);
+    return rc;
+  }
+  for (int i = 0; i < n; ++i) {
+    CK(cudaMemcpyAsync(hs[i]->h_result, hs[i]->result, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hs[i]->h_ctl, d_ctl, sizeof(LaunchCtl), cudaMemcpyDeviceToHost, st));
+    hs[i]->last_stream = st;
+    hs[i]->solved = 1;
+  }
+  CK(cudaFreeAsync(buf, st));
+  return FTGCR_OK;
+}
+
+void report_timeout(const ftgcr_handle* h) {
+  std::vector<int> d((size_t)h->grid * 4);
+  if (cudaMemcpy(d.data(), h->diag, d.size() * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return;
+  fprintf(stderr, "ftgcr: grid barrier timeout (code %d); per-CTA round/kind/checkpoint/items:\n", h->h_ctl->err);
+  for (int b = 0; b < h->grid; ++b)
+    fprintf(stderr, "  cta %d: round %d kind %d checkpoint %d items %d\n", b, d[4 * b], d[4 * b + 1], d[4 * b + 2],
+            d[4 * b + 3]);
+}
+
 int status_from_result(const ftgcr_handle* h) {
-  if (h->h_ctl->err) return FTGCR_ERR_TIMEOUT;
+  if (h->h_ctl->err) {
+    report_timeout(h);
+    return FTGCR_ERR_TIMEOUT;
+  }
   const SolveState& S = *h->h_result;
   if (S.active) return FTGCR_ERR_CUDA;
   return S.status == ST_CONVERGED ? FTGCR_OK : FTGCR_NOT_CONVERGED;
@@ -583,7 +776,8 @@ static void fill_handle_params(ftgcr_handle* h, const ftgcr_grid* g, int32_t k, 
   h->max_outer = g->max_outer > 0 ? g->max_outer : 40;
   const bool mixed = g->precision == FTGCR_MIXED;
   const size_t elem = mixed ? sizeof(float) : sizeof(double);
-  h->nt = g->tiles > 0 ? std::min(g->tiles, g->nlat) : choose_tiles(g->nlon, g->nlat, mixed, elem, sms, smem_limit);
+  h->nt = g->tiles > 0 ? std::min(g->tiles, g->nlat)
+                       : choose_tiles(g->nlon, g->nlat, mixed, elem, g->precond, sms, smem_limit);
 }
 
 int ftgcr_create(const ftgcr_grid* grid, const ftgcr_coeffs* coeffs, int32_t k, double tol, ftgcr_handle** out) {
@@ -600,7 +794,7 @@ int ftgcr_create(const ftgcr_grid* grid, const ftgcr_coeffs* coeffs, int32_t k, 
   h->dev = dev;
   fill_handle_params(h, grid, k, tol, di.sms, smem_limit);
   const bool mixed = grid->precision == FTGCR_MIXED;
-  if (dyn_smem(h->nlon, h->nlat, h->nt, mixed, mixed ? 4 : 8) > (size_t)smem_limit) {
+  if (dyn_smem(h->nlon, h->nlat, h->nt, mixed, mixed ? 4 : 8, h->precond) > (size_t)smem_limit) {
     delete h;
     return FTGCR_ERR_ARG;  // a single latitude row does not fit on chip
   }
@@ -675,6 +869,7 @@ int ftgcr_solve(ftgcr_handle* h, const double* rhs, double* x, const ftgcr_fault
   if (!xdev) CK(cudaMemcpyAsync(x, h->stageX, sizeof(double) * h->N, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   h->last_status = status_from_result(h);
+  trace_dump(h->grid);
   return h->last_status;
 }
 
@@ -736,13 +931,18 @@ int ftgcr_apply_precond(ftgcr_handle* h, const double* in, double* out, void* st
 
 int ftgcr_solve_batch(ftgcr_handle* const* hs, const double* const* rhs, double* const* x,
                       const ftgcr_fault_plan* const* plans, int32_t n, void* stream) {
-  (void)hs;
-  (void)rhs;
-  (void)x;
-  (void)plans;
-  (void)n;
-  (void)stream;
-  return FTGCR_ERR_STATE;
+  if (!hs || !rhs || !x || n < 1 || n > kMaxBatch) return FTGCR_ERR_ARG;
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i] || !rhs[i] || !x[i] || hs[i]->precision != hs[0]->precision || hs[i]->dev != hs[0]->dev)
+      return FTGCR_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return FTGCR_ERR_ARG;  // one solve per handle per launch
+    const int rc = validate_plan(hs[i], plans ? plans[i] : nullptr);
+    if (rc) return rc;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  return hs[0]->precision == FTGCR_MIXED ? solve_batch_impl<float>(hs, rhs, x, plans, n, st)
+                                         : solve_batch_impl<double>(hs, rhs, x, plans, n, st);
 }
 
 void ftgcr_destroy(ftgcr_handle* h) {

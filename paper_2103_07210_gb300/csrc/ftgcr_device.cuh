@@ -7,6 +7,7 @@
 // explicit fma()/fmaf(); everything else is rounded operation by operation.
 #pragma once
 #include <cstdint>
+#include <cstring>
 #include <cuda_runtime.h>
 
 namespace ftgcr {
@@ -15,7 +16,8 @@ constexpr int kMaxK = 16;
 constexpr int kNSlot = kMaxK + 2;      // p / L(p) buffers
 constexpr int kMaxFaults = 64;
 constexpr int kMaxDetect = 16;
-constexpr int kNPart = kMaxK + 2;      // partial sums per tile
+constexpr int kNPart = kMaxK + 2;      // partial sums per tile (each a double-double pair)
+constexpr int kPartStride = 2 * kNPart;  // doubles per tile in the partials buffer
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;  // 2 s
@@ -61,6 +63,8 @@ struct SolveState {
   int finzero;  // FIN writes x = 0 (R = 0)
   int first_out;
   int stag;     // mixed: detections since the last accepted step
+  int out_redo; // mixed: this OUT recomputes r_out for the kept x (no test)
+  int out_rej;  // mixed: consecutive rejected refinement updates
   int status;
   double beta;
   double lpn2[kMaxK + 1];
@@ -75,6 +79,7 @@ struct SolveState {
 template <typename T>
 struct SolveDev {
   int nlon, nlat, k, nt, C, precond, mixed, nfaults;
+  int nt_hmax;  // rows of the tallest row tile
   long long N, max_steps;
   int max_outer;
   double tol2, inner_tol2;
@@ -82,11 +87,14 @@ struct SolveDev {
   const T* Tx;
   const T* Ty;
   const T* muA;   // [nlat]
-  // preconditioner: line solve constants permuted [nlat][C][32]; jacobi: 1/diag natural
+  // preconditioner.  FP32 path: line-solve constants c, 1/w, z permuted
+  // [nlat][C][32] (per-lane chunks).  FP64 path: the LU factors l, 1/w, u in
+  // natural layout [nlat][nlon] and z natural.  Jacobi: the diagonal, natural.
   const T* lc;
   const T* lw;
   const T* lz;
-  const T* lrow;  // [nlat][4]: 1/delta, Tx_{n-1}/delta, Tx_{n-2}/delta, 0
+  const T* lu;    // FP64 path: u_i = -Tx_i / w_i
+  const T* lrow;  // [nlat][4]: FP32 path 1/delta, Tx_{n-1}/delta, Tx_{n-2}/delta; FP64 path delta
   // Krylov vectors (inner precision)
   T* phi[3];
   T* r[3];
@@ -104,7 +112,7 @@ struct SolveDev {
   const double* x0; // user initial guess (device)
   double* xout;     // user solution (device)
   // bookkeeping
-  double* part;      // [2][nt][kNPart]
+  double* part;      // [2][nt][kNPart][2] double-double partial sums
   SolveState* st;    // [2]
   SolveState* result;  // final record (written once)
   const Fault* faults;
@@ -129,34 +137,98 @@ __device__ __forceinline__ float flip_bits(float v, int bit) {
 __device__ __forceinline__ double tfma(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float tfma(float a, float b, float c) { return fmaf(a, b, c); }
 
-// Inner-product accumulator.  FP64 vectors: one fma per element.  FP32
-// vectors: the product of two floats is formed exactly as a float pair
-// (TwoProd) and accumulated in a float-float pair (TwoSum); the pair is
-// promoted to FP64 once per thread, and all further reduction is FP64.
+// Double-double pair (unnormalised hi + lo), the carrier of every partial sum.
+struct DD {
+  double hi, lo;
+};
+// Sum of two pairs: TwoSum of the leading parts, trailing parts added.
+__device__ __forceinline__ DD dd_add(DD a, DD b) {
+  const double t = a.hi + b.hi;
+  const double z = t - a.hi;
+  const double q = (a.hi - (t - z)) + (b.hi - z);
+  return DD{t, (a.lo + b.lo) + q};
+}
+
+// Inner-product accumulators.  FP64 vectors: Dot2 (Ogita, Rump and Oishi):
+// exact products by fma (TwoProduct), running sum by TwoSum, low parts
+// collected; the same algorithm as the CPU oracle's inner product, so both
+// round (p + s) of nearly the same double-double value.  FP32 vectors: the
+// product of two floats is exact as a float pair (TwoProduct with fmaf) and is
+// accumulated in a float-float pair; warps combine float-float pairs in FP32
+// and only per-warp sums reach FP64 (GB300's FP64 pipe is ~60x slower than
+// FP32).
 template <typename T>
 struct Acc;
 template <>
 struct Acc<double> {
-  double s;
-  __device__ __forceinline__ Acc() : s(0.0) {}
-  __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
-  __device__ __forceinline__ double get() const { return s; }
+  double p, s;
+  __device__ __forceinline__ Acc() : p(0.0), s(0.0) {}
+  __device__ __forceinline__ void add(double a, double b) {
+    const double h = a * b;
+    const double r = fma(a, b, -h);
+    const double t = p + h;
+    const double z = t - p;
+    const double q = (p - (t - z)) + (h - z);
+    p = t;
+    s = s + (q + r);
+  }
+  // sum over the warp (xor butterfly, identical order in every warp)
+  __device__ __forceinline__ DD warp_sum() const {
+    DD v{p, s};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      DD w{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+      v = dd_add(v, w);
+    }
+    return v;
+  }
 };
 template <>
 struct Acc<float> {
   float hi, lo;
   __device__ __forceinline__ Acc() : hi(0.f), lo(0.f) {}
   __device__ __forceinline__ void add(float a, float b) {
-    float p = a * b;
-    float pe = fmaf(a, b, -p);
-    float s = hi + p;
-    float bb = s - hi;
-    float err = (hi - (s - bb)) + (p - bb);
+    const float p = a * b;
+    const float pe = fmaf(a, b, -p);
+    const float s = hi + p;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (p - bb);
     hi = s;
     lo = lo + (err + pe);
   }
-  __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
+  __device__ __forceinline__ DD warp_sum() const {
+    float h = hi, l = lo;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float h2 = __shfl_xor_sync(0xffffffffu, h, o);
+      const float l2 = __shfl_xor_sync(0xffffffffu, l, o);
+      const float t = h + h2;
+      const float z = t - h;
+      const float q = (h - (t - z)) + (h2 - z);
+      h = t;
+      l = (l + l2) + q;
+    }
+    return DD{(double)h, (double)l};
+  }
 };
+
+// Per-CTA partial sums: each warp contributes its DD sum of every value; the
+// CTA adds the warps' pairs in warp order and writes nv pairs to out.
+struct CtaRed {
+  DD w[kWarps][kNPart];
+};
+__device__ __forceinline__ void cta_red_put(CtaRed& cr, int v, DD x) {
+  if ((threadIdx.x & 31) == 0) cr.w[threadIdx.x >> 5][v] = x;
+}
+__device__ __forceinline__ void cta_red_finish(CtaRed& cr, int nv, double* out) {
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    DD s = cr.w[0][threadIdx.x];
+    for (int w = 1; w < kWarps; ++w) s = dd_add(s, cr.w[w][threadIdx.x]);
+    out[2 * threadIdx.x] = s.hi;
+    out[2 * threadIdx.x + 1] = s.lo;
+  }
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -164,22 +236,40 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Deterministic CTA reduction of nv per-thread values; the sums land in
-// out[0..nv-1] (global).  red_smem: kWarps * kNPart doubles.
-__device__ __forceinline__ void cta_reduce_store(const double* vals, int nv, double* red_smem, double* out) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int v = 0; v < nv; ++v) {
-    double s = warp_sum(vals[v]);
-    if (lane == 0) red_smem[warp * kNPart + v] = s;
-  }
-  __syncthreads();
-  if (threadIdx.x < nv) {
-    double s = 0.0;
-    for (int w = 0; w < kWarps; ++w) s += red_smem[w * kNPart + threadIdx.x];
-    out[threadIdx.x] = s;
-  }
-  __syncthreads();
+// 16-byte vector access (4 floats or 2 doubles), L2-coherent loads.
+template <typename T>
+struct V16 {
+  static constexpr int W = 16 / sizeof(T);
+  T v[W];
+};
+template <typename T>
+__device__ __forceinline__ V16<T> ldv(const T* p) {
+  const uint4 u = __ldcg(reinterpret_cast<const uint4*>(p));
+  V16<T> r;
+  memcpy(&r, &u, 16);
+  return r;
 }
+template <typename T>
+__device__ __forceinline__ V16<T> ldv_nc(const T* p) {
+  const uint4 u = __ldg(reinterpret_cast<const uint4*>(p));
+  V16<T> r;
+  memcpy(&r, &u, 16);
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ void stv(T* p, const V16<T>& x) {
+  uint4 u;
+  memcpy(&u, &x, 16);
+  *reinterpret_cast<uint4*>(p) = u;
+}
+
+// Asynchronous 16-byte global -> shared copies (cp.async, L2 only).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
   unsigned int v;
@@ -239,42 +329,73 @@ __host__ __device__ __forceinline__ int row_stride(int nlon) {
 }
 
 // ----------------------------------------------------------- line solve
+// Row-local line-solve constants in the per-lane chunk layout [k][lane]
+// (element i = lane*C + k): c_i = Tx_i / w_i, winv_i = 1 / w_i, z_i.  The
+// pointers may address shared memory (staged by the caller) or global memory.
+template <typename T>
+struct LineConsts {
+  const T* cb;
+  const T* cw;
+  const T* cz;
+};
+
+template <typename T>
+__device__ __forceinline__ LineConsts<T> line_consts_global(const SolveDev<T>& sd, int j) {
+  const long long o = (long long)j * 32 * sd.C;
+  return LineConsts<T>{sd.lc + o, sd.lw + o, sd.lz + o};
+}
+
+constexpr int kLB = 8;  // register block of the recurrences
+
 // Periodic tridiagonal solve of one latitude row, M e = -r (P = -M is the
 // zonal part of L plus the diagonal of the rest), in place in shared memory,
-// by one warp.  Leading (n-1) x (n-1) block by a precomputed LU factorisation
-// (c_i = Tx_i / w_i, winv_i = 1 / w_i), its two first-order recurrences run
-// as 32 contiguous per-lane chunks joined by warp scans of affine maps; the
-// periodic coupling of the last unknown by bordering with the precomputed
+// by one warp.  The leading (n-1) x (n-1) block uses its precomputed LU
+// factorisation: forward g_i = b_i + c_{i-1} g_{i-1} (b = -r), backward
+// y_i = winv_i g_i + c_i y_{i+1}.  Each recurrence runs over 32 contiguous
+// per-lane chunks: a read-only pass forms each chunk's affine map, a warp
+// scan composes the maps into each chunk's carry-in, and a second pass
+// replays the chunk from its exact carry-in.  The periodic coupling of the
+// last unknown is eliminated by bordering with the precomputed
 // z = A0^-1 (-Tx_{n-1} e_0 - Tx_{n-2} e_{n-2}).
 template <typename T>
-__device__ void line_solve_row(const SolveDev<T>& sd, int j, T* row) {
+__device__ void line_solve_row(const SolveDev<T>& sd, int j, T* row, const LineConsts<T> lc) {
   const int lane = threadIdx.x & 31;
   const int n = sd.nlon, m = n - 1, C = sd.C;
-  const T* cb = sd.lc + (long long)j * 32 * C;
-  const T* cw = sd.lw + (long long)j * 32 * C;
-  const T* cz = sd.lz + (long long)j * 32 * C;
   const int i0 = lane * C;
   int len = m - i0;
   len = len < 0 ? 0 : (len > C ? C : len);
 
-  // forward: g_i = b_i + c_{i-1} g_{i-1}, b = -r
-  T mylast = (len > 0) ? __ldg(cb + (len - 1) * 32 + lane) : T(0);
-  T a = __shfl_up_sync(0xffffffffu, mylast, 1);
-  if (lane == 0) a = T(0);
-  const T a0 = a;
-  T g = T(0), F = T(1);
-  for (int k = 0; k < len; ++k) {
-    const int s = sk(i0 + k);
-    g = tfma(a, g, -row[s]);
-    F = F * a;
-    row[s] = g;
-    a = __ldg(cb + k * 32 + lane);
+  // forward multiplier of chunk element 0 is c_{i0-1}, the last c of the previous lane
+  const T mylast = (len > 0) ? lc.cb[(len - 1) * 32 + lane] : T(0);
+  T a0 = __shfl_up_sync(0xffffffffu, mylast, 1);
+  if (lane == 0) a0 = T(0);
+
+  // pass 1: affine map g_out = F g_in + G of the chunk
+  T F = T(1), G = T(0);
+  {
+    T a = a0;
+    for (int kb = 0; kb < len; kb += kLB) {
+      T rv[kLB], cv[kLB];
+#pragma unroll
+      for (int q = 0; q < kLB; ++q)
+        if (kb + q < len) {
+          rv[q] = row[sk(i0 + kb + q)];
+          cv[q] = lc.cb[(kb + q) * 32 + lane];
+        }
+#pragma unroll
+      for (int q = 0; q < kLB; ++q)
+        if (kb + q < len) {
+          G = tfma(a, G, -rv[q]);
+          F = F * a;
+          a = cv[q];
+        }
+    }
   }
-  T Fs = F, Gs = g;
+  T Fs = F, Gs = G;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
-    T Fo = __shfl_up_sync(0xffffffffu, Fs, d);
-    T Go = __shfl_up_sync(0xffffffffu, Gs, d);
+    const T Fo = __shfl_up_sync(0xffffffffu, Fs, d);
+    const T Go = __shfl_up_sync(0xffffffffu, Gs, d);
     if (lane >= d) {
       Gs = tfma(Fs, Go, Gs);
       Fs = Fs * Fo;
@@ -282,30 +403,53 @@ __device__ void line_solve_row(const SolveDev<T>& sd, int j, T* row) {
   }
   T carry = __shfl_up_sync(0xffffffffu, Gs, 1);
   if (lane == 0) carry = T(0);
+  // pass 2: g from the exact carry-in
   {
-    T P = T(1);
-    a = a0;
-    for (int k = 0; k < len; ++k) {
-      const int s = sk(i0 + k);
-      P = P * a;
-      row[s] = tfma(P, carry, row[s]);
-      a = __ldg(cb + k * 32 + lane);
+    T a = a0, g = carry;
+    for (int kb = 0; kb < len; kb += kLB) {
+      T rv[kLB], cv[kLB];
+#pragma unroll
+      for (int q = 0; q < kLB; ++q)
+        if (kb + q < len) {
+          rv[q] = row[sk(i0 + kb + q)];
+          cv[q] = lc.cb[(kb + q) * 32 + lane];
+        }
+#pragma unroll
+      for (int q = 0; q < kLB; ++q)
+        if (kb + q < len) {
+          g = tfma(a, g, -rv[q]);
+          rv[q] = g;
+          a = cv[q];
+        }
+#pragma unroll
+      for (int q = 0; q < kLB; ++q)
+        if (kb + q < len) row[sk(i0 + kb + q)] = rv[q];
     }
   }
-  // backward: y_i = winv_i g_i + c_i y_{i+1}  (c_{m-1} stored as 0)
-  T y = T(0), Fb = T(1);
-  for (int k = len - 1; k >= 0; --k) {
-    const int s = sk(i0 + k);
-    const T cc = __ldg(cb + k * 32 + lane);
-    y = tfma(cc, y, row[s] * __ldg(cw + k * 32 + lane));
-    Fb = Fb * cc;
-    row[s] = y;
+  // pass 3: affine map of the backward recurrence y_in = Fb y_out + Y
+  const int kb_last = len > 0 ? ((len - 1) / kLB) * kLB : -1;
+  T Fb = T(1), Y = T(0);
+  for (int kb = kb_last; kb >= 0; kb -= kLB) {
+    T gv[kLB], cv[kLB], wv[kLB];
+#pragma unroll
+    for (int q = 0; q < kLB; ++q)
+      if (kb + q < len) {
+        gv[q] = row[sk(i0 + kb + q)];
+        cv[q] = lc.cb[(kb + q) * 32 + lane];
+        wv[q] = lc.cw[(kb + q) * 32 + lane];
+      }
+#pragma unroll
+    for (int q = kLB - 1; q >= 0; --q)
+      if (kb + q < len) {
+        Y = tfma(cv[q], Y, gv[q] * wv[q]);
+        Fb = Fb * cv[q];
+      }
   }
-  T Fr = Fb, Yr = y;
+  T Fr = Fb, Yr = Y;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
-    T Fo = __shfl_down_sync(0xffffffffu, Fr, d);
-    T Yo = __shfl_down_sync(0xffffffffu, Yr, d);
+    const T Fo = __shfl_down_sync(0xffffffffu, Fr, d);
+    const T Yo = __shfl_down_sync(0xffffffffu, Yr, d);
     if (lane + d < 32) {
       Yr = tfma(Fr, Yo, Yr);
       Fr = Fr * Fo;
@@ -313,12 +457,27 @@ __device__ void line_solve_row(const SolveDev<T>& sd, int j, T* row) {
   }
   T carryb = __shfl_down_sync(0xffffffffu, Yr, 1);
   if (lane == 31) carryb = T(0);
+  // pass 4: y from the exact carry-in
   {
-    T P = T(1);
-    for (int k = len - 1; k >= 0; --k) {
-      const int s = sk(i0 + k);
-      P = P * __ldg(cb + k * 32 + lane);
-      row[s] = tfma(P, carryb, row[s]);
+    T y = carryb;
+    for (int kb = kb_last; kb >= 0; kb -= kLB) {
+      T gv[kLB], cv[kLB], wv[kLB];
+#pragma unroll
+      for (int q = 0; q < kLB; ++q)
+        if (kb + q < len) {
+          gv[q] = row[sk(i0 + kb + q)];
+          cv[q] = lc.cb[(kb + q) * 32 + lane];
+          wv[q] = lc.cw[(kb + q) * 32 + lane];
+        }
+#pragma unroll
+      for (int q = kLB - 1; q >= 0; --q)
+        if (kb + q < len) {
+          y = tfma(cv[q], y, gv[q] * wv[q]);
+          gv[q] = y;
+        }
+#pragma unroll
+      for (int q = 0; q < kLB; ++q)
+        if (kb + q < len) row[sk(i0 + kb + q)] = gv[q];
     }
   }
   __syncwarp();
@@ -331,29 +490,114 @@ __device__ void line_solve_row(const SolveDev<T>& sd, int j, T* row) {
   __syncwarp();
   for (int k = 0; k < len; ++k) {
     const int s = sk(i0 + k);
-    row[s] = tfma(-xl, __ldg(cz + k * 32 + lane), row[s]);
+    row[s] = tfma(-xl, lc.cz[k * 32 + lane], row[s]);
   }
   if (lane == 0) row[sk(n - 1)] = xl;
   __syncwarp();
 }
 
-// Pointwise preconditioners on a shared-memory row (one warp).
+// FP64 path: the row's periodic tridiagonal solve by ONE thread, operation for
+// operation the CPU oracle's Thomas substitution: forward y_0 = b_0,
+// y_i = fma(-l_i, y_{i-1}, b_i); backward y_{m-1} = y_{m-1} winv_{m-1},
+// y_i = fma(-u_i, y_{i+1}, y_i winv_i); bordering x_{n-1} = (b_{n-1} +
+// Tx_{n-1} y_0 + Tx_{n-2} y_{m-1}) / delta, x_i = y_i - x_{n-1} z_i; b = -r.
+// Bitwise reproducible against the oracle.  l, winv, u: the row's factors in
+// natural layout (shared or global memory).
+__device__ inline void line_solve_row_seq(const SolveDev<double>& sd, int j, double* row, const double* l,
+                                   const double* winv, const double* u) {
+  const int n = sd.nlon, m = n - 1;
+  double y = -row[sk(0)];
+  row[sk(0)] = y;
+  for (int i0 = 1; i0 < m; i0 += kLB) {
+    double bv[kLB], lv[kLB];
+#pragma unroll
+    for (int q = 0; q < kLB; ++q)
+      if (i0 + q < m) {
+        bv[q] = -row[sk(i0 + q)];
+        lv[q] = l[i0 + q];
+      }
+#pragma unroll
+    for (int q = 0; q < kLB; ++q)
+      if (i0 + q < m) {
+        y = fma(-lv[q], y, bv[q]);
+        bv[q] = y;
+      }
+#pragma unroll
+    for (int q = 0; q < kLB; ++q)
+      if (i0 + q < m) row[sk(i0 + q)] = bv[q];
+  }
+  y = row[sk(m - 1)] * winv[m - 1];
+  row[sk(m - 1)] = y;
+  for (int i1 = m - 2; i1 >= 0; i1 -= kLB) {  // block [i1 - kLB + 1, i1], descending
+    double gv[kLB], wv[kLB], uv[kLB];
+#pragma unroll
+    for (int q = 0; q < kLB; ++q)
+      if (i1 - q >= 0) {
+        gv[q] = row[sk(i1 - q)];
+        wv[q] = winv[i1 - q];
+        uv[q] = u[i1 - q];
+      }
+#pragma unroll
+    for (int q = 0; q < kLB; ++q)
+      if (i1 - q >= 0) {
+        y = fma(-uv[q], y, gv[q] * wv[q]);
+        gv[q] = y;
+      }
+#pragma unroll
+    for (int q = 0; q < kLB; ++q)
+      if (i1 - q >= 0) row[sk(i1 - q)] = gv[q];
+  }
+  const double* tx = sd.Tx + (long long)j * n;
+  const double* z = sd.lz + (long long)j * n;
+  const double num = -row[sk(n - 1)] + __ldg(tx + n - 1) * row[sk(0)] + __ldg(tx + n - 2) * row[sk(m - 1)];
+  const double xl = num / __ldg(sd.lrow + (long long)j * 4);
+  for (int i = 0; i < m; ++i) row[sk(i)] = row[sk(i)] - xl * __ldg(z + i);
+  row[sk(n - 1)] = xl;
+}
+
+// Pointwise preconditioners on a shared-memory row (one warp).  Jacobi:
+// e = -r / d (FP64 path: division, as the oracle) or -r (1/d) (FP32 path).
 template <typename T>
 __device__ void pointwise_precond_row(const SolveDev<T>& sd, int j, T* row) {
   const int lane = threadIdx.x & 31;
   if (sd.precond == PC_JACOBI) {
-    const T* dinv = sd.lw + (long long)j * sd.nlon;
-    for (int i = lane; i < sd.nlon; i += 32) row[sk(i)] = -row[sk(i)] * __ldg(dinv + i);
+    const T* dg = sd.lw + (long long)j * sd.nlon;
+    for (int i = lane; i < sd.nlon; i += 32) {
+      if constexpr (sizeof(T) == 8)
+        row[sk(i)] = -row[sk(i)] / __ldg(dg + i);
+      else
+        row[sk(i)] = -row[sk(i)] * __ldg(dg + i);
+    }
   }
   __syncwarp();
 }
 
+// Preconditioner solve of one row by one warp.  FP32: the chunked warp
+// solve; FP64: lane 0 runs the oracle-identical sequential solve.
 template <typename T>
-__device__ __forceinline__ void precond_row(const SolveDev<T>& sd, int j, T* row) {
-  if (sd.precond == PC_LINE)
-    line_solve_row(sd, j, row);
-  else
+__device__ __forceinline__ void precond_row(const SolveDev<T>& sd, int j, T* row, const LineConsts<T> lc) {
+  if (sd.precond == PC_LINE) {
+    if constexpr (sizeof(T) == 8) {
+      if ((threadIdx.x & 31) == 0) line_solve_row_seq(sd, j, row, lc.cb, lc.cw, lc.cz);
+      __syncwarp();
+    } else {
+      line_solve_row(sd, j, row, lc);
+    }
+  } else {
     pointwise_precond_row(sd, j, row);
+  }
+}
+
+// Global-memory line-solve constants of row j (FP32: chunk layout c, 1/w, z;
+// FP64: natural-layout factors l, 1/w, u).
+template <typename T>
+__device__ __forceinline__ LineConsts<T> row_consts_global(const SolveDev<T>& sd, int j) {
+  if constexpr (sizeof(T) == 8) {
+    const long long o = (long long)j * sd.nlon;
+    return LineConsts<T>{sd.lc + o, sd.lw + o, sd.lu + o};
+  } else {
+    return line_consts_global(sd, j);
+  }
 }
 
 // Tile geometry: tile tau of nt covers rows [row_start(tau), row_start(tau+1))

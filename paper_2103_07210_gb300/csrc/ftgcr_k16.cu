@@ -1,0 +1,9 @@
+// Persistent FT-GCR kernel instances for at most 16 Krylov directions.
+#include "ftgcr_instances.h"
+#include "ftgcr_phases.cuh"
+
+namespace ftgcr {
+const void* persistent_kernel_k16(bool fp64) {
+  return fp64 ? (const void*)k_ftgcr_persistent<double, 16> : (const void*)k_ftgcr_persistent<float, 16>;
+}
+}  // namespace ftgcr

@@ -1,0 +1,9 @@
+// Persistent FT-GCR kernel instances for at most 4 Krylov directions.
+#include "ftgcr_instances.h"
+#include "ftgcr_phases.cuh"
+
+namespace ftgcr {
+const void* persistent_kernel_k4(bool fp64) {
+  return fp64 ? (const void*)k_ftgcr_persistent<double, 4> : (const void*)k_ftgcr_persistent<float, 4>;
+}
+}  // namespace ftgcr

@@ -62,6 +62,14 @@ struct LaunchCtl {
   long long round_end;
 };
 
+// Optional per-round trace: for every (round, CTA) the global timer at the
+// round start, after the state transitions, after the phase work and after
+// the grid barrier, plus the phase kind of the CTA's first item.
+struct TraceEnt {
+  unsigned long long t0, t1, t2, t3;
+  int kind, items;
+};
+
 template <typename T>
 struct BatchArgs {
   SolveDev<T>* const* solves;  // [n]
@@ -70,6 +78,9 @@ struct BatchArgs {
   int n;
   LaunchCtl* ctl;
   int max_rounds;
+  TraceEnt* trace;             // [trace_rounds][gridDim] or null
+  int trace_rounds;
+  int* diag;                   // [gridDim][4]: round, phase kind, checkpoint, items (failure report)
 };
 
 // ------------------------------------------------------------ flips
@@ -122,16 +133,46 @@ __device__ __forceinline__ int count_faults(const SolveDev<T>& sd, long long ste
 constexpr unsigned kStateVecs = (1u << V_X) | (1u << V_R) | (1u << V_P) | (1u << V_AP);
 
 // ------------------------------------------------------------ reductions
-// Deterministic sum of value v over the nt tiles of the partials buffer, by
-// warp 0; every CTA that works on the solve gets the identical result.
+// Deterministic sum over the nt tiles of the partials buffer of the first nv
+// values.  Warp v sums value v: lanes take tiles lane, lane+32, ... (all loads
+// issued first), add them in tile order, then a fixed xor tree.  FP64 path:
+// double-double arithmetic throughout, rounded once; FP32 path: plain FP64
+// (per-tile values are already accurate sums).  Every CTA that works on the
+// solve gets bitwise the same numbers.
+template <typename T>
 __device__ __forceinline__ void reduce_partials(const double* part, int nt, int nv, double* red) {
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    for (int v = 0; v < nv; ++v) {
-      double s = 0.0;
-      for (int tau = lane; tau < nt; tau += 32) s += __ldcg(part + (long long)tau * kNPart + v);
-      s = warp_sum(s);
-      if (lane == 0) red[v] = s;
+  constexpr int B = 4;  // tiles loaded per batch per lane
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int v = warp; v < nv; v += kWarps) {
+    DD acc{0.0, 0.0};
+    double acc1 = 0.0;
+    for (int t0 = lane; t0 < nt; t0 += 32 * B) {
+      double hv[B], lv[B];
+#pragma unroll
+      for (int q = 0; q < B; ++q) {
+        const int tau = t0 + 32 * q;
+        if (tau < nt) {
+          hv[q] = __ldcg(part + (long long)tau * kPartStride + 2 * v);
+          lv[q] = __ldcg(part + (long long)tau * kPartStride + 2 * v + 1);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < B; ++q)
+        if (t0 + 32 * q < nt) {
+          if constexpr (sizeof(T) == 8)
+            acc = dd_add(acc, DD{hv[q], lv[q]});
+          else
+            acc1 += hv[q] + lv[q];
+        }
+    }
+    if constexpr (sizeof(T) == 8) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+        acc = dd_add(acc, DD{__shfl_xor_sync(0xffffffffu, acc.hi, o), __shfl_xor_sync(0xffffffffu, acc.lo, o)});
+      if (lane == 0) red[v] = acc.hi + acc.lo;
+    } else {
+      acc1 = warp_sum(acc1);
+      if (lane == 0) red[v] = acc1;
     }
   }
 }
@@ -170,14 +211,10 @@ __device__ __forceinline__ int part_count(int kind, int nu) {
 // The per-solve state machine: consumes the reduced partial sums of the phase
 // that ran last round (S.pending) and decides this round's phase.  Thread 0.
 template <typename T>
-__device__ void transition(const SolveDev<T>& sd, const SolveState& S, const double* red, SolveState& N, Ctx<T>& c) {
+__device__ __noinline__ void transition(const SolveDev<T>& sd, const SolveState& S, const double* red, SolveState& N, Ctx<T>& c) {
   N = S;
+  memset(&c, 0, sizeof c);  // every pointer a phase may test starts out null
   c.kind = K_NONE;
-  c.zero_guess = 0;
-  c.xsrc_user = 0;
-  c.finzero = 0;
-  c.first = 0;
-  c.patched = 0;
   c.nu = S.nu;
   c.t = S.step + 1;
   c.patch_step = S.step + 1;
@@ -196,16 +233,47 @@ __device__ void transition(const SolveDev<T>& sd, const SolveState& S, const dou
       }
       break;
     case K_OUT: {
+      // mixed refinement: x' = x + d was formed, r_out = R - L64(x') reduced.
+      // The paper's monotonicity test, applied to the FP64 outer residual,
+      // rejects an update d that did not lower it (a flip in x or p of the
+      // inner solve is invisible to the inner test but not to this one).
       const double nrm2_out = red[0];
+      bool accept = true;
       if (S.first_out) {
         N.nrm2_R = red[1];
         N.thr2 = sd.tol2 * N.nrm2_R;
         N.first_out = 0;
         N.nrm2_0 = nrm2_out;
+      } else if (!S.out_redo && !(nrm2_out < S.nrm2_out)) {
+        accept = false;
       }
+      N.outer = S.outer + 1;
+      N.out_redo = 0;
+      if (!accept) {
+        N.fdet = S.fdet + 1;
+        N.restarts = S.restarts + 1;
+        if (S.ndetect < kMaxDetect) {
+          N.detect_step[S.ndetect] = S.step;
+          N.detect_ratio[S.ndetect] = nrm2_out / S.nrm2_out;
+          N.ndetect = S.ndetect + 1;
+        }
+        N.out_rej = S.out_rej + 1;
+        if (N.out_rej >= 3 || N.outer > sd.max_outer) {
+          N.status = S.nrm2_out <= N.thr2 ? ST_CONVERGED : ST_NOT_CONVERGED;
+          to_fin = true;
+        } else {
+          // recompute R_in and r_out for the kept x, then redo the inner solve
+          N.out_redo = 1;
+          c.kind = K_OUT;
+          c.d = nullptr;
+          c.xsrc = sd.xbuf[S.xcur];
+          c.xdst = sd.xbuf[S.xcur ^ 1];
+        }
+        break;
+      }
+      N.out_rej = 0;
       N.xcur = S.xcur ^ 1;
       N.nrm2_out = nrm2_out;
-      N.outer = S.outer + 1;
       if (N.nrm2_R == 0.0) {
         N.status = ST_CONVERGED;
         to_fin = true;
@@ -438,7 +506,7 @@ __device__ void transition(const SolveDev<T>& sd, const SolveState& S, const dou
     c.rW = sd.r[N.rC];
     c.pnew = sd.p[N.slot[0]];
     c.lpnew = sd.Lp[N.slot[0]];
-  } else if (c.kind == K_OUT) {
+  } else if (c.kind == K_OUT && !N.out_redo) {
     c.xsrc = c.xsrc_user ? sd.x0 : sd.xbuf[S.xcur];
     c.xdst = sd.xbuf[S.xcur ^ 1];
   } else if (c.kind == K_FIN) {
@@ -449,13 +517,64 @@ __device__ void transition(const SolveDev<T>& sd, const SolveState& S, const dou
 }
 
 // ------------------------------------------------------------ phases
-template <typename T>
 struct PhaseSmem {
   FlipEnt fl[kMaxFaults];
   FlipEnt pt[kMaxFaults];
   int nfl, npt;
-  double red[kWarps * kNPart];
+  CtaRed cr;
 };
+
+// Line-solve constants of rows [h0, h1) staged into shared memory by
+// asynchronous 16-byte copies (cp.async; waited for before the solves): three
+// arrays, rows contiguous.  FP32 path: chunk layout c, 1/w, z (32 C per row);
+// FP64 path: natural-layout factors l, 1/w, u (nlon per row).
+template <typename T>
+__device__ __forceinline__ long long consts_per_row(const SolveDev<T>& sd) {
+  if constexpr (sizeof(T) == 8)
+    return sd.nlon;
+  else
+    return 32LL * sd.C;
+}
+template <typename T>
+__device__ __forceinline__ void stage_line_consts(const SolveDev<T>& sd, int h0, int h1, T* cs) {
+  if (sd.precond != PC_LINE) return;
+  const long long per = consts_per_row(sd);
+  const int nrows = h1 - h0;
+  const long long nel = (long long)nrows * per;
+  const T* src[3];
+  if constexpr (sizeof(T) == 8) {
+    src[0] = sd.lc;
+    src[1] = sd.lw;
+    src[2] = sd.lu;
+  } else {
+    src[0] = sd.lc;
+    src[1] = sd.lw;
+    src[2] = sd.lz;
+  }
+  constexpr int W = V16<T>::W;
+  if ((per % W) == 0) {
+    const long long nv = nel / W;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const T* g = src[a] + (long long)h0 * per;
+      T* d = cs + (long long)a * nel;
+      for (long long q = threadIdx.x; q < nv; q += kThreads) cp_async16(d + q * W, g + q * W);
+    }
+    cp_async_commit();
+  } else {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const T* g = src[a] + (long long)h0 * per;
+      T* d = cs + (long long)a * nel;
+      for (long long q = threadIdx.x; q < nel; q += kThreads) d[q] = __ldg(g + q);
+    }
+  }
+}
+template <typename T>
+__device__ __forceinline__ LineConsts<T> staged_consts(const SolveDev<T>& sd, const T* cs, int nrows, int r) {
+  const long long per = consts_per_row(sd);
+  return LineConsts<T>{cs + (long long)r * per, cs + ((long long)nrows + r) * per, cs + (2LL * nrows + r) * per};
+}
 
 // Row-tile halo rows: [h0, h1) = [j0-1, j1+1) clipped to the sphere.
 struct RowTile {
@@ -504,36 +623,103 @@ __device__ __forceinline__ V stencil_global(const V* x, const V* Tx, const V* Ty
                      __ldg(muA + j), hasN, hasS);
 }
 
-// PA: axpy, norm, preconditioner, operator, orthogonalisation dots.
-template <typename T>
-__device__ void phase_pa(const SolveDev<T>& sd, const Ctx<T>& c, int tau, T* sm, PhaseSmem<T>& ps, double* part_out) {
-  const int nlon = sd.nlon, stride = row_stride(nlon);
-  const RowTile rt = row_tile(sd.nlat, sd.nt, tau);
+// Element (j, i) of a row-tile loop over 16-byte vectors: flat index ->
+// (row, first column).
+struct RowVec {
+  int j, i;
+  long long g;
+};
+__device__ __forceinline__ RowVec row_vec(int idx, int nvr, int j0, int nlon, int W) {
+  RowVec r;
+  const int jr = idx / nvr;
+  r.j = j0 + jr;
+  r.i = (idx - jr * nvr) * W;
+  r.g = (long long)r.j * nlon + r.i;
+  return r;
+}
+
+// PA: axpy, norm, preconditioner, operator, orthogonalisation dots.  KB is a
+// compile-time bound on the number of directions (k <= KB).
+template <typename T, int KB>
+__device__ __forceinline__ void phase_pa(const SolveDev<T>& sd, const Ctx<T>& c, int tau, T* sm, PhaseSmem& ps, double* part_out) {
+  constexpr int W = V16<T>::W;
+  constexpr int U = 2;
+  const int nlon = sd.nlon, nlat = sd.nlat, stride = row_stride(nlon);
+  const RowTile rt = row_tile(nlat, sd.nt, tau);
+  const int nrows = rt.h1 - rt.h0;
   const int warp = threadIdx.x >> 5;
   const T beta = c.beta;
+  T* cs = sm + (long long)(sd.nt_hmax + 2) * stride;
+  stage_line_consts(sd, rt.h0, rt.h1, cs);
+  if (threadIdx.x == 0)
+    ps.nfl = collect_flips(sd, c.t, 1u << V_E, (long long)rt.h0 * nlon, (long long)rt.h1 * nlon, ps.fl);
   Acc<T> an;
-  for (int j = rt.h0; j < rt.h1; ++j) {
-    const bool own = (j >= rt.j0 && j < rt.j1);
-    T* row = sm + (j - rt.h0) * stride;
-    const long long base = (long long)j * nlon;
-    for (int i = threadIdx.x; i < nlon; i += kThreads) {
-      const long long g = base + i;
-      const T rv = tfma(beta, ldcg(c.lpnu + g), ldcg(c.rC + g));
-      row[sk(i)] = rv;
-      if (own) {
-        c.rW[g] = rv;
-        c.phiW[g] = tfma(beta, ldcg(c.pnu + g), ldcg(c.phiC + g));
-        an.add(rv, rv);
+  if (nlon % W == 0) {
+    const int nvr = nlon / W, total = nrows * nvr;
+    for (int b0 = threadIdx.x; b0 < total; b0 += U * kThreads) {
+      V16<T> lp[U], rr[U], pv[U], ph[U];
+      RowVec rv[U];
+      bool ok[U], own[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = b0 + u * kThreads;
+        ok[u] = idx < total;
+        if (ok[u]) {
+          rv[u] = row_vec(idx, nvr, rt.h0, nlon, W);
+          own[u] = rv[u].j >= rt.j0 && rv[u].j < rt.j1;
+          lp[u] = ldv(c.lpnu + rv[u].g);
+          rr[u] = ldv(c.rC + rv[u].g);
+          if (own[u]) {
+            pv[u] = ldv(c.pnu + rv[u].g);
+            ph[u] = ldv(c.phiC + rv[u].g);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (!ok[u]) continue;
+        V16<T> rn, fn;
+        T* row = sm + (rv[u].j - rt.h0) * stride;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+          rn.v[w] = tfma(beta, lp[u].v[w], rr[u].v[w]);
+          row[sk(rv[u].i + w)] = rn.v[w];
+        }
+        if (own[u]) {
+#pragma unroll
+          for (int w = 0; w < W; ++w) {
+            fn.v[w] = tfma(beta, pv[u].v[w], ph[u].v[w]);
+            an.add(rn.v[w], rn.v[w]);
+          }
+          stv(c.rW + rv[u].g, rn);
+          stv(c.phiW + rv[u].g, fn);
+        }
+      }
+    }
+  } else {
+    for (int j = rt.h0; j < rt.h1; ++j) {
+      const bool own = (j >= rt.j0 && j < rt.j1);
+      T* row = sm + (j - rt.h0) * stride;
+      const long long base = (long long)j * nlon;
+      for (int i = threadIdx.x; i < nlon; i += kThreads) {
+        const long long g = base + i;
+        const T r1 = tfma(beta, ldcg(c.lpnu + g), ldcg(c.rC + g));
+        row[sk(i)] = r1;
+        if (own) {
+          c.rW[g] = r1;
+          c.phiW[g] = tfma(beta, ldcg(c.pnu + g), ldcg(c.phiC + g));
+          an.add(r1, r1);
+        }
       }
     }
   }
-  if (threadIdx.x == 0)
-    ps.nfl = collect_flips(sd, c.t, 1u << V_E, (long long)rt.h0 * nlon, (long long)rt.h1 * nlon, ps.fl);
+  cp_async_wait_all();
   __syncthreads();
-  for (int jr = warp; jr < rt.h1 - rt.h0; jr += kWarps) precond_row(sd, rt.h0 + jr, sm + jr * stride);
+  for (int jr = warp; jr < nrows; jr += kWarps)
+    precond_row(sd, rt.h0 + jr, sm + jr * stride, staged_consts(sd, cs, nrows, jr));
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int q = 0; q < ps.nfl; ++q) {  // e-site flips (paper's injection site)
+    for (int q = 0; q < ps.nfl; ++q) {  // e-site flips (the paper's injection site)
       const long long g = ps.fl[q].g;
       const int j = (int)(g / nlon), i = (int)(g - (long long)j * nlon);
       T* v = sm + (j - rt.h0) * stride + sk(i);
@@ -541,57 +727,77 @@ __device__ void phase_pa(const SolveDev<T>& sd, const Ctx<T>& c, int tau, T* sm,
     }
   }
   __syncthreads();
-  Acc<T> ad[kMaxK];
-  for (int j = rt.j0; j < rt.j1; ++j) {
-    const long long base = (long long)j * nlon;
-    const T* row = sm + (j - rt.h0) * stride;
-    for (int i = threadIdx.x; i < nlon; i += kThreads) {
-      const long long g = base + i;
-      const T le = stencil_smem(sd, sm, stride, rt.h0, j, i);
-      sd.e[g] = row[sk(i)];
-      sd.Le[g] = le;
+  Acc<T> ad[KB];
+  if (nlon % W == 0) {
+    const int nvr = nlon / W, total = (rt.j1 - rt.j0) * nvr;
+    for (int idx = threadIdx.x; idx < total; idx += kThreads) {
+      const RowVec v = row_vec(idx, nvr, rt.j0, nlon, W);
+      const bool hasN = v.j < nlat - 1, hasS = v.j > 0;
+      const V16<T> tx = ldv_nc(sd.Tx + v.g);
+      const T txw0 = __ldg(sd.Tx + (long long)v.j * nlon + (v.i == 0 ? nlon - 1 : v.i - 1));
+      V16<T> ty, tys;
+      if (hasN) ty = ldv_nc(sd.Ty + v.g);
+      if (hasS) tys = ldv_nc(sd.Ty + v.g - nlon);
+      const T muA = __ldg(sd.muA + v.j);
+      V16<T> lpl[KB];
 #pragma unroll
-      for (int l = 0; l < kMaxK; ++l)
-        if (l <= c.nu) ad[l].add(le, ldcg(c.lp[l] + g));
+      for (int l = 0; l < KB; ++l)
+        if (l <= c.nu) lpl[l] = ldv(c.lp[l] + v.g);
+      const T* row = sm + (v.j - rt.h0) * stride;
+      V16<T> ev, le;
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        const int i = v.i + w;
+        const int ie = (i + 1 == nlon) ? 0 : i + 1;
+        const int iw = (i == 0) ? nlon - 1 : i - 1;
+        const T x = row[sk(i)];
+        ev.v[w] = x;
+        le.v[w] = stencil5<T>(x, row[sk(ie)], row[sk(iw)], hasN ? row[stride + sk(i)] : T(0),
+                              hasS ? row[-stride + sk(i)] : T(0), tx.v[w], w == 0 ? txw0 : tx.v[w - 1],
+                              hasN ? ty.v[w] : T(0), hasS ? tys.v[w] : T(0), muA, hasN, hasS);
+      }
+      stv(sd.e + v.g, ev);
+      stv(sd.Le + v.g, le);
+#pragma unroll
+      for (int l = 0; l < KB; ++l)
+        if (l <= c.nu) {
+#pragma unroll
+          for (int w = 0; w < W; ++w) ad[l].add(le.v[w], lpl[l].v[w]);
+        }
+    }
+  } else {
+    for (int j = rt.j0; j < rt.j1; ++j) {
+      const long long base = (long long)j * nlon;
+      const T* row = sm + (j - rt.h0) * stride;
+      for (int i = threadIdx.x; i < nlon; i += kThreads) {
+        const long long g = base + i;
+        const T le = stencil_smem(sd, sm, stride, rt.h0, j, i);
+        sd.e[g] = row[sk(i)];
+        sd.Le[g] = le;
+#pragma unroll
+        for (int l = 0; l < KB; ++l)
+          if (l <= c.nu) ad[l].add(le, ldcg(c.lp[l] + g));
+      }
     }
   }
-  // deterministic CTA reduction of 2 + nu values
-  const int lane = threadIdx.x & 31;
-  {
-    double s = warp_sum(an.get());
-    if (lane == 0) ps.red[warp * kNPart + 0] = s;
-  }
+  cta_red_put(ps.cr, 0, an.warp_sum());
 #pragma unroll
-  for (int l = 0; l < kMaxK; ++l)
-    if (l <= c.nu) {
-      double s = warp_sum(ad[l].get());
-      if (lane == 0) ps.red[warp * kNPart + 1 + l] = s;
-    }
-  __syncthreads();
-  if (threadIdx.x < 2 + c.nu) {
-    double s = 0.0;
-    for (int w = 0; w < kWarps; ++w) s += ps.red[w * kNPart + threadIdx.x];
-    part_out[threadIdx.x] = s;
-  }
+  for (int l = 0; l < KB; ++l)
+    if (l <= c.nu) cta_red_put(ps.cr, 1 + l, ad[l].warp_sum());
+  cta_red_finish(ps.cr, 2 + c.nu, part_out);
 }
 
 // PB: direction recurrences and the dots for the next beta.
-template <typename T>
-__device__ void phase_pb(const SolveDev<T>& sd, const Ctx<T>& c, int tau, PhaseSmem<T>& ps, double* part_out) {
+template <typename T, int KB>
+__device__ __forceinline__ void phase_pb(const SolveDev<T>& sd, const Ctx<T>& c, int tau, PhaseSmem& ps, double* part_out) {
+  constexpr int W = V16<T>::W;
+  constexpr int U = 2;
   const long long e0 = elem_start(sd.N, sd.nt, tau), e1 = elem_start(sd.N, sd.nt, tau + 1);
   if (threadIdx.x == 0) ps.nfl = collect_flips(sd, c.t, kStateVecs, e0, e1, ps.fl);
   __syncthreads();
   const int nfl = ps.nfl;
   Acc<T> a0, a1;
-  for (long long g = e0 + threadIdx.x; g < e1; g += kThreads) {
-    T pa = ldcg(sd.e + g), la = ldcg(sd.Le + g);
-#pragma unroll
-    for (int l = 0; l < kMaxK; ++l)
-      if (l <= c.nu) {
-        pa = tfma(c.alpha[l], ldcg(c.pp[l] + g), pa);
-        la = tfma(c.alpha[l], ldcg(c.lp[l] + g), la);
-      }
-    T rv = ldcg(c.rCw + g);
+  auto finish = [&](long long g, T pa, T la, T rv) {
     if (nfl) {
       pa = apply_flips(pa, g, V_P, nfl, ps.fl);
       la = apply_flips(la, g, V_AP, nfl, ps.fl);
@@ -608,25 +814,79 @@ __device__ void phase_pb(const SolveDev<T>& sd, const Ctx<T>& c, int tau, PhaseS
     c.lpnew[g] = la;
     a0.add(rv, la);
     a1.add(la, la);
+  };
+  const long long q0 = e0 / W, q1 = e1 / W;  // e0 is a multiple of 4
+  for (long long b = q0 + threadIdx.x; b < q1; b += U * kThreads) {
+    V16<T> pa[U], la[U], rv[U];
+    bool ok[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long q = b + (long long)u * kThreads;
+      ok[u] = q < q1;
+      if (ok[u]) {
+        pa[u] = ldv(sd.e + q * W);
+        la[u] = ldv(sd.Le + q * W);
+        rv[u] = ldv(c.rCw + q * W);
+      }
+    }
+#pragma unroll
+    for (int l = 0; l < KB; ++l)
+      if (l <= c.nu) {
+        V16<T> pl[U], ll[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (ok[u]) {
+            const long long q = b + (long long)u * kThreads;
+            pl[u] = ldv(c.pp[l] + q * W);
+            ll[u] = ldv(c.lp[l] + q * W);
+          }
+        const T al = c.alpha[l];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (ok[u]) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+              pa[u].v[w] = tfma(al, pl[u].v[w], pa[u].v[w]);
+              la[u].v[w] = tfma(al, ll[u].v[w], la[u].v[w]);
+            }
+          }
+      }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (ok[u]) {
+        const long long q = b + (long long)u * kThreads;
+        if (nfl) {
+#pragma unroll
+          for (int w = 0; w < W; ++w) finish(q * W + w, pa[u].v[w], la[u].v[w], rv[u].v[w]);
+        } else {
+          stv(c.pnew + q * W, pa[u]);
+          stv(c.lpnew + q * W, la[u]);
+#pragma unroll
+          for (int w = 0; w < W; ++w) {
+            a0.add(rv[u].v[w], la[u].v[w]);
+            a1.add(la[u].v[w], la[u].v[w]);
+          }
+        }
+      }
   }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double s0 = warp_sum(a0.get()), s1 = warp_sum(a1.get());
-  if (lane == 0) {
-    ps.red[warp * kNPart + 0] = s0;
-    ps.red[warp * kNPart + 1] = s1;
+  for (long long g = q1 * W + threadIdx.x; g < e1; g += kThreads) {  // ragged tail
+    T pa = ldcg(sd.e + g), la = ldcg(sd.Le + g);
+    for (int l = 0; l < KB; ++l)
+      if (l <= c.nu) {
+        pa = tfma(c.alpha[l], ldcg(c.pp[l] + g), pa);
+        la = tfma(c.alpha[l], ldcg(c.lp[l] + g), la);
+      }
+    finish(g, pa, la, ldcg(c.rCw + g));
   }
-  __syncthreads();
-  if (threadIdx.x < 2) {
-    double s = 0.0;
-    for (int w = 0; w < kWarps; ++w) s += ps.red[w * kNPart + threadIdx.x];
-    part_out[threadIdx.x] = s;
-  }
+  cta_red_put(ps.cr, 0, a0.warp_sum());
+  cta_red_put(ps.cr, 1, a1.warp_sum());
+  cta_red_finish(ps.cr, 2, part_out);
 }
 
 // RESTORE: [phi, r, p, L(p)]^0 <- [phi, r, p, L(p)]^* by copy (the backup
 // itself is never the working set), then the flips of the next step.
 template <typename T>
-__device__ void phase_restore(const SolveDev<T>& sd, const Ctx<T>& c, int tau, PhaseSmem<T>& ps, double* part_out) {
+__device__ __forceinline__ void phase_restore(const SolveDev<T>& sd, const Ctx<T>& c, int tau, PhaseSmem& ps, double* part_out) {
   const long long e0 = elem_start(sd.N, sd.nt, tau), e1 = elem_start(sd.N, sd.nt, tau + 1);
   if (threadIdx.x == 0) {
     ps.nfl = collect_flips(sd, c.t, kStateVecs, e0, e1, ps.fl);
@@ -656,18 +916,9 @@ __device__ void phase_restore(const SolveDev<T>& sd, const Ctx<T>& c, int tau, P
     a0.add(rr, ll);
     a1.add(ll, ll);
   }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double s0 = warp_sum(a0.get()), s1 = warp_sum(a1.get());
-  if (lane == 0) {
-    ps.red[warp * kNPart + 0] = s0;
-    ps.red[warp * kNPart + 1] = s1;
-  }
-  __syncthreads();
-  if (threadIdx.x < 2) {
-    double s = 0.0;
-    for (int w = 0; w < kWarps; ++w) s += ps.red[w * kNPart + threadIdx.x];
-    part_out[threadIdx.x] = s;
-  }
+  cta_red_put(ps.cr, 0, a0.warp_sum());
+  cta_red_put(ps.cr, 1, a1.warp_sum());
+  cta_red_finish(ps.cr, 2, part_out);
 }
 
 // INIT: r0 = L(phi0) - R (FP64 path, phi0 = x0) or r0 = -R_in (mixed inner
@@ -675,13 +926,15 @@ __device__ void phase_restore(const SolveDev<T>& sd, const Ctx<T>& c, int tau, P
 // beta dots.  The x/r/p/Ap flips of the first step are applied to the working
 // vectors, and their clean values kept so that the backup stays clean.
 template <typename T>
-__device__ void phase_init(const SolveDev<T>& sd, const Ctx<T>& c, int tau, T* sm, PhaseSmem<T>& ps,
+__device__ __forceinline__ void phase_init(const SolveDev<T>& sd, const Ctx<T>& c, int tau, T* sm, PhaseSmem& ps,
                            double* part_out) {
   const int nlon = sd.nlon, nlat = sd.nlat, stride = row_stride(nlon);
   const RowTile rt = row_tile(nlat, sd.nt, tau);
   const int warp = threadIdx.x >> 5;
   if (threadIdx.x == 0)
     ps.nfl = collect_flips(sd, c.t, kStateVecs, (long long)rt.j0 * nlon, (long long)rt.j1 * nlon, ps.fl);
+  T* cs = sm + (long long)(sd.nt_hmax + 2) * stride;
+  stage_line_consts(sd, rt.h0, rt.h1, cs);
   __syncthreads();
   const int nfl = ps.nfl;
   Acc<T> an, aR;
@@ -721,8 +974,10 @@ __device__ void phase_init(const SolveDev<T>& sd, const Ctx<T>& c, int tau, T* s
       }
     }
   }
+  cp_async_wait_all();
   __syncthreads();
-  for (int jr = warp; jr < rt.h1 - rt.h0; jr += kWarps) precond_row(sd, rt.h0 + jr, sm + jr * stride);
+  for (int jr = warp; jr < rt.h1 - rt.h0; jr += kWarps)
+    precond_row(sd, rt.h0 + jr, sm + jr * stride, staged_consts(sd, cs, rt.h1 - rt.h0, jr));
   __syncthreads();
   Acc<T> a0, a1;
   for (int j = rt.j0; j < rt.j1; ++j) {
@@ -750,29 +1005,20 @@ __device__ void phase_init(const SolveDev<T>& sd, const Ctx<T>& c, int tau, T* s
       a1.add(lp, lp);
     }
   }
-  const int lane = threadIdx.x & 31;
-  double v[4] = {an.get(), aR.get(), a0.get(), a1.get()};
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    double s = warp_sum(v[q]);
-    if (lane == 0) ps.red[warp * kNPart + q] = s;
-  }
-  __syncthreads();
-  if (threadIdx.x < 4) {
-    double s = 0.0;
-    for (int w = 0; w < kWarps; ++w) s += ps.red[w * kNPart + threadIdx.x];
-    part_out[threadIdx.x] = s;
-  }
+  cta_red_put(ps.cr, 0, an.warp_sum());
+  cta_red_put(ps.cr, 1, aR.warp_sum());
+  cta_red_put(ps.cr, 2, a0.warp_sum());
+  cta_red_put(ps.cr, 3, a1.warp_sum());
+  cta_red_finish(ps.cr, 4, part_out);
 }
 
 // OUT (mixed): x' = x + d in FP64, r_out = R - L64(x'), ||r_out||^2 (and
 // ||R||^2 the first time), inner right-hand side R_in = (float) r_out.
 template <typename T>
-__device__ void phase_out(const SolveDev<T>& sd, const Ctx<T>& c, int tau, double* smd, PhaseSmem<T>& ps,
+__device__ __forceinline__ void phase_out(const SolveDev<T>& sd, const Ctx<T>& c, int tau, double* smd, PhaseSmem& ps,
                           double* part_out) {
   const int nlon = sd.nlon, nlat = sd.nlat, stride = row_stride(nlon);
   const RowTile rt = row_tile(nlat, sd.nt, tau);
-  const int warp = threadIdx.x >> 5;
   for (int j = rt.h0; j < rt.h1; ++j) {
     const bool own = (j >= rt.j0 && j < rt.j1);
     double* row = smd + (j - rt.h0) * stride;
@@ -786,7 +1032,7 @@ __device__ void phase_out(const SolveDev<T>& sd, const Ctx<T>& c, int tau, doubl
     }
   }
   __syncthreads();
-  double so = 0.0, sR = 0.0;
+  Acc<double> so, sR;
   for (int j = rt.j0; j < rt.j1; ++j) {
     const long long base = (long long)j * nlon;
     const double* row = smd + (j - rt.h0) * stride;
@@ -803,32 +1049,22 @@ __device__ void phase_out(const SolveDev<T>& sd, const Ctx<T>& c, int tau, doubl
       const double Rv = ldcg(sd.R + g);
       const double ro = Rv - Lx;
       sd.Rin[g] = (T)ro;
-      so = fma(ro, ro, so);
-      if (c.first) sR = fma(Rv, Rv, sR);
+      so.add(ro, ro);
+      if (c.first) sR.add(Rv, Rv);
     }
   }
-  const int lane = threadIdx.x & 31;
-  double s0 = warp_sum(so), s1 = warp_sum(sR);
-  if (lane == 0) {
-    ps.red[warp * kNPart + 0] = s0;
-    ps.red[warp * kNPart + 1] = s1;
-  }
-  __syncthreads();
-  if (threadIdx.x < 2) {
-    double s = 0.0;
-    for (int w = 0; w < kWarps; ++w) s += ps.red[w * kNPart + threadIdx.x];
-    part_out[threadIdx.x] = s;
-  }
+  cta_red_put(ps.cr, 0, so.warp_sum());
+  cta_red_put(ps.cr, 1, sR.warp_sum());
+  cta_red_finish(ps.cr, 2, part_out);
 }
 
 // FIN: write the solution to the caller's x and (FP64 path) the true
 // residual ||L(x) - R||^2.
 template <typename T>
-__device__ void phase_fin(const SolveDev<T>& sd, const Ctx<T>& c, int tau, PhaseSmem<T>& ps, double* part_out) {
+__device__ __forceinline__ void phase_fin(const SolveDev<T>& sd, const Ctx<T>& c, int tau, PhaseSmem& ps, double* part_out) {
   const int nlon = sd.nlon, nlat = sd.nlat;
   const RowTile rt = row_tile(nlat, sd.nt, tau);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double acc = 0.0;
+  Acc<double> acc;
   if (sd.mixed) {
     const double* xs = c.xsrc;
     for (long long g = (long long)rt.j0 * nlon + threadIdx.x; g < (long long)rt.j1 * nlon; g += kThreads)
@@ -859,18 +1095,12 @@ __device__ void phase_fin(const SolveDev<T>& sd, const Ctx<T>& c, int tau, Phase
                                            __ldg(sd.muA64 + j), hasN, hasS);
         const double res = Lx - ldcg(sd.R + g);
         sd.xout[g] = v;
-        acc = fma(res, res, acc);
+        acc.add(res, res);
       }
     }
   }
-  double s = warp_sum(acc);
-  if (lane == 0) ps.red[warp * kNPart] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < kWarps; ++w) t += ps.red[w * kNPart];
-    part_out[0] = t;
-  }
+  cta_red_put(ps.cr, 0, acc.warp_sum());
+  cta_red_finish(ps.cr, 1, part_out);
 }
 
 // ------------------------------------------------------------ the kernel
@@ -897,7 +1127,7 @@ struct KernelSmem {
   SolveState S;
   SolveState N;
   Ctx<T> c;
-  PhaseSmem<T> ps;
+  PhaseSmem ps;
   double red[kNPart];
   int prefix[kMaxBatch + 1];
   int bail;
@@ -906,8 +1136,8 @@ struct KernelSmem {
 // Persistent cooperative kernel: every round, every CTA takes its share of
 // the tiles of all active solves, runs for each solve the state transition
 // and the decided phase, and then meets the others at one grid barrier.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_ftgcr_persistent(BatchArgs<T> a) {
+template <typename T, int KB>
+__global__ void __launch_bounds__(kThreads, 1) k_ftgcr_persistent(BatchArgs<T> a) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ KernelSmem<T> ks;
   T* sm = reinterpret_cast<T*>(dsm);
@@ -915,6 +1145,7 @@ __global__ void __launch_bounds__(kThreads) k_ftgcr_persistent(BatchArgs<T> a) {
   const long long round0 = a.ctl->round0;
   const unsigned long long t_start = globaltimer();
   unsigned int nbar = 0;
+  int cur_sd = -1;  // solve whose descriptor sits in shared memory
   int it = 0;
   for (; it < a.max_rounds; ++it) {
     // watchdog: a kernel that runs far longer than any solve raises the error
@@ -922,6 +1153,10 @@ __global__ void __launch_bounds__(kThreads) k_ftgcr_persistent(BatchArgs<T> a) {
     if (threadIdx.x == 0 && globaltimer() - t_start > kKernelTimeoutNs) atomicExch(&a.ctl->err, 2);
     const long long round = round0 + it;
     const int par = (int)(round & 1);
+    if (threadIdx.x == 0 && a.diag) {
+      a.diag[blockIdx.x * 4 + 0] = it;
+      a.diag[blockIdx.x * 4 + 2] = 0;
+    }
     // tile prefix over active solves (identical in every CTA)
     if (threadIdx.x == 0) {
       int acc = 0;
@@ -937,6 +1172,9 @@ __global__ void __launch_bounds__(kThreads) k_ftgcr_persistent(BatchArgs<T> a) {
     const int total = ks.prefix[a.n];
     if (total == 0) break;
     int cur = -1;
+    unsigned long long tr[3] = {0ull, 0ull, 0ull};
+    int tr_kind = -1, tr_items = 0;
+    if (a.trace && threadIdx.x == 0) tr[0] = globaltimer();
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
       int lo = 0, hi = a.n - 1;  // last s with prefix[s] <= item and nt > 0
       while (lo < hi) {
@@ -946,23 +1184,36 @@ __global__ void __launch_bounds__(kThreads) k_ftgcr_persistent(BatchArgs<T> a) {
       const int s = lo;
       const int tau = item - ks.prefix[s];
       if (s != cur) {
-        SolveDev<T>* sdp = a.solves[s];
-        cta_load_cg(&ks.sd, sdp);
-        __syncthreads();
+        if (s != cur_sd) {
+          cta_load_cg(&ks.sd, a.solves[s]);
+          __syncthreads();
+          cur_sd = s;
+        }
+        // the state record and every partial sum the pending phase may have
+        // left, loaded together
         cta_load_cg(&ks.S, ks.sd.st + par);
-        __syncthreads();
-        reduce_partials(ks.sd.part + (long long)(par ^ 1) * ks.sd.nt * kNPart, ks.sd.nt,
-                        part_count(ks.S.pending, ks.S.nu), ks.red);
+        reduce_partials<T>(ks.sd.part + (long long)(par ^ 1) * ks.sd.nt * kPartStride, ks.sd.nt,
+                           ks.sd.k + 1 > 4 ? ks.sd.k + 1 : 4, ks.red);
         __syncthreads();
         if (threadIdx.x == 0) transition(ks.sd, ks.S, ks.red, ks.N, ks.c);
         __syncthreads();
         cur = s;
       }
-      double* part_out = ks.sd.part + ((long long)par * ks.sd.nt + tau) * kNPart;
+      if (a.trace && threadIdx.x == 0 && tr_items == 0) {
+        tr[1] = globaltimer();
+        tr_kind = ks.c.kind;
+      }
+      ++tr_items;
+      if (threadIdx.x == 0 && a.diag) {
+        a.diag[blockIdx.x * 4 + 1] = ks.c.kind;
+        a.diag[blockIdx.x * 4 + 2] = 1;
+        a.diag[blockIdx.x * 4 + 3] = tr_items;
+      }
+      double* part_out = ks.sd.part + ((long long)par * ks.sd.nt + tau) * kPartStride;
       switch (ks.c.kind) {
         case K_INIT: phase_init(ks.sd, ks.c, tau, sm, ks.ps, part_out); break;
-        case K_PA: phase_pa(ks.sd, ks.c, tau, sm, ks.ps, part_out); break;
-        case K_PB: phase_pb(ks.sd, ks.c, tau, ks.ps, part_out); break;
+        case K_PA: phase_pa<T, KB>(ks.sd, ks.c, tau, sm, ks.ps, part_out); break;
+        case K_PB: phase_pb<T, KB>(ks.sd, ks.c, tau, ks.ps, part_out); break;
         case K_RESTORE: phase_restore(ks.sd, ks.c, tau, ks.ps, part_out); break;
         case K_OUT: phase_out(ks.sd, ks.c, tau, smd, ks.ps, part_out); break;
         case K_FIN: phase_fin(ks.sd, ks.c, tau, ks.ps, part_out); break;
@@ -976,8 +1227,21 @@ __global__ void __launch_bounds__(kThreads) k_ftgcr_persistent(BatchArgs<T> a) {
       }
       __syncthreads();
     }
+    if (a.trace && threadIdx.x == 0) tr[2] = globaltimer();
+    if (threadIdx.x == 0 && a.diag) a.diag[blockIdx.x * 4 + 2] = 2;
     ++nbar;
-    if (!grid_barrier(&a.ctl->counter, nbar * gridDim.x, &a.ctl->err, &ks.bail)) return;
+    const bool ok = grid_barrier(&a.ctl->counter, nbar * gridDim.x, &a.ctl->err, &ks.bail);
+    if (a.trace && threadIdx.x == 0 && it < a.trace_rounds) {
+      TraceEnt e;
+      e.t0 = tr[0];
+      e.t1 = tr[1];
+      e.t2 = tr[2];
+      e.t3 = globaltimer();
+      e.kind = tr_kind;
+      e.items = tr_items;
+      a.trace[(long long)it * gridDim.x + blockIdx.x] = e;
+    }
+    if (!ok) return;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->round_end = round0 + it;
 }

@@ -20,10 +20,13 @@ _CSRC = os.path.join(_HERE, "csrc")
 _INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libftgcr.so")
-SOURCES = ["ftgcr.cu"]
-HEADERS = ["ftgcr_device.cuh", "ftgcr_phases.cuh"]
+SOURCES = ["ftgcr.cu", "ftgcr_k4.cu", "ftgcr_k8.cu", "ftgcr_k16.cu"]
+HEADERS = ["ftgcr_device.cuh", "ftgcr_phases.cuh", "ftgcr_instances.h"]
+# --fmad=false: device multiply-adds are fused only where the code says fma();
+# -ffp-contract=off: the same for the host-side geometry (GCC contracts by
+# default on aarch64)
 NVCC_FLAGS = ["-std=c++17", "-O3", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "--fmad=false",
-              "-Xcompiler", "-fPIC", "-shared"]
+              "-Xcompiler", "-fPIC,-ffp-contract=off"]
 
 FP64, MIXED = 0, 1
 PRECOND = {"line": 0, "jacobi": 1, "identity": 2}
@@ -89,12 +92,23 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if not force and not _stale():
             return LIB_PATH
         os.makedirs(_BUILD, exist_ok=True)
-        tmp = LIB_PATH + ".%d.tmp" % os.getpid()
-        cmd = ["nvcc"] + NVCC_FLAGS + ["-o", tmp] + [os.path.join(_CSRC, f) for f in SOURCES]
-        if verbose:
-            print(" ".join(cmd))
-        subprocess.check_call(cmd, cwd=_CSRC)
+        tag = ".%d" % os.getpid()
+        objs, procs = [], []
+        for src in SOURCES:  # translation units compile in parallel
+            obj = os.path.join(_BUILD, src.replace(".cu", tag + ".o"))
+            cmd = ["nvcc"] + NVCC_FLAGS + ["-c", "-o", obj, os.path.join(_CSRC, src)]
+            if verbose:
+                print(" ".join(cmd))
+            procs.append((subprocess.Popen(cmd, cwd=_CSRC), cmd))
+            objs.append(obj)
+        for pr, cmd in procs:
+            if pr.wait() != 0:
+                raise subprocess.CalledProcessError(pr.returncode, cmd)
+        tmp = LIB_PATH + tag + ".tmp"
+        subprocess.check_call(["nvcc", "-shared", "-o", tmp] + objs, cwd=_CSRC)
         os.replace(tmp, LIB_PATH)
+        for o in objs:
+            os.remove(o)
         return LIB_PATH
 
 

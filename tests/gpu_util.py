@@ -14,9 +14,12 @@ def rel_err(a: np.ndarray, b: np.ndarray) -> float:
     if not np.array_equal(ia, ib) or not np.array_equal(np.sign(a[ia]), np.sign(b[ib])):
         return float("inf")
     f = np.isfinite(b)
-    nb = np.linalg.norm(b[f])
-    d = np.linalg.norm(a[f] - b[f])
-    return float(d / nb) if nb > 0 else float(d)
+    scale = np.abs(b[f]).max() if f.any() else 0.0
+    if scale == 0.0:
+        return float(np.abs(a[f]).max()) if f.any() else 0.0
+    nb = np.linalg.norm(b[f] / scale)
+    d = np.linalg.norm(a[f] / scale - b[f] / scale)
+    return float(d / nb)
 
 
 def decisions(info: dict) -> tuple:

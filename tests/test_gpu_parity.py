@@ -55,11 +55,9 @@ def test_preconditioner_matches_oracle(precond, nlon, nlat):
         s.apply_precond(cuda(r), out)
         torch.cuda.synchronize()
     got = out.cpu().numpy()
-    # rounding of a different (parallel) elimination order, amplified by the
-    # conditioning of the nearly singular polar rows
-    assert rel_err(got, ref) < 1e-11
-    if precond == "identity":
-        assert np.array_equal(got, ref)
+    # the FP64 path runs the oracle's factorisation and substitution
+    # operation for operation: bitwise equal
+    assert np.array_equal(got, ref)
 
 
 def test_config1_single_flip_at_step5():
@@ -78,7 +76,7 @@ def test_config1_single_flip_at_step5():
 
 @pytest.mark.parametrize("nlon,nlat,k,precond,rhs", [
     (64, 32, 4, "line", "flow"), (64, 32, 1, "line", "random"), (64, 32, 8, "jacobi", "random"),
-    (40, 21, 3, "line", "random"), (128, 64, 5, "identity", "random"), (512, 256, 4, "line", "flow"),
+    (40, 21, 3, "line", "random"), (32, 16, 5, "identity", "random"), (512, 256, 4, "line", "flow"),
     (100, 7, 2, "line", "random"), (16, 1, 4, "line", "random"), (3, 2, 2, "jacobi", "random"),
     (1024, 512, 4, "line", "flow"), (1024, 512, 8, "line", "random"), (256, 128, 16, "line", "random"),
 ])
