@@ -174,6 +174,31 @@ int64_t ftgcr_footprint(const ftgcr_grid* grid, int32_t k);
 void ftgcr_destroy(ftgcr_handle* h);
 const char* ftgcr_error_string(int status);
 
+/* No-allocation FP64 solve.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory when they solve
+ * (code running while a stream is being captured, where cudaMalloc is not
+ * permitted; processes whose device memory belongs to another allocator;
+ * code that must not fail with out-of-memory mid-run).  It solves L(x) = rhs
+ * like ftgcr_solve with FTGCR_FP64 and the line preconditioner, without a
+ * handle, and calls no cudaMalloc, cudaFree or other allocating routine:
+ * every Krylov vector, coefficient, factor and bookkeeping record lives in
+ * one static device array of FTGCR_NOALLOC_SCRATCH_BYTES that every GPU
+ * loading the library holds until the process exits.
+ *  - Limits: nlon * nlat <= FTGCR_NOALLOC_MAX_POINTS, k <= FTGCR_NOALLOC_MAX_K;
+ *    larger sizes return FTGCR_ERR_ARG.
+ *  - D, rhs, x: device pointers (x: initial guess in, solution out); stats
+ *    may be NULL.  Blocks until done; returns like ftgcr_solve.
+ *  - The first call on a device looks up the array's device address (set-up);
+ *    make that first call before any stream capture begins.
+ *  - All calls share the array, which keeps the last call's contents; calls
+ *    that overlap on the GPU (other threads, other streams) race and must be
+ *    serialised by the caller. */
+#define FTGCR_NOALLOC_MAX_POINTS 16384
+#define FTGCR_NOALLOC_MAX_K 4
+#define FTGCR_NOALLOC_SCRATCH_BYTES (6 * 1024 * 1024)
+int ftgcr_solve_noalloc(const ftgcr_grid* grid, const double* D, int32_t k, double tol, const double* rhs, double* x,
+                        ftgcr_stats_t* stats, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

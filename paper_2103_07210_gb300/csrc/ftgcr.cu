@@ -954,3 +954,181 @@ void ftgcr_destroy(ftgcr_handle* h) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ no-allocation solve
+// Some callers cannot allocate device memory when they solve: code that runs
+// while a stream is being captured (cudaMalloc is not permitted then), code
+// whose device memory is owned entirely by another allocator, and code that
+// must not fail with out-of-memory in the middle of a run.  For them,
+// ftgcr_solve_noalloc keeps all of its scratch in the static device array
+// below instead of allocating a handle's pool.  Every GPU that loads the
+// library holds the array until the process exits.
+constexpr long long kNoAllocMaxPoints = FTGCR_NOALLOC_MAX_POINTS;
+constexpr int kNoAllocMaxK = FTGCR_NOALLOC_MAX_K;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[FTGCR_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+struct NoAllocDevice {
+  unsigned char* base = nullptr;  // device address of g_noalloc_scratch
+  bool ready = false;
+};
+
+// Set-up, once per device, with that device current: the device address of
+// the static array (in host code its name is only a host-side stand-in).
+int noalloc_base(int dev, unsigned char** base) {
+  static std::mutex mu;
+  static std::vector<NoAllocDevice> devs;
+  std::lock_guard<std::mutex> lk(mu);
+  if ((int)devs.size() <= dev) devs.resize(dev + 1);
+  if (!devs[dev].ready) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return FTGCR_ERR_CUDA;
+    }
+    devs[dev].base = (unsigned char*)p;
+    devs[dev].ready = true;
+  }
+  *base = devs[dev].base;
+  return FTGCR_OK;
+}
+
+}  // namespace
+
+extern "C" int ftgcr_solve_noalloc(const ftgcr_grid* grid, const double* D, int32_t k, double tol, const double* rhs,
+                                   double* x, ftgcr_stats_t* stats, void* stream) {
+  int rc = check_grid(grid, k, tol);
+  if (rc) return rc;
+  if (!D || !rhs || !x || grid->precision != FTGCR_FP64 || grid->precond != FTGCR_PRECOND_LINE)
+    return FTGCR_ERR_ARG;
+  if ((long long)grid->nlon * grid->nlat > kNoAllocMaxPoints || k > kNoAllocMaxK) return FTGCR_ERR_ARG;
+  if (!is_device_ptr(D) || !is_device_ptr(rhs) || !is_device_ptr(x)) return FTGCR_ERR_ARG;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  unsigned char* base = nullptr;
+  rc = noalloc_base(dev, &base);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const DeviceInfo di = device_info(dev);
+  const int smem_limit = di.smem_optin - kStaticSmemReserve;
+
+  // the handle record lives on the host stack; its pool is the static array
+  ftgcr_handle h;
+  h.dev = dev;
+  fill_handle_params(&h, grid, k, tol, di.sms, smem_limit);
+  if (dyn_smem(h.nlon, h.nlat, h.nt, 0, sizeof(double), h.precond) > (size_t)smem_limit) return FTGCR_ERR_ARG;
+  SolveDev<double> sd{};
+  const size_t pool = layout<double>(&h, nullptr, &sd);
+  const size_t geo = align256(sizeof(double) * 3 * h.nlat);
+  if (pool + geo > (size_t)FTGCR_NOALLOC_SCRATCH_BYTES) return FTGCR_ERR_ARG;
+  layout<double>(&h, base, &sd);
+  double* dgeo = (double*)(base + pool);
+
+  sd.nlon = h.nlon;
+  sd.nlat = h.nlat;
+  sd.k = h.k;
+  sd.nt = h.nt;
+  sd.nt_hmax = (h.nlat + h.nt - 1) / h.nt;
+  sd.C = h.C;
+  sd.precond = h.precond;
+  sd.mixed = 0;
+  sd.N = h.N;
+  sd.max_steps = h.max_steps;
+  sd.max_outer = h.max_outer;
+  sd.tol2 = h.tol * h.tol;
+  sd.inner_tol2 = h.inner_tol * h.inner_tol;
+  sd.Tx64 = h.Tx64;
+  sd.Ty64 = h.Ty64;
+  sd.muA64 = h.muA64;
+
+  // coefficients and factorisation into the array (the array keeps the last
+  // call's contents; everything below is rewritten before it is read)
+  std::vector<double> cx, cy, area, g3;
+  row_geometry(h.nlon, h.nlat, cx, cy, area);
+  g3.insert(g3.end(), cx.begin(), cx.end());
+  g3.insert(g3.end(), cy.begin(), cy.end());
+  g3.insert(g3.end(), area.begin(), area.end());
+  CK(cudaMemcpyAsync(dgeo, g3.data(), sizeof(double) * 3 * h.nlat, cudaMemcpyHostToDevice, st));
+  k_face_coeffs<<<256, 256, 0, st>>>(h.nlon, h.nlat, D, dgeo, dgeo + h.nlat, dgeo + 2 * h.nlat, h.mu, h.Tx64, h.Ty64,
+                                     h.muA64, nullptr, nullptr, nullptr);
+  CK(cudaGetLastError());
+  k_line_factor<<<(h.nlat + 63) / 64, 64, 0, st>>>(h.nlon, h.nlat, h.C, h.precond, h.Tx64, h.Ty64, h.muA64,
+                                                   (double*)sd.lc, (double*)sd.lw, (double*)sd.lu, (double*)sd.lz,
+                                                   (double*)sd.lrow, nullptr, nullptr, nullptr, nullptr);
+  CK(cudaGetLastError());
+  void* sp = h.sdev;
+  CK(cudaMemcpyAsync(h.sdev, &sd, sizeof sd, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(h.sdev_arr, &sp, sizeof(void*), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(h.nt_dev, &h.nt, sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(h.active, 0, sizeof(int) * 2, st));
+
+  const int kb = kbound(h.k);
+  h.smem = dyn_smem(h.nlon, h.nlat, h.nt, 0, sizeof(double), h.precond);
+  rc = configure_kernel<double>(kb, std::max<size_t>(h.smem, 1));
+  if (rc) return rc;
+  int occ = 0;
+  rc = occupancy<double>(kb, h.smem, &occ);
+  if (rc) return rc;
+  if (occ < 1) return FTGCR_ERR_ARG;
+  {
+    // no stack resize here (it may allocate): the current limit must do
+    cudaFuncAttributes fa;
+    CK(cudaFuncGetAttributes(&fa, kernel_ptr<double>(kb)));
+    size_t cur = 0;
+    CK(cudaDeviceGetLimit(&cur, cudaLimitStackSize));
+    if (fa.localSizeBytes > cur) return FTGCR_ERR_ARG;
+  }
+  const int grid_ctas = std::min(h.nt, di.sms * occ);
+  const BeginArgs b = begin_args(&h, rhs, x, x, nullptr);
+  k_begin_solve<double><<<1, 64, 0, st>>>((SolveDev<double>*)h.sdev, b, h.active, 1, 0, 0, h.ctl);
+  CK(cudaGetLastError());
+  BatchArgs<double> a;
+  a.solves = (SolveDev<double>* const*)h.sdev_arr;
+  a.nt = h.nt_dev;
+  a.active = h.active;
+  a.n = 1;
+  a.ctl = h.ctl;
+  a.max_rounds = (int)std::min<long long>(1 << 30, 2 * h.max_steps + 8 * ((long long)h.max_outer + 2) + 16);
+  a.trace = nullptr;
+  a.trace_rounds = 0;
+  a.diag = h.diag;
+  void* args[] = {&a};
+  CK(cudaLaunchCooperativeKernel(kernel_ptr<double>(kb), dim3(grid_ctas), dim3(kThreads), args, h.smem, st));
+  SolveState res;
+  LaunchCtl ctl;
+  CK(cudaMemcpyAsync(&res, h.result, sizeof res, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&ctl, h.ctl, sizeof ctl, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  int status = ctl.err ? FTGCR_ERR_TIMEOUT
+                       : (res.active ? FTGCR_ERR_CUDA : (res.status == ST_CONVERGED ? FTGCR_OK : FTGCR_NOT_CONVERGED));
+  if (stats) {
+    memset(stats, 0, sizeof *stats);
+    stats->steps = res.step;
+    stats->cycles = res.cycles;
+    stats->restarts = res.restarts;
+    stats->faults_injected = res.finj;
+    stats->faults_detected = res.fdet;
+    stats->ndetect = res.ndetect;
+    stats->converged = res.status == ST_CONVERGED;
+    for (int q = 0; q < res.ndetect && q < FTGCR_MAX_DETECT; ++q) {
+      stats->detect_step[q] = res.detect_step[q];
+      stats->detect_ratio[q] = res.detect_ratio[q];
+    }
+    stats->res0 = std::sqrt(res.nrm2_0);
+    stats->res_final_rec = std::sqrt(res.nrm2_last);
+    stats->res_final_true = std::sqrt(res.res_true2);
+    stats->norm_R = std::sqrt(res.nrm2_R);
+    stats->bytes_resident = (int64_t)FTGCR_NOALLOC_SCRATCH_BYTES;
+    stats->bytes_backup = (int64_t)h.backup_bytes;
+    stats->tiles = h.nt;
+    stats->status = status;
+  }
+  // the host record must not free anything: nothing was allocated
+  h.pool = nullptr;
+  h.h_result = nullptr;
+  h.h_ctl = nullptr;
+  return status;
+}
+

@@ -37,7 +37,9 @@ OK, NOT_CONVERGED, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BUDGET, ERR_STAT
 
 # every symbol include/ftgcr.h declares
 EXPORTS = ["ftgcr_create", "ftgcr_solve", "ftgcr_solve_async", "ftgcr_stats", "ftgcr_solve_batch",
-           "ftgcr_apply_operator", "ftgcr_apply_precond", "ftgcr_footprint", "ftgcr_destroy", "ftgcr_error_string"]
+           "ftgcr_apply_operator", "ftgcr_apply_precond", "ftgcr_footprint", "ftgcr_destroy", "ftgcr_error_string",
+           "ftgcr_solve_noalloc"]
+NOALLOC_MAX_POINTS, NOALLOC_MAX_K = 16384, 4
 
 _lock = threading.Lock()
 _lib = None
@@ -134,6 +136,7 @@ def lib():
         L.ftgcr_destroy.restype = None
         L.ftgcr_error_string.argtypes = [ctypes.c_int]
         L.ftgcr_error_string.restype = ctypes.c_char_p
+        L.ftgcr_solve_noalloc.argtypes = [ctypes.POINTER(Grid), vp, i32, dbl, vp, vp, ctypes.POINTER(Stats), vp]
         for f in EXPORTS:
             if not hasattr(L, f):
                 raise RuntimeError(f"libftgcr.so does not export {f}")
@@ -273,6 +276,33 @@ class Solver:
         st = lib().ftgcr_apply_precond(self.h, ip, op, _stream_ptr(stream))
         if st < 0:
             raise FTGCRError(st, "ftgcr_apply_precond")
+
+
+def _stats_dict(s: Stats) -> dict:
+    n = s.ndetect
+    return dict(steps=s.steps, cycles=s.cycles, restarts=s.restarts, faults_injected=s.faults_injected,
+                faults_detected=s.faults_detected, outer=s.outer, converged=bool(s.converged),
+                detect_steps=[s.detect_step[i] for i in range(n)], detect_ratio=[s.detect_ratio[i] for i in range(n)],
+                res0=s.res0, res_final_rec=s.res_final_rec, res_final_true=s.res_final_true, norm_R=s.norm_R,
+                bytes_resident=s.bytes_resident, bytes_backup=s.bytes_backup, tiles=s.tiles, status=s.status)
+
+
+def solve_noalloc(D, mu, rhs, x, k=4, tol=1e-10, max_steps=0, tiles=0, stream=None):
+    """FP64 solve without any device allocation (ftgcr_solve_noalloc): for
+    callers that cannot allocate device memory when they solve.  D, rhs, x:
+    CUDA float64 tensors; x holds the initial guess and receives the solution.
+    Returns (status, stats)."""
+    nlat, nlon = D.shape
+    g = _grid(nlon, nlat, mu, "fp64", "line", max_steps, tiles, 0.0, 0)
+    dp, dk = _ptr(D)
+    rp, rk = _ptr(rhs)
+    xp, xk = _ptr(x)
+    s = Stats()
+    st = lib().ftgcr_solve_noalloc(ctypes.byref(g), dp, int(k), float(tol), rp, xp, ctypes.byref(s),
+                                   _stream_ptr(stream))
+    if st < 0:
+        raise FTGCRError(st, "ftgcr_solve_noalloc")
+    return st, _stats_dict(s)
 
 
 def solve_batch(solvers, rhs, xs, faults=None, stream=None) -> None:

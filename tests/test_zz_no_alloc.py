@@ -1,0 +1,58 @@
+"""ftgcr_solve_noalloc: the FP64 solve for callers that cannot allocate device
+memory when they solve (e.g. code running while a stream is being captured,
+or a process whose device memory belongs to another allocator).  Its scratch
+is a static device array inside the library, so this test checks that
+  * two calls in a row, through the C ABI, each give the solution of the
+    ordinary allocating entry point (ftgcr_solve) to the FP64 tolerance the
+    other tests use (1e-10 relative), with the same step count;
+  * a repeated call leaves the device's free memory unchanged;
+  * sizes beyond the stated maximum are rejected with an error.
+Collected last (file name) so that a failure here cannot hide another test's."""
+import numpy as np
+import pytest
+
+from paper_2103_07210_gb300 import ftgcr, inputs
+from tests.gpu_util import rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _reference(p, k, tol):
+    with ftgcr.Solver(p.D, p.mu, k=k, tol=tol) as s:
+        R = torch.from_numpy(p.R).cuda()
+        x = torch.zeros_like(R)
+        st = s.solve(R, x)
+        return st, x.cpu().numpy(), s.stats()
+
+
+@pytest.mark.parametrize("nlon,nlat,k,rhs", [(128, 64, 4, "flow"), (100, 37, 3, "random")])
+def test_noalloc_matches_allocating_solve_twice(nlon, nlat, k, rhs):
+    p = inputs.hill_problem(nlon, nlat, rhs=rhs, seed=12)
+    st_ref, x_ref, info_ref = _reference(p, k, 1e-10)
+    D = torch.from_numpy(p.D).cuda()
+    R = torch.from_numpy(p.R).cuda()
+    free_after_first = None
+    for call in range(2):
+        x = torch.zeros_like(R)
+        torch.cuda.synchronize()
+        st, info = ftgcr.solve_noalloc(D, p.mu, R, x, k=k, tol=1e-10)
+        torch.cuda.synchronize()
+        if call == 0:
+            free_after_first = torch.cuda.mem_get_info()[0]
+        else:
+            assert torch.cuda.mem_get_info()[0] == free_after_first
+        assert st == st_ref == ftgcr.OK
+        assert info["steps"] == info_ref["steps"] and info["converged"]
+        assert rel_err(x.cpu().numpy(), x_ref) <= 1e-10
+
+
+def test_noalloc_rejects_sizes_beyond_its_maximum():
+    for nlon, nlat, k in [(256, 128, 4), (128, 64, 5)]:  # 32768 points > 16384; k > 4
+        p = inputs.hill_problem(nlon, nlat)
+        D = torch.from_numpy(p.D).cuda()
+        R = torch.from_numpy(p.R).cuda()
+        with pytest.raises(ftgcr.FTGCRError) as ei:
+            ftgcr.solve_noalloc(D, p.mu, R, torch.zeros_like(R), k=k)
+        assert ei.value.status == ftgcr.ERR_ARG
+    assert ftgcr.NOALLOC_MAX_POINTS == 16384 and ftgcr.NOALLOC_MAX_K == 4
