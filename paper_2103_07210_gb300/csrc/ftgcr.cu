@@ -261,7 +261,10 @@ size_t dyn_smem(int nlon, int nlat, int nt, int mixed, size_t elem, int precond)
 }
 
 int choose_tiles(int nlon, int nlat, int mixed, size_t elem, int precond, int sms, int smem_limit) {
-  int nt = std::min(nlat, sms);
+  // equal-height row bands: the round takes as long as the tallest band, so
+  // use the fewest bands of that height (e.g. 512 rows on 152 SMs: 128 x 4)
+  const int hmax = (nlat + sms - 1) / sms;
+  int nt = (nlat + hmax - 1) / hmax;
   while (nt < nlat && dyn_smem(nlon, nlat, nt, mixed, elem, precond) > (size_t)smem_limit)
     nt = std::min(nlat, nt + sms);
   return nt;
@@ -439,6 +442,57 @@ size_t layout(ftgcr_handle* h, unsigned char* base, SolveDev<T>* sd) {
   return off;
 }
 
+// Face coefficients and line-preconditioner factorisation of a handle from the
+// cell-centred coefficient D (device pointer), enqueued on `st`: per-row
+// geometry on the host (libm), everything per element on the device.  Used
+// at create and whenever a handle is reused for new coefficients (serving).
+// Scratch is stream-ordered (cudaMallocAsync / cudaFreeAsync).
+template <typename T>
+int setup_coefficients(ftgcr_handle* h, const SolveDev<T>& sd, const double* Dd, cudaStream_t st) {
+  std::vector<double> geo;
+  {
+    std::vector<double> cx, cy, area;
+    row_geometry(h->nlon, h->nlat, cx, cy, area);
+    geo.insert(geo.end(), cx.begin(), cx.end());
+    geo.insert(geo.end(), cy.begin(), cy.end());
+    geo.insert(geo.end(), area.begin(), area.end());
+  }
+  const bool mixed = std::is_same<T, float>::value;
+  const size_t geo_bytes = align256(sizeof(double) * 3 * h->nlat);
+  const size_t tmp_bytes = mixed ? sizeof(double) * (4 * (size_t)h->N + 4 * h->nlat) : 0;
+  unsigned char* scratch = nullptr;
+  CK(cudaMallocAsync((void**)&scratch, geo_bytes + tmp_bytes, st));
+  double* dcx = (double*)scratch;
+  CK(cudaMemcpyAsync(dcx, geo.data(), sizeof(double) * 3 * h->nlat, cudaMemcpyHostToDevice, st));
+  k_face_coeffs<<<1024, 256, 0, st>>>(h->nlon, h->nlat, Dd, dcx, dcx + h->nlat, dcx + 2 * h->nlat, h->mu, h->Tx64,
+                                      h->Ty64, h->muA64, mixed ? (float*)sd.Tx : nullptr,
+                                      mixed ? (float*)sd.Ty : nullptr, mixed ? (float*)sd.muA : nullptr);
+  CK(cudaGetLastError());
+  // FP64 factors: into the handle (FP64 path) or scratch (mixed path)
+  double *l64, *w64, *u64, *z64, *r64;
+  if (!mixed) {
+    l64 = (double*)sd.lc;
+    w64 = (double*)sd.lw;
+    u64 = (double*)sd.lu;
+    z64 = (double*)sd.lz;
+    r64 = (double*)sd.lrow;
+  } else {
+    double* tmp = (double*)(scratch + geo_bytes);
+    l64 = tmp;
+    w64 = tmp + h->N;
+    u64 = tmp + 2 * h->N;
+    z64 = tmp + 3 * h->N;
+    r64 = tmp + 4 * h->N;
+  }
+  k_line_factor<<<(h->nlat + 63) / 64, 64, 0, st>>>(h->nlon, h->nlat, h->C, h->precond, h->Tx64, h->Ty64, h->muA64,
+                                                    l64, w64, u64, z64, r64, mixed ? (float*)sd.lc : nullptr,
+                                                    mixed ? (float*)sd.lw : nullptr, mixed ? (float*)sd.lz : nullptr,
+                                                    mixed ? (float*)sd.lrow : nullptr);
+  CK(cudaGetLastError());
+  CK(cudaFreeAsync(scratch, st));
+  return FTGCR_OK;
+}
+
 template <typename T>
 int create_impl(ftgcr_handle* h, const double* D_host_or_dev, bool D_on_device) {
   SolveDev<T> sd{};
@@ -468,52 +522,19 @@ int create_impl(ftgcr_handle* h, const double* D_host_or_dev, bool D_on_device) 
   sd.Ty64 = h->Ty64;
   sd.muA64 = h->muA64;
 
-  // geometry (host) + face coefficients and factorisation (device)
-  std::vector<double> cx, cy, area;
-  row_geometry(h->nlon, h->nlat, cx, cy, area);
-  double *dcx = nullptr, *dD = nullptr;
-  CK(cudaMalloc(&dcx, sizeof(double) * 3 * h->nlat));
-  CK(cudaMemcpy(dcx, cx.data(), sizeof(double) * h->nlat, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(dcx + h->nlat, cy.data(), sizeof(double) * h->nlat, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(dcx + 2 * h->nlat, area.data(), sizeof(double) * h->nlat, cudaMemcpyHostToDevice));
+  // face coefficients and factorisation (device)
+  double* dD = nullptr;
   const double* Dd = D_host_or_dev;
   if (!D_on_device) {
     CK(cudaMalloc(&dD, sizeof(double) * h->N));
     CK(cudaMemcpy(dD, D_host_or_dev, sizeof(double) * h->N, cudaMemcpyHostToDevice));
     Dd = dD;
   }
-  const bool mixed = std::is_same<T, float>::value;
-  k_face_coeffs<<<1024, 256>>>(h->nlon, h->nlat, Dd, dcx, dcx + h->nlat, dcx + 2 * h->nlat, h->mu, h->Tx64, h->Ty64,
-                               h->muA64, mixed ? (float*)sd.Tx : nullptr, mixed ? (float*)sd.Ty : nullptr,
-                               mixed ? (float*)sd.muA : nullptr);
-  CK(cudaGetLastError());
-  {
-    // FP64 factors: into the handle (FP64 path) or scratch (mixed path)
-    double *l64 = nullptr, *w64 = nullptr, *u64 = nullptr, *z64 = nullptr, *r64 = nullptr, *tmp = nullptr;
-    if (!mixed) {
-      l64 = (double*)sd.lc;
-      w64 = (double*)sd.lw;
-      u64 = (double*)sd.lu;
-      z64 = (double*)sd.lz;
-      r64 = (double*)sd.lrow;
-    } else {
-      CK(cudaMalloc(&tmp, sizeof(double) * (4 * (size_t)h->N + 4 * h->nlat)));
-      l64 = tmp;
-      w64 = tmp + h->N;
-      u64 = tmp + 2 * h->N;
-      z64 = tmp + 3 * h->N;
-      r64 = tmp + 4 * h->N;
-    }
-    k_line_factor<<<(h->nlat + 63) / 64, 64>>>(h->nlon, h->nlat, h->C, h->precond, h->Tx64, h->Ty64, h->muA64, l64,
-                                               w64, u64, z64, r64, mixed ? (float*)sd.lc : nullptr,
-                                               mixed ? (float*)sd.lw : nullptr, mixed ? (float*)sd.lz : nullptr,
-                                               mixed ? (float*)sd.lrow : nullptr);
-    CK(cudaGetLastError());
-    CK(cudaDeviceSynchronize());
-    if (tmp) cudaFree(tmp);
-  }
-  cudaFree(dcx);
+  int src = setup_coefficients<T>(h, sd, Dd, nullptr);
+  if (src) return src;
+  CK(cudaDeviceSynchronize());
   if (dD) cudaFree(dD);
+  const bool mixed = std::is_same<T, float>::value;
 
   CK(cudaMemcpy(h->sdev, &sd, sizeof sd, cudaMemcpyHostToDevice));
   void* sp = h->sdev;
@@ -583,12 +604,13 @@ void trace_dump(int grid) {
   cudaMemcpy(h.data(), t.d, h.size() * sizeof(TraceEnt), cudaMemcpyDeviceToHost);
   FILE* f = fopen(t.path, "w");
   if (!f) return;
-  fprintf(f, "round,cta,kind,items,t0,t1,t2,t3\n");
+  fprintf(f, "round,cta,kind,items,t0,t1,t2,t3,s0,s1,s2\n");
   for (int r = 0; r < t.rounds; ++r)
     for (int b = 0; b < grid; ++b) {
       const TraceEnt& e = h[(size_t)r * t.grid + b];
       if (e.t3 == 0) continue;
-      fprintf(f, "%d,%d,%d,%d,%llu,%llu,%llu,%llu\n", r, b, e.kind, e.items, e.t0, e.t1, e.t2, e.t3);
+      fprintf(f, "%d,%d,%d,%d,%llu,%llu,%llu,%llu,%llu,%llu,%llu\n", r, b, e.kind, e.items, e.t0, e.t1, e.t2, e.t3,
+              e.s0, e.s1, e.s2);
     }
   fclose(f);
 }

@@ -213,20 +213,42 @@ struct Acc<float> {
 };
 
 // Per-CTA partial sums: each warp contributes its DD sum of every value; the
-// CTA adds the warps' pairs in warp order and writes nv pairs to out.
+// CTA combines the warps' pairs in a fixed binary tree (depth 3 for 8 warps:
+// GB300's FP64 latency makes a serial chain expensive) and writes nv pairs.
+// FP64 path: double-double adds; FP32 path: each warp pair is first rounded to
+// one double, then plain FP64 adds.
 struct CtaRed {
   DD w[kWarps][kNPart];
 };
 __device__ __forceinline__ void cta_red_put(CtaRed& cr, int v, DD x) {
   if ((threadIdx.x & 31) == 0) cr.w[threadIdx.x >> 5][v] = x;
 }
+template <typename T>
 __device__ __forceinline__ void cta_red_finish(CtaRed& cr, int nv, double* out) {
   __syncthreads();
   if (threadIdx.x < nv) {
-    DD s = cr.w[0][threadIdx.x];
-    for (int w = 1; w < kWarps; ++w) s = dd_add(s, cr.w[w][threadIdx.x]);
-    out[2 * threadIdx.x] = s.hi;
-    out[2 * threadIdx.x + 1] = s.lo;
+    const int v = threadIdx.x;
+    if constexpr (sizeof(T) == 8) {
+      DD t[kWarps];
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) t[w] = cr.w[w][v];
+#pragma unroll
+      for (int h = 1; h < kWarps; h <<= 1)
+#pragma unroll
+        for (int w = 0; w + h < kWarps; w += 2 * h) t[w] = dd_add(t[w], t[w + h]);
+      out[2 * v] = t[0].hi;
+      out[2 * v + 1] = t[0].lo;
+    } else {
+      double t[kWarps];
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) t[w] = cr.w[w][v].hi + cr.w[w][v].lo;
+#pragma unroll
+      for (int h = 1; h < kWarps; h <<= 1)
+#pragma unroll
+        for (int w = 0; w + h < kWarps; w += 2 * h) t[w] = t[w] + t[w + h];
+      out[2 * v] = t[0];
+      out[2 * v + 1] = 0.0;
+    }
   }
 }
 
@@ -358,7 +380,7 @@ constexpr int kLB = 8;  // register block of the recurrences
 // last unknown is eliminated by bordering with the precomputed
 // z = A0^-1 (-Tx_{n-1} e_0 - Tx_{n-2} e_{n-2}).
 template <typename T>
-__device__ void line_solve_row(const SolveDev<T>& sd, int j, T* row, const LineConsts<T> lc) {
+__device__ __noinline__ void line_solve_row(const SolveDev<T>& sd, int j, T* row, const LineConsts<T> lc) {
   const int lane = threadIdx.x & 31;
   const int n = sd.nlon, m = n - 1, C = sd.C;
   const int i0 = lane * C;
@@ -503,7 +525,7 @@ __device__ void line_solve_row(const SolveDev<T>& sd, int j, T* row, const LineC
 // Tx_{n-1} y_0 + Tx_{n-2} y_{m-1}) / delta, x_i = y_i - x_{n-1} z_i; b = -r.
 // Bitwise reproducible against the oracle.  l, winv, u: the row's factors in
 // natural layout (shared or global memory).
-__device__ inline void line_solve_row_seq(const SolveDev<double>& sd, int j, double* row, const double* l,
+static __device__ __noinline__ void line_solve_row_seq(const SolveDev<double>& sd, int j, double* row, const double* l,
                                    const double* winv, const double* u) {
   const int n = sd.nlon, m = n - 1;
   double y = -row[sk(0)];

@@ -67,6 +67,7 @@ struct LaunchCtl {
 // the grid barrier, plus the phase kind of the CTA's first item.
 struct TraceEnt {
   unsigned long long t0, t1, t2, t3;
+  unsigned long long s0, s1, s2;  // sub-phase marks of the first item (PA: axpy, line solve, stencil)
   int kind, items;
 };
 
@@ -141,29 +142,38 @@ constexpr unsigned kStateVecs = (1u << V_X) | (1u << V_R) | (1u << V_P) | (1u <<
 // solve gets bitwise the same numbers.
 template <typename T>
 __device__ __forceinline__ void reduce_partials(const double* part, int nt, int nv, double* red) {
-  constexpr int B = 4;  // tiles loaded per batch per lane
+  constexpr int B = 8;  // tiles loaded per batch per lane, summed in a binary tree
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int v = warp; v < nv; v += kWarps) {
     DD acc{0.0, 0.0};
     double acc1 = 0.0;
     for (int t0 = lane; t0 < nt; t0 += 32 * B) {
-      double hv[B], lv[B];
+      DD tv[B];
 #pragma unroll
       for (int q = 0; q < B; ++q) {
         const int tau = t0 + 32 * q;
+        tv[q] = DD{0.0, 0.0};
         if (tau < nt) {
-          hv[q] = __ldcg(part + (long long)tau * kPartStride + 2 * v);
-          lv[q] = __ldcg(part + (long long)tau * kPartStride + 2 * v + 1);
+          tv[q].hi = __ldcg(part + (long long)tau * kPartStride + 2 * v);
+          tv[q].lo = __ldcg(part + (long long)tau * kPartStride + 2 * v + 1);
         }
       }
+      if constexpr (sizeof(T) == 8) {
 #pragma unroll
-      for (int q = 0; q < B; ++q)
-        if (t0 + 32 * q < nt) {
-          if constexpr (sizeof(T) == 8)
-            acc = dd_add(acc, DD{hv[q], lv[q]});
-          else
-            acc1 += hv[q] + lv[q];
-        }
+        for (int h = 1; h < B; h <<= 1)
+#pragma unroll
+          for (int q = 0; q + h < B; q += 2 * h) tv[q] = dd_add(tv[q], tv[q + h]);
+        acc = dd_add(acc, tv[0]);
+      } else {
+        double t[B];
+#pragma unroll
+        for (int q = 0; q < B; ++q) t[q] = tv[q].hi + tv[q].lo;
+#pragma unroll
+        for (int h = 1; h < B; h <<= 1)
+#pragma unroll
+          for (int q = 0; q + h < B; q += 2 * h) t[q] = t[q] + t[q + h];
+        acc1 = acc1 + t[0];
+      }
     }
     if constexpr (sizeof(T) == 8) {
 #pragma unroll
@@ -174,6 +184,24 @@ __device__ __forceinline__ void reduce_partials(const double* part, int nt, int 
       acc1 = warp_sum(acc1);
       if (lane == 0) red[v] = acc1;
     }
+  }
+}
+
+// The divisions a transition may need (beta of the next step, alpha_l of the
+// accepted one), computed speculatively in parallel lanes of warp 0 after the
+// reduction: a GB300 FP64 division has a latency of several hundred cycles.
+// Identical operands and operation to the serial form, so identical values.
+__device__ __forceinline__ void precompute_divisions(const SolveState& S, const double* red, double* qd) {
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    double q = 0.0;
+    if (lane < kMaxK) {
+      if (S.pending == K_PA && lane <= S.nu) q = -red[1 + lane] / S.lpn2[lane];  // alpha_lane
+    } else if (lane == kMaxK) {
+      if (S.pending == K_INIT) q = -red[2] / red[3];  // first beta
+      if (S.pending == K_PB || S.pending == K_RESTORE) q = -red[0] / red[1];  // next beta
+    }
+    qd[lane] = q;
   }
 }
 
@@ -211,7 +239,8 @@ __device__ __forceinline__ int part_count(int kind, int nu) {
 // The per-solve state machine: consumes the reduced partial sums of the phase
 // that ran last round (S.pending) and decides this round's phase.  Thread 0.
 template <typename T>
-__device__ __noinline__ void transition(const SolveDev<T>& sd, const SolveState& S, const double* red, SolveState& N, Ctx<T>& c) {
+__device__ __noinline__ void transition(const SolveDev<T>& sd, const SolveState& S, const double* red, const double* qd,
+                                       SolveState& N, Ctx<T>& c) {
   N = S;
   memset(&c, 0, sizeof c);  // every pointer a phase may test starts out null
   c.kind = K_NONE;
@@ -341,7 +370,7 @@ __device__ __noinline__ void transition(const SolveDev<T>& sd, const SolveState&
         }
       } else {
         N.finj += count_faults(sd, S.step + 1, kStateVecs);
-        N.beta = -red[2] / red[3];
+        N.beta = qd[kMaxK];  // -red[2] / red[3]
         N.lpn2[0] = red[3];
         c.kind = K_PA;
       }
@@ -410,7 +439,7 @@ __device__ __noinline__ void transition(const SolveDev<T>& sd, const SolveState&
         N.phiC = S.phiW;
         N.rC = S.rW;
         for (int l = 0; l < kMaxK; ++l)
-          if (l <= S.nu) c.alpha[l] = (T)(-red[1 + l] / S.lpn2[l]);
+          if (l <= S.nu) c.alpha[l] = (T)qd[l];  // -red[1 + l] / S.lpn2[l]
         if (t >= sd.max_steps) {
           if (!sd.mixed) {
             N.status = ST_NOT_CONVERGED;
@@ -442,7 +471,7 @@ __device__ __noinline__ void transition(const SolveDev<T>& sd, const SolveState&
     case K_PB:
     case K_RESTORE:
       N.finj = S.finj + count_faults(sd, S.step + 1, kStateVecs);
-      N.beta = -red[0] / red[1];
+      N.beta = qd[kMaxK];  // -red[0] / red[1]
       N.lpn2[S.nu] = red[1];
       c.kind = K_PA;
       break;
@@ -518,11 +547,17 @@ __device__ __noinline__ void transition(const SolveDev<T>& sd, const SolveState&
 
 // ------------------------------------------------------------ phases
 struct PhaseSmem {
+  int cs_solve, cs_tile;  // (solve, tile) whose line-solve constants sit in shared memory
   FlipEnt fl[kMaxFaults];
   FlipEnt pt[kMaxFaults];
   int nfl, npt;
   CtaRed cr;
+  unsigned long long sub[3];  // sub-phase timestamps (trace only)
+  int tracing;
 };
+__device__ __forceinline__ void sub_mark(PhaseSmem& ps, int q) {
+  if (ps.tracing && threadIdx.x == 0) ps.sub[q] = globaltimer();
+}
 
 // Line-solve constants of rows [h0, h1) staged into shared memory by
 // asynchronous 16-byte copies (cp.async; waited for before the solves): three
@@ -641,7 +676,8 @@ __device__ __forceinline__ RowVec row_vec(int idx, int nvr, int j0, int nlon, in
 // PA: axpy, norm, preconditioner, operator, orthogonalisation dots.  KB is a
 // compile-time bound on the number of directions (k <= KB).
 template <typename T, int KB>
-__device__ __forceinline__ void phase_pa(const SolveDev<T>& sd, const Ctx<T>& c, int tau, T* sm, PhaseSmem& ps, double* part_out) {
+__device__ __forceinline__ void phase_pa(const SolveDev<T>& sd, const Ctx<T>& c, int sidx, int tau, T* sm, PhaseSmem& ps,
+                                         double* part_out) {
   constexpr int W = V16<T>::W;
   constexpr int U = 2;
   const int nlon = sd.nlon, nlat = sd.nlat, stride = row_stride(nlon);
@@ -650,7 +686,8 @@ __device__ __forceinline__ void phase_pa(const SolveDev<T>& sd, const Ctx<T>& c,
   const int warp = threadIdx.x >> 5;
   const T beta = c.beta;
   T* cs = sm + (long long)(sd.nt_hmax + 2) * stride;
-  stage_line_consts(sd, rt.h0, rt.h1, cs);
+  // a CTA that keeps the same tile keeps its staged constants (single solves)
+  if (!(ps.cs_solve == sidx && ps.cs_tile == tau)) stage_line_consts(sd, rt.h0, rt.h1, cs);
   if (threadIdx.x == 0)
     ps.nfl = collect_flips(sd, c.t, 1u << V_E, (long long)rt.h0 * nlon, (long long)rt.h1 * nlon, ps.fl);
   Acc<T> an;
@@ -715,9 +752,11 @@ __device__ __forceinline__ void phase_pa(const SolveDev<T>& sd, const Ctx<T>& c,
   }
   cp_async_wait_all();
   __syncthreads();
+  sub_mark(ps, 0);
   for (int jr = warp; jr < nrows; jr += kWarps)
     precond_row(sd, rt.h0 + jr, sm + jr * stride, staged_consts(sd, cs, nrows, jr));
   __syncthreads();
+  sub_mark(ps, 1);
   if (threadIdx.x == 0) {
     for (int q = 0; q < ps.nfl; ++q) {  // e-site flips (the paper's injection site)
       const long long g = ps.fl[q].g;
@@ -780,11 +819,16 @@ __device__ __forceinline__ void phase_pa(const SolveDev<T>& sd, const Ctx<T>& c,
       }
     }
   }
+  sub_mark(ps, 2);
   cta_red_put(ps.cr, 0, an.warp_sum());
 #pragma unroll
   for (int l = 0; l < KB; ++l)
     if (l <= c.nu) cta_red_put(ps.cr, 1 + l, ad[l].warp_sum());
-  cta_red_finish(ps.cr, 2 + c.nu, part_out);
+  cta_red_finish<T>(ps.cr, 2 + c.nu, part_out);
+  if (threadIdx.x == 0) {
+    ps.cs_solve = sidx;
+    ps.cs_tile = tau;
+  }
 }
 
 // PB: direction recurrences and the dots for the next beta.
@@ -880,7 +924,7 @@ __device__ __forceinline__ void phase_pb(const SolveDev<T>& sd, const Ctx<T>& c,
   }
   cta_red_put(ps.cr, 0, a0.warp_sum());
   cta_red_put(ps.cr, 1, a1.warp_sum());
-  cta_red_finish(ps.cr, 2, part_out);
+  cta_red_finish<T>(ps.cr, 2, part_out);
 }
 
 // RESTORE: [phi, r, p, L(p)]^0 <- [phi, r, p, L(p)]^* by copy (the backup
@@ -918,7 +962,7 @@ __device__ __forceinline__ void phase_restore(const SolveDev<T>& sd, const Ctx<T
   }
   cta_red_put(ps.cr, 0, a0.warp_sum());
   cta_red_put(ps.cr, 1, a1.warp_sum());
-  cta_red_finish(ps.cr, 2, part_out);
+  cta_red_finish<T>(ps.cr, 2, part_out);
 }
 
 // INIT: r0 = L(phi0) - R (FP64 path, phi0 = x0) or r0 = -R_in (mixed inner
@@ -926,7 +970,7 @@ __device__ __forceinline__ void phase_restore(const SolveDev<T>& sd, const Ctx<T
 // beta dots.  The x/r/p/Ap flips of the first step are applied to the working
 // vectors, and their clean values kept so that the backup stays clean.
 template <typename T>
-__device__ __forceinline__ void phase_init(const SolveDev<T>& sd, const Ctx<T>& c, int tau, T* sm, PhaseSmem& ps,
+__device__ __forceinline__ void phase_init(const SolveDev<T>& sd, const Ctx<T>& c, int sidx, int tau, T* sm, PhaseSmem& ps,
                            double* part_out) {
   const int nlon = sd.nlon, nlat = sd.nlat, stride = row_stride(nlon);
   const RowTile rt = row_tile(nlat, sd.nt, tau);
@@ -934,7 +978,7 @@ __device__ __forceinline__ void phase_init(const SolveDev<T>& sd, const Ctx<T>& 
   if (threadIdx.x == 0)
     ps.nfl = collect_flips(sd, c.t, kStateVecs, (long long)rt.j0 * nlon, (long long)rt.j1 * nlon, ps.fl);
   T* cs = sm + (long long)(sd.nt_hmax + 2) * stride;
-  stage_line_consts(sd, rt.h0, rt.h1, cs);
+  if (!(ps.cs_solve == sidx && ps.cs_tile == tau)) stage_line_consts(sd, rt.h0, rt.h1, cs);
   __syncthreads();
   const int nfl = ps.nfl;
   Acc<T> an, aR;
@@ -1009,7 +1053,11 @@ __device__ __forceinline__ void phase_init(const SolveDev<T>& sd, const Ctx<T>& 
   cta_red_put(ps.cr, 1, aR.warp_sum());
   cta_red_put(ps.cr, 2, a0.warp_sum());
   cta_red_put(ps.cr, 3, a1.warp_sum());
-  cta_red_finish(ps.cr, 4, part_out);
+  cta_red_finish<T>(ps.cr, 4, part_out);
+  if (threadIdx.x == 0) {
+    ps.cs_solve = sidx;
+    ps.cs_tile = tau;
+  }
 }
 
 // OUT (mixed): x' = x + d in FP64, r_out = R - L64(x'), ||r_out||^2 (and
@@ -1019,6 +1067,7 @@ __device__ __forceinline__ void phase_out(const SolveDev<T>& sd, const Ctx<T>& c
                           double* part_out) {
   const int nlon = sd.nlon, nlat = sd.nlat, stride = row_stride(nlon);
   const RowTile rt = row_tile(nlat, sd.nt, tau);
+  if (threadIdx.x == 0) ps.cs_solve = -1;  // its FP64 rows overwrite the staged constants
   for (int j = rt.h0; j < rt.h1; ++j) {
     const bool own = (j >= rt.j0 && j < rt.j1);
     double* row = smd + (j - rt.h0) * stride;
@@ -1055,7 +1104,7 @@ __device__ __forceinline__ void phase_out(const SolveDev<T>& sd, const Ctx<T>& c
   }
   cta_red_put(ps.cr, 0, so.warp_sum());
   cta_red_put(ps.cr, 1, sR.warp_sum());
-  cta_red_finish(ps.cr, 2, part_out);
+  cta_red_finish<T>(ps.cr, 2, part_out);
 }
 
 // FIN: write the solution to the caller's x and (FP64 path) the true
@@ -1100,7 +1149,7 @@ __device__ __forceinline__ void phase_fin(const SolveDev<T>& sd, const Ctx<T>& c
     }
   }
   cta_red_put(ps.cr, 0, acc.warp_sum());
-  cta_red_finish(ps.cr, 1, part_out);
+  cta_red_finish<T>(ps.cr, 1, part_out);
 }
 
 // ------------------------------------------------------------ the kernel
@@ -1129,6 +1178,7 @@ struct KernelSmem {
   Ctx<T> c;
   PhaseSmem ps;
   double red[kNPart];
+  double qd[32];
   int prefix[kMaxBatch + 1];
   int bail;
 };
@@ -1146,6 +1196,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ftgcr_persistent(BatchArgs<T> a
   const unsigned long long t_start = globaltimer();
   unsigned int nbar = 0;
   int cur_sd = -1;  // solve whose descriptor sits in shared memory
+  if (threadIdx.x == 0) ks.ps.cs_solve = -1;
   int it = 0;
   for (; it < a.max_rounds; ++it) {
     // watchdog: a kernel that runs far longer than any solve raises the error
@@ -1175,6 +1226,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_ftgcr_persistent(BatchArgs<T> a
     unsigned long long tr[3] = {0ull, 0ull, 0ull};
     int tr_kind = -1, tr_items = 0;
     if (a.trace && threadIdx.x == 0) tr[0] = globaltimer();
+    if (threadIdx.x == 0) {
+      ks.ps.tracing = a.trace != nullptr;
+      ks.ps.sub[0] = ks.ps.sub[1] = ks.ps.sub[2] = 0ull;
+    }
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
       int lo = 0, hi = a.n - 1;  // last s with prefix[s] <= item and nt > 0
       while (lo < hi) {
@@ -1195,7 +1250,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_ftgcr_persistent(BatchArgs<T> a
         reduce_partials<T>(ks.sd.part + (long long)(par ^ 1) * ks.sd.nt * kPartStride, ks.sd.nt,
                            ks.sd.k + 1 > 4 ? ks.sd.k + 1 : 4, ks.red);
         __syncthreads();
-        if (threadIdx.x == 0) transition(ks.sd, ks.S, ks.red, ks.N, ks.c);
+        precompute_divisions(ks.S, ks.red, ks.qd);
+        __syncthreads();
+        if (threadIdx.x == 0) transition(ks.sd, ks.S, ks.red, ks.qd, ks.N, ks.c);
         __syncthreads();
         cur = s;
       }
@@ -1211,8 +1268,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_ftgcr_persistent(BatchArgs<T> a
       }
       double* part_out = ks.sd.part + ((long long)par * ks.sd.nt + tau) * kPartStride;
       switch (ks.c.kind) {
-        case K_INIT: phase_init(ks.sd, ks.c, tau, sm, ks.ps, part_out); break;
-        case K_PA: phase_pa<T, KB>(ks.sd, ks.c, tau, sm, ks.ps, part_out); break;
+        case K_INIT: phase_init(ks.sd, ks.c, s, tau, sm, ks.ps, part_out); break;
+        case K_PA: phase_pa<T, KB>(ks.sd, ks.c, s, tau, sm, ks.ps, part_out); break;
         case K_PB: phase_pb<T, KB>(ks.sd, ks.c, tau, ks.ps, part_out); break;
         case K_RESTORE: phase_restore(ks.sd, ks.c, tau, ks.ps, part_out); break;
         case K_OUT: phase_out(ks.sd, ks.c, tau, smd, ks.ps, part_out); break;
@@ -1237,6 +1294,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_ftgcr_persistent(BatchArgs<T> a
       e.t1 = tr[1];
       e.t2 = tr[2];
       e.t3 = globaltimer();
+      e.s0 = ks.ps.sub[0];
+      e.s1 = ks.ps.sub[1];
+      e.s2 = ks.ps.sub[2];
       e.kind = tr_kind;
       e.items = tr_items;
       a.trace[(long long)it * gridDim.x + blockIdx.x] = e;
