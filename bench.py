@@ -192,6 +192,156 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ batch and serving mixes
+def bench_batch(torch, ftgcr, dev, n=128, seed=42, reps=3):
+    """128 independent mixed-precision solves of sizes U{128x64, 256x128,
+    512x256, 1024x512} (hills: centre, height and width drawn per solve) in
+    ONE persistent launch, against the same solves launched one by one."""
+    sizes = inputs.batch_sizes(seed, n)
+    solvers, Rs, xs = [], [], []
+    for q, (nlon, nlat) in enumerate(sizes):
+        p = inputs.hill_problem(nlon, nlat, **inputs.random_hill(seed * 1000 + q))
+        solvers.append(ftgcr.Solver(p.D, p.mu, k=K, tol=TOL, precision="mixed"))
+        Rs.append(torch.from_numpy(p.R).to(dev))
+        xs.append(torch.zeros_like(Rs[-1]))
+    stream = torch.cuda.current_stream()
+    alone_ms, alone_x = [], []
+    for s, R, x in zip(solvers, Rs, xs):
+        s.solve_async(R, x, stream=stream)  # warm
+        x.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s.solve_async(R, x, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        alone_ms.append(a.elapsed_time(b))
+        alone_x.append(x.clone())
+    times = []
+    for rep in range(reps + 1):
+        for x in xs:
+            x.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ftgcr.solve_batch(solvers, Rs, xs, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if rep:
+            times.append(a.elapsed_time(b))
+    same = all(bool(torch.equal(x, y)) for x, y in zip(xs, alone_x))
+    steps = sum(s.stats()["steps"] for s in solvers)
+    for s in solvers:
+        s.close()
+    ms = float(np.median(times))
+    return {"solves": n, "sizes": "U{128x64,256x128,512x256,1024x512}", "seed": seed, "precision": "mixed",
+            "launch_ms": ms, "solves_per_s": n * 1e3 / ms, "iters_per_s": steps * 1e3 / ms,
+            "sequential_ms": float(np.sum(alone_ms)), "speedup_vs_sequential": float(np.sum(alone_ms)) / ms,
+            "bitwise_equal_to_alone": same}
+
+
+def bench_serving(torch, ftgcr, dev, n_req=2000, load=0.8, seed=7, hills_per_size=4, n_cap=300):
+    """Open-loop serving: n_req requests with Poisson arrivals at `load` x the
+    measured capacity; sizes U{256x128, 512x256, 1024x512, 2048x1024}, mixed
+    precision, hills drawn per problem, 1% carrying one bit flip.  Right-hand
+    side and solution in host memory, coefficients resident on the device;
+    latency = arrival -> solution on the host."""
+    import threading
+
+    sizes = [(256, 128), (512, 256), (1024, 512), (2048, 1024)]
+    probs = []
+    for si, (nlon, nlat) in enumerate(sizes):
+        for hq in range(hills_per_size):
+            p = inputs.hill_problem(nlon, nlat, **inputs.random_hill(seed * 100 + si * 10 + hq))
+            probs.append((p, torch.from_numpy(p.D).to(dev)))
+    g = inputs.SplitMix64(seed)
+    reqs = []
+    for i in range(max(n_req, n_cap)):
+        pi = g.below(len(sizes)) * hills_per_size + g.below(hills_per_size)
+        faults = ()
+        if g.below(100) == 0:
+            N = probs[pi][0].R.size
+            faults = [inputs.sweep_flip(seed, i, 10, N, nbits=32, vecs=("r", "ap"))]
+        reqs.append((pi, faults))
+
+    def submit(srv, i):
+        pi, faults = reqs[i]
+        p, Dd = probs[pi]
+        x = np.zeros_like(p.R)
+        return srv.submit(Dd, p.mu, p.R, x, k=K, tol=TOL, precision="mixed", faults=faults), x
+
+    with ftgcr.Server(max_slots=64, epoch_rounds=24) as srv:
+        for pi in range(len(probs)):  # create every shape's handle once
+            srv.submit(probs[pi][1], probs[pi][0].mu, probs[pi][0].R, np.zeros_like(probs[pi][0].R), k=K, tol=TOL,
+                       precision="mixed")
+        for _ in probs:
+            srv.next()
+        # capacity: closed loop, everything queued at once
+        t0 = time.perf_counter()
+        for i in range(n_cap):
+            submit(srv, i)
+        for i in range(n_cap):
+            srv.next()
+        cap = n_cap / (time.perf_counter() - t0)
+        # open loop
+        arr = inputs.poisson_arrivals(seed, n_req, load * cap)
+        sample = set(range(0, n_req, max(1, n_req // 8)))  # solutions kept for the equality check
+        t_arr, xs, lat = {}, {}, []
+        lock = threading.Lock()
+        start = time.perf_counter()
+
+        def producer():
+            for i in range(n_req):
+                d = start + arr[i] - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                ta = time.perf_counter()
+                t, x = submit(srv, i)
+                with lock:
+                    t_arr[t] = ta
+                    if i in sample:
+                        xs[t] = (i, x)
+
+        th = threading.Thread(target=producer)
+        th.start()
+        done, results = 0, {}
+        while done < n_req:
+            r = srv.next(timeout=30)
+            if r is None:
+                break
+            now = time.perf_counter()
+            t, st, ss = r
+            with lock:
+                ta = t_arr.get(t)
+            while ta is None:  # the producer has not recorded it yet
+                time.sleep(1e-5)
+                with lock:
+                    ta = t_arr.get(t)
+            lat.append(now - ta)
+            results[t] = (st, ss)
+            done += 1
+        th.join()
+        wall = time.perf_counter() - start
+        info = srv.info()
+    # a sample of served results against the same request solved alone
+    same = True
+    for t in sorted(xs):
+        i, x = xs[t]
+        pi, faults = reqs[i]
+        p = probs[pi][0]
+        with ftgcr.Solver(p.D, p.mu, k=K, tol=TOL, precision="mixed") as s:
+            xa = np.zeros_like(p.R)
+            s.solve(p.R, xa, faults=faults)
+        same = same and np.array_equal(x, xa)
+    ok = sum(1 for st, _ in results.values() if st == 0)
+    lat_ms = 1e3 * np.array(lat)
+    return {"requests": n_req, "completed_ok": ok, "load": load, "capacity_solves_per_s": cap,
+            "offered_per_s": load * cap, "achieved_solves_per_s": n_req / wall,
+            "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
+                           "max": float(lat_ms.max())},
+            "faulty_requests": sum(1 for _, f in reqs[:n_req] if f), "epochs": info["epochs"],
+            "handles": info["handles"], "sizes": "U{256x128,512x256,1024x512,2048x1024}", "precision": "mixed",
+            "io": "rhs and x in host memory, D resident", "bitwise_equal_to_alone_sample": same}
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_ours(args):
     import torch
@@ -305,6 +455,10 @@ def run_ours(args):
             "gpu_launches": 2 * args.steps,
             "clocks": clocks,
         }
+        if not args.no_batch and ws == 1:
+            line["batch"] = bench_batch(torch, ftgcr, dev)
+        if not args.no_serving and ws == 1:
+            line["serving"] = bench_serving(torch, ftgcr, dev, n_req=args.serving_requests, load=args.serving_load)
         if not args.no_cpu_baseline and ws == 1:
             cb = oracle_throughput()
             line["cpu_baseline"] = {"value": cb["value"], "unit": "solves/s", "cores": cb["cores"], "kind": "oracle",
@@ -326,6 +480,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 128-solve batched launch")
+    ap.add_argument("--no-serving", action="store_true", help="skip the open-loop serving run")
+    ap.add_argument("--serving-requests", type=int, default=2000)
+    ap.add_argument("--serving-load", type=float, default=0.8, help="arrival rate / measured capacity")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -49,6 +49,7 @@ extern "C" {
 #define FTGCR_ERR_TIMEOUT (-4)  /* an in-kernel grid barrier gave up waiting */
 #define FTGCR_ERR_BUDGET (-5)   /* serving: request larger than the memory budget */
 #define FTGCR_ERR_STATE (-6)    /* call out of order (e.g. stats before any solve) */
+#define FTGCR_PENDING 2         /* serving: the request has not finished yet */
 
 /* ---- precision of the iteration ---- */
 #define FTGCR_FP64 0  /* every vector, stencil, preconditioner and reduction in FP64 */
@@ -168,6 +169,15 @@ int ftgcr_apply_operator(ftgcr_handle* h, const double* in, double* out, void* s
  * (Algorithm 1, e = P^-1(r)). */
 int ftgcr_apply_precond(ftgcr_handle* h, const double* in, double* out, void* stream);
 
+/* Replace the coefficient field of an existing handle: rebuild the face
+ * coefficients and the preconditioner factorisation from D (same grid, mu,
+ * k and tol), as ftgcr_create does, without reallocating anything.  D:
+ * [N] FP64, host or device; a host D is read before the call returns, a
+ * device D must stay valid until `stream` has passed this call.  Must not
+ * overlap a solve of h.  Errors: FTGCR_ERR_ARG (non-finite or non-positive
+ * host D), FTGCR_ERR_CUDA. */
+int ftgcr_set_coeffs(ftgcr_handle* h, const ftgcr_coeffs* coeffs, void* stream);
+
 /* Device bytes a handle for this grid would hold (admission control). */
 int64_t ftgcr_footprint(const ftgcr_grid* grid, int32_t k);
 
@@ -198,6 +208,69 @@ const char* ftgcr_error_string(int status);
 #define FTGCR_NOALLOC_SCRATCH_BYTES (6 * 1024 * 1024)
 int ftgcr_solve_noalloc(const ftgcr_grid* grid, const double* D, int32_t k, double tol, const double* rhs, double* x,
                         ftgcr_stats_t* stats, void* stream);
+
+/* ---- serving: continuous batching of independent solves ----
+ * The paper solves one elliptic problem per model time step (Section 2); a
+ * server runs many such requests at once.  It owns a scheduler thread, a
+ * CUDA stream, a pool of solver handles and two tables of max_slots solve
+ * slots (one per precision).  Each epoch it admits queued requests (first
+ * come, first served) while a slot of the request's precision is free and its
+ * handle fits the budget, then runs every running solve for at most
+ * epoch_rounds rounds of one persistent launch, and hands back the solves
+ * that finished.  Unfinished solves resume in the next epoch beside the newly
+ * admitted ones.  Every result, statistics included, is bitwise the result
+ * of the same request solved alone with ftgcr_solve.
+ *  - Memory: a request is charged ftgcr_footprint(grid, k) while its handle is
+ *    held; idle handles are pooled by shape (grid, k, tol) and reused (their
+ *    coefficients are rebuilt from the new D), and evicted least recently used
+ *    first when a new shape does not fit.  budget_bytes = 0 means half of the
+ *    device memory free at creation.
+ *  - Pointers: D, rhs and x may be host or device memory and must stay valid,
+ *    and x untouched by the caller, until poll/wait reports the result.
+ *  - Thread safety: submit, poll, wait and info may be called from any
+ *    thread; destroy must not overlap any other call on the same server. */
+typedef struct ftgcr_server ftgcr_server;
+typedef struct {
+  int64_t submitted, completed, queued, running;
+  int64_t epochs;       /* persistent launches made */
+  int64_t handles;      /* handles held (running and pooled) */
+  int64_t bytes_in_use; /* their footprint */
+  int64_t budget_bytes;
+} ftgcr_server_info_t;
+
+/* Start a server on the current device.  max_slots: 1..1024 solves of each
+ * precision running at once; epoch_rounds >= 1 rounds per launch (an inner
+ * step takes two).  Errors: FTGCR_ERR_ARG, FTGCR_ERR_OOM, FTGCR_ERR_CUDA. */
+int ftgcr_server_create(int64_t budget_bytes, int32_t max_slots, int32_t epoch_rounds, ftgcr_server** out);
+
+/* Queue one solve of L(x) = rhs for the grid and coefficients given (as
+ * ftgcr_create + ftgcr_solve would).  plan: NULL or a fault plan (copied).
+ * *ticket identifies the request.  Errors: FTGCR_ERR_ARG (bad grid, k, tol,
+ * pointer or plan), FTGCR_ERR_BUDGET (footprint above the whole budget),
+ * FTGCR_ERR_STATE (server stopping). */
+int ftgcr_server_submit(ftgcr_server* srv, const ftgcr_grid* grid, const ftgcr_coeffs* coeffs, int32_t k, double tol,
+                        const double* rhs, double* x, const ftgcr_fault_plan* plan, int64_t* ticket);
+
+/* FTGCR_PENDING while the request runs; once it has finished, its status
+ * (as ftgcr_solve returns it) with *stats filled (stats may be NULL), after
+ * which the ticket is released.  FTGCR_ERR_ARG for an unknown ticket. */
+int ftgcr_server_poll(ftgcr_server* srv, int64_t ticket, ftgcr_stats_t* stats);
+
+/* Like poll, but blocks until the request finishes or timeout_s seconds pass
+ * (timeout_s < 0: no limit); FTGCR_PENDING on timeout. */
+int ftgcr_server_wait(ftgcr_server* srv, int64_t ticket, double timeout_s, ftgcr_stats_t* stats);
+
+/* Completion queue: the earliest-finished request not yet collected, with its
+ * ticket in *ticket, its status returned and *stats filled, as poll does;
+ * FTGCR_PENDING if none finishes within timeout_s seconds (timeout_s < 0: no
+ * limit, but FTGCR_ERR_STATE when no request is outstanding at all). */
+int ftgcr_server_next(ftgcr_server* srv, double timeout_s, int64_t* ticket, ftgcr_stats_t* stats);
+
+int ftgcr_server_info(ftgcr_server* srv, ftgcr_server_info_t* out);
+
+/* Stop: queued requests end with FTGCR_ERR_STATE, running ones finish; then
+ * every handle and buffer is freed. */
+int ftgcr_server_destroy(ftgcr_server* srv);
 
 #ifdef __cplusplus
 }

@@ -16,6 +16,7 @@
 #include "ftgcr_device.cuh"
 #include "ftgcr_phases.cuh"
 #include "ftgcr_instances.h"
+#include "ftgcr_serve.h"
 
 using namespace ftgcr;
 
@@ -201,8 +202,8 @@ __global__ void k_begin_solve(SolveDev<T>* sd, BeginArgs b, int* active, int n_a
     if (ctl) {
       ctl->counter = 0;
       ctl->err = 0;
-      ctl->round0 = 0;
-      ctl->round_end = 0;
+      ctl->round0 = par;
+      ctl->round_end = par;
     }
   }
   for (int q = threadIdx.x; q < b.nfaults; q += blockDim.x) const_cast<Fault*>(sd->faults)[q] = b.faults[q];
@@ -732,6 +733,59 @@ int solve_batch_impl(ftgcr_handle* const* hs, const double* const* rhs, double* 
   return FTGCR_OK;
 }
 
+// ------------------------------------------------------------ slot tables
+// The launch arrays of a resumable persistent launch, kept across launches:
+// per slot the solve descriptor and tile count, the double-buffered active
+// flags, and the control block whose round counter carries the round parity
+// from one launch to the next.
+struct SlotTableImpl {
+  int precision = 0, n = 0, dev = 0;
+  long long round = 0;  // index of the next round to run
+  unsigned char* buf = nullptr;
+  void** d_solves = nullptr;
+  int* d_nt = nullptr;
+  int* d_act = nullptr;
+  LaunchCtl* d_ctl = nullptr;
+  int* d_diag = nullptr;
+  LaunchCtl* h_ctl_in = nullptr;   // pinned: control block written before a launch
+  LaunchCtl* h_ctl_out = nullptr;  // pinned: control block read back after it
+  int* h_act = nullptr;            // pinned: active flags read back after it
+  int grid_cap = 0;
+  std::vector<ftgcr_handle*> slot;
+};
+
+template <typename T>
+int table_run_impl(SlotTableImpl* t, int max_rounds, cudaStream_t st) {
+  int kb = 4;
+  size_t smem = 1;
+  long long tiles = 0;
+  for (ftgcr_handle* h : t->slot)
+    if (h) {
+      kb = std::max(kb, kbound(h->k));
+      smem = std::max(smem, h->smem);
+      tiles += h->nt;
+    }
+  if (tiles == 0) return FTGCR_OK;
+  int rc = configure_kernel<T>(kb, smem);
+  if (rc) return rc;
+  int occ = 0;
+  rc = occupancy<T>(kb, smem, &occ);
+  if (rc) return rc;
+  if (occ < 1) return FTGCR_ERR_ARG;
+  const int grid = (int)std::min<long long>({tiles, (long long)device_info(t->dev).sms * occ, (long long)t->grid_cap});
+  t->h_ctl_in->counter = 0;
+  t->h_ctl_in->err = 0;
+  t->h_ctl_in->round0 = t->round;
+  t->h_ctl_in->round_end = t->round;
+  CK(cudaMemcpyAsync(t->d_ctl, t->h_ctl_in, sizeof(LaunchCtl), cudaMemcpyHostToDevice, st));
+  rc = launch_persistent<T>(kb, (SolveDev<T>* const*)t->d_solves, t->d_nt, t->d_act, t->n, t->d_ctl, t->d_diag,
+                            max_rounds, grid, smem, st);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(t->h_ctl_out, t->d_ctl, sizeof(LaunchCtl), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(t->h_act, t->d_act, sizeof(int) * 2 * t->n, cudaMemcpyDeviceToHost, st));
+  return FTGCR_OK;
+}
+
 void report_timeout(const ftgcr_handle* h) {
   std::vector<int> d((size_t)h->grid * 4);
   if (cudaMemcpy(d.data(), h->diag, d.size() * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return;
@@ -835,6 +889,26 @@ int ftgcr_create(const ftgcr_grid* grid, const ftgcr_coeffs* coeffs, int32_t k, 
   }
   *out = h;
   return FTGCR_OK;
+}
+
+int ftgcr_set_coeffs(ftgcr_handle* h, const ftgcr_coeffs* coeffs, void* stream) {
+  if (!h || !coeffs || !coeffs->D) return FTGCR_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool Ddev = is_device_ptr(coeffs->D);
+  const double* Dd = coeffs->D;
+  double* dD = nullptr;
+  if (!Ddev) {
+    for (long long i = 0; i < h->N; ++i)
+      if (!std::isfinite(coeffs->D[i]) || !(coeffs->D[i] > 0.0)) return FTGCR_ERR_ARG;
+    CK(cudaMallocAsync((void**)&dD, sizeof(double) * h->N, st));
+    CK(cudaMemcpyAsync(dD, coeffs->D, sizeof(double) * h->N, cudaMemcpyHostToDevice, st));
+    Dd = dD;
+  }
+  const int rc = h->precision == FTGCR_MIXED ? setup_coefficients<float>(h, h->sd32, Dd, st)
+                                             : setup_coefficients<double>(h, h->sd64, Dd, st);
+  if (dD) cudaFreeAsync(dD, st);
+  if (!Ddev) CK(cudaStreamSynchronize(st));  // the host array may be reused as soon as this returns
+  return rc;
 }
 
 int64_t ftgcr_footprint(const ftgcr_grid* grid, int32_t k) {
@@ -976,6 +1050,134 @@ void ftgcr_destroy(ftgcr_handle* h) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ slot tables (scheduler interface)
+namespace ftgcr {
+namespace serve {
+
+struct SlotTable : SlotTableImpl {};
+
+int table_create(int precision, int max_slots, SlotTable** out) {
+  if (!out || max_slots < 1 || max_slots > 1024 || (precision != FTGCR_FP64 && precision != FTGCR_MIXED))
+    return FTGCR_ERR_ARG;
+  SlotTable* t = new SlotTable();
+  t->precision = precision;
+  t->n = max_slots;
+  t->slot.assign(max_slots, nullptr);
+  CK(cudaGetDevice(&t->dev));
+  const DeviceInfo di = device_info(t->dev);
+  t->grid_cap = di.sms * 4;
+  const size_t b_solves = align256(sizeof(void*) * max_slots), b_nt = align256(sizeof(int) * max_slots),
+               b_act = align256(sizeof(int) * 2 * max_slots), b_ctl = align256(sizeof(LaunchCtl)),
+               b_diag = align256(sizeof(int) * 4 * t->grid_cap);
+  if (cudaMalloc(&t->buf, b_solves + b_nt + b_act + b_ctl + b_diag) != cudaSuccess) {
+    cudaGetLastError();
+    delete t;
+    return FTGCR_ERR_OOM;
+  }
+  t->d_solves = (void**)t->buf;
+  t->d_nt = (int*)(t->buf + b_solves);
+  t->d_act = (int*)(t->buf + b_solves + b_nt);
+  t->d_ctl = (LaunchCtl*)(t->buf + b_solves + b_nt + b_act);
+  t->d_diag = (int*)(t->buf + b_solves + b_nt + b_act + b_ctl);
+  int rc = cuda_status(cudaMemset(t->buf, 0, b_solves + b_nt + b_act + b_ctl + b_diag));
+  if (!rc) rc = cuda_status(cudaMallocHost(&t->h_ctl_in, sizeof(LaunchCtl)));
+  if (!rc) rc = cuda_status(cudaMallocHost(&t->h_ctl_out, sizeof(LaunchCtl)));
+  if (!rc) rc = cuda_status(cudaMallocHost(&t->h_act, sizeof(int) * 2 * max_slots));
+  if (rc) {
+    table_destroy(t);
+    return rc;
+  }
+  *out = t;
+  return FTGCR_OK;
+}
+
+void table_destroy(SlotTable* t) {
+  if (!t) return;
+  if (t->buf) cudaFree(t->buf);
+  if (t->h_ctl_in) cudaFreeHost(t->h_ctl_in);
+  if (t->h_ctl_out) cudaFreeHost(t->h_ctl_out);
+  if (t->h_act) cudaFreeHost(t->h_act);
+  delete t;
+}
+
+int table_begin(SlotTable* t, int slot, ftgcr_handle* h, const double* rhs, double* x, const ftgcr_fault_plan* plan,
+                cudaStream_t st) {
+  if (!t || !h || !rhs || !x || slot < 0 || slot >= t->n || t->slot[slot] || h->precision != t->precision)
+    return FTGCR_ERR_ARG;
+  for (ftgcr_handle* o : t->slot)
+    if (o == h) return FTGCR_ERR_ARG;  // one running solve per handle
+  int rc = validate_plan(h, plan);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(t->d_solves + slot, &h->sdev, sizeof(void*), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(t->d_nt + slot, &h->nt, sizeof(int), cudaMemcpyHostToDevice, st));
+  const BeginArgs b = begin_args(h, rhs, x, x, plan);
+  const int par = (int)(t->round & 1);
+  if (t->precision == FTGCR_MIXED)
+    k_begin_solve<float><<<1, 64, 0, st>>>((SolveDev<float>*)h->sdev, b, t->d_act, t->n, slot, par, nullptr);
+  else
+    k_begin_solve<double><<<1, 64, 0, st>>>((SolveDev<double>*)h->sdev, b, t->d_act, t->n, slot, par, nullptr);
+  CK(cudaGetLastError());
+  t->slot[slot] = h;
+  return FTGCR_OK;
+}
+
+int table_run(SlotTable* t, int max_rounds, cudaStream_t st) {
+  if (!t || max_rounds < 1) return FTGCR_ERR_ARG;
+  return t->precision == FTGCR_MIXED ? table_run_impl<float>(t, max_rounds, st)
+                                     : table_run_impl<double>(t, max_rounds, st);
+}
+
+int table_collect(SlotTable* t, cudaStream_t st, int* finished) {
+  if (!t || !finished) return FTGCR_ERR_ARG;
+  for (int s = 0; s < t->n; ++s) finished[s] = 0;
+  if (table_occupied(t) == 0) return FTGCR_OK;
+  CK(cudaStreamSynchronize(st));
+  const int err = t->h_ctl_out->err;
+  t->round = t->h_ctl_out->round_end;
+  const int par = (int)(t->round & 1);
+  for (int s = 0; s < t->n; ++s) {
+    ftgcr_handle* h = t->slot[s];
+    if (!h) continue;
+    if (!err && t->h_act[par * t->n + s]) continue;
+    CK(cudaMemcpy(h->h_result, h->result, sizeof(SolveState), cudaMemcpyDeviceToHost));
+    *h->h_ctl = *t->h_ctl_out;
+    h->last_stream = st;
+    h->solved = 1;
+    h->last_status = err ? FTGCR_ERR_TIMEOUT : status_from_result(h);
+    finished[s] = 1;
+    t->slot[s] = nullptr;
+  }
+  if (err) {
+    // the launch is abandoned: its solves' state is not resumable, and the
+    // next launch starts from a clean table
+    CK(cudaMemsetAsync(t->d_act, 0, sizeof(int) * 2 * t->n, st));
+    CK(cudaStreamSynchronize(st));
+    return FTGCR_ERR_TIMEOUT;
+  }
+  return FTGCR_OK;
+}
+
+void table_abandon(SlotTable* t, cudaStream_t st) {
+  for (auto& h : t->slot) h = nullptr;
+  cudaMemsetAsync(t->d_act, 0, sizeof(int) * 2 * t->n, st);
+  cudaStreamSynchronize(st);
+}
+
+int table_occupied(const SlotTable* t) {
+  int n = 0;
+  for (ftgcr_handle* h : t->slot) n += h != nullptr;
+  return n;
+}
+int table_slots(const SlotTable* t) { return t->n; }
+
+double* handle_stage_rhs(ftgcr_handle* h) { return h->stageR; }
+double* handle_stage_x(ftgcr_handle* h) { return h->stageX; }
+long long handle_points(const ftgcr_handle* h) { return h->N; }
+int handle_precision(const ftgcr_handle* h) { return h->precision; }
+
+}  // namespace serve
+}  // namespace ftgcr
 
 // ------------------------------------------------------------ no-allocation solve
 // Some callers cannot allocate device memory when they solve: code that runs

@@ -20,8 +20,8 @@ _CSRC = os.path.join(_HERE, "csrc")
 _INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libftgcr.so")
-SOURCES = ["ftgcr.cu", "ftgcr_k4.cu", "ftgcr_k8.cu", "ftgcr_k16.cu"]
-HEADERS = ["ftgcr_device.cuh", "ftgcr_phases.cuh", "ftgcr_instances.h"]
+SOURCES = ["ftgcr.cu", "ftgcr_k4.cu", "ftgcr_k8.cu", "ftgcr_k16.cu", "ftgcr_server.cu"]
+HEADERS = ["ftgcr_device.cuh", "ftgcr_phases.cuh", "ftgcr_instances.h", "ftgcr_serve.h"]
 # --fmad=false: device multiply-adds are fused only where the code says fma();
 # -ffp-contract=off: the same for the host-side geometry (GCC contracts by
 # default on aarch64)
@@ -34,11 +34,14 @@ VEC = {"x": 0, "r": 1, "p": 2, "ap": 3, "e": 4}
 MAX_FAULTS, MAX_K, MAX_DETECT = 64, 16, 16
 
 OK, NOT_CONVERGED, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BUDGET, ERR_STATE = 0, 1, -1, -2, -3, -4, -5, -6
+PENDING = 2
 
 # every symbol include/ftgcr.h declares
 EXPORTS = ["ftgcr_create", "ftgcr_solve", "ftgcr_solve_async", "ftgcr_stats", "ftgcr_solve_batch",
            "ftgcr_apply_operator", "ftgcr_apply_precond", "ftgcr_footprint", "ftgcr_destroy", "ftgcr_error_string",
-           "ftgcr_solve_noalloc"]
+           "ftgcr_solve_noalloc", "ftgcr_set_coeffs", "ftgcr_server_create", "ftgcr_server_submit",
+           "ftgcr_server_poll", "ftgcr_server_wait", "ftgcr_server_next", "ftgcr_server_info",
+           "ftgcr_server_destroy"]
 NOALLOC_MAX_POINTS, NOALLOC_MAX_K = 16384, 4
 
 _lock = threading.Lock()
@@ -71,6 +74,11 @@ class Stats(ctypes.Structure):
                 ("res0", ctypes.c_double), ("res_final_rec", ctypes.c_double), ("res_final_true", ctypes.c_double),
                 ("norm_R", ctypes.c_double), ("bytes_resident", ctypes.c_int64), ("bytes_backup", ctypes.c_int64),
                 ("tiles", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+
+class ServerInfo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "queued", "running", "epochs", "handles",
+                                              "bytes_in_use", "budget_bytes")]
 
 
 class FTGCRError(RuntimeError):
@@ -137,6 +145,15 @@ def lib():
         L.ftgcr_error_string.argtypes = [ctypes.c_int]
         L.ftgcr_error_string.restype = ctypes.c_char_p
         L.ftgcr_solve_noalloc.argtypes = [ctypes.POINTER(Grid), vp, i32, dbl, vp, vp, ctypes.POINTER(Stats), vp]
+        L.ftgcr_set_coeffs.argtypes = [vp, ctypes.POINTER(Coeffs), vp]
+        L.ftgcr_server_create.argtypes = [i64, i32, i32, ctypes.POINTER(vp)]
+        L.ftgcr_server_submit.argtypes = [vp, ctypes.POINTER(Grid), ctypes.POINTER(Coeffs), i32, dbl, vp, vp,
+                                          ctypes.POINTER(FaultPlan), ctypes.POINTER(i64)]
+        L.ftgcr_server_poll.argtypes = [vp, i64, ctypes.POINTER(Stats)]
+        L.ftgcr_server_wait.argtypes = [vp, i64, dbl, ctypes.POINTER(Stats)]
+        L.ftgcr_server_next.argtypes = [vp, dbl, ctypes.POINTER(i64), ctypes.POINTER(Stats)]
+        L.ftgcr_server_info.argtypes = [vp, ctypes.POINTER(ServerInfo)]
+        L.ftgcr_server_destroy.argtypes = [vp]
         for f in EXPORTS:
             if not hasattr(L, f):
                 raise RuntimeError(f"libftgcr.so does not export {f}")
@@ -277,6 +294,14 @@ class Solver:
         if st < 0:
             raise FTGCRError(st, "ftgcr_apply_precond")
 
+    def set_coeffs(self, D, stream=None):
+        """Rebuild the operator and preconditioner from a new D (same grid)."""
+        dp, keep = _ptr(D)
+        c = Coeffs(dp)
+        st = lib().ftgcr_set_coeffs(self.h, ctypes.byref(c), _stream_ptr(stream))
+        if st < 0:
+            raise FTGCRError(st, "ftgcr_set_coeffs")
+
 
 def _stats_dict(s: Stats) -> dict:
     n = s.ndetect
@@ -329,3 +354,98 @@ def solve_batch(solvers, rhs, xs, faults=None, stream=None) -> None:
     st = lib().ftgcr_solve_batch(H, Rp, Xp, P, n, _stream_ptr(stream))
     if st < 0:
         raise FTGCRError(st, "ftgcr_solve_batch")
+
+
+class Server:
+    """Continuous batching of independent solves (ftgcr_server_*): submit
+    returns a ticket at once; poll / wait return (status, stats) once the
+    solve has finished.  The arrays passed to submit are kept alive here until
+    their result has been taken."""
+
+    def __init__(self, budget_bytes=0, max_slots=64, epoch_rounds=48):
+        srv = ctypes.c_void_p()
+        st = lib().ftgcr_server_create(int(budget_bytes), int(max_slots), int(epoch_rounds), ctypes.byref(srv))
+        if st != OK:
+            raise FTGCRError(st, "ftgcr_server_create")
+        self.srv = srv
+        self._keep = {}
+
+    def submit(self, D, mu, rhs, x, k=4, tol=1e-10, precision="fp64", precond="line", faults=(), max_steps=0,
+               tiles=0, inner_tol=0.0, max_outer=0) -> int:
+        nlat, nlon = D.shape
+        g = _grid(nlon, nlat, mu, precision, precond, max_steps, tiles, inner_tol, max_outer)
+        dp, dk = _ptr(D)
+        rp, rk = _ptr(rhs)
+        xp, xk = _ptr(x)
+        plan, arr = _plan(faults)
+        t = ctypes.c_int64()
+        st = lib().ftgcr_server_submit(self.srv, ctypes.byref(g), ctypes.byref(Coeffs(dp)), int(k), float(tol), rp,
+                                       xp, ctypes.byref(plan) if plan else None, ctypes.byref(t))
+        if st < 0:
+            raise FTGCRError(st, "ftgcr_server_submit")
+        self._keep[t.value] = (dk, rk, xk)
+        return t.value
+
+    def _result(self, ticket, st, s):
+        if st == PENDING:
+            return None
+        self._keep.pop(ticket, None)
+        return st, _stats_dict(s)
+
+    def _check(self, ticket):
+        if ticket not in self._keep:
+            raise FTGCRError(ERR_ARG, f"unknown or already collected ticket {ticket}")
+
+    def poll(self, ticket):
+        """None while running, else (status, stats); the status is that of
+        ftgcr_solve (OK, NOT_CONVERGED or a negative error)."""
+        self._check(ticket)
+        s = Stats()
+        return self._result(ticket, lib().ftgcr_server_poll(self.srv, int(ticket), ctypes.byref(s)), s)
+
+    def wait(self, ticket, timeout=None):
+        """Block until done (or timeout seconds: None on timeout)."""
+        self._check(ticket)
+        s = Stats()
+        st = lib().ftgcr_server_wait(self.srv, int(ticket), -1.0 if timeout is None else float(timeout),
+                                     ctypes.byref(s))
+        return self._result(ticket, st, s)
+
+    def next(self, timeout=None):
+        """The earliest-finished request not yet collected: (ticket, status,
+        stats), or None if none finishes within timeout seconds."""
+        s = Stats()
+        t = ctypes.c_int64()
+        st = lib().ftgcr_server_next(self.srv, -1.0 if timeout is None else float(timeout), ctypes.byref(t),
+                                     ctypes.byref(s))
+        if st == PENDING:
+            return None
+        if st == ERR_STATE and not self._keep:
+            raise FTGCRError(st, "no request outstanding")
+        self._keep.pop(t.value, None)
+        return t.value, st, _stats_dict(s)
+
+    def info(self) -> dict:
+        i = ServerInfo()
+        st = lib().ftgcr_server_info(self.srv, ctypes.byref(i))
+        if st < 0:
+            raise FTGCRError(st, "ftgcr_server_info")
+        return {n: getattr(i, n) for n, _ in ServerInfo._fields_}
+
+    def close(self):
+        if getattr(self, "srv", None):
+            lib().ftgcr_server_destroy(self.srv)
+            self.srv = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

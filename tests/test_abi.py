@@ -55,3 +55,16 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(ftgcr, "build", no_build)
     with pytest.raises(Exception):
         ftgcr.lib()
+
+
+def test_server_refuses_bad_arguments_and_a_missing_gpu_without_crashing():
+    L = ftgcr.lib()
+    srv = ctypes.c_void_p()
+    assert L.ftgcr_server_create(0, 0, 8, ctypes.byref(srv)) == ftgcr.ERR_ARG  # no slots
+    assert L.ftgcr_server_create(0, 1025, 8, ctypes.byref(srv)) == ftgcr.ERR_ARG  # above the table limit
+    assert L.ftgcr_server_create(-1, 4, 8, ctypes.byref(srv)) == ftgcr.ERR_ARG
+    assert L.ftgcr_server_create(0, 4, 0, ctypes.byref(srv)) == ftgcr.ERR_ARG
+    import torch
+    if not torch.cuda.is_available():
+        assert L.ftgcr_server_create(0, 4, 8, ctypes.byref(srv)) == ftgcr.ERR_CUDA
+        assert srv.value is None
