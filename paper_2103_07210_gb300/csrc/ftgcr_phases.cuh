@@ -241,8 +241,8 @@ __device__ __forceinline__ int part_count(int kind, int nu) {
 template <typename T>
 __device__ __noinline__ void transition(const SolveDev<T>& sd, const SolveState& S, const double* red, const double* qd,
                                        SolveState& N, Ctx<T>& c) {
-  N = S;
-  memset(&c, 0, sizeof c);  // every pointer a phase may test starts out null
+  // On entry N is a copy of S and c is zeroed (every pointer a phase may
+  // test starts out null); the caller makes both copies block-wide.
   c.kind = K_NONE;
   c.nu = S.nu;
   c.t = S.step + 1;
@@ -1163,6 +1163,12 @@ __device__ __forceinline__ void cta_load_cg(S* dst, const S* src) {
   for (int i = threadIdx.x; i < (int)(sizeof(S) / 8); i += blockDim.x) d[i] = __ldcg(s + i);
 }
 template <typename S>
+__device__ __forceinline__ void cta_zero(S* dst) {
+  static_assert(sizeof(S) % 8 == 0, "record size");
+  long long* d = reinterpret_cast<long long*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(S) / 8); i += blockDim.x) d[i] = 0;
+}
+template <typename S>
 __device__ __forceinline__ void cta_store(S* dst, const S* src) {
   static_assert(sizeof(S) % 8 == 0, "record size");
   const long long* s = reinterpret_cast<const long long*>(src);
@@ -1196,6 +1202,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_ftgcr_persistent(BatchArgs<T> a
   const unsigned long long t_start = globaltimer();
   unsigned int nbar = 0;
   int cur_sd = -1;  // solve whose descriptor sits in shared memory
+  int last_s = -1;  // solve whose transition ks.N holds, and its round
+  long long last_round = -2;
   if (threadIdx.x == 0) ks.ps.cs_solve = -1;
   int it = 0;
   for (; it < a.max_rounds; ++it) {
@@ -1208,16 +1216,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_ftgcr_persistent(BatchArgs<T> a
       a.diag[blockIdx.x * 4 + 0] = it;
       a.diag[blockIdx.x * 4 + 2] = 0;
     }
-    // tile prefix over active solves (identical in every CTA)
-    if (threadIdx.x == 0) {
+    // tile prefix over active solves (identical in every CTA): warp 0 scans
+    // 32 solves at a time
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
       int acc = 0;
-      for (int s = 0; s < a.n; ++s) {
-        const int act = __ldcg(a.active + par * a.n + s);
-        ks.prefix[s] = acc;
-        acc += act ? a.nt[s] : 0;
-        if (!act && blockIdx.x == 0) a.active[(par ^ 1) * a.n + s] = 0;
+      for (int s0 = 0; s0 < a.n; s0 += 32) {
+        const int s = s0 + lane;
+        int v = 0;
+        if (s < a.n) {
+          const int act = __ldcg(a.active + par * a.n + s);
+          v = act ? a.nt[s] : 0;
+          if (!act && blockIdx.x == 0) a.active[(par ^ 1) * a.n + s] = 0;
+        }
+        int inc = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, inc, d);
+          if (lane >= d) inc += y;
+        }
+        if (s < a.n) ks.prefix[s] = acc + inc - v;
+        acc += __shfl_sync(0xffffffffu, inc, 31);
       }
-      ks.prefix[a.n] = acc;
+      if (lane == 0) ks.prefix[a.n] = acc;
     }
     __syncthreads();
     const int total = ks.prefix[a.n];
@@ -1245,16 +1266,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_ftgcr_persistent(BatchArgs<T> a
           cur_sd = s;
         }
         // the state record and every partial sum the pending phase may have
-        // left, loaded together
-        cta_load_cg(&ks.S, ks.sd.st + par);
+        // left, loaded together.  A CTA that ran this solve's transition in
+        // the previous round holds the record already (every CTA computes
+        // the same transition from the same inputs).
+        if (s == last_s && round == last_round + 1)
+          cta_store(&ks.S, &ks.N);
+        else
+          cta_load_cg(&ks.S, ks.sd.st + par);
         reduce_partials<T>(ks.sd.part + (long long)(par ^ 1) * ks.sd.nt * kPartStride, ks.sd.nt,
                            ks.sd.k + 1 > 4 ? ks.sd.k + 1 : 4, ks.red);
         __syncthreads();
         precompute_divisions(ks.S, ks.red, ks.qd);
+        cta_store(&ks.N, &ks.S);
+        cta_zero(&ks.c);
         __syncthreads();
         if (threadIdx.x == 0) transition(ks.sd, ks.S, ks.red, ks.qd, ks.N, ks.c);
         __syncthreads();
         cur = s;
+        last_s = s;
+        last_round = round;
       }
       if (a.trace && threadIdx.x == 0 && tr_items == 0) {
         tr[1] = globaltimer();
