@@ -18,6 +18,10 @@ Parity status per function (what pins it, see ``tests/test_oracle_*.py``):
   apply_P / solve_P        pinned: P equals the diagonal-block part of L,
                            P(P^-1 r) = r, dense LAPACK solve.
   dot                      pinned: numpy on the same data.
+  splitmix64               pinned: the published SplitMix64 reference outputs
+                           for seed 1234567.
+  data-loss events         pinned: flip positions and bits against an
+                           independent Python restatement; XOR involution.
   flip_bit                 pinned: numpy bit pattern XOR.
   ftgcr                    pinned: dense direct solve, manufactured solution,
                            strictly decreasing norms, exact preconditioner
@@ -56,13 +60,19 @@ class _Fault(ctypes.Structure):
 class _Problem(ctypes.Structure):
     _fields_ = [("nlon", ctypes.c_int32), ("nlat", ctypes.c_int32), ("mu", ctypes.c_double),
                 ("k", ctypes.c_int32), ("tol", ctypes.c_double), ("max_steps", ctypes.c_int64),
-                ("precond", ctypes.c_int32), ("D", ctypes.c_void_p), ("dense_pinv", ctypes.c_void_p)]
+                ("precond", ctypes.c_int32), ("D", ctypes.c_void_p), ("dense_pinv", ctypes.c_void_p),
+                ("protect", ctypes.c_int32)]
+
+
+class _Loss(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int64), ("rank", ctypes.c_int32), ("nranks", ctypes.c_int32),
+                ("count", ctypes.c_int64), ("seed", ctypes.c_uint64), ("nbits", ctypes.c_int32)]
 
 
 class _Result(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("cycles", ctypes.c_int64), ("restarts", ctypes.c_int64),
                 ("faults_injected", ctypes.c_int64), ("faults_detected", ctypes.c_int64),
-                ("converged", ctypes.c_int32), ("ndetect", ctypes.c_int32),
+                ("loss_events", ctypes.c_int64), ("converged", ctypes.c_int32), ("ndetect", ctypes.c_int32),
                 ("detect_step", ctypes.c_int64 * MAX_DETECT), ("nrm2_R", ctypes.c_double),
                 ("nrm2_0", ctypes.c_double), ("nrm2_final", ctypes.c_double), ("res_true", ctypes.c_double)]
 
@@ -97,7 +107,9 @@ def lib():
         L.orc_flip_bit.argtypes = [ctypes.c_double, ctypes.c_int]
         L.orc_flip_bit.restype = ctypes.c_double
         L.orc_ftgcr.argtypes = [ctypes.POINTER(_Problem), dp, dp, ctypes.POINTER(_Fault), ctypes.c_int,
-                                ctypes.POINTER(_Result), dp, dp, dp, dp]
+                                ctypes.POINTER(_Loss), ctypes.c_int, ctypes.POINTER(_Result), dp, dp, dp, dp]
+        L.orc_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+        L.orc_splitmix64.restype = ctypes.c_uint64
         L.orc_ftgcr.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -178,10 +190,18 @@ def dense_matrix(apply, nlat: int, nlon: int) -> np.ndarray:
     return M
 
 
+def splitmix64(seed: int, i: int) -> int:
+    """Output i (i >= 1) of SplitMix64 started at state ``seed``."""
+    return int(lib().orc_splitmix64(seed & 0xFFFFFFFFFFFFFFFF, i))
+
+
 def ftgcr(D, R, mu, k, tol, x0=None, faults=(), max_steps=None, precond=PRECOND_LINE, dense_pinv=None,
-          trace_lp=False):
+          trace_lp=False, losses=(), protect=True):
     """Run FT-GCR(k) (Algorithm 1).  ``faults`` is a sequence of
     (step, vec, index, bit) tuples, ``vec`` an int or one of x, r, p, ap, e.
+    ``losses`` is a sequence of data-loss events (step, rank, nranks, count,
+    seed, nbits) hitting e after the preconditioner (Section 3).
+    ``protect=False`` runs plain GCR(k): no fault test, backup or restore.
     Returns a dict with the solution, status, counters and per-step history."""
     D, R = _f64(D), _f64(R)
     nlat, nlon = D.shape
@@ -192,22 +212,26 @@ def ftgcr(D, R, mu, k, tol, x0=None, faults=(), max_steps=None, precond=PRECOND_
     fa = (_Fault * max(1, len(faults)))()
     for q, (st, vec, idx, bit) in enumerate(faults):
         fa[q].step, fa[q].vec, fa[q].index, fa[q].bit = int(st), VEC_NAMES.get(vec, vec), int(idx), int(bit)
+    la = (_Loss * max(1, len(losses)))()
+    for q, (st, rank, nranks, count, seed, nbits) in enumerate(losses):
+        la[q].step, la[q].rank, la[q].nranks = int(st), int(rank), int(nranks)
+        la[q].count, la[q].seed, la[q].nbits = int(count), int(seed) & 0xFFFFFFFFFFFFFFFF, int(nbits)
     dpv = _f64(dense_pinv) if dense_pinv is not None else None
     pb = _Problem(nlon, nlat, float(mu), int(k), float(tol), int(max_steps), int(precond), D.ctypes.data,
-                  dpv.ctypes.data if dpv is not None else None)
+                  dpv.ctypes.data if dpv is not None else None, 1 if protect else 0)
     res = _Result()
     nrm2 = np.full(max_steps, np.nan)
     ev = np.full(max_steps, -1, dtype=np.int32)
     beta = np.full(max_steps, np.nan)
     lpt = np.empty((max_steps, N)) if trace_lp else None
-    st = lib().orc_ftgcr(ctypes.byref(pb), _ptr(R), _ptr(x), fa, len(faults), ctypes.byref(res), _ptr(nrm2),
-                         _ptr(ev), _ptr(beta), _ptr(lpt) if lpt is not None else None)
+    st = lib().orc_ftgcr(ctypes.byref(pb), _ptr(R), _ptr(x), fa, len(faults), la, len(losses), ctypes.byref(res),
+                         _ptr(nrm2), _ptr(ev), _ptr(beta), _ptr(lpt) if lpt is not None else None)
     if st < 0:
         raise ValueError("oracle rejected the arguments")
     n = res.steps
     out = dict(x=x, status=st, steps=n, cycles=res.cycles, restarts=res.restarts,
                faults_injected=res.faults_injected, faults_detected=res.faults_detected,
-               converged=bool(res.converged), detect_steps=[res.detect_step[i] for i in range(res.ndetect)],
+               loss_events=res.loss_events, converged=bool(res.converged), detect_steps=[res.detect_step[i] for i in range(res.ndetect)],
                nrm2_R=res.nrm2_R, nrm2_0=res.nrm2_0, nrm2_final=res.nrm2_final, res_true=res.res_true,
                nrm2_hist=nrm2[:n].copy(), events=ev[:n].copy(), beta_hist=beta[:n].copy())
     if trace_lp:

@@ -31,6 +31,14 @@
  *               single-bit flips {step, vector, index, bit} fires at the start
  *               of executed step `step` (x, r, p, Ap: before beta is formed)
  *               or right after the preconditioner of that step (e).
+ *               Section 3's data-loss events are also modelled: at a given
+ *               step, `count` entries of e inside one "process" block (the
+ *               block `rank` of `nranks` equal contiguous blocks of the
+ *               row-major array) each suffer one bit flip; entry and bit of
+ *               flip i come from output i of SplitMix64 (Steele, Lea and
+ *               Flood, 2014) started at the event's seed.
+ *  - Protection: `protect` = 0 runs plain GCR(k) (the paper's unprotected
+ *               runs): no fault test, no backup, no restore.
  *
  * Every reduction is a sequential sum in index order accumulated in twice the
  * working precision and rounded once (Dot2).  Every pointwise update is
@@ -65,11 +73,26 @@ typedef struct {
   int32_t precond;       /* ORC_PRECOND_* */
   const double* D;       /* [nlat][nlon] cell-centred coefficient */
   const double* dense_pinv; /* [N][N] row-major, only for ORC_PRECOND_DENSE */
+  int32_t protect;       /* 1: FT-GCR(k) (Algorithm 1); 0: plain GCR(k), no fault test */
 } orc_problem;
+
+/* One data-loss event (Section 3): at executed step `step`, right after the
+ * preconditioner, `count` single-bit flips hit e inside block `rank` of
+ * `nranks`: elements [floor(rank N / nranks), floor((rank + 1) N / nranks)).
+ * Flip i (i = 1..count) takes z = output i of SplitMix64 started at `seed`,
+ * element block_start + z mod block_len and bit (z >> 32) mod nbits. */
+typedef struct {
+  int64_t step;
+  int32_t rank, nranks;
+  int64_t count;
+  uint64_t seed;
+  int32_t nbits;
+} orc_loss;
 
 #define ORC_MAX_DETECT 64
 typedef struct {
   int64_t steps, cycles, restarts, faults_injected, faults_detected;
+  int64_t loss_events;     /* data-loss events that fired */
   int32_t converged, ndetect;
   int64_t detect_step[ORC_MAX_DETECT];
   double nrm2_R, nrm2_0, nrm2_final, res_true;
@@ -311,6 +334,38 @@ static int orc_inject(const orc_fault* f, int nf, int64_t t, int vec, double* v,
   return fired;
 }
 
+/* Output i (i >= 1) of SplitMix64 started at state `seed`: the state advances
+ * by the golden-ratio increment 0x9E3779B97F4A7C15 per output and each output
+ * is the state passed through the published finaliser (xor-shift 30, multiply
+ * by 0xBF58476D1CE4E5B9, xor-shift 27, multiply by 0x94D049BB133111EB,
+ * xor-shift 31). */
+uint64_t orc_splitmix64(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + i * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+/* Apply every data-loss event of executed step t to e; returns how many fired. */
+static int orc_data_loss(const orc_loss* ev, int nev, int64_t t, double* e, long N) {
+  int fired = 0;
+  for (int q = 0; q < nev; ++q) {
+    if (ev[q].step != t || ev[q].nranks < 1 || ev[q].rank < 0 || ev[q].rank >= ev[q].nranks) continue;
+    long b0 = (long)((int64_t)ev[q].rank * N / ev[q].nranks);
+    long b1 = (long)((int64_t)(ev[q].rank + 1) * N / ev[q].nranks);
+    long len = b1 - b0;
+    if (len <= 0) continue;
+    for (int64_t i = 1; i <= ev[q].count; ++i) {
+      uint64_t z = orc_splitmix64(ev[q].seed, (uint64_t)i);
+      long idx = b0 + (long)(z % (uint64_t)len);
+      int bit = (int)((z >> 32) % (uint64_t)ev[q].nbits);
+      e[idx] = orc_flip_bit(e[idx], bit);
+    }
+    ++fired;
+  }
+  return fired;
+}
+
 /* ------------------------------------------------------------- FT-GCR(k) */
 /* Algorithm 1 of the paper with the readings listed at the top of this file.
  * x: in = initial guess phi^0, out = solution.  Optional per-step outputs
@@ -319,7 +374,8 @@ static int orc_inject(const orc_fault* f, int nf, int64_t t, int vec, double* v,
  * receives L(p^nu) used by step t at lp_trace[(t-1)*N ...] (tiny grids only).
  * Returns 0 when converged, 1 when max_steps ran out, -1 on bad arguments. */
 int orc_ftgcr(const orc_problem* pb, const double* R, double* x, const orc_fault* faults, int nfaults,
-              orc_result* res, double* nrm2_hist, int32_t* event_hist, double* beta_hist, double* lp_trace) {
+              const orc_loss* losses, int nlosses, orc_result* res, double* nrm2_hist, int32_t* event_hist,
+              double* beta_hist, double* lp_trace) {
   int nlon = pb->nlon, nlat = pb->nlat, k = pb->k;
   if (nlon < 3 || nlat < 1 || k < 1 || !(pb->tol > 0.0)) return -1;
   long N = (long)nlon * nlat;
@@ -411,7 +467,7 @@ int orc_ftgcr(const orc_problem* pb, const double* R, double* x, const orc_fault
       status = 0;
       goto done;
     }
-    if (!(nrm2 < nrm2_prev)) { /* fault: restore the backup, redo the cycle */
+    if (pb->protect && !(nrm2 < nrm2_prev)) { /* fault: restore the backup, redo the cycle */
       if (event_hist) event_hist[t - 1] = ORC_EVENT_FAULT;
       if (res->ndetect < ORC_MAX_DETECT) res->detect_step[res->ndetect++] = t;
       res->faults_detected += 1;
@@ -425,7 +481,7 @@ int orc_ftgcr(const orc_problem* pb, const double* R, double* x, const orc_fault
       continue;
     }
     if (event_hist) event_hist[t - 1] = ORC_EVENT_ACCEPT;
-    if (nu == 0) { /* first step of the cycle passed: ^* <- ^0 */
+    if (pb->protect && nu == 0) { /* first step of the cycle passed: ^* <- ^0 */
       orc_copy(N, phi, phi_s);
       orc_copy(N, r, r_s);
       orc_copy(N, p[0], p_s);
@@ -439,6 +495,7 @@ int orc_ftgcr(const orc_problem* pb, const double* R, double* x, const orc_fault
 
     orc_solve_P(nlon, nlat, pb->mu, Tx, Ty, area, pb->precond, pb->dense_pinv, r, e);
     res->faults_injected += orc_inject(faults, nfaults, t, ORC_VEC_E, e, N);
+    res->loss_events += orc_data_loss(losses, nlosses, t, e, N);
     orc_apply_L(nlon, nlat, pb->mu, Tx, Ty, area, e, Le);
     for (int l = 0; l <= nu; ++l) alpha[l] = -orc_dot(N, Le, Lp[l]) / orc_dot(N, Lp[l], Lp[l]);
     for (long c = 0; c < N; ++c) {
