@@ -83,7 +83,13 @@ typedef struct {
   double inner_tol;  /* FTGCR_MIXED only: relative tolerance of each inner FP32 solve;
                         0 = 1e-5 */
   int32_t max_outer; /* FTGCR_MIXED only: refinement sweeps limit; 0 = 40 */
+  int32_t flags;     /* FTGCR_FLAG_* */
 } ftgcr_grid;
+
+/* Run plain GCR(k), the paper's unprotected baseline (Section 3): no fault
+ * test, so no backup restore (and, in the mixed path, no rejection of
+ * refinement updates).  Faults still fire. */
+#define FTGCR_FLAG_UNPROTECTED 1
 
 typedef struct {
   const double* D;   /* [nlat][nlon] cell-centred coefficient (column depth 1 - h), > 0 */
@@ -103,11 +109,31 @@ typedef struct {
   int32_t bit;
 } ftgcr_fault;
 
+/* One data-loss event, the fault model of Section 3: at executed step `step`,
+ * right after the preconditioner (like an e flip), `count` entries of e inside
+ * one process block each suffer one bit flip.  The block is `rank` of
+ * `nranks` equal contiguous blocks of the row-major array: elements
+ * [floor(rank N / nranks), floor((rank + 1) N / nranks)).  Flip i = 1..count
+ * takes z = output i of SplitMix64 started at state `seed` (state advanced by
+ * 0x9E3779B97F4A7C15 per output, then the generator's published finaliser),
+ * element block_start + z mod block_len and bit (z >> 32) mod 64 (FTGCR_FP64)
+ * or mod 32 (FTGCR_MIXED).  Two flips of the same bit cancel. */
+typedef struct {
+  int64_t step;
+  int32_t rank;
+  int32_t nranks; /* >= 1 */
+  int64_t count;  /* >= 0 */
+  uint64_t seed;
+} ftgcr_loss;
+
 typedef struct {
   const ftgcr_fault* faults; /* host memory, n entries */
   int32_t n;                 /* 0..FTGCR_MAX_FAULTS */
+  const ftgcr_loss* losses;  /* host memory, nlosses entries (may be NULL) */
+  int32_t nlosses;           /* 0..FTGCR_MAX_LOSSES */
 } ftgcr_fault_plan;
 
+#define FTGCR_MAX_LOSSES 16
 #define FTGCR_MAX_FAULTS 64
 #define FTGCR_MAX_K 16
 #define FTGCR_MAX_DETECT 16
@@ -131,6 +157,7 @@ typedef struct {
   int64_t bytes_backup;    /* of which the backup [phi, r, p, L(p)]^* (Section 4: 4 arrays) */
   int32_t tiles;           /* row bands used */
   int32_t status;          /* status of the last solve */
+  int64_t loss_events;     /* data-loss events that fired */
 } ftgcr_stats_t;
 
 /* Create a solver for one grid and coefficient field.  Copies D, builds the

@@ -21,6 +21,8 @@
 using namespace ftgcr;
 
 static_assert(sizeof(Fault) == sizeof(ftgcr_fault), "fault layout");
+static_assert(sizeof(LossEv) == sizeof(ftgcr_loss), "loss layout");
+static_assert(kMaxLosses == FTGCR_MAX_LOSSES, "max losses");
 static_assert(kMaxK == FTGCR_MAX_K, "max k");
 static_assert(kMaxFaults == FTGCR_MAX_FAULTS, "max faults");
 static_assert(kMaxDetect == FTGCR_MAX_DETECT, "max detect");
@@ -175,8 +177,10 @@ struct BeginArgs {
   const double* x0;
   double* xout;
   int nfaults;
+  int nlosses;
   long long max_steps;
   Fault faults[kMaxFaults];
+  LossEv losses[kMaxLosses];
 };
 
 template <typename T>
@@ -187,6 +191,7 @@ __global__ void k_begin_solve(SolveDev<T>* sd, BeginArgs b, int* active, int n_a
     sd->x0 = b.x0;
     sd->xout = b.xout;
     sd->nfaults = b.nfaults;
+    sd->nlosses = b.nlosses;
     SolveState S;
     memset(&S, 0, sizeof S);
     S.active = 1;
@@ -207,6 +212,7 @@ __global__ void k_begin_solve(SolveDev<T>* sd, BeginArgs b, int* active, int n_a
     }
   }
   for (int q = threadIdx.x; q < b.nfaults; q += blockDim.x) const_cast<Fault*>(sd->faults)[q] = b.faults[q];
+  for (int q = threadIdx.x; q < b.nlosses; q += blockDim.x) const_cast<LossEv*>(sd->losses)[q] = b.losses[q];
 }
 
 // ------------------------------------------------------------ host helpers
@@ -294,6 +300,7 @@ struct ftgcr_handle {
   long long N = 0, max_steps = 0;
   double tol = 0, mu = 0, inner_tol = 0;
   int max_outer = 0;
+  int flags = 0;
   unsigned char* pool = nullptr;
   size_t pool_bytes = 0;
   size_t backup_bytes = 0;
@@ -373,7 +380,14 @@ bool is_device_ptr(const void* p) {
 }
 
 int validate_plan(const ftgcr_handle* h, const ftgcr_fault_plan* plan) {
-  if (!plan || plan->n == 0) return FTGCR_OK;
+  if (!plan) return FTGCR_OK;
+  if (plan->nlosses < 0 || plan->nlosses > FTGCR_MAX_LOSSES || (plan->nlosses > 0 && !plan->losses))
+    return FTGCR_ERR_ARG;
+  for (int q = 0; q < plan->nlosses; ++q) {
+    const ftgcr_loss& l = plan->losses[q];
+    if (l.step < 1 || l.nranks < 1 || l.rank < 0 || l.rank >= l.nranks || l.count < 0) return FTGCR_ERR_ARG;
+  }
+  if (plan->n == 0) return FTGCR_OK;
   if (plan->n < 0 || plan->n > FTGCR_MAX_FAULTS || !plan->faults) return FTGCR_ERR_ARG;
   const int maxbit = h->precision == FTGCR_MIXED ? 31 : 63;
   for (int q = 0; q < plan->n; ++q) {
@@ -415,8 +429,15 @@ size_t layout(ftgcr_handle* h, unsigned char* base, SolveDev<T>* sd) {
   size_t before = off;
   for (int q = 0; q < 3; ++q) sd->phi[q] = (T*)take(vT);
   for (int q = 0; q < 3; ++q) sd->r[q] = (T*)take(vT);
-  sd->e = (T*)take(vT);
-  sd->Le = (T*)take(vT);
+  sd->e[0] = (T*)take(vT);
+  sd->Le[0] = (T*)take(vT);
+  if (std::is_same<T, float>::value) {  // mixed path: fused steps double-buffer e, L(e)
+    sd->e[1] = (T*)take(vT);
+    sd->Le[1] = (T*)take(vT);
+  } else {
+    sd->e[1] = sd->e[0];
+    sd->Le[1] = sd->Le[0];
+  }
   for (int s = 0; s < kNSlot; ++s) {
     sd->p[s] = s < k + 2 ? (T*)take(vT) : nullptr;
     sd->Lp[s] = s < k + 2 ? (T*)take(vT) : nullptr;
@@ -432,6 +453,7 @@ size_t layout(ftgcr_handle* h, unsigned char* base, SolveDev<T>* sd) {
   sd->st = (SolveState*)take(sizeof(SolveState) * 2);
   sd->result = (SolveState*)take(sizeof(SolveState));
   sd->faults = (const Fault*)take(sizeof(Fault) * kMaxFaults);
+  sd->losses = (const LossEv*)take(sizeof(LossEv) * kMaxLosses);
   sd->patchval = (double*)take(sizeof(double) * kMaxFaults);
   h->sdev = take(sizeof(SolveDev<T>));
   h->sdev_arr = (void**)take(sizeof(void*));
@@ -519,6 +541,7 @@ int create_impl(ftgcr_handle* h, const double* D_host_or_dev, bool D_on_device) 
   sd.max_outer = h->max_outer;
   sd.tol2 = h->tol * h->tol;
   sd.inner_tol2 = h->inner_tol * h->inner_tol;
+  sd.protect = (h->flags & FTGCR_FLAG_UNPROTECTED) ? 0 : 1;
   sd.Tx64 = h->Tx64;
   sd.Ty64 = h->Ty64;
   sd.muA64 = h->muA64;
@@ -641,8 +664,10 @@ BeginArgs begin_args(const ftgcr_handle* h, const double* R, const double* x0, d
   b.x0 = x0;
   b.xout = xout;
   b.nfaults = plan ? plan->n : 0;
+  b.nlosses = plan && plan->losses ? plan->nlosses : 0;
   b.max_steps = h->max_steps;
   for (int q = 0; q < b.nfaults; ++q) memcpy(&b.faults[q], &plan->faults[q], sizeof(Fault));
+  for (int q = 0; q < b.nlosses; ++q) memcpy(&b.losses[q], &plan->losses[q], sizeof(LossEv));
   return b;
 }
 
@@ -834,6 +859,9 @@ static int check_grid(const ftgcr_grid* g, int32_t k, double tol) {
   if (!(tol > 0.0) || !std::isfinite(tol)) return FTGCR_ERR_ARG;
   if (g->max_steps < 0 || g->tiles < 0 || g->max_outer < 0 || !(g->inner_tol >= 0.0) || g->inner_tol >= 1.0)
     return FTGCR_ERR_ARG;
+  if (g->flags & ~FTGCR_FLAG_UNPROTECTED) return FTGCR_ERR_ARG;
+  // mu = 0 on a single latitude row leaves the zonal line systems singular
+  if (g->mu == 0.0 && g->nlat < 2 && g->precond != FTGCR_PRECOND_IDENTITY) return FTGCR_ERR_ARG;
   return FTGCR_OK;
 }
 
@@ -850,6 +878,7 @@ static void fill_handle_params(ftgcr_handle* h, const ftgcr_grid* g, int32_t k, 
   h->max_steps = g->max_steps > 0 ? g->max_steps : 100LL * (long long)std::ceil(std::sqrt((double)h->N)) + 100;
   h->inner_tol = g->inner_tol > 0 ? g->inner_tol : 1e-5;
   h->max_outer = g->max_outer > 0 ? g->max_outer : 40;
+  h->flags = g->flags;
   const bool mixed = g->precision == FTGCR_MIXED;
   const size_t elem = mixed ? sizeof(float) : sizeof(double);
   h->nt = g->tiles > 0 ? std::min(g->tiles, g->nlat)
@@ -996,6 +1025,7 @@ int ftgcr_stats(ftgcr_handle* h, ftgcr_stats_t* out) {
   out->bytes_backup = (int64_t)h->backup_bytes;
   out->tiles = h->nt;
   out->status = h->last_status;
+  out->loss_events = S.lossev;
   return FTGCR_OK;
 }
 
@@ -1263,6 +1293,7 @@ extern "C" int ftgcr_solve_noalloc(const ftgcr_grid* grid, const double* D, int3
   sd.max_outer = h.max_outer;
   sd.tol2 = h.tol * h.tol;
   sd.inner_tol2 = h.inner_tol * h.inner_tol;
+  sd.protect = (h.flags & FTGCR_FLAG_UNPROTECTED) ? 0 : 1;
   sd.Tx64 = h.Tx64;
   sd.Ty64 = h.Ty64;
   sd.muA64 = h.muA64;

@@ -8,6 +8,7 @@
 #pragma once
 #include <cstdint>
 #include <cstring>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace ftgcr {
@@ -16,7 +17,7 @@ constexpr int kMaxK = 16;
 constexpr int kNSlot = kMaxK + 2;      // p / L(p) buffers
 constexpr int kMaxFaults = 64;
 constexpr int kMaxDetect = 16;
-constexpr int kNPart = kMaxK + 2;      // partial sums per tile (each a double-double pair)
+constexpr int kNPart = kMaxK + 4;      // partial sums per tile (each a double-double pair)
 constexpr int kPartStride = 2 * kNPart;  // doubles per tile in the partials buffer
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
@@ -31,7 +32,8 @@ enum Kind : int {
   K_PB = 3,       // p^{nu+1}, L(p^{nu+1}) recurrences + next-beta dots
   K_RESTORE = 4,  // [phi, r, p, L(p)]^0 <- ^* after a detected fault
   K_OUT = 5,      // mixed: x += d, r_out = R - L64(x), inner right-hand side
-  K_FIN = 6       // write x, true residual
+  K_FIN = 6,      // write x, true residual
+  K_PF = 7        // mixed: the recurrences of the previous step fused with PA
 };
 enum Vec : int { V_X = 0, V_R = 1, V_P = 2, V_AP = 3, V_E = 4 };
 enum Precond : int { PC_LINE = 0, PC_JACOBI = 1, PC_IDENTITY = 2 };
@@ -43,6 +45,26 @@ struct Fault {  // same layout as ftgcr_fault
   long long index;
   int bit;
 };
+
+// Data-loss event of Section 3 (same layout as ftgcr_loss): at step `step`
+// `count` entries of e in block `rank` of `nranks` each get one bit flip.
+struct LossEv {
+  long long step;
+  int rank, nranks;
+  long long count;
+  unsigned long long seed;
+};
+constexpr int kMaxLosses = 16;
+
+// Output i (i >= 1) of SplitMix64 started at state `seed` (Steele, Lea and
+// Flood 2014): the state advances by the golden-ratio increment per output,
+// each output is the state through the generator's finaliser.
+__host__ __device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long seed, unsigned long long i) {
+  unsigned long long z = seed + i * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
 
 // Record of one solve, double-buffered by round parity.  Written by the CTA
 // that owns tile 0 of the solve, read by every CTA that works on the solve in
@@ -69,8 +91,9 @@ struct SolveState {
   double beta;
   double lpn2[kMaxK + 1];
   double nrm2_prev, nrm2_S, nrm2_R, thr2, nrm2_0, nrm2_last, nrm2_out, thr2_in, res_true2;
-  long long cycles, restarts, finj, fdet;
-  int ndetect, pad;
+  long long cycles, restarts, finj, fdet, lossev;
+  int ndetect;
+  int ecur;  // buffer of e, L(e) written by the latest PA / PF
   long long detect_step[kMaxDetect];
   double detect_ratio[kMaxDetect];
 };
@@ -98,8 +121,8 @@ struct SolveDev {
   // Krylov vectors (inner precision)
   T* phi[3];
   T* r[3];
-  T* e;
-  T* Le;
+  T* e[2];   // e = P^-1 r and L(e), double-buffered in the mixed path (a fused
+  T* Le[2];  // step reads the previous step's while writing its own)
   T* p[kNSlot];
   T* Lp[kNSlot];
   T* Rin;          // mixed: FP32 inner right-hand side
@@ -117,6 +140,9 @@ struct SolveDev {
   SolveState* result;  // final record (written once)
   const Fault* faults;
   double* patchval;  // [kMaxFaults]
+  const LossEv* losses;  // [kMaxLosses]
+  int nlosses;
+  int protect;  // 0: plain GCR(k), no fault test (the paper's unprotected runs)
 };
 
 // --------------------------------------------------------------- helpers
@@ -181,6 +207,20 @@ struct Acc<double> {
       v = dd_add(v, w);
     }
     return v;
+  }
+};
+// Plain FP64 accumulation (one fma per element), for the mixed path's outer
+// residual norm: its decisions need FP64 accuracy, not the oracle's
+// compensated sum, and GB300's FP64 pipe makes each extra operation costly.
+struct AccF64 {
+  double s;
+  __device__ __forceinline__ AccF64() : s(0.0) {}
+  __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+  __device__ __forceinline__ DD warp_sum() const {
+    double v = s;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return DD{v, 0.0};
   }
 };
 template <>
@@ -386,6 +426,10 @@ __device__ __noinline__ void line_solve_row(const SolveDev<T>& sd, int j, T* row
   const int i0 = lane * C;
   int len = m - i0;
   len = len < 0 ? 0 : (len > C ? C : len);
+  // the row's bordering constants, loaded first so that their latency hides
+  // behind the recurrences
+  const T* lr = sd.lrow + (long long)j * 4;
+  const T lr0 = __ldg(lr + 0), lr1 = __ldg(lr + 1), lr2 = __ldg(lr + 2);
 
   // forward multiplier of chunk element 0 is c_{i0-1}, the last c of the previous lane
   const T mylast = (len > 0) ? lc.cb[(len - 1) * 32 + lane] : T(0);
@@ -504,12 +548,12 @@ __device__ __noinline__ void line_solve_row(const SolveDev<T>& sd, int j, T* row
   }
   __syncwarp();
   // bordering: x_{n-1} = (b_{n-1} + Tx_{n-1} y_0 + Tx_{n-2} y_{m-1}) / delta
-  const T* lr = sd.lrow + (long long)j * 4;
   const T y0 = row[sk(0)];
   const T ym = row[sk(m - 1)];
   const T bl = -row[sk(n - 1)];
-  const T xl = tfma(__ldg(lr + 2), ym, tfma(__ldg(lr + 1), y0, bl * __ldg(lr + 0)));
+  const T xl = tfma(lr2, ym, tfma(lr1, y0, bl * lr0));
   __syncwarp();
+#pragma unroll 8
   for (int k = 0; k < len; ++k) {
     const int s = sk(i0 + k);
     row[s] = tfma(-xl, lc.cz[k * 32 + lane], row[s]);

@@ -37,6 +37,12 @@ struct Ctx {
   const T* lpnu;
   const T* pp[kMaxK];
   const T* lp[kMaxK];
+  const T* lo[kMaxK];  // PF: L(p^l) of the previous step's directions (lp: this step's)
+  int nuo;             // PF: nu of the previous step
+  T* eW;               // PA, PF: e and L(e) written
+  T* LeW;
+  const T* eR;         // PF, PB: e and L(e) of the previous step
+  const T* LeR;
   T* pnew;
   T* lpnew;
   T* phiCw;  // PB: current phi (x flips)
@@ -133,6 +139,13 @@ __device__ __forceinline__ int count_faults(const SolveDev<T>& sd, long long ste
 
 constexpr unsigned kStateVecs = (1u << V_X) | (1u << V_R) | (1u << V_P) | (1u << V_AP);
 
+template <typename T>
+__device__ __forceinline__ int count_losses(const SolveDev<T>& sd, long long step) {
+  int c = 0;
+  for (int q = 0; q < sd.nlosses; ++q) c += sd.losses[q].step == step;
+  return c;
+}
+
 // ------------------------------------------------------------ reductions
 // Deterministic sum over the nt tiles of the partials buffer of the first nv
 // values.  Warp v sums value v: lanes take tiles lane, lane+32, ... (all loads
@@ -191,15 +204,31 @@ __device__ __forceinline__ void reduce_partials(const double* part, int nt, int 
 // accepted one), computed speculatively in parallel lanes of warp 0 after the
 // reduction: a GB300 FP64 division has a latency of several hundred cycles.
 // Identical operands and operation to the serial form, so identical values.
-__device__ __forceinline__ void precompute_divisions(const SolveState& S, const double* red, double* qd) {
+__device__ __forceinline__ void precompute_divisions(const SolveState& S, const double* red, double* qd, int mixed) {
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
+    const bool step = S.pending == K_PA || S.pending == K_PF;
     double q = 0.0;
     if (lane < kMaxK) {
-      if (S.pending == K_PA && lane <= S.nu) q = -red[1 + lane] / S.lpn2[lane];  // alpha_lane
+      if (step && lane <= S.nu) q = -red[1 + lane] / S.lpn2[lane];  // alpha_lane
     } else if (lane == kMaxK) {
       if (S.pending == K_INIT) q = -red[2] / red[3];  // first beta
       if (S.pending == K_PB || S.pending == K_RESTORE) q = -red[0] / red[1];  // next beta
+    }
+    if (mixed && step) {
+      // The next direction's dots without forming it (mixed path, fused
+      // step): L(p') = L(e) + sum_l alpha_l L(p^l) with the L(p^l) mutually
+      // orthogonal and r' orthogonal to them (GCR), so
+      //   <r', L(p')>    = <r', L(e)> = h,
+      //   <L(p'), L(p')> = <L(e), L(e)> + sum_l alpha_l <L(e), L(p^l)> = q + sum_l alpha_l d_l.
+      const double ad = lane < kMaxK && lane <= S.nu ? q * red[1 + lane] : 0.0;
+      const double sum = warp_sum(ad);
+      const double h = red[2 + S.nu], qq = red[3 + S.nu];
+      const double den = qq + sum;
+      // use the identities only while they keep three digits of <L(p'),L(p')>
+      const bool ok = den > 1e-3 * qq && isfinite(den) && isfinite(h);
+      if (lane == kMaxK + 1) q = ok ? -h / den : 0.0;  // next beta
+      if (lane == kMaxK + 2) q = ok ? den : -1.0;      // <L(p'), L(p')>, or -1: form p' (PB)
     }
     qd[lane] = q;
   }
@@ -223,11 +252,20 @@ __device__ int new_slot(const SolveDev<T>& sd, const SolveState& N, int nu) {
   return 0;
 }
 
+// Partial sums reduced every round: the most any phase leaves (PA / PF: the
+// norm, k dots and, on the mixed path, h and q; INIT: 4).
+template <typename T>
+__device__ __forceinline__ int part_values(const SolveDev<T>& sd) {
+  const int n = sd.mixed ? sd.k + 3 : sd.k + 1;
+  return n > 4 ? n : 4;
+}
+
 // Number of partial sums the phase `kind` leaves per tile.
 __device__ __forceinline__ int part_count(int kind, int nu) {
   switch (kind) {
     case K_INIT: return 4;
-    case K_PA: return 2 + nu;
+    case K_PA:
+    case K_PF: return 4 + nu;  // FP64 path: 2 + nu (no h, q)
     case K_PB:
     case K_RESTORE: return 2;
     case K_OUT: return 2;
@@ -273,7 +311,7 @@ __device__ __noinline__ void transition(const SolveDev<T>& sd, const SolveState&
         N.thr2 = sd.tol2 * N.nrm2_R;
         N.first_out = 0;
         N.nrm2_0 = nrm2_out;
-      } else if (!S.out_redo && !(nrm2_out < S.nrm2_out)) {
+      } else if (sd.protect && !S.out_redo && !(nrm2_out < S.nrm2_out)) {
         accept = false;
       }
       N.outer = S.outer + 1;
@@ -376,7 +414,8 @@ __device__ __noinline__ void transition(const SolveDev<T>& sd, const SolveState&
       }
       break;
     }
-    case K_PA: {
+    case K_PA:
+    case K_PF: {
       const long long t = S.step + 1;
       N.step = t;
       const double nrm2 = red[0];
@@ -391,7 +430,7 @@ __device__ __noinline__ void transition(const SolveDev<T>& sd, const SolveState&
           dbuf = S.phiW;
           to_out = true;
         }
-      } else if (!(nrm2 < S.nrm2_prev)) {  // fault test (Algorithm 1, red part)
+      } else if (sd.protect && !(nrm2 < S.nrm2_prev)) {  // fault test (Algorithm 1, red part)
         N.fdet = S.fdet + 1;
         N.restarts = S.restarts + 1;
         if (S.ndetect < kMaxDetect) {
@@ -428,6 +467,7 @@ __device__ __noinline__ void transition(const SolveDev<T>& sd, const SolveState&
       } else {  // accepted
         N.stag = 0;
         N.finj = S.finj + count_faults(sd, t, 1u << V_E);
+        N.lossev = S.lossev + count_losses(sd, t);
         if (S.nu == 0) {  // ^* <- ^0
           N.phiS = S.phiC;
           N.rS = S.rC;
@@ -438,8 +478,6 @@ __device__ __noinline__ void transition(const SolveDev<T>& sd, const SolveState&
         N.nrm2_prev = nrm2;
         N.phiC = S.phiW;
         N.rC = S.rW;
-        for (int l = 0; l < kMaxK; ++l)
-          if (l <= S.nu) c.alpha[l] = (T)qd[l];  // -red[1 + l] / S.lpn2[l]
         if (t >= sd.max_steps) {
           if (!sd.mixed) {
             N.status = ST_NOT_CONVERGED;
@@ -464,6 +502,15 @@ __device__ __noinline__ void transition(const SolveDev<T>& sd, const SolveState&
           }
           c.pnew = sd.p[ns];
           c.lpnew = sd.Lp[ns];
+          if (sd.mixed && qd[kMaxK + 2] > 0.0) {
+            // mixed path: form p' and take step t + 1 with it in one round
+            // (PF), beta and <L(p'), L(p')> from the identities
+            c.kind = K_PF;
+            c.nuo = S.nu;
+            N.beta = qd[kMaxK + 1];
+            N.lpn2[N.nu] = qd[kMaxK + 2];
+            N.finj += count_faults(sd, t + 1, kStateVecs);
+          }
         }
       }
       break;
@@ -496,7 +543,7 @@ __device__ __noinline__ void transition(const SolveDev<T>& sd, const SolveState&
     }
   }
   // pointers for this round's phase
-  if (c.kind == K_PA) {
+  if (c.kind == K_PA || c.kind == K_PF) {
     N.phiW = first_not2(N.phiC, N.phiS);
     N.rW = first_not2(N.rC, N.rS);
     c.nu = N.nu;
@@ -508,16 +555,18 @@ __device__ __noinline__ void transition(const SolveDev<T>& sd, const SolveState&
     c.rW = sd.r[N.rW];
     c.pnu = sd.p[N.slot[N.nu]];
     c.lpnu = sd.Lp[N.slot[N.nu]];
-    for (int l = 0; l < kMaxK; ++l)
-      if (l <= N.nu) c.lp[l] = sd.Lp[N.slot[l]];
+    if (c.kind == K_PF) {
+      c.eR = sd.e[S.ecur];
+      c.LeR = sd.Le[S.ecur];
+    }
+    N.ecur = sd.mixed ? (S.ecur ^ 1) : 0;
+    c.eW = sd.e[N.ecur];
+    c.LeW = sd.Le[N.ecur];
   } else if (c.kind == K_PB) {
-    for (int l = 0; l < kMaxK; ++l)
-      if (l <= S.nu) {
-        c.pp[l] = sd.p[S.slot[l]];
-        c.lp[l] = sd.Lp[S.slot[l]];
-      }
     c.phiCw = sd.phi[N.phiC];
     c.rCw = sd.r[N.rC];
+    c.eR = sd.e[S.ecur];
+    c.LeR = sd.Le[S.ecur];
   } else if (c.kind == K_RESTORE) {
     c.phiS = sd.phi[S.phiS];
     c.rS = sd.r[S.rS];
@@ -543,6 +592,28 @@ __device__ __noinline__ void transition(const SolveDev<T>& sd, const SolveState&
   }
   N.pending = c.kind;
   if (c.kind == K_NONE) N.active = 0;
+}
+
+// The per-direction entries of the context the transition chose (alpha and
+// the p / L(p) slot pointers), one direction per thread: threads 0..kMaxK-1
+// of the block, after the transition.
+template <typename T>
+__device__ __forceinline__ void fill_directions(const SolveDev<T>& sd, const SolveState& S, const SolveState& N,
+                                                const double* qd, Ctx<T>& c) {
+  const int l = threadIdx.x;
+  if (l >= kMaxK) return;
+  if (c.kind == K_PA || c.kind == K_PF) {
+    if (l <= N.nu) c.lp[l] = sd.Lp[N.slot[l]];
+    if (c.kind == K_PF && l <= S.nu) {
+      c.pp[l] = sd.p[S.slot[l]];
+      c.lo[l] = sd.Lp[S.slot[l]];
+      c.alpha[l] = (T)qd[l];  // -<L(e), L(p^l)> / <L(p^l), L(p^l)>
+    }
+  } else if (c.kind == K_PB && l <= S.nu) {
+    c.pp[l] = sd.p[S.slot[l]];
+    c.lp[l] = sd.Lp[S.slot[l]];
+    c.alpha[l] = (T)qd[l];
+  }
 }
 
 // ------------------------------------------------------------ phases
@@ -673,13 +744,46 @@ __device__ __forceinline__ RowVec row_vec(int idx, int nvr, int j0, int nlon, in
   return r;
 }
 
+// The data-loss events of step t (Section 3) on the e rows [h0, h1) staged in
+// shared memory: every thread takes flips i = 1 + threadIdx.x, ... of each
+// event and XORs those that land in the tile (atomically: two flips may hit
+// the same word, and XOR makes their order irrelevant).
+template <typename T>
+__device__ __forceinline__ void apply_losses(const SolveDev<T>& sd, long long t, int h0, int h1, T* sm, int stride) {
+  using U = typename std::conditional<sizeof(T) == 8, unsigned long long, unsigned int>::type;
+  constexpr unsigned kBits = 8 * sizeof(T);
+  const int nlon = sd.nlon;
+  const long long g0 = (long long)h0 * nlon, g1 = (long long)h1 * nlon;
+  for (int q = 0; q < sd.nlosses; ++q) {
+    const LossEv ev = sd.losses[q];
+    if (ev.step != t) continue;
+    const long long b0 = (long long)ev.rank * sd.N / ev.nranks, b1 = (long long)(ev.rank + 1) * sd.N / ev.nranks;
+    const long long len = b1 - b0;
+    if (len <= 0 || b1 <= g0 || b0 >= g1) continue;
+    for (long long i = 1 + threadIdx.x; i <= ev.count; i += kThreads) {
+      const unsigned long long z = splitmix64_at(ev.seed, (unsigned long long)i);
+      const long long g = b0 + (long long)(z % (unsigned long long)len);
+      if (g < g0 || g >= g1) continue;
+      const int j = (int)(g / nlon), col = (int)(g - (long long)j * nlon);
+      U* w = reinterpret_cast<U*>(sm + (j - h0) * stride + sk(col));
+      atomicXor(w, (U)1 << (unsigned)((z >> 32) % kBits));
+    }
+  }
+}
+
 // PA: axpy, norm, preconditioner, operator, orthogonalisation dots.  KB is a
-// compile-time bound on the number of directions (k <= KB).
-template <typename T, int KB>
-__device__ __forceinline__ void phase_pa(const SolveDev<T>& sd, const Ctx<T>& c, int sidx, int tau, T* sm, PhaseSmem& ps,
-                                         double* part_out) {
+// compile-time bound on the number of directions (k <= KB).  The mixed path
+// also reduces h = <r', L(e)> and q = <L(e), L(e)>, from which the next
+// direction's dots follow without forming it (see precompute_divisions).
+// FUSED (PF, mixed path): the round first forms the previous step's new
+// direction p', L(p') (the recurrences of Algorithm 1, as PB does) and takes
+// this step's axpy with it, so an accepted step costs one round, not two.
+template <typename T, int KB, bool FUSED>
+__device__ __noinline__ void phase_pa(const SolveDev<T>& sd, const Ctx<T>& c, int sidx, int tau, T* sm, PhaseSmem& ps,
+                                      double* part_out) {
   constexpr int W = V16<T>::W;
   constexpr int U = 2;
+  constexpr bool kMixed = sizeof(T) == 4;
   const int nlon = sd.nlon, nlat = sd.nlat, stride = row_stride(nlon);
   const RowTile rt = row_tile(nlat, sd.nt, tau);
   const int nrows = rt.h1 - rt.h0;
@@ -689,9 +793,103 @@ __device__ __forceinline__ void phase_pa(const SolveDev<T>& sd, const Ctx<T>& c,
   // a CTA that keeps the same tile keeps its staged constants (single solves)
   if (!(ps.cs_solve == sidx && ps.cs_tile == tau)) stage_line_consts(sd, rt.h0, rt.h1, cs);
   if (threadIdx.x == 0)
-    ps.nfl = collect_flips(sd, c.t, 1u << V_E, (long long)rt.h0 * nlon, (long long)rt.h1 * nlon, ps.fl);
+    ps.nfl = collect_flips(sd, c.t, FUSED ? (kStateVecs | (1u << V_E)) : (1u << V_E), (long long)rt.h0 * nlon,
+                           (long long)rt.h1 * nlon, ps.fl);
   Acc<T> an;
-  if (nlon % W == 0) {
+  if constexpr (FUSED) {
+    // p' = e + sum_l alpha_l p^l, L(p') = L(e) + sum_l alpha_l L(p^l) (l in
+    // increasing order, one fma per term, as PB), then the flips of the
+    // start of this step (x, r, p', L(p')), then r'' = r' + beta L(p') and
+    // phi'' = phi' + beta p'.  Halo rows form only L(p') and r''.
+    __syncthreads();
+    const int nfl = ps.nfl;
+    auto fuse = [&](long long g, T& ln, T& rr, T& pn, T& ph, bool own) {
+      if (nfl) {
+        rr = apply_flips(rr, g, V_R, nfl, ps.fl);
+        ln = apply_flips(ln, g, V_AP, nfl, ps.fl);
+        if (own) {
+          ph = apply_flips(ph, g, V_X, nfl, ps.fl);
+          pn = apply_flips(pn, g, V_P, nfl, ps.fl);
+        }
+      }
+    };
+    if (nlon % W == 0) {
+      const int nvr = nlon / W, total = nrows * nvr;
+      for (int idx = threadIdx.x; idx < total; idx += kThreads) {
+        const RowVec rv = row_vec(idx, nvr, rt.h0, nlon, W);
+        const bool own = rv.j >= rt.j0 && rv.j < rt.j1;
+        V16<T> ln = ldv(c.LeR + rv.g), rr = ldv(c.rC + rv.g), pn, ph;
+#pragma unroll
+        for (int w = 0; w < W; ++w) pn.v[w] = ph.v[w] = T(0);
+        if (own) {
+          pn = ldv(c.eR + rv.g);
+          ph = ldv(c.phiC + rv.g);
+        }
+#pragma unroll
+        for (int l = 0; l < KB; ++l)
+          if (l <= c.nuo) {
+            const T al = c.alpha[l];
+            const V16<T> ll = ldv(c.lo[l] + rv.g);
+#pragma unroll
+            for (int w = 0; w < W; ++w) ln.v[w] = tfma(al, ll.v[w], ln.v[w]);
+            if (own) {
+              const V16<T> pl = ldv(c.pp[l] + rv.g);
+#pragma unroll
+              for (int w = 0; w < W; ++w) pn.v[w] = tfma(al, pl.v[w], pn.v[w]);
+            }
+          }
+#pragma unroll
+        for (int w = 0; w < W; ++w) fuse(rv.g + w, ln.v[w], rr.v[w], pn.v[w], ph.v[w], own);
+        T* row = sm + (rv.j - rt.h0) * stride;
+        V16<T> rn, fn;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+          rn.v[w] = tfma(beta, ln.v[w], rr.v[w]);
+          row[sk(rv.i + w)] = rn.v[w];
+        }
+        if (own) {
+#pragma unroll
+          for (int w = 0; w < W; ++w) {
+            fn.v[w] = tfma(beta, pn.v[w], ph.v[w]);
+            an.add(rn.v[w], rn.v[w]);
+          }
+          stv(c.pnew + rv.g, pn);
+          stv(c.lpnew + rv.g, ln);
+          stv(c.rW + rv.g, rn);
+          stv(c.phiW + rv.g, fn);
+        }
+      }
+    } else {
+      for (int j = rt.h0; j < rt.h1; ++j) {
+        const bool own = (j >= rt.j0 && j < rt.j1);
+        T* row = sm + (j - rt.h0) * stride;
+        const long long base = (long long)j * nlon;
+        for (int i = threadIdx.x; i < nlon; i += kThreads) {
+          const long long g = base + i;
+          T ln = ldcg(c.LeR + g), rr = ldcg(c.rC + g), pn = T(0), ph = T(0);
+          if (own) {
+            pn = ldcg(c.eR + g);
+            ph = ldcg(c.phiC + g);
+          }
+          for (int l = 0; l < KB; ++l)
+            if (l <= c.nuo) {
+              ln = tfma(c.alpha[l], ldcg(c.lo[l] + g), ln);
+              if (own) pn = tfma(c.alpha[l], ldcg(c.pp[l] + g), pn);
+            }
+          fuse(g, ln, rr, pn, ph, own);
+          const T rn = tfma(beta, ln, rr);
+          row[sk(i)] = rn;
+          if (own) {
+            c.pnew[g] = pn;
+            c.lpnew[g] = ln;
+            c.rW[g] = rn;
+            c.phiW[g] = tfma(beta, pn, ph);
+            an.add(rn, rn);
+          }
+        }
+      }
+    }
+  } else if (nlon % W == 0) {
     const int nvr = nlon / W, total = nrows * nvr;
     for (int b0 = threadIdx.x; b0 < total; b0 += U * kThreads) {
       V16<T> lp[U], rr[U], pv[U], ph[U];
@@ -759,18 +957,26 @@ __device__ __forceinline__ void phase_pa(const SolveDev<T>& sd, const Ctx<T>& c,
   sub_mark(ps, 1);
   if (threadIdx.x == 0) {
     for (int q = 0; q < ps.nfl; ++q) {  // e-site flips (the paper's injection site)
+      if (ps.fl[q].vec != V_E) continue;
       const long long g = ps.fl[q].g;
       const int j = (int)(g / nlon), i = (int)(g - (long long)j * nlon);
       T* v = sm + (j - rt.h0) * stride + sk(i);
       *v = flip_bits(*v, ps.fl[q].bit);
     }
   }
+  if (sd.nlosses) {
+    __syncthreads();  // thread 0's single flips are plain read-modify-writes
+    apply_losses(sd, c.t, rt.h0, rt.h1, sm, stride);
+  }
   __syncthreads();
   Acc<T> ad[KB];
+  Acc<T> ah, aq;  // mixed: <r', L(e)>, <L(e), L(e)>
   if (nlon % W == 0) {
     const int nvr = nlon / W, total = (rt.j1 - rt.j0) * nvr;
     for (int idx = threadIdx.x; idx < total; idx += kThreads) {
       const RowVec v = row_vec(idx, nvr, rt.j0, nlon, W);
+      V16<T> rn;
+      if constexpr (kMixed) rn = ldv(c.rW + v.g);  // r' of this step (written above)
       const bool hasN = v.j < nlat - 1, hasS = v.j > 0;
       const V16<T> tx = ldv_nc(sd.Tx + v.g);
       const T txw0 = __ldg(sd.Tx + (long long)v.j * nlon + (v.i == 0 ? nlon - 1 : v.i - 1));
@@ -795,14 +1001,21 @@ __device__ __forceinline__ void phase_pa(const SolveDev<T>& sd, const Ctx<T>& c,
                               hasS ? row[-stride + sk(i)] : T(0), tx.v[w], w == 0 ? txw0 : tx.v[w - 1],
                               hasN ? ty.v[w] : T(0), hasS ? tys.v[w] : T(0), muA, hasN, hasS);
       }
-      stv(sd.e + v.g, ev);
-      stv(sd.Le + v.g, le);
+      stv(c.eW + v.g, ev);
+      stv(c.LeW + v.g, le);
 #pragma unroll
       for (int l = 0; l < KB; ++l)
         if (l <= c.nu) {
 #pragma unroll
           for (int w = 0; w < W; ++w) ad[l].add(le.v[w], lpl[l].v[w]);
         }
+      if constexpr (kMixed) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+          ah.add(rn.v[w], le.v[w]);
+          aq.add(le.v[w], le.v[w]);
+        }
+      }
     }
   } else {
     for (int j = rt.j0; j < rt.j1; ++j) {
@@ -811,11 +1024,15 @@ __device__ __forceinline__ void phase_pa(const SolveDev<T>& sd, const Ctx<T>& c,
       for (int i = threadIdx.x; i < nlon; i += kThreads) {
         const long long g = base + i;
         const T le = stencil_smem(sd, sm, stride, rt.h0, j, i);
-        sd.e[g] = row[sk(i)];
-        sd.Le[g] = le;
+        c.eW[g] = row[sk(i)];
+        c.LeW[g] = le;
 #pragma unroll
         for (int l = 0; l < KB; ++l)
           if (l <= c.nu) ad[l].add(le, ldcg(c.lp[l] + g));
+        if constexpr (kMixed) {
+          ah.add(ldcg(c.rW + g), le);
+          aq.add(le, le);
+        }
       }
     }
   }
@@ -824,7 +1041,13 @@ __device__ __forceinline__ void phase_pa(const SolveDev<T>& sd, const Ctx<T>& c,
 #pragma unroll
   for (int l = 0; l < KB; ++l)
     if (l <= c.nu) cta_red_put(ps.cr, 1 + l, ad[l].warp_sum());
-  cta_red_finish<T>(ps.cr, 2 + c.nu, part_out);
+  if constexpr (kMixed) {
+    cta_red_put(ps.cr, 2 + c.nu, ah.warp_sum());
+    cta_red_put(ps.cr, 3 + c.nu, aq.warp_sum());
+    cta_red_finish<T>(ps.cr, 4 + c.nu, part_out);
+  } else {
+    cta_red_finish<T>(ps.cr, 2 + c.nu, part_out);
+  }
   if (threadIdx.x == 0) {
     ps.cs_solve = sidx;
     ps.cs_tile = tau;
@@ -833,7 +1056,7 @@ __device__ __forceinline__ void phase_pa(const SolveDev<T>& sd, const Ctx<T>& c,
 
 // PB: direction recurrences and the dots for the next beta.
 template <typename T, int KB>
-__device__ __forceinline__ void phase_pb(const SolveDev<T>& sd, const Ctx<T>& c, int tau, PhaseSmem& ps, double* part_out) {
+__device__ __noinline__ void phase_pb(const SolveDev<T>& sd, const Ctx<T>& c, int tau, PhaseSmem& ps, double* part_out) {
   constexpr int W = V16<T>::W;
   constexpr int U = 2;
   const long long e0 = elem_start(sd.N, sd.nt, tau), e1 = elem_start(sd.N, sd.nt, tau + 1);
@@ -868,8 +1091,8 @@ __device__ __forceinline__ void phase_pb(const SolveDev<T>& sd, const Ctx<T>& c,
       const long long q = b + (long long)u * kThreads;
       ok[u] = q < q1;
       if (ok[u]) {
-        pa[u] = ldv(sd.e + q * W);
-        la[u] = ldv(sd.Le + q * W);
+        pa[u] = ldv(c.eR + q * W);
+        la[u] = ldv(c.LeR + q * W);
         rv[u] = ldv(c.rCw + q * W);
       }
     }
@@ -914,7 +1137,7 @@ __device__ __forceinline__ void phase_pb(const SolveDev<T>& sd, const Ctx<T>& c,
       }
   }
   for (long long g = q1 * W + threadIdx.x; g < e1; g += kThreads) {  // ragged tail
-    T pa = ldcg(sd.e + g), la = ldcg(sd.Le + g);
+    T pa = ldcg(c.eR + g), la = ldcg(c.LeR + g);
     for (int l = 0; l < KB; ++l)
       if (l <= c.nu) {
         pa = tfma(c.alpha[l], ldcg(c.pp[l] + g), pa);
@@ -930,7 +1153,7 @@ __device__ __forceinline__ void phase_pb(const SolveDev<T>& sd, const Ctx<T>& c,
 // RESTORE: [phi, r, p, L(p)]^0 <- [phi, r, p, L(p)]^* by copy (the backup
 // itself is never the working set), then the flips of the next step.
 template <typename T>
-__device__ __forceinline__ void phase_restore(const SolveDev<T>& sd, const Ctx<T>& c, int tau, PhaseSmem& ps, double* part_out) {
+__device__ __noinline__ void phase_restore(const SolveDev<T>& sd, const Ctx<T>& c, int tau, PhaseSmem& ps, double* part_out) {
   const long long e0 = elem_start(sd.N, sd.nt, tau), e1 = elem_start(sd.N, sd.nt, tau + 1);
   if (threadIdx.x == 0) {
     ps.nfl = collect_flips(sd, c.t, kStateVecs, e0, e1, ps.fl);
@@ -970,7 +1193,7 @@ __device__ __forceinline__ void phase_restore(const SolveDev<T>& sd, const Ctx<T
 // beta dots.  The x/r/p/Ap flips of the first step are applied to the working
 // vectors, and their clean values kept so that the backup stays clean.
 template <typename T>
-__device__ __forceinline__ void phase_init(const SolveDev<T>& sd, const Ctx<T>& c, int sidx, int tau, T* sm, PhaseSmem& ps,
+__device__ __noinline__ void phase_init(const SolveDev<T>& sd, const Ctx<T>& c, int sidx, int tau, T* sm, PhaseSmem& ps,
                            double* part_out) {
   const int nlon = sd.nlon, nlat = sd.nlat, stride = row_stride(nlon);
   const RowTile rt = row_tile(nlat, sd.nt, tau);
@@ -1063,25 +1286,41 @@ __device__ __forceinline__ void phase_init(const SolveDev<T>& sd, const Ctx<T>& 
 // OUT (mixed): x' = x + d in FP64, r_out = R - L64(x'), ||r_out||^2 (and
 // ||R||^2 the first time), inner right-hand side R_in = (float) r_out.
 template <typename T>
-__device__ __forceinline__ void phase_out(const SolveDev<T>& sd, const Ctx<T>& c, int tau, double* smd, PhaseSmem& ps,
+__device__ __noinline__ void phase_out(const SolveDev<T>& sd, const Ctx<T>& c, int tau, double* smd, PhaseSmem& ps,
                           double* part_out) {
   const int nlon = sd.nlon, nlat = sd.nlat, stride = row_stride(nlon);
   const RowTile rt = row_tile(nlat, sd.nt, tau);
   if (threadIdx.x == 0) ps.cs_solve = -1;  // its FP64 rows overwrite the staged constants
-  for (int j = rt.h0; j < rt.h1; ++j) {
-    const bool own = (j >= rt.j0 && j < rt.j1);
-    double* row = smd + (j - rt.h0) * stride;
-    const long long base = (long long)j * nlon;
-    for (int i = threadIdx.x; i < nlon; i += kThreads) {
-      const long long g = base + i;
-      double xv = ldcg(c.xsrc + g);
-      if (c.d) xv = xv + (double)ldcg(c.d + g);
-      row[sk(i)] = xv;
-      if (own) c.xdst[g] = xv;
+  {
+    // x' = x + d over the tile and its halo rows, as one flat loop so that
+    // each thread keeps several loads in flight
+    const int nrows = rt.h1 - rt.h0, total = nrows * nlon;
+    constexpr int U = 4;
+    for (int b = threadIdx.x; b < total; b += U * kThreads) {
+      double xv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = b + u * kThreads;
+        if (idx < total) {
+          const long long g = (long long)rt.h0 * nlon + idx;
+          xv[u] = ldcg(c.xsrc + g);
+          if (c.d) xv[u] = xv[u] + (double)ldcg(c.d + g);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = b + u * kThreads;
+        if (idx < total) {
+          const int jr = idx / nlon, i = idx - jr * nlon;
+          smd[jr * stride + sk(i)] = xv[u];
+          const int j = rt.h0 + jr;
+          if (j >= rt.j0 && j < rt.j1) c.xdst[(long long)rt.h0 * nlon + idx] = xv[u];
+        }
+      }
     }
   }
   __syncthreads();
-  Acc<double> so, sR;
+  AccF64 so, sR;
   for (int j = rt.j0; j < rt.j1; ++j) {
     const long long base = (long long)j * nlon;
     const double* row = smd + (j - rt.h0) * stride;
@@ -1110,7 +1349,7 @@ __device__ __forceinline__ void phase_out(const SolveDev<T>& sd, const Ctx<T>& c
 // FIN: write the solution to the caller's x and (FP64 path) the true
 // residual ||L(x) - R||^2.
 template <typename T>
-__device__ __forceinline__ void phase_fin(const SolveDev<T>& sd, const Ctx<T>& c, int tau, PhaseSmem& ps, double* part_out) {
+__device__ __noinline__ void phase_fin(const SolveDev<T>& sd, const Ctx<T>& c, int tau, PhaseSmem& ps, double* part_out) {
   const int nlon = sd.nlon, nlat = sd.nlat;
   const RowTile rt = row_tile(nlat, sd.nt, tau);
   Acc<double> acc;
@@ -1274,13 +1513,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_ftgcr_persistent(BatchArgs<T> a
         else
           cta_load_cg(&ks.S, ks.sd.st + par);
         reduce_partials<T>(ks.sd.part + (long long)(par ^ 1) * ks.sd.nt * kPartStride, ks.sd.nt,
-                           ks.sd.k + 1 > 4 ? ks.sd.k + 1 : 4, ks.red);
+                           part_values(ks.sd), ks.red);
         __syncthreads();
-        precompute_divisions(ks.S, ks.red, ks.qd);
+        precompute_divisions(ks.S, ks.red, ks.qd, ks.sd.mixed);
         cta_store(&ks.N, &ks.S);
         cta_zero(&ks.c);
         __syncthreads();
         if (threadIdx.x == 0) transition(ks.sd, ks.S, ks.red, ks.qd, ks.N, ks.c);
+        __syncthreads();
+        fill_directions(ks.sd, ks.S, ks.N, ks.qd, ks.c);
         __syncthreads();
         cur = s;
         last_s = s;
@@ -1299,7 +1540,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_ftgcr_persistent(BatchArgs<T> a
       double* part_out = ks.sd.part + ((long long)par * ks.sd.nt + tau) * kPartStride;
       switch (ks.c.kind) {
         case K_INIT: phase_init(ks.sd, ks.c, s, tau, sm, ks.ps, part_out); break;
-        case K_PA: phase_pa<T, KB>(ks.sd, ks.c, s, tau, sm, ks.ps, part_out); break;
+        case K_PA: phase_pa<T, KB, false>(ks.sd, ks.c, s, tau, sm, ks.ps, part_out); break;
+        case K_PF:
+          if constexpr (sizeof(T) == 4) phase_pa<T, KB, true>(ks.sd, ks.c, s, tau, sm, ks.ps, part_out);
+          break;
         case K_PB: phase_pb<T, KB>(ks.sd, ks.c, tau, ks.ps, part_out); break;
         case K_RESTORE: phase_restore(ks.sd, ks.c, tau, ks.ps, part_out); break;
         case K_OUT: phase_out(ks.sd, ks.c, tau, smd, ks.ps, part_out); break;

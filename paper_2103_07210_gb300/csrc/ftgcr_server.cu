@@ -46,7 +46,7 @@ struct HandleKey {
     return grid.nlon == o.grid.nlon && grid.nlat == o.grid.nlat && grid.mu == o.grid.mu &&
            grid.precision == o.grid.precision && grid.precond == o.grid.precond && grid.max_steps == o.grid.max_steps &&
            grid.tiles == o.grid.tiles && grid.inner_tol == o.grid.inner_tol && grid.max_outer == o.grid.max_outer &&
-           k == o.k && tol == o.tol;
+           grid.flags == o.grid.flags && k == o.k && tol == o.tol;
   }
 };
 
@@ -65,6 +65,7 @@ struct Request {
   const double* rhs = nullptr;
   double* x = nullptr;
   std::vector<ftgcr_fault> faults;
+  std::vector<ftgcr_loss> losses;
   int64_t footprint = 0;
   // placement
   PoolEntry* entry = nullptr;
@@ -208,8 +209,9 @@ struct ftgcr_server {
       X = handle_stage_x(h);
     }
     r->x_host = !xdev;
-    ftgcr_fault_plan plan{r->faults.data(), (int32_t)r->faults.size()};
-    return table_begin(tables[r->table], r->slot, h, R, X, r->faults.empty() ? nullptr : &plan, st);
+    ftgcr_fault_plan plan{r->faults.data(), (int32_t)r->faults.size(), r->losses.data(), (int32_t)r->losses.size()};
+    const bool any = !r->faults.empty() || !r->losses.empty();
+    return table_begin(tables[r->table], r->slot, h, R, X, any ? &plan : nullptr, st);
   }
   void complete(Request* r) {
     ftgcr_handle* h = r->entry->h;
@@ -337,6 +339,20 @@ int ftgcr_server_submit(ftgcr_server* srv, const ftgcr_grid* grid, const ftgcr_c
   if (fp < 0) return FTGCR_ERR_ARG;
   const long long N = (long long)grid->nlon * grid->nlat;
   Request* r = new Request();
+  if (plan && plan->nlosses) {
+    if (plan->nlosses < 0 || plan->nlosses > FTGCR_MAX_LOSSES || !plan->losses) {
+      delete r;
+      return FTGCR_ERR_ARG;
+    }
+    for (int q = 0; q < plan->nlosses; ++q) {
+      const ftgcr_loss& l = plan->losses[q];
+      if (l.step < 1 || l.nranks < 1 || l.rank < 0 || l.rank >= l.nranks || l.count < 0) {
+        delete r;
+        return FTGCR_ERR_ARG;
+      }
+    }
+    r->losses.assign(plan->losses, plan->losses + plan->nlosses);
+  }
   if (plan && plan->n) {
     if (plan->n < 0 || plan->n > FTGCR_MAX_FAULTS || !plan->faults) {
       delete r;

@@ -31,7 +31,8 @@ NVCC_FLAGS = ["-std=c++17", "-O3", "-gencode", "arch=compute_103a,code=sm_103a",
 FP64, MIXED = 0, 1
 PRECOND = {"line": 0, "jacobi": 1, "identity": 2}
 VEC = {"x": 0, "r": 1, "p": 2, "ap": 3, "e": 4}
-MAX_FAULTS, MAX_K, MAX_DETECT = 64, 16, 16
+MAX_FAULTS, MAX_K, MAX_DETECT, MAX_LOSSES = 64, 16, 16, 16
+FLAG_UNPROTECTED = 1
 
 OK, NOT_CONVERGED, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BUDGET, ERR_STATE = 0, 1, -1, -2, -3, -4, -5, -6
 PENDING = 2
@@ -51,7 +52,8 @@ _lib = None
 class Grid(ctypes.Structure):
     _fields_ = [("nlon", ctypes.c_int32), ("nlat", ctypes.c_int32), ("mu", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("precond", ctypes.c_int32), ("max_steps", ctypes.c_int64),
-                ("tiles", ctypes.c_int32), ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int32)]
+                ("tiles", ctypes.c_int32), ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int32),
+                ("flags", ctypes.c_int32)]
 
 
 class Coeffs(ctypes.Structure):
@@ -62,8 +64,14 @@ class Fault(ctypes.Structure):
     _fields_ = [("step", ctypes.c_int64), ("vec", ctypes.c_int32), ("index", ctypes.c_int64), ("bit", ctypes.c_int32)]
 
 
+class Loss(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int64), ("rank", ctypes.c_int32), ("nranks", ctypes.c_int32),
+                ("count", ctypes.c_int64), ("seed", ctypes.c_uint64)]
+
+
 class FaultPlan(ctypes.Structure):
-    _fields_ = [("faults", ctypes.POINTER(Fault)), ("n", ctypes.c_int32)]
+    _fields_ = [("faults", ctypes.POINTER(Fault)), ("n", ctypes.c_int32), ("losses", ctypes.POINTER(Loss)),
+                ("nlosses", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -73,7 +81,7 @@ class Stats(ctypes.Structure):
                 ("detect_step", ctypes.c_int64 * MAX_DETECT), ("detect_ratio", ctypes.c_double * MAX_DETECT),
                 ("res0", ctypes.c_double), ("res_final_rec", ctypes.c_double), ("res_final_true", ctypes.c_double),
                 ("norm_R", ctypes.c_double), ("bytes_resident", ctypes.c_int64), ("bytes_backup", ctypes.c_int64),
-                ("tiles", ctypes.c_int32), ("status", ctypes.c_int32)]
+                ("tiles", ctypes.c_int32), ("status", ctypes.c_int32), ("loss_events", ctypes.c_int64)]
 
 
 class ServerInfo(ctypes.Structure):
@@ -188,23 +196,30 @@ def _stream_ptr(stream):
     return stream.cuda_stream  # torch.cuda.Stream
 
 
-def _plan(faults):
-    if not faults:
+def _plan(faults, losses=()):
+    """(FaultPlan, keep-alive) of single flips (step, vec, index, bit) and
+    data-loss events (step, rank, nranks, count, seed)."""
+    if not faults and not losses:
         return None, None
-    if len(faults) > MAX_FAULTS:
+    if len(faults) > MAX_FAULTS or len(losses) > MAX_LOSSES:
         raise ValueError("too many faults")
-    arr = (Fault * len(faults))()
+    arr = (Fault * max(1, len(faults)))()
     for q, (step, vec, idx, bit) in enumerate(faults):
         arr[q].step, arr[q].vec, arr[q].index, arr[q].bit = int(step), VEC.get(vec, vec), int(idx), int(bit)
-    plan = FaultPlan(ctypes.cast(arr, ctypes.POINTER(Fault)), len(faults))
-    return plan, arr
+    larr = (Loss * max(1, len(losses)))()
+    for q, (step, rank, nranks, count, seed) in enumerate(losses):
+        larr[q].step, larr[q].rank, larr[q].nranks = int(step), int(rank), int(nranks)
+        larr[q].count, larr[q].seed = int(count), int(seed) & 0xFFFFFFFFFFFFFFFF
+    plan = FaultPlan(ctypes.cast(arr, ctypes.POINTER(Fault)), len(faults), ctypes.cast(larr, ctypes.POINTER(Loss)),
+                     len(losses))
+    return plan, (arr, larr)
 
 
-def _grid(nlon, nlat, mu, precision, precond, max_steps, tiles, inner_tol, max_outer):
+def _grid(nlon, nlat, mu, precision, precond, max_steps, tiles, inner_tol, max_outer, protect=True):
     prec = {"fp64": FP64, "mixed": MIXED}.get(precision, precision)
     pc = PRECOND.get(precond, precond)
     return Grid(int(nlon), int(nlat), float(mu), int(prec), int(pc), int(max_steps), int(tiles), float(inner_tol),
-                int(max_outer))
+                int(max_outer), 0 if protect else FLAG_UNPROTECTED)
 
 
 def footprint(nlon, nlat, k=4, precision="fp64", precond="line", tiles=0) -> int:
@@ -216,12 +231,14 @@ class Solver:
     """One FT-GCR(k) problem resident on the GPU (ftgcr_create)."""
 
     def __init__(self, D, mu, k=4, tol=1e-10, precision="fp64", precond="line", max_steps=0, tiles=0,
-                 inner_tol=0.0, max_outer=0):
+                 inner_tol=0.0, max_outer=0, protect=True):
+        """protect=False: plain GCR(k), the paper's unprotected baseline (no
+        fault test, no restore)."""
         L = lib()
         nlat, nlon = D.shape
         self.nlon, self.nlat, self.k, self.tol = int(nlon), int(nlat), int(k), float(tol)
         self.precision = precision
-        g = _grid(nlon, nlat, mu, precision, precond, max_steps, tiles, inner_tol, max_outer)
+        g = _grid(nlon, nlat, mu, precision, precond, max_steps, tiles, inner_tol, max_outer, protect)
         dp, keep = _ptr(D)
         c = Coeffs(dp)
         h = ctypes.c_void_p()
@@ -248,21 +265,23 @@ class Solver:
     def __exit__(self, *a):
         self.close()
 
-    def solve(self, rhs, x, faults=(), stream=None) -> int:
+    def solve(self, rhs, x, faults=(), stream=None, losses=()) -> int:
         """Blocking solve; x holds the initial guess on entry and the solution
-        on exit.  Returns OK or NOT_CONVERGED, raises on errors."""
+        on exit.  faults: single flips (step, vec, index, bit); losses:
+        data-loss events (step, rank, nranks, count, seed).  Returns OK or
+        NOT_CONVERGED, raises on errors."""
         rp, rk = _ptr(rhs)
         xp, xk = _ptr(x)
-        plan, keep = _plan(faults)
+        plan, keep = _plan(faults, losses)
         st = lib().ftgcr_solve(self.h, rp, xp, ctypes.byref(plan) if plan else None, _stream_ptr(stream))
         if st < 0:
             raise FTGCRError(st, "ftgcr_solve")
         return st
 
-    def solve_async(self, rhs, x, faults=(), stream=None) -> None:
+    def solve_async(self, rhs, x, faults=(), stream=None, losses=()) -> None:
         rp, rk = _ptr(rhs)
         xp, xk = _ptr(x)
-        plan, keep = _plan(faults)
+        plan, keep = _plan(faults, losses)
         st = lib().ftgcr_solve_async(self.h, rp, xp, ctypes.byref(plan) if plan else None, _stream_ptr(stream))
         if st < 0:
             raise FTGCRError(st, "ftgcr_solve_async")
@@ -278,7 +297,7 @@ class Solver:
                     detect_steps=[s.detect_step[i] for i in range(n)],
                     detect_ratio=[s.detect_ratio[i] for i in range(n)], res0=s.res0, res_final_rec=s.res_final_rec,
                     res_final_true=s.res_final_true, norm_R=s.norm_R, bytes_resident=s.bytes_resident,
-                    bytes_backup=s.bytes_backup, tiles=s.tiles, status=s.status)
+                    bytes_backup=s.bytes_backup, tiles=s.tiles, status=s.status, loss_events=s.loss_events)
 
     def apply_operator(self, inp, out, stream=None):
         ip, ik = _ptr(inp)
@@ -309,7 +328,8 @@ def _stats_dict(s: Stats) -> dict:
                 faults_detected=s.faults_detected, outer=s.outer, converged=bool(s.converged),
                 detect_steps=[s.detect_step[i] for i in range(n)], detect_ratio=[s.detect_ratio[i] for i in range(n)],
                 res0=s.res0, res_final_rec=s.res_final_rec, res_final_true=s.res_final_true, norm_R=s.norm_R,
-                bytes_resident=s.bytes_resident, bytes_backup=s.bytes_backup, tiles=s.tiles, status=s.status)
+                bytes_resident=s.bytes_resident, bytes_backup=s.bytes_backup, tiles=s.tiles, status=s.status,
+                loss_events=s.loss_events)
 
 
 def solve_noalloc(D, mu, rhs, x, k=4, tol=1e-10, max_steps=0, tiles=0, stream=None):
@@ -330,7 +350,7 @@ def solve_noalloc(D, mu, rhs, x, k=4, tol=1e-10, max_steps=0, tiles=0, stream=No
     return st, _stats_dict(s)
 
 
-def solve_batch(solvers, rhs, xs, faults=None, stream=None) -> None:
+def solve_batch(solvers, rhs, xs, faults=None, stream=None, losses=None) -> None:
     """Enqueue all solves in one persistent launch (ftgcr_solve_batch)."""
     n = len(solvers)
     H = (ctypes.c_void_p * n)(*[s.h.value for s in solvers])
@@ -347,7 +367,8 @@ def solve_batch(solvers, rhs, xs, faults=None, stream=None) -> None:
     P = (ctypes.POINTER(FaultPlan) * n)()
     for i in range(n):
         f = faults[i] if faults else ()
-        plan, arr = _plan(f)
+        lo = losses[i] if losses else ()
+        plan, arr = _plan(f, lo)
         if plan is not None:
             keep += [plan, arr]
             P[i] = ctypes.pointer(plan)
@@ -371,13 +392,13 @@ class Server:
         self._keep = {}
 
     def submit(self, D, mu, rhs, x, k=4, tol=1e-10, precision="fp64", precond="line", faults=(), max_steps=0,
-               tiles=0, inner_tol=0.0, max_outer=0) -> int:
+               tiles=0, inner_tol=0.0, max_outer=0, losses=(), protect=True) -> int:
         nlat, nlon = D.shape
-        g = _grid(nlon, nlat, mu, precision, precond, max_steps, tiles, inner_tol, max_outer)
+        g = _grid(nlon, nlat, mu, precision, precond, max_steps, tiles, inner_tol, max_outer, protect)
         dp, dk = _ptr(D)
         rp, rk = _ptr(rhs)
         xp, xk = _ptr(x)
-        plan, arr = _plan(faults)
+        plan, arr = _plan(faults, losses)
         t = ctypes.c_int64()
         st = lib().ftgcr_server_submit(self.srv, ctypes.byref(g), ctypes.byref(Coeffs(dp)), int(k), float(tol), rp,
                                        xp, ctypes.byref(plan) if plan else None, ctypes.byref(t))
