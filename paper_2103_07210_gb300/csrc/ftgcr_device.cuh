@@ -617,6 +617,7 @@ static __device__ __noinline__ void line_solve_row_seq(const SolveDev<double>& s
   const double* z = sd.lz + (long long)j * n;
   const double num = -row[sk(n - 1)] + __ldg(tx + n - 1) * row[sk(0)] + __ldg(tx + n - 2) * row[sk(m - 1)];
   const double xl = num / __ldg(sd.lrow + (long long)j * 4);
+#pragma unroll 8
   for (int i = 0; i < m; ++i) row[sk(i)] = row[sk(i)] - xl * __ldg(z + i);
   row[sk(n - 1)] = xl;
 }

@@ -682,6 +682,29 @@ __device__ __forceinline__ LineConsts<T> staged_consts(const SolveDev<T>& sd, co
   return LineConsts<T>{cs + (long long)r * per, cs + ((long long)nrows + r) * per, cs + (2LL * nrows + r) * per};
 }
 
+// The preconditioner on the nrows rows of a tile staged in shared memory.
+// FP32 line solve and the pointwise preconditioners: one warp per row.  FP64
+// line solve: one lane per row, the rows side by side in the first warp(s).
+// Each row's solve is the oracle's serial elimination, a chain of dependent
+// FP64 operations, and GB300 issues an FP64 warp instruction at the same cost
+// whatever the number of active lanes (measured: 64 cycles per dependent FMA
+// for 1 to 32 lanes of one warp, 152 with eight warps on the SM), so rows
+// side by side in lanes cost one row's instructions instead of one per row.
+template <typename T>
+__device__ __forceinline__ void precond_tile(const SolveDev<T>& sd, int h0, int nrows, T* sm, int stride, const T* cs) {
+  if constexpr (sizeof(T) == 8) {
+    if (sd.precond == PC_LINE) {
+      for (int jr = threadIdx.x; jr < nrows; jr += kThreads) {
+        const LineConsts<T> lc = staged_consts(sd, cs, nrows, jr);
+        line_solve_row_seq(sd, h0 + jr, sm + jr * stride, lc.cb, lc.cw, lc.cz);
+      }
+      return;
+    }
+  }
+  const int warp = threadIdx.x >> 5;
+  for (int jr = warp; jr < nrows; jr += kWarps) precond_row(sd, h0 + jr, sm + jr * stride, staged_consts(sd, cs, nrows, jr));
+}
+
 // Row-tile halo rows: [h0, h1) = [j0-1, j1+1) clipped to the sphere.
 struct RowTile {
   int j0, j1, h0, h1;
@@ -951,8 +974,7 @@ __device__ __noinline__ void phase_pa(const SolveDev<T>& sd, const Ctx<T>& c, in
   cp_async_wait_all();
   __syncthreads();
   sub_mark(ps, 0);
-  for (int jr = warp; jr < nrows; jr += kWarps)
-    precond_row(sd, rt.h0 + jr, sm + jr * stride, staged_consts(sd, cs, nrows, jr));
+  precond_tile(sd, rt.h0, nrows, sm, stride, cs);
   __syncthreads();
   sub_mark(ps, 1);
   if (threadIdx.x == 0) {
@@ -1243,8 +1265,7 @@ __device__ __noinline__ void phase_init(const SolveDev<T>& sd, const Ctx<T>& c, 
   }
   cp_async_wait_all();
   __syncthreads();
-  for (int jr = warp; jr < rt.h1 - rt.h0; jr += kWarps)
-    precond_row(sd, rt.h0 + jr, sm + jr * stride, staged_consts(sd, cs, rt.h1 - rt.h0, jr));
+  precond_tile(sd, rt.h0, rt.h1 - rt.h0, sm, stride, cs);
   __syncthreads();
   Acc<T> a0, a1;
   for (int j = rt.j0; j < rt.j1; ++j) {
