@@ -394,6 +394,28 @@ __host__ __device__ __forceinline__ int row_stride(int nlon) {
 // Row-local line-solve constants in the per-lane chunk layout [k][lane]
 // (element i = lane*C + k): c_i = Tx_i / w_i, winv_i = 1 / w_i, z_i.  The
 // pointers may address shared memory (staged by the caller) or global memory.
+// Explicit shared-memory accesses.  An out-of-line device function receives
+// shared-memory pointers as generic pointers and, not knowing their state
+// space, accesses them through the slower generic path; the row solves below
+// take the 32-bit shared address once and use ld.shared / st.shared.
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+template <typename T>
+__device__ __forceinline__ T lds(unsigned a);
+template <>
+__device__ __forceinline__ float lds<float>(unsigned a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+  return v;
+}
+template <>
+__device__ __forceinline__ double lds<double>(unsigned a) {
+  double v;
+  asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void sts(unsigned a, float v) { asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory"); }
+__device__ __forceinline__ void sts(unsigned a, double v) { asm volatile("st.shared.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory"); }
+
 template <typename T>
 struct LineConsts {
   const T* cb;
@@ -418,9 +440,10 @@ constexpr int kLB = 8;  // register block of the recurrences
 // scan composes the maps into each chunk's carry-in, and a second pass
 // replays the chunk from its exact carry-in.  The periodic coupling of the
 // last unknown is eliminated by bordering with the precomputed
-// z = A0^-1 (-Tx_{n-1} e_0 - Tx_{n-2} e_{n-2}).
+// z = A0^-1 (-Tx_{n-1} e_0 - Tx_{n-2} e_{n-2}).  row and the constants must be
+// in shared memory.
 template <typename T>
-__device__ __noinline__ void line_solve_row(const SolveDev<T>& sd, int j, T* row, const LineConsts<T> lc) {
+__device__ __noinline__ void line_solve_row(const SolveDev<T>& sd, int j, T* row_, const LineConsts<T> lc) {
   const int lane = threadIdx.x & 31;
   const int n = sd.nlon, m = n - 1, C = sd.C;
   const int i0 = lane * C;
@@ -430,12 +453,16 @@ __device__ __noinline__ void line_solve_row(const SolveDev<T>& sd, int j, T* row
   // behind the recurrences
   const T* lr = sd.lrow + (long long)j * 4;
   const T lr0 = __ldg(lr + 0), lr1 = __ldg(lr + 1), lr2 = __ldg(lr + 2);
-
+  const unsigned rb = smem_addr(row_), cbb = smem_addr(lc.cb), cwb = smem_addr(lc.cw), czb = smem_addr(lc.cz);
+  constexpr unsigned E = sizeof(T);
+  auto R = [&](int i) { return rb + E * (unsigned)sk(i); };
+  auto Cb = [&](int k) { return cbb + E * (unsigned)(k * 32 + lane); };
+  auto Cw = [&](int k) { return cwb + E * (unsigned)(k * 32 + lane); };
+  auto Cz = [&](int k) { return czb + E * (unsigned)(k * 32 + lane); };
   // forward multiplier of chunk element 0 is c_{i0-1}, the last c of the previous lane
-  const T mylast = (len > 0) ? lc.cb[(len - 1) * 32 + lane] : T(0);
+  const T mylast = (len > 0) ? lds<T>(Cb(len - 1)) : T(0);
   T a0 = __shfl_up_sync(0xffffffffu, mylast, 1);
   if (lane == 0) a0 = T(0);
-
   // pass 1: affine map g_out = F g_in + G of the chunk
   T F = T(1), G = T(0);
   {
@@ -445,8 +472,8 @@ __device__ __noinline__ void line_solve_row(const SolveDev<T>& sd, int j, T* row
 #pragma unroll
       for (int q = 0; q < kLB; ++q)
         if (kb + q < len) {
-          rv[q] = row[sk(i0 + kb + q)];
-          cv[q] = lc.cb[(kb + q) * 32 + lane];
+          rv[q] = lds<T>(R(i0 + kb + q));
+          cv[q] = lds<T>(Cb(kb + q));
         }
 #pragma unroll
       for (int q = 0; q < kLB; ++q)
@@ -477,8 +504,8 @@ __device__ __noinline__ void line_solve_row(const SolveDev<T>& sd, int j, T* row
 #pragma unroll
       for (int q = 0; q < kLB; ++q)
         if (kb + q < len) {
-          rv[q] = row[sk(i0 + kb + q)];
-          cv[q] = lc.cb[(kb + q) * 32 + lane];
+          rv[q] = lds<T>(R(i0 + kb + q));
+          cv[q] = lds<T>(Cb(kb + q));
         }
 #pragma unroll
       for (int q = 0; q < kLB; ++q)
@@ -489,7 +516,7 @@ __device__ __noinline__ void line_solve_row(const SolveDev<T>& sd, int j, T* row
         }
 #pragma unroll
       for (int q = 0; q < kLB; ++q)
-        if (kb + q < len) row[sk(i0 + kb + q)] = rv[q];
+        if (kb + q < len) sts(R(i0 + kb + q), rv[q]);
     }
   }
   // pass 3: affine map of the backward recurrence y_in = Fb y_out + Y
@@ -500,9 +527,9 @@ __device__ __noinline__ void line_solve_row(const SolveDev<T>& sd, int j, T* row
 #pragma unroll
     for (int q = 0; q < kLB; ++q)
       if (kb + q < len) {
-        gv[q] = row[sk(i0 + kb + q)];
-        cv[q] = lc.cb[(kb + q) * 32 + lane];
-        wv[q] = lc.cw[(kb + q) * 32 + lane];
+        gv[q] = lds<T>(R(i0 + kb + q));
+        cv[q] = lds<T>(Cb(kb + q));
+        wv[q] = lds<T>(Cw(kb + q));
       }
 #pragma unroll
     for (int q = kLB - 1; q >= 0; --q)
@@ -531,9 +558,9 @@ __device__ __noinline__ void line_solve_row(const SolveDev<T>& sd, int j, T* row
 #pragma unroll
       for (int q = 0; q < kLB; ++q)
         if (kb + q < len) {
-          gv[q] = row[sk(i0 + kb + q)];
-          cv[q] = lc.cb[(kb + q) * 32 + lane];
-          wv[q] = lc.cw[(kb + q) * 32 + lane];
+          gv[q] = lds<T>(R(i0 + kb + q));
+          cv[q] = lds<T>(Cb(kb + q));
+          wv[q] = lds<T>(Cw(kb + q));
         }
 #pragma unroll
       for (int q = kLB - 1; q >= 0; --q)
@@ -543,22 +570,19 @@ __device__ __noinline__ void line_solve_row(const SolveDev<T>& sd, int j, T* row
         }
 #pragma unroll
       for (int q = 0; q < kLB; ++q)
-        if (kb + q < len) row[sk(i0 + kb + q)] = gv[q];
+        if (kb + q < len) sts(R(i0 + kb + q), gv[q]);
     }
   }
   __syncwarp();
   // bordering: x_{n-1} = (b_{n-1} + Tx_{n-1} y_0 + Tx_{n-2} y_{m-1}) / delta
-  const T y0 = row[sk(0)];
-  const T ym = row[sk(m - 1)];
-  const T bl = -row[sk(n - 1)];
+  const T y0 = lds<T>(R(0));
+  const T ym = lds<T>(R(m - 1));
+  const T bl = -lds<T>(R(n - 1));
   const T xl = tfma(lr2, ym, tfma(lr1, y0, bl * lr0));
   __syncwarp();
 #pragma unroll 8
-  for (int k = 0; k < len; ++k) {
-    const int s = sk(i0 + k);
-    row[s] = tfma(-xl, lc.cz[k * 32 + lane], row[s]);
-  }
-  if (lane == 0) row[sk(n - 1)] = xl;
+  for (int k = 0; k < len; ++k) sts(R(i0 + k), tfma(-xl, lds<T>(Cz(k)), lds<T>(R(i0 + k))));
+  if (lane == 0) sts(R(n - 1), xl);
   __syncwarp();
 }
 
@@ -641,6 +665,61 @@ __device__ void pointwise_precond_row(const SolveDev<T>& sd, int j, T* row) {
 
 // Preconditioner solve of one row by one warp.  FP32: the chunked warp
 // solve; FP64: lane 0 runs the oracle-identical sequential solve.
+// The same serial solve with the row and its factors in shared memory
+// (explicit ld.shared / st.shared), stopping at x_{n-1}: the caller applies
+// x_i = y_i - x_{n-1} z_i to all rows of the tile block-wide, the same
+// operations element by element.
+static __device__ __noinline__ void line_solve_row_seq_sh(const SolveDev<double>& sd, int j, double* row_, const double* l_,
+                                     const double* winv_, const double* u_) {
+  const int n = sd.nlon, m = n - 1;
+  const unsigned rb = smem_addr(row_), lb = smem_addr(l_), wb = smem_addr(winv_), ub = smem_addr(u_);
+  auto R = [&](int i) { return rb + 8u * (unsigned)sk(i); };
+  double y = -lds<double>(R(0));
+  sts(R(0), y);
+  for (int i0 = 1; i0 < m; i0 += kLB) {
+    double bv[kLB], lv[kLB];
+#pragma unroll
+    for (int q = 0; q < kLB; ++q)
+      if (i0 + q < m) {
+        bv[q] = -lds<double>(R(i0 + q));
+        lv[q] = lds<double>(lb + 8u * (unsigned)(i0 + q));
+      }
+#pragma unroll
+    for (int q = 0; q < kLB; ++q)
+      if (i0 + q < m) {
+        y = fma(-lv[q], y, bv[q]);
+        bv[q] = y;
+      }
+#pragma unroll
+    for (int q = 0; q < kLB; ++q)
+      if (i0 + q < m) sts(R(i0 + q), bv[q]);
+  }
+  y = lds<double>(R(m - 1)) * lds<double>(wb + 8u * (unsigned)(m - 1));
+  sts(R(m - 1), y);
+  for (int i1 = m - 2; i1 >= 0; i1 -= kLB) {
+    double gv[kLB], wv[kLB], uv[kLB];
+#pragma unroll
+    for (int q = 0; q < kLB; ++q)
+      if (i1 - q >= 0) {
+        gv[q] = lds<double>(R(i1 - q));
+        wv[q] = lds<double>(wb + 8u * (unsigned)(i1 - q));
+        uv[q] = lds<double>(ub + 8u * (unsigned)(i1 - q));
+      }
+#pragma unroll
+    for (int q = 0; q < kLB; ++q)
+      if (i1 - q >= 0) {
+        y = fma(-uv[q], y, gv[q] * wv[q]);
+        gv[q] = y;
+      }
+#pragma unroll
+    for (int q = 0; q < kLB; ++q)
+      if (i1 - q >= 0) sts(R(i1 - q), gv[q]);
+  }
+  const double* tx = sd.Tx + (long long)j * n;
+  const double num = -lds<double>(R(n - 1)) + __ldg(tx + n - 1) * lds<double>(R(0)) + __ldg(tx + n - 2) * lds<double>(R(m - 1));
+  sts(R(n - 1), num / __ldg(sd.lrow + (long long)j * 4));
+}
+
 template <typename T>
 __device__ __forceinline__ void precond_row(const SolveDev<T>& sd, int j, T* row, const LineConsts<T> lc) {
   if (sd.precond == PC_LINE) {

@@ -696,7 +696,15 @@ __device__ __forceinline__ void precond_tile(const SolveDev<T>& sd, int h0, int 
     if (sd.precond == PC_LINE) {
       for (int jr = threadIdx.x; jr < nrows; jr += kThreads) {
         const LineConsts<T> lc = staged_consts(sd, cs, nrows, jr);
-        line_solve_row_seq(sd, h0 + jr, sm + jr * stride, lc.cb, lc.cw, lc.cz);
+        line_solve_row_seq_sh(sd, h0 + jr, sm + jr * stride, lc.cb, lc.cw, lc.cz);
+      }
+      __syncthreads();
+      // bordering, x_i = y_i - x_{n-1} z_i, all rows at once
+      const int n = sd.nlon, m = n - 1;
+      for (int idx = threadIdx.x; idx < nrows * m; idx += kThreads) {
+        const int jr = idx / m, i = idx - jr * m;
+        T* row = sm + jr * stride;
+        row[sk(i)] = row[sk(i)] - row[sk(n - 1)] * __ldg(sd.lz + (long long)(h0 + jr) * n + i);
       }
       return;
     }
