@@ -192,6 +192,43 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ larger grids
+def bench_large(torch, ftgcr, dev, flush, sizes=((2048, 1024), (4096, 2048)), reps=3):
+    """Single mixed solves on grids whose working set exceeds the 129 MB L2
+    (1024x512 stays L2-resident), so that the roofline fraction measures HBM:
+    per size the event-timed solve, inner steps, algorithmic bytes and
+    achieved bandwidth against the measured copy peak."""
+    peak, peak_kind = read_peaks()
+    stream = torch.cuda.current_stream()
+    out = {}
+    for nlon, nlat in sizes:
+        p = inputs.hill_problem(nlon, nlat)
+        R = torch.from_numpy(p.R).to(dev)
+        x = torch.zeros_like(R)
+        with ftgcr.Solver(p.D, p.mu, k=K, tol=TOL, precision="mixed") as s:
+            s.solve_async(R, x, stream=stream)  # warm
+            ms = []
+            for _ in range(reps):
+                x.zero_()
+                flush.fill_(3)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                s.solve_async(R, x, stream=stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+            info = s.stats()
+        t = float(np.median(ms))
+        nb = algorithmic_bytes(info["steps"], info["outer"], N=nlon * nlat)
+        gbs = nb / (t * 1e-3) / 1e9
+        out[f"{nlon}x{nlat}"] = {"ms": t, "solves_per_s": 1e3 / t, "inner_steps": info["steps"],
+                                 "refinement_sweeps": info["outer"], "tiles": info["tiles"],
+                                 "algorithmic_bytes": nb, "achieved_gbs": gbs, "frac": gbs / peak,
+                                 "peak_kind": peak_kind, "converged": info["converged"],
+                                 "residual_rel": info["res_final_true"] / info["norm_R"]}
+    return out
+
+
 # ------------------------------------------------------------------ batch and serving mixes
 def bench_batch(torch, ftgcr, dev, n=128, seed=42, reps=3):
     """128 independent mixed-precision solves of sizes U{128x64, 256x128,
@@ -455,6 +492,8 @@ def run_ours(args):
             "gpu_launches": 2 * args.steps,
             "clocks": clocks,
         }
+        if not args.no_large and ws == 1:
+            line["large_grids"] = bench_large(torch, ftgcr, dev, flush)
         if not args.no_batch and ws == 1:
             line["batch"] = bench_batch(torch, ftgcr, dev)
         if not args.no_serving and ws == 1:
@@ -481,6 +520,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 128-solve batched launch")
+    ap.add_argument("--no-large", action="store_true", help="skip the 2048x1024 and 4096x2048 solves")
     ap.add_argument("--no-serving", action="store_true", help="skip the open-loop serving run")
     ap.add_argument("--serving-requests", type=int, default=2000)
     ap.add_argument("--serving-load", type=float, default=0.8, help="arrival rate / measured capacity")

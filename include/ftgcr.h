@@ -73,7 +73,10 @@ extern "C" {
 typedef struct ftgcr_handle ftgcr_handle;
 
 typedef struct {
-  int32_t nlon;      /* >= 3 */
+  int32_t nlon;      /* >= 3; one latitude row with its two halo rows and, for the line
+                        preconditioner, their factors must fit in one SM's shared
+                        memory: nlon <= about 2150 (FTGCR_FP64) or 4350 (FTGCR_MIXED),
+                        else FTGCR_ERR_ARG */
   int32_t nlat;      /* >= 1 */
   double mu;         /* Helmholtz coefficient per unit area, >= 0 (mu > 0 makes -L definite) */
   int32_t precision; /* FTGCR_FP64 | FTGCR_MIXED */

@@ -1,0 +1,52 @@
+"""Wide latitude rows (FP64 2048 x 32; mixed 4096 x 16), whose staged rows and
+line-solve constants fill shared memory so that each band holds a single
+row: the same results as the oracle (FP64: identical decisions, solution
+rel <= 1e-10; mixed: converged at tol 1e-10 with a true residual below it,
+solution within 1e-7 of the oracle's at tol 1e-12 -- these strongly
+anisotropic grids keep the true residual of any solve near 1e-12 relative, so
+the mixed path's FP64 refinement cannot be asked for 1e-13 here).  Rows too
+wide for one band on chip are refused at creation."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_07210_gb300 import ftgcr, inputs
+from tests.gpu_util import rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _solve(p, k, tol, precision, faults=()):
+    with ftgcr.Solver(p.D, p.mu, k=k, tol=tol, precision=precision) as s:
+        R = torch.from_numpy(p.R).cuda()
+        x = torch.zeros_like(R)
+        st = s.solve(R, x, faults=faults)
+        return st, x.cpu().numpy(), s.stats()
+
+
+def test_fp64_wide_rows_match_oracle():
+    p = inputs.hill_problem(2048, 32, rhs="random", seed=31)
+    faults = [(4, "r", 40000, 62)]
+    o = oracle.ftgcr(p.D, p.R, p.mu, 4, 1e-10, faults=faults)
+    st, x, s = _solve(p, 4, 1e-10, "fp64", faults)
+    assert s["tiles"] == 32
+    assert s["steps"] == o["steps"] and s["detect_steps"] == o["detect_steps"] and s["converged"] == o["converged"]
+    assert rel_err(x, o["x"]) <= 1e-10
+
+
+def test_mixed_wide_rows_match_oracle():
+    p = inputs.hill_problem(4096, 16, rhs="random", seed=32)
+    o = oracle.ftgcr(p.D, p.R, p.mu, 4, 1e-12)
+    st, x, s = _solve(p, 4, 1e-10, "mixed")
+    assert st == ftgcr.OK and s["converged"] and s["tiles"] == 16
+    assert s["res_final_true"] <= 1e-10 * s["norm_R"]
+    assert rel_err(x, o["x"]) <= 1e-7
+
+
+def test_rows_too_wide_for_one_band_are_refused():
+    p = inputs.hill_problem(8192, 8)
+    for prec in ("fp64", "mixed"):
+        with pytest.raises(ftgcr.FTGCRError) as ei:
+            ftgcr.Solver(p.D, p.mu, precision=prec)
+        assert ei.value.status == ftgcr.ERR_ARG
