@@ -178,7 +178,9 @@ int ftgcr_solve(ftgcr_handle* h, const double* rhs, double* x, const ftgcr_fault
 
 /* Same as ftgcr_solve but only enqueues the work on `stream` and returns;
  * rhs and x must be device memory.  The status of the solve is read with
- * ftgcr_stats() once the stream has reached the end of the solve. */
+ * ftgcr_stats() once the stream has reached the end of the solve.  It
+ * allocates nothing and synchronises nothing, so it may be captured into a
+ * CUDA graph (stream capture) and the graph replayed. */
 int ftgcr_solve_async(ftgcr_handle* h, const double* rhs, double* x, const ftgcr_fault_plan* plan, void* stream);
 
 /* Statistics of the last solve of h (synchronises with its stream). */
