@@ -96,6 +96,11 @@ typedef struct {
 
 typedef struct {
   const double* D;   /* [nlat][nlon] cell-centred coefficient (column depth 1 - h), > 0 */
+  uint64_t key;      /* serving only: 0, or a caller-chosen identity of D's contents.
+                        Passing the same (D, key) pair promises the same contents,
+                        so a pooled handle already set up from it is reused without
+                        rebuilding its operator and factorisation (the paper's
+                        operator is fixed across a model's time steps). */
 } ftgcr_coeffs;
 
 /* One single-bit flip: at executed step `step` (1-based, re-executed steps
@@ -258,7 +263,9 @@ int ftgcr_solve_noalloc(const ftgcr_grid* grid, const double* D, int32_t k, doub
  *    first when a new shape does not fit.  budget_bytes = 0 means half of the
  *    device memory free at creation.
  *  - Pointers: D, rhs and x may be host or device memory and must stay valid,
- *    and x untouched by the caller, until poll/wait reports the result.
+ *    and x untouched by the caller, until poll/wait reports the result.  Host
+ *    rhs and x are checked for finite values by submit itself (on the
+ *    caller's thread); pinned host memory is copied asynchronously.
  *  - Thread safety: submit, poll, wait and info may be called from any
  *    thread; destroy must not overlap any other call on the same server. */
 typedef struct ftgcr_server ftgcr_server;

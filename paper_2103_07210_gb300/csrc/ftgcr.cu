@@ -200,15 +200,19 @@ __global__ void k_begin_solve(SolveDev<T>* sd, BeginArgs b, int* active, int n_a
     S.phiS = S.rS = 0;
     S.phiW = S.rW = 1;
     S.status = ST_RUNNING;
-    sd->st[par] = S;
-    sd->st[par ^ 1] = S;
+    // par < 0: the round parity of the launch that will run the solve is not
+    // known yet (the solve joins a resumable launch), so mark it active in both
+    const int p = par < 0 ? 0 : par;
+    sd->st[p] = S;
+    sd->st[p ^ 1] = S;
     *sd->result = S;
-    active[par * n_active + slot] = 1;
+    active[p * n_active + slot] = 1;
+    if (par < 0) active[(p ^ 1) * n_active + slot] = 1;
     if (ctl) {
       ctl->counter = 0;
       ctl->err = 0;
-      ctl->round0 = par;
-      ctl->round_end = par;
+      ctl->round0 = p;
+      ctl->round_end = p;
     }
   }
   for (int q = threadIdx.x; q < b.nfaults; q += blockDim.x) const_cast<Fault*>(sd->faults)[q] = b.faults[q];
@@ -777,6 +781,7 @@ struct SlotTableImpl {
   int* h_act = nullptr;            // pinned: active flags read back after it
   int grid_cap = 0;
   std::vector<ftgcr_handle*> slot;
+  std::vector<char> launched;  // slots occupied when the last launch was enqueued
 };
 
 template <typename T>
@@ -798,6 +803,7 @@ int table_run_impl(SlotTableImpl* t, int max_rounds, cudaStream_t st) {
   if (rc) return rc;
   if (occ < 1) return FTGCR_ERR_ARG;
   const int grid = (int)std::min<long long>({tiles, (long long)device_info(t->dev).sms * occ, (long long)t->grid_cap});
+  for (int s = 0; s < t->n; ++s) t->launched[s] = t->slot[s] != nullptr;
   t->h_ctl_in->counter = 0;
   t->h_ctl_in->err = 0;
   t->h_ctl_in->round0 = t->round;
@@ -1094,6 +1100,7 @@ int table_create(int precision, int max_slots, SlotTable** out) {
   t->precision = precision;
   t->n = max_slots;
   t->slot.assign(max_slots, nullptr);
+  t->launched.assign(max_slots, 0);
   CK(cudaGetDevice(&t->dev));
   const DeviceInfo di = device_info(t->dev);
   t->grid_cap = di.sms * 4;
@@ -1142,11 +1149,11 @@ int table_begin(SlotTable* t, int slot, ftgcr_handle* h, const double* rhs, doub
   CK(cudaMemcpyAsync(t->d_solves + slot, &h->sdev, sizeof(void*), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(t->d_nt + slot, &h->nt, sizeof(int), cudaMemcpyHostToDevice, st));
   const BeginArgs b = begin_args(h, rhs, x, x, plan);
-  const int par = (int)(t->round & 1);
+  // parity -1: the begin may be enqueued behind a launch still running
   if (t->precision == FTGCR_MIXED)
-    k_begin_solve<float><<<1, 64, 0, st>>>((SolveDev<float>*)h->sdev, b, t->d_act, t->n, slot, par, nullptr);
+    k_begin_solve<float><<<1, 64, 0, st>>>((SolveDev<float>*)h->sdev, b, t->d_act, t->n, slot, -1, nullptr);
   else
-    k_begin_solve<double><<<1, 64, 0, st>>>((SolveDev<double>*)h->sdev, b, t->d_act, t->n, slot, par, nullptr);
+    k_begin_solve<double><<<1, 64, 0, st>>>((SolveDev<double>*)h->sdev, b, t->d_act, t->n, slot, -1, nullptr);
   CK(cudaGetLastError());
   t->slot[slot] = h;
   return FTGCR_OK;
@@ -1161,14 +1168,17 @@ int table_run(SlotTable* t, int max_rounds, cudaStream_t st) {
 int table_collect(SlotTable* t, cudaStream_t st, int* finished) {
   if (!t || !finished) return FTGCR_ERR_ARG;
   for (int s = 0; s < t->n; ++s) finished[s] = 0;
-  if (table_occupied(t) == 0) return FTGCR_OK;
+  bool any = false;
+  for (int s = 0; s < t->n; ++s) any = any || (t->launched[s] && t->slot[s]);
+  if (!any) return FTGCR_OK;
   CK(cudaStreamSynchronize(st));
   const int err = t->h_ctl_out->err;
   t->round = t->h_ctl_out->round_end;
   const int par = (int)(t->round & 1);
   for (int s = 0; s < t->n; ++s) {
     ftgcr_handle* h = t->slot[s];
-    if (!h) continue;
+    if (!h || !t->launched[s]) continue;  // begun after the launch: runs in the next one
+    t->launched[s] = 0;
     if (!err && t->h_act[par * t->n + s]) continue;
     CK(cudaMemcpy(h->h_result, h->result, sizeof(SolveState), cudaMemcpyDeviceToHost));
     *h->h_ctl = *t->h_ctl_out;

@@ -23,15 +23,16 @@ int table_create(int precision, int max_slots, SlotTable** out);
 void table_destroy(SlotTable* t);
 
 // Begin a solve of h in a free slot.  rhs, x: device pointers (x: initial
-// guess in, solution out), valid until the solve has finished.  Enqueued on st.
+// guess in, solution out), valid until the solve has finished.  Enqueued on st;
+// it may be enqueued behind a launch still in flight, and then joins the next.
 int table_begin(SlotTable* t, int slot, ftgcr_handle* h, const double* rhs, double* x, const ftgcr_fault_plan* plan,
                 cudaStream_t st);
 
 // Run every occupied slot for at most max_rounds rounds (enqueued on st).
 int table_run(SlotTable* t, int max_rounds, cudaStream_t st);
 
-// Once st has passed table_run: finished[s] = 1 for every slot whose solve
-// ended in that run (its handle then holds the result that ftgcr_stats()
+// Once st has passed table_run: finished[s] = 1 for every slot of that run
+// whose solve ended in it (its handle then holds the result that ftgcr_stats()
 // reports, and the slot is free again), else 0.  A launch whose grid barrier
 // gave up ends every occupied slot, each with FTGCR_ERR_TIMEOUT.
 int table_collect(SlotTable* t, cudaStream_t st, int* finished);

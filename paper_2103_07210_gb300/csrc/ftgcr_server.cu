@@ -53,6 +53,8 @@ struct HandleKey {
 struct PoolEntry {
   HandleKey key;
   ftgcr_handle* h = nullptr;  // created by the scheduler thread on first use
+  const double* setup_D = nullptr;  // coefficients the handle was last set up from
+  uint64_t setup_key = 0;           // with their caller-given identity (0: none)
   int64_t bytes = 0;
   bool busy = false;
   uint64_t last_used = 0;
@@ -62,6 +64,7 @@ struct Request {
   int64_t ticket = 0;
   HandleKey key;
   const double* D = nullptr;
+  uint64_t ckey = 0;
   const double* rhs = nullptr;
   double* x = nullptr;
   std::vector<ftgcr_fault> faults;
@@ -106,10 +109,16 @@ struct ftgcr_server {
       if (!slot_req[t][s]) return s;
     return -1;
   }
-  PoolEntry* idle_entry(const HandleKey& key) {
-    for (PoolEntry& e : pool)
-      if (!e.busy && e.h && e.key == key) return &e;
-    return nullptr;
+  // An idle handle of the request's shape, preferably one already set up
+  // from the same coefficients.
+  PoolEntry* idle_entry(const Request* r) {
+    PoolEntry* any = nullptr;
+    for (PoolEntry& e : pool) {
+      if (e.busy || !e.h || !(e.key == r->key)) continue;
+      if (r->ckey && e.setup_key == r->ckey && e.setup_D == r->D) return &e;
+      if (!any) any = &e;
+    }
+    return any;
   }
   // Evict idle handles (least recently used first) until `need` more bytes
   // fit; the evicted handles are destroyed by the caller, outside the lock.
@@ -131,11 +140,13 @@ struct ftgcr_server {
       const int t = table_of(r->key.grid.precision);
       const int slot = free_slot(t);
       if (slot < 0) break;
-      PoolEntry* e = idle_entry(r->key);
+      PoolEntry* e = idle_entry(r);
       if (!e) {
         if (!make_room(r->footprint, victims)) break;  // wait for running solves to free memory
-        pool.push_back(PoolEntry{r->key, nullptr, r->footprint, false, 0});
+        pool.emplace_back();
         e = &pool.back();
+        e->key = r->key;
+        e->bytes = r->footprint;
         in_use += r->footprint;
       }
       e->busy = true;
@@ -173,7 +184,7 @@ struct ftgcr_server {
   // ---- scheduler thread, outside the lock
   int start(Request* r) {
     PoolEntry* e = r->entry;
-    ftgcr_coeffs co{r->D};
+    ftgcr_coeffs co{r->D, r->ckey};
     int rc;
     if (!e->h) {
       ftgcr_handle* h = nullptr;
@@ -181,10 +192,13 @@ struct ftgcr_server {
       if (rc) return rc;
       std::lock_guard<std::mutex> lk(mu);
       e->h = h;
-    } else {
+    } else if (!(r->ckey && e->setup_key == r->ckey && e->setup_D == r->D)) {
+      e->setup_key = 0;  // invalid until the rebuild is enqueued
       rc = ftgcr_set_coeffs(e->h, &co, st);
       if (rc) return rc;
     }
+    e->setup_D = r->D;
+    e->setup_key = r->ckey;
     ftgcr_handle* h = e->h;
     const long long N = handle_points(h);
     const double* R = r->rhs;
@@ -194,16 +208,13 @@ struct ftgcr_server {
     cudaGetLastError();
     const bool xdev = cudaPointerGetAttributes(&at, X) == cudaSuccess && at.type == cudaMemoryTypeDevice;
     cudaGetLastError();
+    // host arrays were checked for finite values at submit, by the caller's thread
     if (!rdev) {
-      for (long long i = 0; i < N; ++i)
-        if (!std::isfinite(R[i])) return FTGCR_ERR_ARG;
       if (cudaMemcpyAsync(handle_stage_rhs(h), R, sizeof(double) * N, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return FTGCR_ERR_CUDA;
       R = handle_stage_rhs(h);
     }
     if (!xdev) {
-      for (long long i = 0; i < N; ++i)
-        if (!std::isfinite(X[i])) return FTGCR_ERR_ARG;
       if (cudaMemcpyAsync(handle_stage_x(h), X, sizeof(double) * N, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return FTGCR_ERR_CUDA;
       X = handle_stage_x(h);
@@ -238,15 +249,42 @@ struct ftgcr_server {
     for (Request* r : lost) finish_locked(r, status);
   }
 
+  // Collect the launches in flight: hand back their finished solves.
+  void collect(bool* inflight, std::vector<int>& fin) {
+    for (int t = 0; t < 2; ++t) {
+      if (!inflight[t]) continue;
+      inflight[t] = false;
+      const int rc = table_collect(tables[t], st, fin.data());
+      if (rc && rc != FTGCR_ERR_TIMEOUT) {
+        fail_table(t, rc);
+        cv_done.notify_all();
+        continue;
+      }
+      std::vector<Request*> done;
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        for (int s = 0; s < max_slots; ++s)
+          if (fin[s] && slot_req[t][s]) done.push_back(slot_req[t][s]);
+      }
+      for (Request* r : done) complete(r);
+      if (!done.empty()) cv_done.notify_all();
+    }
+  }
+
+  // One epoch per iteration, pipelined: while launch e runs on the GPU the
+  // thread admits and prepares new requests (host checks, copies and begin
+  // kernels queued behind launch e), then collects launch e and enqueues
+  // launch e + 1, which the prepared requests join.
   void loop() {
     cudaSetDevice(dev);
     std::vector<int> fin(max_slots);
+    bool inflight[2] = {false, false};
     for (;;) {
       std::vector<Request*> adm;
       std::vector<ftgcr_handle*> victims;
       {
         std::unique_lock<std::mutex> lk(mu);
-        cv_work.wait(lk, [&] { return stop || running > 0 || !queue.empty(); });
+        if (!inflight[0] && !inflight[1]) cv_work.wait(lk, [&] { return stop || running > 0 || !queue.empty(); });
         if (stop && running == 0) break;
         admit(adm, victims);
       }
@@ -259,7 +297,7 @@ struct ftgcr_server {
           cv_done.notify_all();
         }
       }
-      bool launched[2] = {false, false};
+      collect(inflight, fin);
       for (int t = 0; t < 2; ++t) {
         if (table_occupied(tables[t]) == 0) continue;
         const int rc = table_run(tables[t], epoch_rounds, st);
@@ -268,29 +306,13 @@ struct ftgcr_server {
           cv_done.notify_all();
           continue;
         }
-        launched[t] = true;
+        inflight[t] = true;
         std::lock_guard<std::mutex> lk(mu);
         ++epochs;
       }
-      for (int t = 0; t < 2; ++t) {
-        if (!launched[t]) continue;
-        const int rc = table_collect(tables[t], st, fin.data());
-        if (rc && rc != FTGCR_ERR_TIMEOUT) {
-          fail_table(t, rc);
-          cv_done.notify_all();
-          continue;
-        }
-        std::vector<Request*> done;
-        {
-          std::lock_guard<std::mutex> lk(mu);
-          for (int s = 0; s < max_slots; ++s)
-            if (fin[s] && slot_req[t][s]) done.push_back(slot_req[t][s]);
-        }
-        for (Request* r : done) complete(r);
-        if (!done.empty()) cv_done.notify_all();
-      }
     }
   }
+
 };
 
 extern "C" {
@@ -369,10 +391,26 @@ int ftgcr_server_submit(ftgcr_server* srv, const ftgcr_grid* grid, const ftgcr_c
     }
     r->faults.assign(plan->faults, plan->faults + plan->n);
   }
+  // host arrays: reject non-finite values here, on the submitting thread, so
+  // that the scheduler thread only copies them
+  auto host_finite = [&](const double* a) {
+    cudaPointerAttributes at;
+    const bool dev = cudaPointerGetAttributes(&at, a) == cudaSuccess && at.type == cudaMemoryTypeDevice;
+    cudaGetLastError();
+    if (dev) return true;
+    for (long long i = 0; i < N; ++i)
+      if (!std::isfinite(a[i])) return false;
+    return true;
+  };
+  if (!host_finite(rhs) || !host_finite(x)) {
+    delete r;
+    return FTGCR_ERR_ARG;
+  }
   r->key.grid = *grid;
   r->key.k = k;
   r->key.tol = tol;
   r->D = coeffs->D;
+  r->ckey = coeffs->key;
   r->rhs = rhs;
   r->x = x;
   r->footprint = fp;

@@ -57,7 +57,7 @@ class Grid(ctypes.Structure):
 
 
 class Coeffs(ctypes.Structure):
-    _fields_ = [("D", ctypes.c_void_p)]
+    _fields_ = [("D", ctypes.c_void_p), ("key", ctypes.c_uint64)]
 
 
 class Fault(ctypes.Structure):
@@ -240,7 +240,7 @@ class Solver:
         self.precision = precision
         g = _grid(nlon, nlat, mu, precision, precond, max_steps, tiles, inner_tol, max_outer, protect)
         dp, keep = _ptr(D)
-        c = Coeffs(dp)
+        c = Coeffs(dp, 0)
         h = ctypes.c_void_p()
         st = L.ftgcr_create(ctypes.byref(g), ctypes.byref(c), int(k), float(tol), ctypes.byref(h))
         del keep
@@ -316,7 +316,7 @@ class Solver:
     def set_coeffs(self, D, stream=None):
         """Rebuild the operator and preconditioner from a new D (same grid)."""
         dp, keep = _ptr(D)
-        c = Coeffs(dp)
+        c = Coeffs(dp, 0)
         st = lib().ftgcr_set_coeffs(self.h, ctypes.byref(c), _stream_ptr(stream))
         if st < 0:
             raise FTGCRError(st, "ftgcr_set_coeffs")
@@ -392,7 +392,9 @@ class Server:
         self._keep = {}
 
     def submit(self, D, mu, rhs, x, k=4, tol=1e-10, precision="fp64", precond="line", faults=(), max_steps=0,
-               tiles=0, inner_tol=0.0, max_outer=0, losses=(), protect=True) -> int:
+               tiles=0, inner_tol=0.0, max_outer=0, losses=(), protect=True, coeff_key=0) -> int:
+        """coeff_key: 0, or an identity of D's contents; the same (D, key) pair
+        lets a pooled handle already set up from it skip the set-up."""
         nlat, nlon = D.shape
         g = _grid(nlon, nlat, mu, precision, precond, max_steps, tiles, inner_tol, max_outer, protect)
         dp, dk = _ptr(D)
@@ -400,7 +402,7 @@ class Server:
         xp, xk = _ptr(x)
         plan, arr = _plan(faults, losses)
         t = ctypes.c_int64()
-        st = lib().ftgcr_server_submit(self.srv, ctypes.byref(g), ctypes.byref(Coeffs(dp)), int(k), float(tol), rp,
+        st = lib().ftgcr_server_submit(self.srv, ctypes.byref(g), ctypes.byref(Coeffs(dp, int(coeff_key))), int(k), float(tol), rp,
                                        xp, ctypes.byref(plan) if plan else None, ctypes.byref(t))
         if st < 0:
             raise FTGCRError(st, "ftgcr_server_submit")

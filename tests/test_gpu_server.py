@@ -110,6 +110,22 @@ def test_a_pooled_handle_takes_the_next_requests_coefficients():
         assert np.array_equal(x, xa) and ss["steps"] == sa["steps"]
 
 
+def test_coefficient_keys_reuse_set_up_handles_correctly():
+    a = inputs.hill_problem(256, 128, **inputs.random_hill(13))
+    b = inputs.hill_problem(256, 128, **inputs.random_hill(14))
+    Da, Db = torch.from_numpy(a.D).cuda(), torch.from_numpy(b.D).cuda()
+    with ftgcr.Server(max_slots=2) as srv:
+        out = []
+        for p, D, key in ((a, Da, 1), (b, Db, 2), (a, Da, 1), (b, Db, 2), (a, Da, 0)):
+            x = torch.zeros(p.R.shape, dtype=torch.float64, device="cuda")
+            st, ss = srv.wait(srv.submit(D, p.mu, torch.from_numpy(p.R).cuda(), x, coeff_key=key), timeout=60)
+            assert st == ftgcr.OK
+            out.append((p, x.cpu().numpy(), ss))
+    for p, x, ss in out:
+        xa, sa = _alone(p, "fp64", (), 4)
+        assert np.array_equal(x, xa) and ss["steps"] == sa["steps"]
+
+
 def test_admission_stays_within_the_budget():
     small = ftgcr.footprint(256, 128, 4)
     budget = int(small * 2.5)
@@ -145,5 +161,10 @@ def test_invalid_requests_are_refused_at_submit():
         assert ei.value.status == ftgcr.ERR_ARG
         with pytest.raises(ftgcr.FTGCRError):
             srv.submit(p.D, p.mu, p.R, np.zeros_like(p.R), k=0)
+        bad = p.R.copy()
+        bad[3, 5] = np.nan
+        with pytest.raises(ftgcr.FTGCRError) as ei:
+            srv.submit(p.D, p.mu, bad, np.zeros_like(p.R))  # non-finite host right-hand side
+        assert ei.value.status == ftgcr.ERR_ARG
         with pytest.raises(ftgcr.FTGCRError):
             srv.poll(12345)
