@@ -44,7 +44,9 @@ def algorithmic_bytes(steps: int, outer: int, k: int = K, s: int = 4, N: int = N
 
 # DRAM traffic per launch of the persistent kernel from one ncu capture, valid
 # only for the kernel sources it was taken on (sha256 of the CUDA sources).
-NCU_TRAFFIC = {"sources_sha256": None, "bytes_per_launch": None}
+NCU_TRAFFIC = {"sources_sha256": "057ba0944ea6107791645aa8da187bce8282dab946fe3f3c601de35107ce3faa",
+               "bytes_per_launch": 29746176 + 13582080,  # mixed 1024x512 (read + write)
+               "large": {"2048x1024": 2799437056 + 1395389184, "4096x2048": 11733839104 + 5141067008}}
 
 
 def sources_hash() -> str:
@@ -221,7 +223,8 @@ def bench_large(torch, ftgcr, dev, flush, sizes=((2048, 1024), (4096, 2048)), re
         t = float(np.median(ms))
         nb = algorithmic_bytes(info["steps"], info["outer"], N=nlon * nlat)
         gbs = nb / (t * 1e-3) / 1e9
-        out[f"{nlon}x{nlat}"] = {"ms": t, "solves_per_s": 1e3 / t, "inner_steps": info["steps"],
+        traffic = NCU_TRAFFIC["large"].get(f"{nlon}x{nlat}") if NCU_TRAFFIC["sources_sha256"] == sources_hash() else None
+        out[f"{nlon}x{nlat}"] = {"ms": t, "solves_per_s": 1e3 / t, "inner_steps": info["steps"], "traffic": traffic,
                                  "refinement_sweeps": info["outer"], "tiles": info["tiles"],
                                  "algorithmic_bytes": nb, "achieved_gbs": gbs, "frac": gbs / peak,
                                  "peak_kind": peak_kind, "converged": info["converged"],
