@@ -232,6 +232,39 @@ def bench_large(torch, ftgcr, dev, flush, sizes=((2048, 1024), (4096, 2048)), re
     return out
 
 
+# ------------------------------------------------------------------ k sweep, cost of the protection
+def bench_ksweep(torch, ftgcr, dev, flush, ks=(1, 2, 4, 5, 8), reps=5):
+    """Fault-free mixed solves of the 1024x512 problem for several Krylov
+    cycle lengths, protected (FT-GCR(k)) and unprotected (plain GCR(k)): the
+    cost of the fault test and backup (Section 4 expects it near zero)."""
+    p = inputs.hill_problem(NLON, NLAT)
+    R = torch.from_numpy(p.R).to(dev)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for k in ks:
+        row = {}
+        for mode, protect in (("ftgcr", True), ("gcr", False)):
+            with ftgcr.Solver(p.D, p.mu, k=k, tol=TOL, precision="mixed", protect=protect) as s:
+                x = torch.zeros_like(R)
+                s.solve_async(R, x, stream=stream)
+                ms = []
+                for _ in range(reps):
+                    x.zero_()
+                    flush.fill_(5)
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    s.solve_async(R, x, stream=stream)
+                    b.record(stream)
+                    torch.cuda.synchronize()
+                    ms.append(a.elapsed_time(b))
+                info = s.stats()
+            row[mode + "_ms"] = float(np.median(ms))
+            row[mode + "_steps"] = info["steps"]
+        row["overhead"] = row["ftgcr_ms"] / row["gcr_ms"] - 1.0
+        out[f"k{k}"] = row
+    return out
+
+
 # ------------------------------------------------------------------ batch and serving mixes
 def bench_batch(torch, ftgcr, dev, n=128, seed=42, reps=3):
     """128 independent mixed-precision solves of sizes U{128x64, 256x128,
@@ -524,6 +557,8 @@ def run_ours(args):
         }
         if not args.no_large and ws == 1:
             line["large_grids"] = bench_large(torch, ftgcr, dev, flush)
+        if not args.no_ksweep and ws == 1:
+            line["k_sweep"] = bench_ksweep(torch, ftgcr, dev, flush)
         if not args.no_batch and ws == 1:
             line["batch"] = bench_batch(torch, ftgcr, dev)
         if not args.no_serving and ws == 1:
@@ -551,6 +586,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 128-solve batched launch")
     ap.add_argument("--no-large", action="store_true", help="skip the 2048x1024 and 4096x2048 solves")
+    ap.add_argument("--no-ksweep", action="store_true", help="skip the k sweep (protected vs unprotected)")
     ap.add_argument("--no-serving", action="store_true", help="skip the open-loop serving run")
     ap.add_argument("--serving-requests", type=int, default=2000)
     ap.add_argument("--serving-load", type=float, default=0.8, help="arrival rate / measured capacity")

@@ -14,3 +14,23 @@ def oracle_trial(args):
     f = inputs.sweep_flip(seed, trial, nff, nlon * nlat)
     o = oracle.ftgcr(p.D, p.R, p.mu, k, tol, faults=[f])
     return trial, f, decisions(o), o["faults_injected"], o["x"]
+
+
+def fp64_bit_of_fp32_bit(b):
+    """The FP64 bit playing the role of FP32 bit b: sign to sign, the exponent's
+    low seven bits to the low seven of FP64's, its top bit to FP64's top
+    exponent bit, the 23 mantissa bits to the top 23 of FP64's mantissa."""
+    if b == 31:
+        return 63
+    if b == 30:
+        return 62
+    return b + 29
+
+
+def oracle_mixed_counterpart(args):
+    """FP64 oracle run of a mixed-path trial's flip, bit mapped to FP64."""
+    nlon, nlat, k, tol, seed, trial, nsteps = args
+    p = inputs.hill_problem(nlon, nlat)
+    step, vec, idx, bit = inputs.sweep_flip(seed, trial, nsteps, nlon * nlat, nbits=32)
+    o = oracle.ftgcr(p.D, p.R, p.mu, k, tol, faults=[(step, vec, idx, fp64_bit_of_fp32_bit(bit))])
+    return trial, o["faults_detected"] > 0, o["converged"]
