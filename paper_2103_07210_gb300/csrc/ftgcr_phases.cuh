@@ -153,11 +153,14 @@ __device__ __forceinline__ int count_losses(const SolveDev<T>& sd, long long ste
 // double-double arithmetic throughout, rounded once; FP32 path: plain FP64
 // (per-tile values are already accurate sums).  Every CTA that works on the
 // solve gets bitwise the same numbers.
+// Warps w0..kWarps-1 take part (warp w0 + i sums values i, i + (kWarps - w0),
+// ...); the order within a value is the same whichever warp sums it.
 template <typename T>
-__device__ __forceinline__ void reduce_partials(const double* part, int nt, int nv, double* red) {
+__device__ __forceinline__ void reduce_partials(const double* part, int nt, int nv, double* red, int w0 = 0) {
   constexpr int B = 8;  // tiles loaded per batch per lane, summed in a binary tree
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int v = warp; v < nv; v += kWarps) {
+  if (warp < w0) return;
+  for (int v = warp - w0; v < nv; v += kWarps - w0) {
     DD acc{0.0, 0.0};
     double acc1 = 0.0;
     for (int t0 = lane; t0 < nt; t0 += 32 * B) {
@@ -1484,6 +1487,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_ftgcr_persistent(BatchArgs<T> a
       a.diag[blockIdx.x * 4 + 0] = it;
       a.diag[blockIdx.x * 4 + 2] = 0;
     }
+    // speculative: a CTA that ran a solve's transition last round will most
+    // likely run the same solve first this round; warps 1.. reduce its
+    // partial sums while warp 0 forms the tile prefix
+    const int spec_s = (cur_sd >= 0 && last_s == cur_sd && last_round == round - 1) ? cur_sd : -1;
+    if (spec_s >= 0)
+      reduce_partials<T>(ks.sd.part + (long long)(par ^ 1) * ks.sd.nt * kPartStride, ks.sd.nt, part_values(ks.sd),
+                         ks.red, 1);
+    bool red_ready = spec_s >= 0;
     // tile prefix over active solves (identical in every CTA): warp 0 scans
     // 32 solves at a time
     if (threadIdx.x < 32) {
@@ -1541,8 +1552,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_ftgcr_persistent(BatchArgs<T> a
           cta_store(&ks.S, &ks.N);
         else
           cta_load_cg(&ks.S, ks.sd.st + par);
-        reduce_partials<T>(ks.sd.part + (long long)(par ^ 1) * ks.sd.nt * kPartStride, ks.sd.nt,
-                           part_values(ks.sd), ks.red);
+        if (!(red_ready && s == spec_s))
+          reduce_partials<T>(ks.sd.part + (long long)(par ^ 1) * ks.sd.nt * kPartStride, ks.sd.nt,
+                             part_values(ks.sd), ks.red);
+        red_ready = false;
         __syncthreads();
         precompute_divisions(ks.S, ks.red, ks.qd, ks.sd.mixed);
         cta_store(&ks.N, &ks.S);
