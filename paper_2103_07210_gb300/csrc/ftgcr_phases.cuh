@@ -1238,7 +1238,31 @@ __device__ __noinline__ void phase_init(const SolveDev<T>& sd, const Ctx<T>& c, 
   __syncthreads();
   const int nfl = ps.nfl;
   Acc<T> an, aR;
-  for (int j = rt.h0; j < rt.h1; ++j) {
+  constexpr int W = V16<T>::W;
+  const bool vec = c.zero_guess && nfl == 0 && nlon % W == 0;  // the common case, 16-byte accesses
+  if (vec) {
+    // r0 = -R_in (zero guess), x0 = 0
+    const int nvr = nlon / W, total = (rt.h1 - rt.h0) * nvr;
+    for (int idx = threadIdx.x; idx < total; idx += kThreads) {
+      const RowVec v = row_vec(idx, nvr, rt.h0, nlon, W);
+      const V16<T> rin = ldv(sd.Rin + v.g);
+      V16<T> rv, zv;
+      T* row = sm + (v.j - rt.h0) * stride;
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        rv.v[w] = -rin.v[w];
+        zv.v[w] = T(0);
+        row[sk(v.i + w)] = rv.v[w];
+      }
+      if (v.j >= rt.j0 && v.j < rt.j1) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) an.add(rv.v[w], rv.v[w]);
+        stv(c.phiW + v.g, zv);
+        stv(c.rW + v.g, rv);
+      }
+    }
+  }
+  for (int j = rt.h0; j < (vec ? rt.h0 : rt.h1); ++j) {
     const bool own = (j >= rt.j0 && j < rt.j1);
     T* row = sm + (j - rt.h0) * stride;
     const long long base = (long long)j * nlon;
@@ -1279,7 +1303,39 @@ __device__ __noinline__ void phase_init(const SolveDev<T>& sd, const Ctx<T>& c, 
   precond_tile(sd, rt.h0, rt.h1 - rt.h0, sm, stride, cs);
   __syncthreads();
   Acc<T> a0, a1;
-  for (int j = rt.j0; j < rt.j1; ++j) {
+  if (vec) {
+    // p0 = P^-1 r0 (in the rows), L(p0) and the first dots, 16-byte accesses
+    const int nvr = nlon / W, total = (rt.j1 - rt.j0) * nvr;
+    for (int idx = threadIdx.x; idx < total; idx += kThreads) {
+      const RowVec v = row_vec(idx, nvr, rt.j0, nlon, W);
+      const bool hasN = v.j < nlat - 1, hasS = v.j > 0;
+      const V16<T> tx = ldv_nc(sd.Tx + v.g);
+      const T txw0 = __ldg(sd.Tx + (long long)v.j * nlon + (v.i == 0 ? nlon - 1 : v.i - 1));
+      V16<T> ty, tys;
+      if (hasN) ty = ldv_nc(sd.Ty + v.g);
+      if (hasS) tys = ldv_nc(sd.Ty + v.g - nlon);
+      const T muA = __ldg(sd.muA + v.j);
+      const V16<T> rr = ldv(c.rW + v.g);
+      const T* row = sm + (v.j - rt.h0) * stride;
+      V16<T> pv, lv;
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        const int i = v.i + w;
+        const int ie = (i + 1 == nlon) ? 0 : i + 1;
+        const int iw = (i == 0) ? nlon - 1 : i - 1;
+        const T x = row[sk(i)];
+        pv.v[w] = x;
+        lv.v[w] = stencil5<T>(x, row[sk(ie)], row[sk(iw)], hasN ? row[stride + sk(i)] : T(0),
+                              hasS ? row[-stride + sk(i)] : T(0), tx.v[w], w == 0 ? txw0 : tx.v[w - 1],
+                              hasN ? ty.v[w] : T(0), hasS ? tys.v[w] : T(0), muA, hasN, hasS);
+        a0.add(rr.v[w], lv.v[w]);
+        a1.add(lv.v[w], lv.v[w]);
+      }
+      stv(c.pnew + v.g, pv);
+      stv(c.lpnew + v.g, lv);
+    }
+  }
+  for (int j = rt.j0; j < (vec ? rt.j0 : rt.j1); ++j) {
     const long long base = (long long)j * nlon;
     const T* row = sm + (j - rt.h0) * stride;
     for (int i = threadIdx.x; i < nlon; i += kThreads) {
@@ -1323,6 +1379,7 @@ __device__ __noinline__ void phase_out(const SolveDev<T>& sd, const Ctx<T>& c, i
   const int nlon = sd.nlon, nlat = sd.nlat, stride = row_stride(nlon);
   const RowTile rt = row_tile(nlat, sd.nt, tau);
   if (threadIdx.x == 0) ps.cs_solve = -1;  // its FP64 rows overwrite the staged constants
+  int nz = 0;
   {
     // x' = x + d over the tile and its halo rows, as one flat loop so that
     // each thread keeps several loads in flight
@@ -1345,18 +1402,32 @@ __device__ __noinline__ void phase_out(const SolveDev<T>& sd, const Ctx<T>& c, i
         if (idx < total) {
           const int jr = idx / nlon, i = idx - jr * nlon;
           smd[jr * stride + sk(i)] = xv[u];
+          nz |= xv[u] != 0.0;
           const int j = rt.h0 + jr;
           if (j >= rt.j0 && j < rt.j1) c.xdst[(long long)rt.h0 * nlon + idx] = xv[u];
         }
       }
     }
   }
-  __syncthreads();
+  // a tile whose x' (halo included) is all zero, as at the start of a solve
+  // from a zero guess, has L64(x') = 0: skip the FP64 stencil
+  const bool zero = !__syncthreads_or(nz);
   AccF64 so, sR;
   for (int j = rt.j0; j < rt.j1; ++j) {
     const long long base = (long long)j * nlon;
     const double* row = smd + (j - rt.h0) * stride;
     const bool hasN = j < nlat - 1, hasS = j > 0;
+    if (zero) {
+      for (int i = threadIdx.x; i < nlon; i += kThreads) {
+        const long long g = base + i;
+        const double Rv = ldcg(sd.R + g);
+        const double ro = Rv - 0.0;
+        sd.Rin[g] = (T)ro;
+        so.add(ro, ro);
+        if (c.first) sR.add(Rv, Rv);
+      }
+      continue;
+    }
     for (int i = threadIdx.x; i < nlon; i += kThreads) {
       const long long g = base + i;
       const int ie = (i + 1 == nlon) ? 0 : i + 1;
