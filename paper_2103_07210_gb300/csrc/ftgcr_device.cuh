@@ -351,8 +351,9 @@ __device__ __forceinline__ unsigned long long globaltimer() {
 __device__ __forceinline__ bool grid_barrier(unsigned int* counter, unsigned int target, int* err, int* bail_smem) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(counter, 1u);
+    // arrive with release semantics (the block's writes, ordered before by the
+    // block barrier, become visible with the count), wait with acquire loads
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(counter), "r"(1u) : "memory");
     unsigned long long t0 = globaltimer();
     unsigned int it = 0;
     while (ld_acquire_u32(counter) < target) {
@@ -360,10 +361,9 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* counter, unsigned int
         atomicExch(err, 1);
         break;
       }
-      __nanosleep(40);
+      __nanosleep(20);
     }
-    __threadfence();
-    *bail_smem = *(volatile int*)err;
+    *bail_smem = ld_acquire_u32(reinterpret_cast<const unsigned int*>(err));
   }
   __syncthreads();
   return *bail_smem == 0;
