@@ -254,7 +254,6 @@ void row_geometry(int nlon, int nlat, std::vector<double>& cx, std::vector<doubl
   }
 }
 
-int chunk_len(int nlon) { return (nlon - 1 + 31) / 32; }
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 

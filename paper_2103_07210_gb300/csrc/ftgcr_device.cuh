@@ -385,8 +385,22 @@ __device__ __forceinline__ T stencil5(T v, T ve, T vw, T vn, T vs, T txc, T txw,
 // word per 32), which keeps both the coalesced sweeps and the per-lane
 // contiguous chunks of the line solve free of bank conflicts.
 __host__ __device__ __forceinline__ int sk(int i) { return i + (i >> 5); }
+
+// Elements per lane of the FP32 line solve: the n-1 unknowns of the row's
+// leading block over 32 lanes, rounded up to whole register blocks of 8 (the
+// solve runs every lane's chunk in full; positions past the block carry zero
+// factors).
+__host__ __device__ __forceinline__ int chunk_len(int nlon) {
+  const int c = (nlon - 1 + 31) / 32;
+  return (c + 7) & ~7;
+}
+
+// Floats (or doubles) per staged row: the row, its pad words, and room for the
+// line solve's padded chunk positions.
 __host__ __device__ __forceinline__ int row_stride(int nlon) {
-  int s = nlon + (nlon >> 5) + 1;
+  const int pad = 32 * chunk_len(nlon) + 1;
+  const int ne = nlon > pad ? nlon : pad;
+  int s = ne + (ne >> 5) + 1;
   return (s + 3) & ~3;
 }
 
@@ -447,8 +461,7 @@ __device__ __noinline__ void line_solve_row(const SolveDev<T>& sd, int j, T* row
   const int lane = threadIdx.x & 31;
   const int n = sd.nlon, m = n - 1, C = sd.C;
   const int i0 = lane * C;
-  int len = m - i0;
-  len = len < 0 ? 0 : (len > C ? C : len);
+  const int len = C;  // every lane runs its whole chunk (chunk_len)
   // the row's bordering constants, loaded first so that their latency hides
   // behind the recurrences
   const T* lr = sd.lrow + (long long)j * 4;
@@ -459,8 +472,15 @@ __device__ __noinline__ void line_solve_row(const SolveDev<T>& sd, int j, T* row
   auto Cb = [&](int k) { return cbb + E * (unsigned)(k * 32 + lane); };
   auto Cw = [&](int k) { return cwb + E * (unsigned)(k * 32 + lane); };
   auto Cz = [&](int k) { return czb + E * (unsigned)(k * 32 + lane); };
+  // b_{n-1}, read before the passes: its slot may lie in the last lane's chunk
+  const T bl = -lds<T>(R(n - 1));
+  // positions past the row hold no data: make them finite (their factors are zero)
+  if (i0 + C > n)
+    for (int k = 0; k < C; ++k)
+      if (i0 + k >= n) sts(R(i0 + k), T(0));
+  __syncwarp();
   // forward multiplier of chunk element 0 is c_{i0-1}, the last c of the previous lane
-  const T mylast = (len > 0) ? lds<T>(Cb(len - 1)) : T(0);
+  const T mylast = lds<T>(Cb(C - 1));
   T a0 = __shfl_up_sync(0xffffffffu, mylast, 1);
   if (lane == 0) a0 = T(0);
   // pass 1: affine map g_out = F g_in + G of the chunk
@@ -470,18 +490,16 @@ __device__ __noinline__ void line_solve_row(const SolveDev<T>& sd, int j, T* row
     for (int kb = 0; kb < len; kb += kLB) {
       T rv[kLB], cv[kLB];
 #pragma unroll
-      for (int q = 0; q < kLB; ++q)
-        if (kb + q < len) {
-          rv[q] = lds<T>(R(i0 + kb + q));
-          cv[q] = lds<T>(Cb(kb + q));
-        }
+      for (int q = 0; q < kLB; ++q) {
+        rv[q] = lds<T>(R(i0 + kb + q));
+        cv[q] = lds<T>(Cb(kb + q));
+      }
 #pragma unroll
-      for (int q = 0; q < kLB; ++q)
-        if (kb + q < len) {
-          G = tfma(a, G, -rv[q]);
-          F = F * a;
-          a = cv[q];
-        }
+      for (int q = 0; q < kLB; ++q) {
+        G = tfma(a, G, -rv[q]);
+        F = F * a;
+        a = cv[q];
+      }
     }
   }
   T Fs = F, Gs = G;
@@ -502,21 +520,19 @@ __device__ __noinline__ void line_solve_row(const SolveDev<T>& sd, int j, T* row
     for (int kb = 0; kb < len; kb += kLB) {
       T rv[kLB], cv[kLB];
 #pragma unroll
-      for (int q = 0; q < kLB; ++q)
-        if (kb + q < len) {
-          rv[q] = lds<T>(R(i0 + kb + q));
-          cv[q] = lds<T>(Cb(kb + q));
-        }
+      for (int q = 0; q < kLB; ++q) {
+        rv[q] = lds<T>(R(i0 + kb + q));
+        cv[q] = lds<T>(Cb(kb + q));
+      }
+#pragma unroll
+      for (int q = 0; q < kLB; ++q) {
+        g = tfma(a, g, -rv[q]);
+        rv[q] = g;
+        a = cv[q];
+      }
 #pragma unroll
       for (int q = 0; q < kLB; ++q)
-        if (kb + q < len) {
-          g = tfma(a, g, -rv[q]);
-          rv[q] = g;
-          a = cv[q];
-        }
-#pragma unroll
-      for (int q = 0; q < kLB; ++q)
-        if (kb + q < len) sts(R(i0 + kb + q), rv[q]);
+        sts(R(i0 + kb + q), rv[q]);
     }
   }
   // pass 3: affine map of the backward recurrence y_in = Fb y_out + Y
@@ -525,18 +541,16 @@ __device__ __noinline__ void line_solve_row(const SolveDev<T>& sd, int j, T* row
   for (int kb = kb_last; kb >= 0; kb -= kLB) {
     T gv[kLB], cv[kLB], wv[kLB];
 #pragma unroll
-    for (int q = 0; q < kLB; ++q)
-      if (kb + q < len) {
-        gv[q] = lds<T>(R(i0 + kb + q));
-        cv[q] = lds<T>(Cb(kb + q));
-        wv[q] = lds<T>(Cw(kb + q));
-      }
+    for (int q = 0; q < kLB; ++q) {
+      gv[q] = lds<T>(R(i0 + kb + q));
+      cv[q] = lds<T>(Cb(kb + q));
+      wv[q] = lds<T>(Cw(kb + q));
+    }
 #pragma unroll
-    for (int q = kLB - 1; q >= 0; --q)
-      if (kb + q < len) {
-        Y = tfma(cv[q], Y, gv[q] * wv[q]);
-        Fb = Fb * cv[q];
-      }
+    for (int q = kLB - 1; q >= 0; --q) {
+      Y = tfma(cv[q], Y, gv[q] * wv[q]);
+      Fb = Fb * cv[q];
+    }
   }
   T Fr = Fb, Yr = Y;
 #pragma unroll
@@ -556,32 +570,30 @@ __device__ __noinline__ void line_solve_row(const SolveDev<T>& sd, int j, T* row
     for (int kb = kb_last; kb >= 0; kb -= kLB) {
       T gv[kLB], cv[kLB], wv[kLB];
 #pragma unroll
-      for (int q = 0; q < kLB; ++q)
-        if (kb + q < len) {
-          gv[q] = lds<T>(R(i0 + kb + q));
-          cv[q] = lds<T>(Cb(kb + q));
-          wv[q] = lds<T>(Cw(kb + q));
-        }
+      for (int q = 0; q < kLB; ++q) {
+        gv[q] = lds<T>(R(i0 + kb + q));
+        cv[q] = lds<T>(Cb(kb + q));
+        wv[q] = lds<T>(Cw(kb + q));
+      }
 #pragma unroll
-      for (int q = kLB - 1; q >= 0; --q)
-        if (kb + q < len) {
-          y = tfma(cv[q], y, gv[q] * wv[q]);
-          gv[q] = y;
-        }
+      for (int q = kLB - 1; q >= 0; --q) {
+        y = tfma(cv[q], y, gv[q] * wv[q]);
+        gv[q] = y;
+      }
 #pragma unroll
       for (int q = 0; q < kLB; ++q)
-        if (kb + q < len) sts(R(i0 + kb + q), gv[q]);
+        sts(R(i0 + kb + q), gv[q]);
     }
   }
   __syncwarp();
   // bordering: x_{n-1} = (b_{n-1} + Tx_{n-1} y_0 + Tx_{n-2} y_{m-1}) / delta
   const T y0 = lds<T>(R(0));
   const T ym = lds<T>(R(m - 1));
-  const T bl = -lds<T>(R(n - 1));
   const T xl = tfma(lr2, ym, tfma(lr1, y0, bl * lr0));
   __syncwarp();
 #pragma unroll 8
   for (int k = 0; k < len; ++k) sts(R(i0 + k), tfma(-xl, lds<T>(Cz(k)), lds<T>(R(i0 + k))));
+  __syncwarp();
   if (lane == 0) sts(R(n - 1), xl);
   __syncwarp();
 }
