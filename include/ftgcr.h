@@ -237,9 +237,10 @@ const char* ftgcr_error_string(int status);
  *    may be NULL.  Blocks until done; returns like ftgcr_solve.
  *  - The first call on a device looks up the array's device address (set-up);
  *    make that first call before any stream capture begins.
- *  - All calls share the array, which keeps the last call's contents; calls
- *    that overlap on the GPU (other threads, other streams) race and must be
- *    serialised by the caller. */
+ *  - All calls share the array, which keeps the last call's contents; each
+ *    call clears the part it uses before it starts, so a result does not
+ *    depend on earlier calls.  Calls that overlap on the GPU (other threads,
+ *    other streams) race and must be serialised by the caller. */
 #define FTGCR_NOALLOC_MAX_POINTS 16384
 #define FTGCR_NOALLOC_MAX_K 4
 #define FTGCR_NOALLOC_SCRATCH_BYTES (6 * 1024 * 1024)

@@ -1307,8 +1307,10 @@ extern "C" int ftgcr_solve_noalloc(const ftgcr_grid* grid, const double* D, int3
   sd.Ty64 = h.Ty64;
   sd.muA64 = h.muA64;
 
-  // coefficients and factorisation into the array (the array keeps the last
-  // call's contents; everything below is rewritten before it is read)
+  // The array keeps the last call's contents, laid out for that call's sizes:
+  // clear the part this call uses, so that it starts from the state of a
+  // freshly created handle, then write the coefficients and factorisation.
+  CK(cudaMemsetAsync(base, 0, pool + geo, st));
   std::vector<double> cx, cy, area, g3;
   row_geometry(h.nlon, h.nlat, cx, cy, area);
   g3.insert(g3.end(), cx.begin(), cx.end());

@@ -6,6 +6,7 @@ is a static device array inside the library, so this test checks that
     ordinary allocating entry point (ftgcr_solve) to the FP64 tolerance the
     other tests use (1e-10 relative), with the same step count;
   * a repeated call leaves the device's free memory unchanged;
+  * a result does not depend on the sizes of the calls before it;
   * sizes beyond the stated maximum are rejected with an error.
 Collected last (file name) so that a failure here cannot hide another test's."""
 import numpy as np
@@ -45,6 +46,19 @@ def test_noalloc_matches_allocating_solve_twice(nlon, nlat, k, rhs):
         assert st == st_ref == ftgcr.OK
         assert info["steps"] == info_ref["steps"] and info["converged"]
         assert rel_err(x.cpu().numpy(), x_ref) <= 1e-10
+
+
+def test_noalloc_result_does_not_depend_on_the_previous_call_sizes():
+    # the array keeps the last call's contents, laid out for that call's sizes
+    probs = [inputs.hill_problem(n, m, rhs="random", seed=n + m) for n, m in ((128, 64), (40, 21), (96, 48))]
+    refs = [_reference(p, 4, 1e-10) for p in probs]
+    for q in (0, 1, 2, 1, 0, 2):
+        p = probs[q]
+        R = torch.from_numpy(p.R).cuda()
+        x = torch.zeros_like(R)
+        st, info = ftgcr.solve_noalloc(torch.from_numpy(p.D).cuda(), p.mu, R, x, k=4, tol=1e-10)
+        assert st == ftgcr.OK and info["steps"] == refs[q][2]["steps"]
+        assert rel_err(x.cpu().numpy(), refs[q][1]) <= 1e-10
 
 
 def test_noalloc_rejects_sizes_beyond_its_maximum():
