@@ -75,8 +75,9 @@ typedef struct ftgcr_handle ftgcr_handle;
 typedef struct {
   int32_t nlon;      /* >= 3; one latitude row with its two halo rows and, for the line
                         preconditioner, their factors must fit in one SM's shared
-                        memory: nlon <= about 2150 (FTGCR_FP64) or 4350 (FTGCR_MIXED),
-                        else FTGCR_ERR_ARG */
+                        memory: nlon <= about 2150 (FTGCR_FP64) or 8500 (FTGCR_MIXED;
+                        beyond about 4350 only with split rounds, see
+                        FTGCR_FLAG_SPLIT_ROUNDS), else FTGCR_ERR_ARG */
   int32_t nlat;      /* >= 1 */
   double mu;         /* Helmholtz coefficient per unit area, >= 0 (mu > 0 makes -L definite) */
   int32_t precision; /* FTGCR_FP64 | FTGCR_MIXED */
@@ -93,6 +94,17 @@ typedef struct {
  * test, so no backup restore (and, in the mixed path, no rejection of
  * refinement updates).  Faults still fire. */
 #define FTGCR_FLAG_UNPROTECTED 1
+/* FTGCR_MIXED with the line preconditioner: how a step's rounds are laid out.
+ * By default a solve whose row bands shared memory cuts below three rows
+ * (wide rows: the line-solve constants fill it) runs split rounds: its
+ * tiles first form e on their own rows only, and after a grid barrier form
+ * L(e) and the dots from e with its halo rows, instead of recomputing two
+ * halo rows of e per tile.  These flags force one layout or the other
+ * (results differ only by rounding; both are deterministic); both together,
+ * or FTGCR_FLAG_SPLIT_ROUNDS on another precision or preconditioner, are
+ * FTGCR_ERR_ARG. */
+#define FTGCR_FLAG_SPLIT_ROUNDS 2
+#define FTGCR_FLAG_FUSED_ROUNDS 4
 
 typedef struct {
   const double* D;   /* [nlat][nlon] cell-centred coefficient (column depth 1 - h), > 0 */
@@ -166,6 +178,7 @@ typedef struct {
   int32_t tiles;           /* row bands used */
   int32_t status;          /* status of the last solve */
   int64_t loss_events;     /* data-loss events that fired */
+  int32_t split_rounds;    /* 1: the solve ran split rounds (FTGCR_FLAG_SPLIT_ROUNDS) */
 } ftgcr_stats_t;
 
 /* Create a solver for one grid and coefficient field.  Copies D, builds the

@@ -257,27 +257,75 @@ void row_geometry(int nlon, int nlat, std::vector<double>& cx, std::vector<doubl
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-// Dynamic shared memory of the persistent kernel for a solve with nt tiles:
-// the tile's rows plus halo (inner precision) and, for the line
-// preconditioner, the three staged constant arrays of those rows; the mixed
-// path's refinement phase holds the same rows in FP64.
-size_t dyn_smem(int nlon, int nlat, int nt, int mixed, size_t elem, int precond) {
-  const size_t hmax = (size_t)((nlat + nt - 1) / nt);
-  const size_t rows = (hmax + 2) * row_stride(nlon) * elem;
+// Dynamic shared memory of the persistent kernel for a solve with nt tiles.
+// One-pass rounds: the tile's rows plus two halo rows (inner precision)
+// followed by the line-solve constants of those rows.  Split rounds: the
+// first pass holds the own rows and their constants, the second the rows with
+// halos; the constants go after room for the halo rows when that fits (they
+// then survive the second pass), else right after the own rows.  The mixed
+// path's refinement phase holds the rows with halos in FP64.
+struct SmemPlan {
+  size_t bytes;
+  long long cs_off;  // elements of the inner type
+  int cs_clobber;
+};
+SmemPlan smem_plan(int nlon, int nlat, int nt, int mixed, size_t elem, int precond, int split, size_t limit) {
+  const size_t h = (size_t)((nlat + nt - 1) / nt);
+  const size_t st = (size_t)row_stride(nlon);
   const size_t per_row = mixed ? 32 * (size_t)chunk_len(nlon) : (size_t)nlon;  // chunk vs natural layout
-  const size_t consts = precond == FTGCR_PRECOND_LINE ? 3 * (hmax + 2) * per_row * elem : 0;
-  const size_t out = mixed ? (hmax + 2) * row_stride(nlon) * sizeof(double) : 0;
-  return std::max(rows + consts, out);
+  const size_t out = mixed ? (h + 2) * st * sizeof(double) : 0;
+  const bool line = precond == FTGCR_PRECOND_LINE;
+  SmemPlan p;
+  if (!split) {
+    const size_t consts = line ? 3 * (h + 2) * per_row * elem : 0;
+    p.bytes = std::max((h + 2) * st * elem + consts, out);
+    p.cs_off = (long long)((h + 2) * st);
+    p.cs_clobber = 0;
+    return p;
+  }
+  const size_t consts = line ? 3 * h * per_row * elem : 0;
+  const size_t roomy = std::max((h + 2) * st * elem + consts, out);
+  if (roomy <= limit) {
+    p.bytes = roomy;
+    p.cs_off = (long long)((h + 2) * st);
+    p.cs_clobber = 0;
+  } else {
+    p.bytes = std::max({h * st * elem + consts, (h + 2) * st * elem, out});
+    p.cs_off = (long long)(h * st);
+    p.cs_clobber = 1;
+  }
+  return p;
 }
 
-int choose_tiles(int nlon, int nlat, int mixed, size_t elem, int precond, int sms, int smem_limit) {
-  // equal-height row bands: the round takes as long as the tallest band, so
-  // use the fewest bands of that height (e.g. 512 rows on 152 SMs: 128 x 4)
-  const int hmax = (nlat + sms - 1) / sms;
-  int nt = (nlat + hmax - 1) / hmax;
-  while (nt < nlat && dyn_smem(nlon, nlat, nt, mixed, elem, precond) > (size_t)smem_limit)
-    nt = std::min(nlat, nt + sms);
-  return nt;
+// Row bands and round structure of a solve.  Equal-height row bands: the
+// round takes as long as the tallest band, so use the fewest bands of that
+// height (e.g. 512 rows on 152 SMs: 128 x 4), as tall as shared memory allows.
+// Split rounds (mixed path, line preconditioner) when shared memory, not the
+// SM count, cuts one-pass tiles below three rows (each tile would then
+// recompute at least twice its own rows as halo), or when one row with its
+// halo rows and their constants does not fit at all.
+void choose_tiling(int nlon, int nlat, int mixed, size_t elem, int precond, int flags, int tiles, int sms,
+                   size_t limit, int* nt_out, int* split_out) {
+  const int hpar = (nlat + sms - 1) / sms;  // band height the SM count alone gives
+  auto fit = [&](int split) {
+    int nt = (nlat + hpar - 1) / hpar;
+    while (nt < nlat && smem_plan(nlon, nlat, nt, mixed, elem, precond, split, limit).bytes > limit)
+      nt = std::min(nlat, nt + sms);
+    return nt;
+  };
+  int split = 0;
+  if (mixed && precond == FTGCR_PRECOND_LINE) {
+    if (flags & FTGCR_FLAG_SPLIT_ROUNDS)
+      split = 1;
+    else if (!(flags & FTGCR_FLAG_FUSED_ROUNDS)) {
+      const int nt1 = tiles > 0 ? std::min(tiles, nlat) : fit(0);
+      const int h1 = (nlat + nt1 - 1) / nt1;
+      const bool fits = smem_plan(nlon, nlat, nt1, mixed, elem, precond, 0, limit).bytes <= limit;
+      split = !fits || (h1 < hpar && h1 < 3);
+    }
+  }
+  *split_out = split;
+  *nt_out = tiles > 0 ? std::min(tiles, nlat) : fit(split);
 }
 
 int cuda_status(cudaError_t e) {
@@ -322,6 +370,8 @@ struct ftgcr_handle {
   SolveDev<double> sd64{};
   SolveDev<float> sd32{};
   size_t smem = 0;
+  int split = 0;  // split rounds (see choose_tiling)
+  SmemPlan plan{};
   int grid = 0;
   cudaStream_t last_stream = nullptr;
   int solved = 0;
@@ -334,21 +384,22 @@ namespace {
 int kbound(int k) { return k <= 4 ? 4 : (k <= 8 ? 8 : 16); }
 
 // The persistent kernel instances live in their own translation units
-// (ftgcr_k4.cu, ftgcr_k8.cu, ftgcr_k16.cu) so that they compile in parallel.
+// (ftgcr_k4.cu, ftgcr_k8.cu, ftgcr_k16.cu and their split-round twins) so that
+// they compile in parallel.
 template <typename T>
-const void* kernel_ptr(int kb) {
-  return ftgcr::persistent_kernel_ptr(kb, sizeof(T) == 8);
+const void* kernel_ptr(int kb, int split) {
+  return ftgcr::persistent_kernel_ptr(kb, sizeof(T) == 8, split != 0);
 }
 
 // The dynamic shared memory attribute of a kernel is process-wide: only ever
 // raise it, so that a handle created later never shrinks what an earlier one
 // needs.
 template <typename T>
-int configure_kernel(int kb, size_t smem) {
+int configure_kernel(int kb, int split, size_t smem) {
   static std::mutex mu;
   static std::vector<std::pair<const void*, size_t>> set;
   std::lock_guard<std::mutex> lk(mu);
-  const void* f = kernel_ptr<T>(kb);
+  const void* f = kernel_ptr<T>(kb, split);
   for (auto& e : set)
     if (e.first == f) {
       if (e.second >= smem) return FTGCR_OK;
@@ -362,8 +413,8 @@ int configure_kernel(int kb, size_t smem) {
 }
 
 template <typename T>
-int occupancy(int kb, size_t smem, int* occ) {
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kernel_ptr<T>(kb), kThreads, smem));
+int occupancy(int kb, int split, size_t smem, int* occ) {
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kernel_ptr<T>(kb, split), kThreads, smem));
   return FTGCR_OK;
 }
 
@@ -545,6 +596,9 @@ int create_impl(ftgcr_handle* h, const double* D_host_or_dev, bool D_on_device) 
   sd.tol2 = h->tol * h->tol;
   sd.inner_tol2 = h->inner_tol * h->inner_tol;
   sd.protect = (h->flags & FTGCR_FLAG_UNPROTECTED) ? 0 : 1;
+  sd.split = h->split;
+  sd.cs_off = (int)h->plan.cs_off;
+  sd.cs_clobber = h->plan.cs_clobber;
   sd.Tx64 = h->Tx64;
   sd.Ty64 = h->Ty64;
   sd.muA64 = h->muA64;
@@ -572,17 +626,18 @@ int create_impl(ftgcr_handle* h, const double* D_host_or_dev, bool D_on_device) 
   else
     h->sd64 = sd;
 
-  h->smem = dyn_smem(h->nlon, h->nlat, h->nt, mixed, sizeof(T), h->precond);
-  int rc = configure_kernel<T>(kbound(h->k), std::max<size_t>(h->smem, 1));
+  (void)mixed;
+  h->smem = h->plan.bytes;
+  int rc = configure_kernel<T>(kbound(h->k), h->split, std::max<size_t>(h->smem, 1));
   if (rc) return rc;
   int occ = 0;
-  rc = occupancy<T>(kbound(h->k), h->smem, &occ);
+  rc = occupancy<T>(kbound(h->k), h->split, h->smem, &occ);
   if (rc) return rc;
   if (occ < 1) return FTGCR_ERR_ARG;
   {
     // the per-thread stack must hold the kernel's spill frame
     cudaFuncAttributes fa;
-    CK(cudaFuncGetAttributes(&fa, kernel_ptr<T>(kbound(h->k))));
+    CK(cudaFuncGetAttributes(&fa, kernel_ptr<T>(kbound(h->k), h->split)));
     size_t cur = 0;
     CK(cudaDeviceGetLimit(&cur, cudaLimitStackSize));
     if (fa.localSizeBytes + 256 > cur) CK(cudaDeviceSetLimit(cudaLimitStackSize, fa.localSizeBytes + 256));
@@ -644,7 +699,7 @@ void trace_dump(int grid) {
 
 template <typename T>
 int launch_persistent(int kb, SolveDev<T>* const* solves, const int* nt, int* active, int n, LaunchCtl* ctl,
-                      int* diag, int max_rounds, int grid, size_t smem, cudaStream_t st) {
+                      int* diag, int max_rounds, int grid, size_t smem, int split, cudaStream_t st) {
   BatchArgs<T> a;
   a.solves = solves;
   a.nt = nt;
@@ -655,7 +710,7 @@ int launch_persistent(int kb, SolveDev<T>* const* solves, const int* nt, int* ac
   a.trace = trace_ptr(grid, &a.trace_rounds);
   a.diag = diag;
   void* args[] = {&a};
-  CK(cudaLaunchCooperativeKernel(kernel_ptr<T>(kb), dim3(grid), dim3(kThreads), args, smem, st));
+  CK(cudaLaunchCooperativeKernel(kernel_ptr<T>(kb, split), dim3(grid), dim3(kThreads), args, smem, st));
   return FTGCR_OK;
 }
 
@@ -683,7 +738,7 @@ int solve_async_impl(ftgcr_handle* h, const double* R, const double* x0, double*
   // every inner step takes two rounds, every refinement sweep a few more
   const int max_rounds = (int)std::min<long long>(1 << 30, 2 * h->max_steps + 8 * ((long long)h->max_outer + 2) + 16);
   int rc = launch_persistent<T>(kbound(h->k), (SolveDev<T>* const*)h->sdev_arr, h->nt_dev, h->active, 1, h->ctl,
-                                h->diag, max_rounds, h->grid, h->smem, st);
+                                h->diag, max_rounds, h->grid, h->smem, h->split, st);
   if (rc) return rc;
   CK(cudaMemcpyAsync(h->h_result, h->result, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(LaunchCtl), cudaMemcpyDeviceToHost, st));
@@ -704,18 +759,19 @@ int solve_batch_impl(ftgcr_handle* const* hs, const double* const* rhs, double* 
   int kb = 4;
   size_t smem = 1;
   long long max_steps = 0, total_tiles = 0;
-  int max_outer = 0;
+  int max_outer = 0, split = 0;
   for (int i = 0; i < n; ++i) {
+    split |= hs[i]->split;
     kb = std::max(kb, kbound(hs[i]->k));
     smem = std::max(smem, hs[i]->smem);
     max_steps = std::max(max_steps, hs[i]->max_steps);
     max_outer = std::max(max_outer, hs[i]->max_outer);
     total_tiles += hs[i]->nt;
   }
-  int rc = configure_kernel<T>(kb, smem);
+  int rc = configure_kernel<T>(kb, split, smem);
   if (rc) return rc;
   int occ = 0;
-  rc = occupancy<T>(kb, smem, &occ);
+  rc = occupancy<T>(kb, split, smem, &occ);
   if (rc) return rc;
   if (occ < 1) return FTGCR_ERR_ARG;
   const DeviceInfo di = device_info(hs[0]->dev);
@@ -746,7 +802,7 @@ int solve_batch_impl(ftgcr_handle* const* hs, const double* const* rhs, double* 
   }
   const int max_rounds = (int)std::min<long long>(1 << 30, 2 * max_steps + 8 * ((long long)max_outer + 2) + 16);
   rc = launch_persistent<T>(kb, (SolveDev<T>* const*)d_solves, d_nt, d_act, n, d_ctl, d_diag, max_rounds, grid, smem,
-                            st);
+                            split, st);
   if (rc) {
     cudaFreeAsync(buf, st);
     return rc;
@@ -788,17 +844,19 @@ int table_run_impl(SlotTableImpl* t, int max_rounds, cudaStream_t st) {
   int kb = 4;
   size_t smem = 1;
   long long tiles = 0;
+  int split = 0;
   for (ftgcr_handle* h : t->slot)
     if (h) {
+      split |= h->split;
       kb = std::max(kb, kbound(h->k));
       smem = std::max(smem, h->smem);
       tiles += h->nt;
     }
   if (tiles == 0) return FTGCR_OK;
-  int rc = configure_kernel<T>(kb, smem);
+  int rc = configure_kernel<T>(kb, split, smem);
   if (rc) return rc;
   int occ = 0;
-  rc = occupancy<T>(kb, smem, &occ);
+  rc = occupancy<T>(kb, split, smem, &occ);
   if (rc) return rc;
   if (occ < 1) return FTGCR_ERR_ARG;
   const int grid = (int)std::min<long long>({tiles, (long long)device_info(t->dev).sms * occ, (long long)t->grid_cap});
@@ -809,7 +867,7 @@ int table_run_impl(SlotTableImpl* t, int max_rounds, cudaStream_t st) {
   t->h_ctl_in->round_end = t->round;
   CK(cudaMemcpyAsync(t->d_ctl, t->h_ctl_in, sizeof(LaunchCtl), cudaMemcpyHostToDevice, st));
   rc = launch_persistent<T>(kb, (SolveDev<T>* const*)t->d_solves, t->d_nt, t->d_act, t->n, t->d_ctl, t->d_diag,
-                            max_rounds, grid, smem, st);
+                            max_rounds, grid, smem, split, st);
   if (rc) return rc;
   CK(cudaMemcpyAsync(t->h_ctl_out, t->d_ctl, sizeof(LaunchCtl), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(t->h_act, t->d_act, sizeof(int) * 2 * t->n, cudaMemcpyDeviceToHost, st));
@@ -864,7 +922,10 @@ static int check_grid(const ftgcr_grid* g, int32_t k, double tol) {
   if (!(tol > 0.0) || !std::isfinite(tol)) return FTGCR_ERR_ARG;
   if (g->max_steps < 0 || g->tiles < 0 || g->max_outer < 0 || !(g->inner_tol >= 0.0) || g->inner_tol >= 1.0)
     return FTGCR_ERR_ARG;
-  if (g->flags & ~FTGCR_FLAG_UNPROTECTED) return FTGCR_ERR_ARG;
+  if (g->flags & ~(FTGCR_FLAG_UNPROTECTED | FTGCR_FLAG_SPLIT_ROUNDS | FTGCR_FLAG_FUSED_ROUNDS)) return FTGCR_ERR_ARG;
+  if ((g->flags & FTGCR_FLAG_SPLIT_ROUNDS) && (g->flags & FTGCR_FLAG_FUSED_ROUNDS)) return FTGCR_ERR_ARG;
+  if ((g->flags & FTGCR_FLAG_SPLIT_ROUNDS) && (g->precision != FTGCR_MIXED || g->precond != FTGCR_PRECOND_LINE))
+    return FTGCR_ERR_ARG;
   // mu = 0 on a single latitude row leaves the zonal line systems singular
   if (g->mu == 0.0 && g->nlat < 2 && g->precond != FTGCR_PRECOND_IDENTITY) return FTGCR_ERR_ARG;
   return FTGCR_OK;
@@ -886,8 +947,9 @@ static void fill_handle_params(ftgcr_handle* h, const ftgcr_grid* g, int32_t k, 
   h->flags = g->flags;
   const bool mixed = g->precision == FTGCR_MIXED;
   const size_t elem = mixed ? sizeof(float) : sizeof(double);
-  h->nt = g->tiles > 0 ? std::min(g->tiles, g->nlat)
-                       : choose_tiles(g->nlon, g->nlat, mixed, elem, g->precond, sms, smem_limit);
+  choose_tiling(g->nlon, g->nlat, mixed, elem, g->precond, g->flags, g->tiles, sms, (size_t)smem_limit, &h->nt,
+                &h->split);
+  h->plan = smem_plan(h->nlon, h->nlat, h->nt, mixed, elem, h->precond, h->split, (size_t)smem_limit);
 }
 
 int ftgcr_create(const ftgcr_grid* grid, const ftgcr_coeffs* coeffs, int32_t k, double tol, ftgcr_handle** out) {
@@ -904,7 +966,7 @@ int ftgcr_create(const ftgcr_grid* grid, const ftgcr_coeffs* coeffs, int32_t k, 
   h->dev = dev;
   fill_handle_params(h, grid, k, tol, di.sms, smem_limit);
   const bool mixed = grid->precision == FTGCR_MIXED;
-  if (dyn_smem(h->nlon, h->nlat, h->nt, mixed, mixed ? 4 : 8, h->precond) > (size_t)smem_limit) {
+  if (h->plan.bytes > (size_t)smem_limit) {
     delete h;
     return FTGCR_ERR_ARG;  // a single latitude row does not fit on chip
   }
@@ -1031,6 +1093,7 @@ int ftgcr_stats(ftgcr_handle* h, ftgcr_stats_t* out) {
   out->tiles = h->nt;
   out->status = h->last_status;
   out->loss_events = S.lossev;
+  out->split_rounds = h->split;
   return FTGCR_OK;
 }
 
@@ -1281,7 +1344,7 @@ extern "C" int ftgcr_solve_noalloc(const ftgcr_grid* grid, const double* D, int3
   ftgcr_handle h;
   h.dev = dev;
   fill_handle_params(&h, grid, k, tol, di.sms, smem_limit);
-  if (dyn_smem(h.nlon, h.nlat, h.nt, 0, sizeof(double), h.precond) > (size_t)smem_limit) return FTGCR_ERR_ARG;
+  if (h.plan.bytes > (size_t)smem_limit) return FTGCR_ERR_ARG;
   SolveDev<double> sd{};
   const size_t pool = layout<double>(&h, nullptr, &sd);
   const size_t geo = align256(sizeof(double) * 3 * h.nlat);
@@ -1303,6 +1366,9 @@ extern "C" int ftgcr_solve_noalloc(const ftgcr_grid* grid, const double* D, int3
   sd.tol2 = h.tol * h.tol;
   sd.inner_tol2 = h.inner_tol * h.inner_tol;
   sd.protect = (h.flags & FTGCR_FLAG_UNPROTECTED) ? 0 : 1;
+  sd.split = 0;
+  sd.cs_off = (int)h.plan.cs_off;
+  sd.cs_clobber = 0;
   sd.Tx64 = h.Tx64;
   sd.Ty64 = h.Ty64;
   sd.muA64 = h.muA64;
@@ -1331,17 +1397,17 @@ extern "C" int ftgcr_solve_noalloc(const ftgcr_grid* grid, const double* D, int3
   CK(cudaMemsetAsync(h.active, 0, sizeof(int) * 2, st));
 
   const int kb = kbound(h.k);
-  h.smem = dyn_smem(h.nlon, h.nlat, h.nt, 0, sizeof(double), h.precond);
-  rc = configure_kernel<double>(kb, std::max<size_t>(h.smem, 1));
+  h.smem = h.plan.bytes;
+  rc = configure_kernel<double>(kb, 0, std::max<size_t>(h.smem, 1));
   if (rc) return rc;
   int occ = 0;
-  rc = occupancy<double>(kb, h.smem, &occ);
+  rc = occupancy<double>(kb, 0, h.smem, &occ);
   if (rc) return rc;
   if (occ < 1) return FTGCR_ERR_ARG;
   {
     // no stack resize here (it may allocate): the current limit must do
     cudaFuncAttributes fa;
-    CK(cudaFuncGetAttributes(&fa, kernel_ptr<double>(kb)));
+    CK(cudaFuncGetAttributes(&fa, kernel_ptr<double>(kb, 0)));
     size_t cur = 0;
     CK(cudaDeviceGetLimit(&cur, cudaLimitStackSize));
     if (fa.localSizeBytes > cur) return FTGCR_ERR_ARG;
@@ -1361,7 +1427,7 @@ extern "C" int ftgcr_solve_noalloc(const ftgcr_grid* grid, const double* D, int3
   a.trace_rounds = 0;
   a.diag = h.diag;
   void* args[] = {&a};
-  CK(cudaLaunchCooperativeKernel(kernel_ptr<double>(kb), dim3(grid_ctas), dim3(kThreads), args, h.smem, st));
+  CK(cudaLaunchCooperativeKernel(kernel_ptr<double>(kb, 0), dim3(grid_ctas), dim3(kThreads), args, h.smem, st));
   SolveState res;
   LaunchCtl ctl;
   CK(cudaMemcpyAsync(&res, h.result, sizeof res, cudaMemcpyDeviceToHost, st));

@@ -143,6 +143,11 @@ struct SolveDev {
   const LossEv* losses;  // [kMaxLosses]
   int nlosses;
   int protect;  // 0: plain GCR(k), no fault test (the paper's unprotected runs)
+  // split rounds: the step phases run as two passes over the tiles with a
+  // grid barrier between them (no recomputed halo rows); cs_off: offset of
+  // the staged line-solve constants in the dynamic shared memory (elements);
+  // cs_clobber: the second pass's rows overlap them
+  int split, cs_off, cs_clobber;
 };
 
 // --------------------------------------------------------------- helpers
@@ -264,9 +269,9 @@ __device__ __forceinline__ void cta_red_put(CtaRed& cr, int v, DD x) {
   if ((threadIdx.x & 31) == 0) cr.w[threadIdx.x >> 5][v] = x;
 }
 template <typename T>
-__device__ __forceinline__ void cta_red_finish(CtaRed& cr, int nv, double* out) {
+__device__ __forceinline__ void cta_red_finish(CtaRed& cr, int nv, double* out, int v0 = 0) {
   __syncthreads();
-  if (threadIdx.x < nv) {
+  if (threadIdx.x >= v0 && threadIdx.x < nv) {
     const int v = threadIdx.x;
     if constexpr (sizeof(T) == 8) {
       DD t[kWarps];
@@ -675,63 +680,81 @@ __device__ void pointwise_precond_row(const SolveDev<T>& sd, int j, T* row) {
   __syncwarp();
 }
 
-// Preconditioner solve of one row by one warp.  FP32: the chunked warp
-// solve; FP64: lane 0 runs the oracle-identical sequential solve.
 // The same serial solve with the row and its factors in shared memory
-// (explicit ld.shared / st.shared), stopping at x_{n-1}: the caller applies
-// x_i = y_i - x_{n-1} z_i to all rows of the tile block-wide, the same
-// operations element by element.
-static __device__ __noinline__ void line_solve_row_seq_sh(const SolveDev<double>& sd, int j, double* row_, const double* l_,
-                                     const double* winv_, const double* u_) {
-  const int n = sd.nlon, m = n - 1;
-  const unsigned rb = smem_addr(row_), lb = smem_addr(l_), wb = smem_addr(winv_), ub = smem_addr(u_);
+// (explicit ld.shared / st.shared), split in three so that only the two
+// dependent chains run lane-serial.  The backward step's product g_i winv_i
+// does not depend on the chain: the caller forms it for all rows block-wide
+// between the passes (the same rounded product, so the same values), and
+// applies x_i = y_i - x_{n-1} z_i block-wide after them.  GB300's FP64 unit
+// takes 64 cycles per warp instruction whatever the active lanes, so each
+// FP64 instruction moved off a chain saves 64 cycles per element.  Whole
+// blocks of kLB elements carry no per-element bounds tests (a scalar loop
+// takes the remainder), which lets the block's loads issue together.
+// Forward pass: y_0 = b_0, y_i = fma(-l_i, y_{i-1}, b_i), b = -r, i < m.
+static __device__ __noinline__ void line_solve_fwd_sh(int n, double* row_, const double* l_) {
+  const int m = n - 1;
+  const unsigned rb = smem_addr(row_), lb = smem_addr(l_);
   auto R = [&](int i) { return rb + 8u * (unsigned)sk(i); };
+  auto Lf = [&](int i) { return lb + 8u * (unsigned)i; };
   double y = -lds<double>(R(0));
   sts(R(0), y);
-  for (int i0 = 1; i0 < m; i0 += kLB) {
+  int i0 = 1;
+  for (; i0 + kLB <= m; i0 += kLB) {
     double bv[kLB], lv[kLB];
 #pragma unroll
-    for (int q = 0; q < kLB; ++q)
-      if (i0 + q < m) {
-        bv[q] = -lds<double>(R(i0 + q));
-        lv[q] = lds<double>(lb + 8u * (unsigned)(i0 + q));
-      }
+    for (int q = 0; q < kLB; ++q) {
+      bv[q] = -lds<double>(R(i0 + q));
+      lv[q] = lds<double>(Lf(i0 + q));
+    }
 #pragma unroll
-    for (int q = 0; q < kLB; ++q)
-      if (i0 + q < m) {
-        y = fma(-lv[q], y, bv[q]);
-        bv[q] = y;
-      }
+    for (int q = 0; q < kLB; ++q) {
+      y = fma(-lv[q], y, bv[q]);
+      bv[q] = y;
+    }
 #pragma unroll
-    for (int q = 0; q < kLB; ++q)
-      if (i0 + q < m) sts(R(i0 + q), bv[q]);
+    for (int q = 0; q < kLB; ++q) sts(R(i0 + q), bv[q]);
   }
-  y = lds<double>(R(m - 1)) * lds<double>(wb + 8u * (unsigned)(m - 1));
-  sts(R(m - 1), y);
-  for (int i1 = m - 2; i1 >= 0; i1 -= kLB) {
-    double gv[kLB], wv[kLB], uv[kLB];
+  for (; i0 < m; ++i0) {
+    y = fma(-lds<double>(Lf(i0)), y, -lds<double>(R(i0)));
+    sts(R(i0), y);
+  }
+}
+// Backward pass on the products gw_i = g_i winv_i (i < m) already in the row:
+// y_{m-1} = gw_{m-1}, y_i = fma(-u_i, y_{i+1}, gw_i); then
+// x_{n-1} = (b_{n-1} + Tx_{n-1} y_0 + Tx_{n-2} y_{m-1}) / delta into slot n-1.
+static __device__ __noinline__ void line_solve_bwd_sh(const SolveDev<double>& sd, int j, double* row_, const double* u_) {
+  const int n = sd.nlon, m = n - 1;
+  const unsigned rb = smem_addr(row_), ub = smem_addr(u_);
+  auto R = [&](int i) { return rb + 8u * (unsigned)sk(i); };
+  auto Uf = [&](int i) { return ub + 8u * (unsigned)i; };
+  double y = lds<double>(R(m - 1));
+  int i1 = m - 2;
+  for (; i1 - kLB + 1 >= 0; i1 -= kLB) {  // block [i1 - kLB + 1, i1], descending
+    double gv[kLB], uv[kLB];
 #pragma unroll
-    for (int q = 0; q < kLB; ++q)
-      if (i1 - q >= 0) {
-        gv[q] = lds<double>(R(i1 - q));
-        wv[q] = lds<double>(wb + 8u * (unsigned)(i1 - q));
-        uv[q] = lds<double>(ub + 8u * (unsigned)(i1 - q));
-      }
+    for (int q = 0; q < kLB; ++q) {
+      gv[q] = lds<double>(R(i1 - q));
+      uv[q] = lds<double>(Uf(i1 - q));
+    }
 #pragma unroll
-    for (int q = 0; q < kLB; ++q)
-      if (i1 - q >= 0) {
-        y = fma(-uv[q], y, gv[q] * wv[q]);
-        gv[q] = y;
-      }
+    for (int q = 0; q < kLB; ++q) {
+      y = fma(-uv[q], y, gv[q]);
+      gv[q] = y;
+    }
 #pragma unroll
-    for (int q = 0; q < kLB; ++q)
-      if (i1 - q >= 0) sts(R(i1 - q), gv[q]);
+    for (int q = 0; q < kLB; ++q) sts(R(i1 - q), gv[q]);
+  }
+  for (; i1 >= 0; --i1) {
+    y = fma(-lds<double>(Uf(i1)), y, lds<double>(R(i1)));
+    sts(R(i1), y);
   }
   const double* tx = sd.Tx + (long long)j * n;
   const double num = -lds<double>(R(n - 1)) + __ldg(tx + n - 1) * lds<double>(R(0)) + __ldg(tx + n - 2) * lds<double>(R(m - 1));
   sts(R(n - 1), num / __ldg(sd.lrow + (long long)j * 4));
 }
 
+// Preconditioner solve of one row by one warp.  FP32: the chunked warp
+// solve; FP64: lane 0 runs the oracle-identical sequential solve.
 template <typename T>
 __device__ __forceinline__ void precond_row(const SolveDev<T>& sd, int j, T* row, const LineConsts<T> lc) {
   if (sd.precond == PC_LINE) {

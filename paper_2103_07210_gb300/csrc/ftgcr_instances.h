@@ -1,12 +1,21 @@
 // Entry points of the persistent-kernel instances compiled in separate
-// translation units (one per compile-time direction bound).
+// translation units (one per compile-time direction bound and round layout).
 #pragma once
 
 namespace ftgcr {
 const void* persistent_kernel_k4(bool fp64);
 const void* persistent_kernel_k8(bool fp64);
 const void* persistent_kernel_k16(bool fp64);
-inline const void* persistent_kernel_ptr(int kb, bool fp64) {
+const void* persistent_kernel_k4_split();
+const void* persistent_kernel_k8_split();
+const void* persistent_kernel_k16_split();
+// split: the mixed-path instance with split rounds
+inline const void* persistent_kernel_ptr(int kb, bool fp64, bool split) {
+  if (split && !fp64) {
+    if (kb == 4) return persistent_kernel_k4_split();
+    if (kb == 8) return persistent_kernel_k8_split();
+    return persistent_kernel_k16_split();
+  }
   if (kb == 4) return persistent_kernel_k4(fp64);
   if (kb == 8) return persistent_kernel_k8(fp64);
   return persistent_kernel_k16(fp64);

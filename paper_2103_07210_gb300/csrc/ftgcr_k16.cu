@@ -4,6 +4,6 @@
 
 namespace ftgcr {
 const void* persistent_kernel_k16(bool fp64) {
-  return fp64 ? (const void*)k_ftgcr_persistent<double, 16> : (const void*)k_ftgcr_persistent<float, 16>;
+  return fp64 ? (const void*)k_ftgcr_persistent<double, 16, false> : (const void*)k_ftgcr_persistent<float, 16, false>;
 }
 }  // namespace ftgcr

@@ -1,0 +1,8 @@
+// Persistent FT-GCR kernel instance with split rounds (mixed path) for at
+// most 16 Krylov directions.
+#include "ftgcr_instances.h"
+#include "ftgcr_phases.cuh"
+
+namespace ftgcr {
+const void* persistent_kernel_k16_split() { return (const void*)k_ftgcr_persistent<float, 16, true>; }
+}  // namespace ftgcr

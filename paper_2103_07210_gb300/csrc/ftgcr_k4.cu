@@ -4,6 +4,6 @@
 
 namespace ftgcr {
 const void* persistent_kernel_k4(bool fp64) {
-  return fp64 ? (const void*)k_ftgcr_persistent<double, 4> : (const void*)k_ftgcr_persistent<float, 4>;
+  return fp64 ? (const void*)k_ftgcr_persistent<double, 4, false> : (const void*)k_ftgcr_persistent<float, 4, false>;
 }
 }  // namespace ftgcr

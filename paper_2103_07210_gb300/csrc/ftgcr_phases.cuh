@@ -697,13 +697,21 @@ template <typename T>
 __device__ __forceinline__ void precond_tile(const SolveDev<T>& sd, int h0, int nrows, T* sm, int stride, const T* cs) {
   if constexpr (sizeof(T) == 8) {
     if (sd.precond == PC_LINE) {
-      for (int jr = threadIdx.x; jr < nrows; jr += kThreads) {
-        const LineConsts<T> lc = staged_consts(sd, cs, nrows, jr);
-        line_solve_row_seq_sh(sd, h0 + jr, sm + jr * stride, lc.cb, lc.cw, lc.cz);
+      const int n = sd.nlon, m = n - 1;
+      for (int jr = threadIdx.x; jr < nrows; jr += kThreads)
+        line_solve_fwd_sh(n, sm + jr * stride, staged_consts(sd, cs, nrows, jr).cb);
+      __syncthreads();
+      // the backward step's products g_i winv_i, all rows at once
+      for (int idx = threadIdx.x; idx < nrows * m; idx += kThreads) {
+        const int jr = idx / m, i = idx - jr * m;
+        T* row = sm + jr * stride;
+        row[sk(i)] = row[sk(i)] * staged_consts(sd, cs, nrows, jr).cw[i];
       }
       __syncthreads();
+      for (int jr = threadIdx.x; jr < nrows; jr += kThreads)
+        line_solve_bwd_sh(sd, h0 + jr, sm + jr * stride, staged_consts(sd, cs, nrows, jr).cz);
+      __syncthreads();
       // bordering, x_i = y_i - x_{n-1} z_i, all rows at once
-      const int n = sd.nlon, m = n - 1;
       for (int idx = threadIdx.x; idx < nrows * m; idx += kThreads) {
         const int jr = idx / m, i = idx - jr * m;
         T* row = sm + jr * stride;
@@ -778,6 +786,60 @@ __device__ __forceinline__ RowVec row_vec(int idx, int nvr, int j0, int nlon, in
   return r;
 }
 
+// Rows [h0, h1) of a vector written by other CTAs this round into the
+// shared-memory row layout (L2 loads, four 16-byte loads per thread in flight).
+template <typename T>
+__device__ __forceinline__ void stage_rows(const T* src, int h0, int h1, int nlon, T* sm, int stride) {
+  constexpr int W = V16<T>::W, U = 4;
+  if (nlon % W == 0) {
+    const int nvr = nlon / W, total = (h1 - h0) * nvr;
+    for (int b0 = threadIdx.x; b0 < total; b0 += U * kThreads) {
+      V16<T> v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = b0 + u * kThreads;
+        if (idx < total) v[u] = ldv(src + (long long)h0 * nlon + (long long)idx * W);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = b0 + u * kThreads;
+        if (idx < total) {
+          const int jr = idx / nvr, i = (idx - jr * nvr) * W;
+          T* row = sm + jr * stride;
+#pragma unroll
+          for (int w = 0; w < W; ++w) row[sk(i + w)] = v[u].v[w];
+        }
+      }
+    }
+  } else {
+    for (int j = h0; j < h1; ++j) {
+      T* row = sm + (j - h0) * stride;
+      for (int i = threadIdx.x; i < nlon; i += kThreads) row[sk(i)] = ldcg(src + (long long)j * nlon + i);
+    }
+  }
+}
+// Rows [h0, h1) of the shared-memory row layout out to a vector.
+template <typename T>
+__device__ __forceinline__ void store_rows(T* dst, int h0, int h1, int nlon, const T* sm, int stride) {
+  constexpr int W = V16<T>::W;
+  if (nlon % W == 0) {
+    const int nvr = nlon / W, total = (h1 - h0) * nvr;
+    for (int idx = threadIdx.x; idx < total; idx += kThreads) {
+      const int jr = idx / nvr, i = (idx - jr * nvr) * W;
+      const T* row = sm + jr * stride;
+      V16<T> v;
+#pragma unroll
+      for (int w = 0; w < W; ++w) v.v[w] = row[sk(i + w)];
+      stv(dst + (long long)h0 * nlon + (long long)idx * W, v);
+    }
+  } else {
+    for (int j = h0; j < h1; ++j) {
+      const T* row = sm + (j - h0) * stride;
+      for (int i = threadIdx.x; i < nlon; i += kThreads) dst[(long long)j * nlon + i] = row[sk(i)];
+    }
+  }
+}
+
 // The data-loss events of step t (Section 3) on the e rows [h0, h1) staged in
 // shared memory: every thread takes flips i = 1 + threadIdx.x, ... of each
 // event and XORs those that land in the tile (atomically: two flips may hit
@@ -805,31 +867,21 @@ __device__ __forceinline__ void apply_losses(const SolveDev<T>& sd, long long t,
   }
 }
 
-// PA: axpy, norm, preconditioner, operator, orthogonalisation dots.  KB is a
-// compile-time bound on the number of directions (k <= KB).  The mixed path
-// also reduces h = <r', L(e)> and q = <L(e), L(e)>, from which the next
-// direction's dots follow without forming it (see precompute_divisions).
-// FUSED (PF, mixed path): the round first forms the previous step's new
-// direction p', L(p') (the recurrences of Algorithm 1, as PB does) and takes
-// this step's axpy with it, so an accepted step costs one round, not two.
+// The parts of a step phase (PA, PF), inlined into the one-pass phase and
+// into the two passes of a split round.  Rows [rt.h0, rt.h1) are staged in
+// shared memory (own rows [rt.j0, rt.j1) and, in one-pass rounds, a halo row
+// each side).
+// (1) The axpy: r' (and, fused, the new direction) into the staged rows; the
+// state vectors of the own rows written; an += ||r'||^2 over own rows.
 template <typename T, int KB, bool FUSED>
-__device__ __noinline__ void phase_pa(const SolveDev<T>& sd, const Ctx<T>& c, int sidx, int tau, T* sm, PhaseSmem& ps,
-                                      double* part_out) {
+__device__ __forceinline__ void step_axpy(const SolveDev<T>& sd, const Ctx<T>& c, const RowTile& rt, T* sm,
+                                          PhaseSmem& ps, Acc<T>& an) {
   constexpr int W = V16<T>::W;
   constexpr int U = 2;
   constexpr bool kMixed = sizeof(T) == 4;
   const int nlon = sd.nlon, nlat = sd.nlat, stride = row_stride(nlon);
-  const RowTile rt = row_tile(nlat, sd.nt, tau);
   const int nrows = rt.h1 - rt.h0;
-  const int warp = threadIdx.x >> 5;
   const T beta = c.beta;
-  T* cs = sm + (long long)(sd.nt_hmax + 2) * stride;
-  // a CTA that keeps the same tile keeps its staged constants (single solves)
-  if (!(ps.cs_solve == sidx && ps.cs_tile == tau)) stage_line_consts(sd, rt.h0, rt.h1, cs);
-  if (threadIdx.x == 0)
-    ps.nfl = collect_flips(sd, c.t, FUSED ? (kStateVecs | (1u << V_E)) : (1u << V_E), (long long)rt.h0 * nlon,
-                           (long long)rt.h1 * nlon, ps.fl);
-  Acc<T> an;
   if constexpr (FUSED) {
     // p' = e + sum_l alpha_l p^l, L(p') = L(e) + sum_l alpha_l L(p^l) (l in
     // increasing order, one fma per term, as PB), then the flips of the
@@ -982,6 +1034,14 @@ __device__ __noinline__ void phase_pa(const SolveDev<T>& sd, const Ctx<T>& c, in
       }
     }
   }
+}
+// (2) e = P^-1 r' on the staged rows, then the e-site flips and data-loss
+// events of the step.
+template <typename T>
+__device__ __forceinline__ void step_precond(const SolveDev<T>& sd, const Ctx<T>& c, const RowTile& rt, T* sm,
+                                             const T* cs, PhaseSmem& ps) {
+  const int nlon = sd.nlon, stride = row_stride(nlon);
+  const int nrows = rt.h1 - rt.h0;
   cp_async_wait_all();
   __syncthreads();
   sub_mark(ps, 0);
@@ -1002,6 +1062,17 @@ __device__ __noinline__ void phase_pa(const SolveDev<T>& sd, const Ctx<T>& c, in
     apply_losses(sd, c.t, rt.h0, rt.h1, sm, stride);
   }
   __syncthreads();
+}
+// (3) L(e) on the own rows from the staged e rows (with halo rows), the dots
+// and the tile's partial sums (write_e: also e itself and the norm an).
+template <typename T, int KB>
+__device__ __forceinline__ void step_stencil(const SolveDev<T>& sd, const Ctx<T>& c, const RowTile& rt, const T* sm,
+                                             PhaseSmem& ps, double* part_out, const Acc<T>* an, bool write_e) {
+  constexpr int W = V16<T>::W;
+  constexpr int U = 2;
+  constexpr bool kMixed = sizeof(T) == 4;
+  const int nlon = sd.nlon, nlat = sd.nlat, stride = row_stride(nlon);
+  const int nrows = rt.h1 - rt.h0;
   Acc<T> ad[KB];
   Acc<T> ah, aq;  // mixed: <r', L(e)>, <L(e), L(e)>
   if (nlon % W == 0) {
@@ -1034,7 +1105,7 @@ __device__ __noinline__ void phase_pa(const SolveDev<T>& sd, const Ctx<T>& c, in
                               hasS ? row[-stride + sk(i)] : T(0), tx.v[w], w == 0 ? txw0 : tx.v[w - 1],
                               hasN ? ty.v[w] : T(0), hasS ? tys.v[w] : T(0), muA, hasN, hasS);
       }
-      stv(c.eW + v.g, ev);
+      if (write_e) stv(c.eW + v.g, ev);
       stv(c.LeW + v.g, le);
 #pragma unroll
       for (int l = 0; l < KB; ++l)
@@ -1057,7 +1128,7 @@ __device__ __noinline__ void phase_pa(const SolveDev<T>& sd, const Ctx<T>& c, in
       for (int i = threadIdx.x; i < nlon; i += kThreads) {
         const long long g = base + i;
         const T le = stencil_smem(sd, sm, stride, rt.h0, j, i);
-        c.eW[g] = row[sk(i)];
+        if (write_e) c.eW[g] = row[sk(i)];
         c.LeW[g] = le;
 #pragma unroll
         for (int l = 0; l < KB; ++l)
@@ -1070,21 +1141,81 @@ __device__ __noinline__ void phase_pa(const SolveDev<T>& sd, const Ctx<T>& c, in
     }
   }
   sub_mark(ps, 2);
-  cta_red_put(ps.cr, 0, an.warp_sum());
+  if (write_e) cta_red_put(ps.cr, 0, an->warp_sum());
 #pragma unroll
   for (int l = 0; l < KB; ++l)
     if (l <= c.nu) cta_red_put(ps.cr, 1 + l, ad[l].warp_sum());
   if constexpr (kMixed) {
     cta_red_put(ps.cr, 2 + c.nu, ah.warp_sum());
     cta_red_put(ps.cr, 3 + c.nu, aq.warp_sum());
-    cta_red_finish<T>(ps.cr, 4 + c.nu, part_out);
+    cta_red_finish<T>(ps.cr, 4 + c.nu, part_out, write_e ? 0 : 1);
   } else {
-    cta_red_finish<T>(ps.cr, 2 + c.nu, part_out);
+    cta_red_finish<T>(ps.cr, 2 + c.nu, part_out, write_e ? 0 : 1);
   }
+}
+
+template <typename T, int KB, bool FUSED>
+__device__ __noinline__ void phase_pa(const SolveDev<T>& sd, const Ctx<T>& c, int sidx, int tau, T* sm, PhaseSmem& ps,
+                                      double* part_out) {
+  const int nlon = sd.nlon, nlat = sd.nlat, stride = row_stride(nlon);
+  const RowTile rt = row_tile(nlat, sd.nt, tau);
+  T* cs = sm + sd.cs_off;
+  // a CTA that keeps the same tile keeps its staged constants (single solves)
+  if (!(ps.cs_solve == sidx && ps.cs_tile == tau)) stage_line_consts(sd, rt.h0, rt.h1, cs);
+  if (threadIdx.x == 0)
+    ps.nfl = collect_flips(sd, c.t, FUSED ? (kStateVecs | (1u << V_E)) : (1u << V_E), (long long)rt.h0 * nlon,
+                           (long long)rt.h1 * nlon, ps.fl);
+  Acc<T> an;
+  step_axpy<T, KB, FUSED>(sd, c, rt, sm, ps, an);
+  step_precond<T>(sd, c, rt, sm, cs, ps);
+  step_stencil<T, KB>(sd, c, rt, sm, ps, part_out, &an, true);
   if (threadIdx.x == 0) {
     ps.cs_solve = sidx;
     ps.cs_tile = tau;
   }
+}
+
+// The step phase in the kernel instance with split rounds (wide rows, where
+// shared memory leaves a tile few rows and recomputed halo rows would
+// multiply the work).  mode 0: as phase_pa (a solve in one-pass rounds);
+// mode 1, the first pass: the tile's own rows up to e, e written out, the norm
+// as partial sum 0; mode 2, the second pass after a grid barrier: e of the own
+// and halo rows read back, L(e), the dots.  One function for the three, as the
+// instance's register allocation fares best with few phase functions.
+template <typename T, int KB, bool FUSED>
+__device__ __noinline__ void phase_pa_any(const SolveDev<T>& sd, const Ctx<T>& c, int sidx, int tau, T* sm,
+                                          PhaseSmem& ps, double* part_out, int mode) {
+  const int nlon = sd.nlon, stride = row_stride(nlon);
+  RowTile rt = row_tile(sd.nlat, sd.nt, tau);
+  Acc<T> an;
+  if (mode == 2) {
+    stage_rows(c.eW, rt.h0, rt.h1, nlon, sm, stride);
+    if (sd.cs_clobber && threadIdx.x == 0) ps.cs_solve = -1;  // the rows overwrote staged constants
+    __syncthreads();
+  } else {
+    if (mode == 1) {  // own rows only
+      rt.h0 = rt.j0;
+      rt.h1 = rt.j1;
+    }
+    T* cs = sm + sd.cs_off;
+    if (!(ps.cs_solve == sidx && ps.cs_tile == tau)) stage_line_consts(sd, rt.h0, rt.h1, cs);
+    if (threadIdx.x == 0)
+      ps.nfl = collect_flips(sd, c.t, FUSED ? (kStateVecs | (1u << V_E)) : (1u << V_E), (long long)rt.h0 * nlon,
+                             (long long)rt.h1 * nlon, ps.fl);
+    step_axpy<T, KB, FUSED>(sd, c, rt, sm, ps, an);
+    step_precond<T>(sd, c, rt, sm, cs, ps);
+    if (threadIdx.x == 0) {
+      ps.cs_solve = sidx;
+      ps.cs_tile = tau;
+    }
+    if (mode == 1) {
+      store_rows(c.eW, rt.h0, rt.h1, nlon, sm, stride);
+      cta_red_put(ps.cr, 0, an.warp_sum());
+      cta_red_finish<T>(ps.cr, 1, part_out);
+      return;
+    }
+  }
+  step_stencil<T, KB>(sd, c, rt, sm, ps, part_out, &an, mode == 0);
 }
 
 // PB: direction recurrences and the dots for the next beta.
@@ -1221,25 +1352,15 @@ __device__ __noinline__ void phase_restore(const SolveDev<T>& sd, const Ctx<T>& 
   cta_red_finish<T>(ps.cr, 2, part_out);
 }
 
-// INIT: r0 = L(phi0) - R (FP64 path, phi0 = x0) or r0 = -R_in (mixed inner
-// solve, phi0 = 0); p0 = P^-1(r0); L(p0); ||r0||^2, ||R||^2 and the first
-// beta dots.  The x/r/p/Ap flips of the first step are applied to the working
-// vectors, and their clean values kept so that the backup stays clean.
+// The parts of INIT, inlined into the one-pass phase and the two passes of a
+// split round.  (1) r0 into the staged rows [rt.h0, rt.h1), the own rows'
+// x0, r0 written (with the step's x / r flips and their clean values kept).
 template <typename T>
-__device__ __noinline__ void phase_init(const SolveDev<T>& sd, const Ctx<T>& c, int sidx, int tau, T* sm, PhaseSmem& ps,
-                           double* part_out) {
+__device__ __forceinline__ void init_rows(const SolveDev<T>& sd, const Ctx<T>& c, const RowTile& rt, T* sm,
+                                          PhaseSmem& ps, Acc<T>& an, Acc<T>& aR, bool vec) {
   const int nlon = sd.nlon, nlat = sd.nlat, stride = row_stride(nlon);
-  const RowTile rt = row_tile(nlat, sd.nt, tau);
-  const int warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0)
-    ps.nfl = collect_flips(sd, c.t, kStateVecs, (long long)rt.j0 * nlon, (long long)rt.j1 * nlon, ps.fl);
-  T* cs = sm + (long long)(sd.nt_hmax + 2) * stride;
-  if (!(ps.cs_solve == sidx && ps.cs_tile == tau)) stage_line_consts(sd, rt.h0, rt.h1, cs);
-  __syncthreads();
-  const int nfl = ps.nfl;
-  Acc<T> an, aR;
   constexpr int W = V16<T>::W;
-  const bool vec = c.zero_guess && nfl == 0 && nlon % W == 0;  // the common case, 16-byte accesses
+  const int nfl = ps.nfl;
   if (vec) {
     // r0 = -R_in (zero guess), x0 = 0
     const int nvr = nlon / W, total = (rt.h1 - rt.h0) * nvr;
@@ -1298,10 +1419,17 @@ __device__ __noinline__ void phase_init(const SolveDev<T>& sd, const Ctx<T>& c, 
       }
     }
   }
-  cp_async_wait_all();
-  __syncthreads();
-  precond_tile(sd, rt.h0, rt.h1 - rt.h0, sm, stride, cs);
-  __syncthreads();
+}
+// (2) L(p0) on the own rows from the staged p0 rows, the p / Ap flips, p0 and
+// L(p0) written, the dots and the tile's partial sums (full: also ||r0||^2
+// and ||R||^2).
+template <typename T>
+__device__ __forceinline__ void init_stencil(const SolveDev<T>& sd, const Ctx<T>& c, const RowTile& rt, const T* sm,
+                                             PhaseSmem& ps, double* part_out, const Acc<T>* an, const Acc<T>* aR,
+                                             bool vec, bool full) {
+  const int nlon = sd.nlon, nlat = sd.nlat, stride = row_stride(nlon);
+  constexpr int W = V16<T>::W;
+  const int nfl = ps.nfl;
   Acc<T> a0, a1;
   if (vec) {
     // p0 = P^-1 r0 (in the rows), L(p0) and the first dots, 16-byte accesses
@@ -1360,15 +1488,89 @@ __device__ __noinline__ void phase_init(const SolveDev<T>& sd, const Ctx<T>& c, 
       a1.add(lp, lp);
     }
   }
-  cta_red_put(ps.cr, 0, an.warp_sum());
-  cta_red_put(ps.cr, 1, aR.warp_sum());
+  if (full) {
+    cta_red_put(ps.cr, 0, an->warp_sum());
+    cta_red_put(ps.cr, 1, aR->warp_sum());
+  }
   cta_red_put(ps.cr, 2, a0.warp_sum());
   cta_red_put(ps.cr, 3, a1.warp_sum());
-  cta_red_finish<T>(ps.cr, 4, part_out);
+  cta_red_finish<T>(ps.cr, 4, part_out, full ? 0 : 2);
+}
+
+// INIT: r0 = L(phi0) - R (FP64 path, phi0 = x0) or r0 = -R_in (mixed inner
+// solve, phi0 = 0); p0 = P^-1(r0); L(p0); ||r0||^2, ||R||^2 and the first
+// beta dots.  The x/r/p/Ap flips of the first step are applied to the working
+// vectors, and their clean values kept so that the backup stays clean.
+template <typename T>
+__device__ __noinline__ void phase_init(const SolveDev<T>& sd, const Ctx<T>& c, int sidx, int tau, T* sm, PhaseSmem& ps,
+                           double* part_out) {
+  const int nlon = sd.nlon, nlat = sd.nlat, stride = row_stride(nlon);
+  const RowTile rt = row_tile(nlat, sd.nt, tau);
+  if (threadIdx.x == 0)
+    ps.nfl = collect_flips(sd, c.t, kStateVecs, (long long)rt.j0 * nlon, (long long)rt.j1 * nlon, ps.fl);
+  T* cs = sm + sd.cs_off;
+  if (!(ps.cs_solve == sidx && ps.cs_tile == tau)) stage_line_consts(sd, rt.h0, rt.h1, cs);
+  __syncthreads();
+  Acc<T> an, aR;
+  constexpr int W = V16<T>::W;
+  const bool vec = c.zero_guess && ps.nfl == 0 && nlon % W == 0;  // the common case, 16-byte accesses
+  init_rows<T>(sd, c, rt, sm, ps, an, aR, vec);
+  cp_async_wait_all();
+  __syncthreads();
+  precond_tile(sd, rt.h0, rt.h1 - rt.h0, sm, stride, cs);
+  __syncthreads();
+  init_stencil<T>(sd, c, rt, sm, ps, part_out, &an, &aR, vec, true);
   if (threadIdx.x == 0) {
     ps.cs_solve = sidx;
     ps.cs_tile = tau;
   }
+}
+
+// INIT in the kernel instance with split rounds.  mode 0: as phase_init;
+// mode 1: r0 and p0 = P^-1(r0) of the own rows, p0 (unflipped) into the
+// scratch vector e[0], the two norms; mode 2: p0 with its halo rows read back
+// from e[0], L(p0), flips, dots.
+template <typename T>
+__device__ __noinline__ void phase_init_any(const SolveDev<T>& sd, const Ctx<T>& c, int sidx, int tau, T* sm,
+                                            PhaseSmem& ps, double* part_out, int mode) {
+  const int nlon = sd.nlon, stride = row_stride(nlon);
+  RowTile rt = row_tile(sd.nlat, sd.nt, tau);
+  if (threadIdx.x == 0)
+    ps.nfl = collect_flips(sd, c.t, kStateVecs, (long long)rt.j0 * nlon, (long long)rt.j1 * nlon, ps.fl);
+  Acc<T> an, aR;
+  constexpr int W = V16<T>::W;
+  if (mode == 2) {
+    stage_rows(sd.e[0], rt.h0, rt.h1, nlon, sm, stride);
+    if (sd.cs_clobber && threadIdx.x == 0) ps.cs_solve = -1;
+    __syncthreads();
+  } else {
+    if (mode == 1) {
+      rt.h0 = rt.j0;
+      rt.h1 = rt.j1;
+    }
+    T* cs = sm + sd.cs_off;
+    if (!(ps.cs_solve == sidx && ps.cs_tile == tau)) stage_line_consts(sd, rt.h0, rt.h1, cs);
+    __syncthreads();
+    const bool vec = c.zero_guess && ps.nfl == 0 && nlon % W == 0;
+    init_rows<T>(sd, c, rt, sm, ps, an, aR, vec);
+    cp_async_wait_all();
+    __syncthreads();
+    precond_tile(sd, rt.h0, rt.h1 - rt.h0, sm, stride, cs);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      ps.cs_solve = sidx;
+      ps.cs_tile = tau;
+    }
+    if (mode == 1) {
+      store_rows(sd.e[0], rt.h0, rt.h1, nlon, sm, stride);
+      cta_red_put(ps.cr, 0, an.warp_sum());
+      cta_red_put(ps.cr, 1, aR.warp_sum());
+      cta_red_finish<T>(ps.cr, 2, part_out);
+      return;
+    }
+  }
+  const bool vec = c.zero_guess && ps.nfl == 0 && nlon % W == 0;
+  init_stencil<T>(sd, c, rt, sm, ps, part_out, &an, &aR, vec, mode == 0);
 }
 
 // OUT (mixed): x' = x + d in FP64, r_out = R - L64(x'), ||r_out||^2 (and
@@ -1531,21 +1733,103 @@ struct KernelSmem {
   int bail;
 };
 
+// Loop state of a CTA (the same in every thread).
+struct LoopState {
+  int cur_sd = -1;            // solve whose descriptor sits in ks.sd
+  int last_s = -1;            // solve whose transition ks.N holds, and its round
+  long long last_round = -2;
+  int cur = -1;               // solve whose context ks.c holds this round
+  int spec_s = -1;            // solve whose partial sums ks.red holds already (speculative)
+  bool red_ready = false;
+};
+
+// Entering solve s in a round: its descriptor, its state record and every
+// partial sum the pending phase may have left, this round's transition into
+// ks.N and ks.c.  A CTA that ran this solve's transition in the previous
+// round holds the record already (every CTA computes the same transition
+// from the same inputs).
+template <typename T>
+__device__ __forceinline__ void enter_solve(SolveDev<T>* const* solves, KernelSmem<T>& ks, LoopState& ls, int s,
+                                            int par, long long round) {
+  if (s != ls.cur_sd) {
+    cta_load_cg(&ks.sd, solves[s]);
+    __syncthreads();
+    ls.cur_sd = s;
+  }
+  if (s == ls.last_s && round == ls.last_round + 1)
+    cta_store(&ks.S, &ks.N);
+  else
+    cta_load_cg(&ks.S, ks.sd.st + par);
+  if (!(ls.red_ready && s == ls.spec_s))
+    reduce_partials<T>(ks.sd.part + (long long)(par ^ 1) * ks.sd.nt * kPartStride, ks.sd.nt, part_values(ks.sd),
+                       ks.red);
+  ls.red_ready = false;
+  __syncthreads();
+  precompute_divisions(ks.S, ks.red, ks.qd, ks.sd.mixed);
+  cta_store(&ks.N, &ks.S);
+  cta_zero(&ks.c);
+  __syncthreads();
+  if (threadIdx.x == 0) transition(ks.sd, ks.S, ks.red, ks.qd, ks.N, ks.c);
+  __syncthreads();
+  fill_directions(ks.sd, ks.S, ks.N, ks.qd, ks.c);
+  __syncthreads();
+  ls.cur = s;
+  ls.last_s = s;
+  ls.last_round = round;
+}
+
+// The phase of tile tau of the solve in ks.  pass 0: a one-pass round, or the
+// first pass of a split round; pass 1: the second pass of a split round (the
+// step phases of split solves only).
+template <typename T, int KB, bool SPLIT>
+__device__ __forceinline__ void run_phase(KernelSmem<T>& ks, int pass, int s, int tau, T* sm, double* part_out) {
+  const int kind = ks.c.kind;
+  if constexpr (SPLIT) {
+    const int mode = ks.sd.split ? 1 + pass : 0;
+    if (pass == 1 && mode == 0) return;
+    switch (kind) {
+      case K_INIT: phase_init_any<T>(ks.sd, ks.c, s, tau, sm, ks.ps, part_out, mode); return;
+      case K_PA: phase_pa_any<T, KB, false>(ks.sd, ks.c, s, tau, sm, ks.ps, part_out, mode); return;
+      case K_PF: phase_pa_any<T, KB, true>(ks.sd, ks.c, s, tau, sm, ks.ps, part_out, mode); return;
+      default:
+        if (pass == 1) return;
+        break;
+    }
+  } else {
+    switch (kind) {
+      case K_INIT: phase_init(ks.sd, ks.c, s, tau, sm, ks.ps, part_out); return;
+      case K_PA: phase_pa<T, KB, false>(ks.sd, ks.c, s, tau, sm, ks.ps, part_out); return;
+      case K_PF:
+        if constexpr (sizeof(T) == 4) phase_pa<T, KB, true>(ks.sd, ks.c, s, tau, sm, ks.ps, part_out);
+        return;
+      default: break;
+    }
+  }
+  switch (kind) {
+    case K_PB: phase_pb<T, KB>(ks.sd, ks.c, tau, ks.ps, part_out); break;
+    case K_RESTORE: phase_restore(ks.sd, ks.c, tau, ks.ps, part_out); break;
+    case K_OUT: phase_out(ks.sd, ks.c, tau, reinterpret_cast<double*>(sm), ks.ps, part_out); break;
+    case K_FIN: phase_fin(ks.sd, ks.c, tau, ks.ps, part_out); break;
+    default: break;
+  }
+}
+
 // Persistent cooperative kernel: every round, every CTA takes its share of
 // the tiles of all active solves, runs for each solve the state transition
 // and the decided phase, and then meets the others at one grid barrier.
-template <typename T, int KB>
+// SPLIT (mixed path): the instance for launches with split-round solves, whose
+// every round takes a second pass over the tiles after a further barrier; the
+// one-pass instance carries none of that code.
+template <typename T, int KB, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1) k_ftgcr_persistent(BatchArgs<T> a) {
+  static_assert(!SPLIT || sizeof(T) == 4, "split rounds exist on the mixed path only");
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ KernelSmem<T> ks;
   T* sm = reinterpret_cast<T*>(dsm);
-  double* smd = reinterpret_cast<double*>(dsm);
   const long long round0 = a.ctl->round0;
   const unsigned long long t_start = globaltimer();
   unsigned int nbar = 0;
-  int cur_sd = -1;  // solve whose descriptor sits in shared memory
-  int last_s = -1;  // solve whose transition ks.N holds, and its round
-  long long last_round = -2;
+  LoopState ls;
   if (threadIdx.x == 0) ks.ps.cs_solve = -1;
   int it = 0;
   for (; it < a.max_rounds; ++it) {
@@ -1561,11 +1845,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_ftgcr_persistent(BatchArgs<T> a
     // speculative: a CTA that ran a solve's transition last round will most
     // likely run the same solve first this round; warps 1.. reduce its
     // partial sums while warp 0 forms the tile prefix
-    const int spec_s = (cur_sd >= 0 && last_s == cur_sd && last_round == round - 1) ? cur_sd : -1;
+    const int spec_s = (ls.cur_sd >= 0 && ls.last_s == ls.cur_sd && ls.last_round == round - 1) ? ls.cur_sd : -1;
+    ls.spec_s = spec_s;
+    ls.red_ready = spec_s >= 0;
+    ls.cur = -1;
     if (spec_s >= 0)
       reduce_partials<T>(ks.sd.part + (long long)(par ^ 1) * ks.sd.nt * kPartStride, ks.sd.nt, part_values(ks.sd),
                          ks.red, 1);
-    bool red_ready = spec_s >= 0;
     // tile prefix over active solves (identical in every CTA): warp 0 scans
     // 32 solves at a time
     if (threadIdx.x < 32) {
@@ -1593,93 +1879,61 @@ __global__ void __launch_bounds__(kThreads, 1) k_ftgcr_persistent(BatchArgs<T> a
     __syncthreads();
     const int total = ks.prefix[a.n];
     if (total == 0) break;
-    int cur = -1;
-    unsigned long long tr[3] = {0ull, 0ull, 0ull};
+    unsigned long long tr0 = 0ull, tr1 = 0ull, tr2 = 0ull;
     int tr_kind = -1, tr_items = 0;
-    if (a.trace && threadIdx.x == 0) tr[0] = globaltimer();
+    if (a.trace && threadIdx.x == 0) tr0 = globaltimer();
     if (threadIdx.x == 0) {
       ks.ps.tracing = a.trace != nullptr;
       ks.ps.sub[0] = ks.ps.sub[1] = ks.ps.sub[2] = 0ull;
     }
-    for (int item = blockIdx.x; item < total; item += gridDim.x) {
-      int lo = 0, hi = a.n - 1;  // last s with prefix[s] <= item and nt > 0
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (ks.prefix[mid] <= item) lo = mid; else hi = mid - 1;
+    constexpr int npass = SPLIT ? 2 : 1;
+    for (int pass = 0; pass < npass; ++pass) {
+      if (pass == 1) {
+        // second pass of split rounds: after every tile's e is written,
+        // L(e) and the dots of the split solves' tiles
+        ++nbar;
+        if (!grid_barrier(&a.ctl->counter, nbar * gridDim.x, &a.ctl->err, &ks.bail)) return;
       }
-      const int s = lo;
-      const int tau = item - ks.prefix[s];
-      if (s != cur) {
-        if (s != cur_sd) {
-          cta_load_cg(&ks.sd, a.solves[s]);
-          __syncthreads();
-          cur_sd = s;
+      for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        int lo = 0, hi = a.n - 1;  // the last solve s with prefix[s] <= item
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (ks.prefix[mid] <= item) lo = mid; else hi = mid - 1;
         }
-        // the state record and every partial sum the pending phase may have
-        // left, loaded together.  A CTA that ran this solve's transition in
-        // the previous round holds the record already (every CTA computes
-        // the same transition from the same inputs).
-        if (s == last_s && round == last_round + 1)
-          cta_store(&ks.S, &ks.N);
-        else
-          cta_load_cg(&ks.S, ks.sd.st + par);
-        if (!(red_ready && s == spec_s))
-          reduce_partials<T>(ks.sd.part + (long long)(par ^ 1) * ks.sd.nt * kPartStride, ks.sd.nt,
-                             part_values(ks.sd), ks.red);
-        red_ready = false;
+        const int s = lo;
+        const int tau = item - ks.prefix[s];
+        if (s != ls.cur) enter_solve<T>(a.solves, ks, ls, s, par, round);
+        if (pass == 0) {
+          if (a.trace && threadIdx.x == 0 && tr_items == 0) {
+            tr1 = globaltimer();
+            tr_kind = ks.c.kind;
+          }
+          ++tr_items;
+          if (threadIdx.x == 0 && a.diag) {
+            a.diag[blockIdx.x * 4 + 1] = ks.c.kind;
+            a.diag[blockIdx.x * 4 + 2] = 1;
+            a.diag[blockIdx.x * 4 + 3] = tr_items;
+          }
+        }
+        run_phase<T, KB, SPLIT>(ks, pass, s, tau, sm, ks.sd.part + ((long long)par * ks.sd.nt + tau) * kPartStride);
         __syncthreads();
-        precompute_divisions(ks.S, ks.red, ks.qd, ks.sd.mixed);
-        cta_store(&ks.N, &ks.S);
-        cta_zero(&ks.c);
-        __syncthreads();
-        if (threadIdx.x == 0) transition(ks.sd, ks.S, ks.red, ks.qd, ks.N, ks.c);
-        __syncthreads();
-        fill_directions(ks.sd, ks.S, ks.N, ks.qd, ks.c);
-        __syncthreads();
-        cur = s;
-        last_s = s;
-        last_round = round;
+        if (pass == 0 && tau == 0) {
+          cta_store(ks.sd.st + (par ^ 1), &ks.N);
+          if (!ks.N.active) cta_store(ks.sd.result, &ks.N);
+          if (threadIdx.x == 0) a.active[(par ^ 1) * a.n + s] = ks.N.active;
+          __syncthreads();
+        }
       }
-      if (a.trace && threadIdx.x == 0 && tr_items == 0) {
-        tr[1] = globaltimer();
-        tr_kind = ks.c.kind;
-      }
-      ++tr_items;
-      if (threadIdx.x == 0 && a.diag) {
-        a.diag[blockIdx.x * 4 + 1] = ks.c.kind;
-        a.diag[blockIdx.x * 4 + 2] = 1;
-        a.diag[blockIdx.x * 4 + 3] = tr_items;
-      }
-      double* part_out = ks.sd.part + ((long long)par * ks.sd.nt + tau) * kPartStride;
-      switch (ks.c.kind) {
-        case K_INIT: phase_init(ks.sd, ks.c, s, tau, sm, ks.ps, part_out); break;
-        case K_PA: phase_pa<T, KB, false>(ks.sd, ks.c, s, tau, sm, ks.ps, part_out); break;
-        case K_PF:
-          if constexpr (sizeof(T) == 4) phase_pa<T, KB, true>(ks.sd, ks.c, s, tau, sm, ks.ps, part_out);
-          break;
-        case K_PB: phase_pb<T, KB>(ks.sd, ks.c, tau, ks.ps, part_out); break;
-        case K_RESTORE: phase_restore(ks.sd, ks.c, tau, ks.ps, part_out); break;
-        case K_OUT: phase_out(ks.sd, ks.c, tau, smd, ks.ps, part_out); break;
-        case K_FIN: phase_fin(ks.sd, ks.c, tau, ks.ps, part_out); break;
-        default: break;
-      }
-      __syncthreads();
-      if (tau == 0) {
-        cta_store(ks.sd.st + (par ^ 1), &ks.N);
-        if (!ks.N.active) cta_store(ks.sd.result, &ks.N);
-        if (threadIdx.x == 0) a.active[(par ^ 1) * a.n + s] = ks.N.active;
-      }
-      __syncthreads();
     }
-    if (a.trace && threadIdx.x == 0) tr[2] = globaltimer();
+    if (a.trace && threadIdx.x == 0) tr2 = globaltimer();
     if (threadIdx.x == 0 && a.diag) a.diag[blockIdx.x * 4 + 2] = 2;
     ++nbar;
     const bool ok = grid_barrier(&a.ctl->counter, nbar * gridDim.x, &a.ctl->err, &ks.bail);
     if (a.trace && threadIdx.x == 0 && it < a.trace_rounds) {
       TraceEnt e;
-      e.t0 = tr[0];
-      e.t1 = tr[1];
-      e.t2 = tr[2];
+      e.t0 = tr0;
+      e.t1 = tr1;
+      e.t2 = tr2;
       e.t3 = globaltimer();
       e.s0 = ks.ps.sub[0];
       e.s1 = ks.ps.sub[1];

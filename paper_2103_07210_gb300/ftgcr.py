@@ -20,7 +20,8 @@ _CSRC = os.path.join(_HERE, "csrc")
 _INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libftgcr.so")
-SOURCES = ["ftgcr.cu", "ftgcr_k4.cu", "ftgcr_k8.cu", "ftgcr_k16.cu", "ftgcr_server.cu"]
+SOURCES = ["ftgcr.cu", "ftgcr_k4.cu", "ftgcr_k8.cu", "ftgcr_k16.cu", "ftgcr_k4s.cu", "ftgcr_k8s.cu", "ftgcr_k16s.cu",
+           "ftgcr_server.cu"]
 HEADERS = ["ftgcr_device.cuh", "ftgcr_phases.cuh", "ftgcr_instances.h", "ftgcr_serve.h"]
 # --fmad=false: device multiply-adds are fused only where the code says fma();
 # -ffp-contract=off: the same for the host-side geometry (GCC contracts by
@@ -32,7 +33,7 @@ FP64, MIXED = 0, 1
 PRECOND = {"line": 0, "jacobi": 1, "identity": 2}
 VEC = {"x": 0, "r": 1, "p": 2, "ap": 3, "e": 4}
 MAX_FAULTS, MAX_K, MAX_DETECT, MAX_LOSSES = 64, 16, 16, 16
-FLAG_UNPROTECTED = 1
+FLAG_UNPROTECTED, FLAG_SPLIT_ROUNDS, FLAG_FUSED_ROUNDS = 1, 2, 4
 
 OK, NOT_CONVERGED, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BUDGET, ERR_STATE = 0, 1, -1, -2, -3, -4, -5, -6
 PENDING = 2
@@ -81,7 +82,8 @@ class Stats(ctypes.Structure):
                 ("detect_step", ctypes.c_int64 * MAX_DETECT), ("detect_ratio", ctypes.c_double * MAX_DETECT),
                 ("res0", ctypes.c_double), ("res_final_rec", ctypes.c_double), ("res_final_true", ctypes.c_double),
                 ("norm_R", ctypes.c_double), ("bytes_resident", ctypes.c_int64), ("bytes_backup", ctypes.c_int64),
-                ("tiles", ctypes.c_int32), ("status", ctypes.c_int32), ("loss_events", ctypes.c_int64)]
+                ("tiles", ctypes.c_int32), ("status", ctypes.c_int32), ("loss_events", ctypes.c_int64),
+                ("split_rounds", ctypes.c_int32)]
 
 
 class ServerInfo(ctypes.Structure):
@@ -215,11 +217,15 @@ def _plan(faults, losses=()):
     return plan, (arr, larr)
 
 
-def _grid(nlon, nlat, mu, precision, precond, max_steps, tiles, inner_tol, max_outer, protect=True):
+ROUNDS = {"auto": 0, "split": FLAG_SPLIT_ROUNDS, "fused": FLAG_FUSED_ROUNDS}
+
+
+def _grid(nlon, nlat, mu, precision, precond, max_steps, tiles, inner_tol, max_outer, protect=True, rounds="auto"):
     prec = {"fp64": FP64, "mixed": MIXED}.get(precision, precision)
     pc = PRECOND.get(precond, precond)
+    flags = (0 if protect else FLAG_UNPROTECTED) | ROUNDS[rounds]
     return Grid(int(nlon), int(nlat), float(mu), int(prec), int(pc), int(max_steps), int(tiles), float(inner_tol),
-                int(max_outer), 0 if protect else FLAG_UNPROTECTED)
+                int(max_outer), flags)
 
 
 def footprint(nlon, nlat, k=4, precision="fp64", precond="line", tiles=0) -> int:
@@ -231,14 +237,15 @@ class Solver:
     """One FT-GCR(k) problem resident on the GPU (ftgcr_create)."""
 
     def __init__(self, D, mu, k=4, tol=1e-10, precision="fp64", precond="line", max_steps=0, tiles=0,
-                 inner_tol=0.0, max_outer=0, protect=True):
+                 inner_tol=0.0, max_outer=0, protect=True, rounds="auto"):
         """protect=False: plain GCR(k), the paper's unprotected baseline (no
-        fault test, no restore)."""
+        fault test, no restore).  rounds: "auto", "split" or "fused"
+        (FTGCR_FLAG_SPLIT_ROUNDS / FTGCR_FLAG_FUSED_ROUNDS)."""
         L = lib()
         nlat, nlon = D.shape
         self.nlon, self.nlat, self.k, self.tol = int(nlon), int(nlat), int(k), float(tol)
         self.precision = precision
-        g = _grid(nlon, nlat, mu, precision, precond, max_steps, tiles, inner_tol, max_outer, protect)
+        g = _grid(nlon, nlat, mu, precision, precond, max_steps, tiles, inner_tol, max_outer, protect, rounds)
         dp, keep = _ptr(D)
         c = Coeffs(dp, 0)
         h = ctypes.c_void_p()
@@ -297,7 +304,8 @@ class Solver:
                     detect_steps=[s.detect_step[i] for i in range(n)],
                     detect_ratio=[s.detect_ratio[i] for i in range(n)], res0=s.res0, res_final_rec=s.res_final_rec,
                     res_final_true=s.res_final_true, norm_R=s.norm_R, bytes_resident=s.bytes_resident,
-                    bytes_backup=s.bytes_backup, tiles=s.tiles, status=s.status, loss_events=s.loss_events)
+                    bytes_backup=s.bytes_backup, tiles=s.tiles, status=s.status, loss_events=s.loss_events,
+                    split_rounds=bool(s.split_rounds))
 
     def apply_operator(self, inp, out, stream=None):
         ip, ik = _ptr(inp)
@@ -329,7 +337,7 @@ def _stats_dict(s: Stats) -> dict:
                 detect_steps=[s.detect_step[i] for i in range(n)], detect_ratio=[s.detect_ratio[i] for i in range(n)],
                 res0=s.res0, res_final_rec=s.res_final_rec, res_final_true=s.res_final_true, norm_R=s.norm_R,
                 bytes_resident=s.bytes_resident, bytes_backup=s.bytes_backup, tiles=s.tiles, status=s.status,
-                loss_events=s.loss_events)
+                loss_events=s.loss_events, split_rounds=bool(s.split_rounds))
 
 
 def solve_noalloc(D, mu, rhs, x, k=4, tol=1e-10, max_steps=0, tiles=0, stream=None):
@@ -392,11 +400,11 @@ class Server:
         self._keep = {}
 
     def submit(self, D, mu, rhs, x, k=4, tol=1e-10, precision="fp64", precond="line", faults=(), max_steps=0,
-               tiles=0, inner_tol=0.0, max_outer=0, losses=(), protect=True, coeff_key=0) -> int:
+               tiles=0, inner_tol=0.0, max_outer=0, losses=(), protect=True, coeff_key=0, rounds="auto") -> int:
         """coeff_key: 0, or an identity of D's contents; the same (D, key) pair
         lets a pooled handle already set up from it skip the set-up."""
         nlat, nlon = D.shape
-        g = _grid(nlon, nlat, mu, precision, precond, max_steps, tiles, inner_tol, max_outer, protect)
+        g = _grid(nlon, nlat, mu, precision, precond, max_steps, tiles, inner_tol, max_outer, protect, rounds)
         dp, dk = _ptr(D)
         rp, rk = _ptr(rhs)
         xp, xk = _ptr(x)

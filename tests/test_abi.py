@@ -68,3 +68,21 @@ def test_server_refuses_bad_arguments_and_a_missing_gpu_without_crashing():
     if not torch.cuda.is_available():
         assert L.ftgcr_server_create(0, 4, 8, ctypes.byref(srv)) == ftgcr.ERR_CUDA
         assert srv.value is None
+
+
+def test_round_layout_flags_are_validated_before_any_device_call():
+    import numpy as np
+
+    L = ftgcr.lib()
+    D = np.ones((8, 16))
+    h = ctypes.c_void_p()
+    c = ftgcr.Coeffs(D.ctypes.data, 0)
+    bad = [ftgcr._grid(16, 8, 1.0, "mixed", "line", 0, 0, 0.0, 0, rounds="split"),
+           ftgcr._grid(16, 8, 1.0, "fp64", "line", 0, 0, 0.0, 0, rounds="split"),  # FP64 has no split rounds
+           ftgcr._grid(16, 8, 1.0, "mixed", "jacobi", 0, 0, 0.0, 0, rounds="split")]
+    bad[0].flags |= ftgcr.FLAG_FUSED_ROUNDS  # both layouts at once
+    for g in bad:
+        assert L.ftgcr_create(ctypes.byref(g), ctypes.byref(c), 4, 1e-10, ctypes.byref(h)) == ftgcr.ERR_ARG
+    unknown = ftgcr._grid(16, 8, 1.0, "mixed", "line", 0, 0, 0.0, 0)
+    unknown.flags = 8
+    assert L.ftgcr_create(ctypes.byref(unknown), ctypes.byref(c), 4, 1e-10, ctypes.byref(h)) == ftgcr.ERR_ARG
