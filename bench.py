@@ -44,9 +44,9 @@ def algorithmic_bytes(steps: int, outer: int, k: int = K, s: int = 4, N: int = N
 
 # DRAM traffic per launch of the persistent kernel from one ncu capture, valid
 # only for the kernel sources it was taken on (sha256 of the CUDA sources).
-NCU_TRAFFIC = {"sources_sha256": "a637a8e46403d780fbc8290d54485fe4f219f288fa130104ec7d96dee3caf899",
-               "bytes_per_launch": 27715840 + 7970048,  # mixed 1024x512 (read + write)
-               "large": {"2048x1024": 2717294592 + 1348806144, "4096x2048": 11590680832 + 5096615680}}
+NCU_TRAFFIC = {"sources_sha256": "138d404a238b9ab040dfe2942149cf3c59072699e4871352f65ddcdf12672cff",
+               "bytes_per_launch": 27844864 + 8030976,  # mixed 1024x512 (read + write)
+               "large": {"2048x1024": 2706766336 + 1349251840, "4096x2048": 15110482432 + 5188121344}}
 
 
 def sources_hash() -> str:
