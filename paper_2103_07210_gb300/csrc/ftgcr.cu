@@ -142,6 +142,243 @@ __global__ void k_line_factor(int nlon, int nlat, int C, int precond, const doub
   }
 }
 
+// The same factorisation as k_line_factor, split into its three dependent
+// chains and the elementwise work between them.  The chains run one lane per
+// latitude row, 32 rows to a warp, because GB300's FP64 unit costs the same
+// per warp instruction for 1 or 32 active lanes.  Each lane loads a block of
+// inputs ahead while it steps through the current one.  The off-chain work
+// runs one thread per element: the diagonal, the reciprocal pivots, u, the
+// products of the backward substitution and the FP32 layout.  Every value is
+// formed by the same operations in the same order as in k_line_factor and the
+// CPU oracle, so the factors are bitwise the same.
+constexpr int kLfBlock = 8;  // inputs loaded ahead per lane
+
+// d_i of every element (the diagonal of the row systems).
+__global__ void k_lf_diag(int nlon, int nlat, const double* __restrict__ Tx, const double* __restrict__ Ty,
+                          const double* __restrict__ muA, double* dg) {
+  const long long N = (long long)nlon * nlat;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N; g += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(g / nlon), i = (int)(g - (long long)j * nlon);
+    double s = 0.0;
+    if (j < nlat - 1) s = s + Ty[g];
+    if (j > 0) s = s + Ty[g - nlon];
+    s = s + muA[j];
+    dg[g] = Tx[g] + Tx[(long long)j * nlon + (i + nlon - 1) % nlon] + s;
+  }
+}
+
+// Chain 1: w_0 = d_0, l_i = -Tx_{i-1} / w_{i-1}, w_i = d_i - l_i (-Tx_{i-1}),
+// i < m; l and the pivots w (not yet inverted) stored.
+__global__ void k_lf_chain_lw(int nlon, int nlat, const double* __restrict__ Tx, const double* __restrict__ dg,
+                              double* __restrict__ l, double* __restrict__ wout) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nlat) return;
+  const int m = nlon - 1;
+  const long long rb = (long long)j * nlon;
+  const double* tx = Tx + rb;
+  const double* d = dg + rb;
+  double w = d[0];
+  wout[rb] = w;
+  l[rb] = 0.0;
+  double ta[kLfBlock], da[kLfBlock], tb[kLfBlock], db[kLfBlock];
+  auto load = [&](int i0, double* t, double* dd) {
+#pragma unroll
+    for (int q = 0; q < kLfBlock; ++q)
+      if (i0 + q < m) {
+        t[q] = tx[i0 + q - 1];
+        dd[q] = d[i0 + q];
+      }
+  };
+  auto step = [&](int i0, const double* t, const double* dd) {
+#pragma unroll
+    for (int q = 0; q < kLfBlock; ++q)
+      if (i0 + q < m) {
+        const double li = -t[q] / w;
+        w = dd[q] - li * -t[q];
+        l[rb + i0 + q] = li;
+        wout[rb + i0 + q] = w;
+      }
+  };
+  load(1, ta, da);
+  for (int i0 = 1; i0 < m; i0 += 2 * kLfBlock) {
+    load(i0 + kLfBlock, tb, db);
+    step(i0, ta, da);
+    load(i0 + 2 * kLfBlock, ta, da);
+    step(i0 + kLfBlock, tb, db);
+  }
+}
+
+// winv_i = 1 / w_i, u_i = -Tx_i winv_i (u_{m-1} = 0), the padding l_m = winv_m
+// = u_m = 0, and the bordering right-hand side c into z:
+// c = (-Tx_{n-1}, 0, ..., 0, 0 + -Tx_{n-2}), z_m = 0.
+__global__ void k_lf_recip(int nlon, int nlat, const double* __restrict__ Tx, double* l, double* winv, double* u,
+                           double* z) {
+  const long long N = (long long)nlon * nlat;
+  const int m = nlon - 1;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N; g += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(g / nlon), i = (int)(g - (long long)j * nlon);
+    const long long rb = (long long)j * nlon;
+    if (i < m) {
+      const double wi = 1.0 / winv[g];
+      winv[g] = wi;
+      u[g] = (i < m - 1) ? -Tx[g] * wi : 0.0;
+      double c = 0.0;
+      if (i == 0) c = -Tx[rb + nlon - 1];
+      if (i == m - 1) c = c + -Tx[rb + nlon - 2];
+      z[g] = c;
+    } else {
+      winv[g] = 0.0;
+      u[g] = 0.0;
+      l[g] = 0.0;
+      z[g] = 0.0;
+    }
+  }
+}
+
+// Chain 2: forward substitution of c, z_i = fma(-l_i, z_{i-1}, z_i), i < m.
+__global__ void k_lf_chain_fwd(int nlon, int nlat, const double* __restrict__ l, double* __restrict__ z) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nlat) return;
+  const int m = nlon - 1;
+  const long long rb = (long long)j * nlon;
+  double y = z[rb];
+  double la[kLfBlock], ca[kLfBlock], lb[kLfBlock], cb[kLfBlock];
+  auto load = [&](int i0, double* ll, double* cc) {
+#pragma unroll
+    for (int q = 0; q < kLfBlock; ++q)
+      if (i0 + q < m) {
+        ll[q] = l[rb + i0 + q];
+        cc[q] = z[rb + i0 + q];
+      }
+  };
+  auto step = [&](int i0, const double* ll, const double* cc) {
+#pragma unroll
+    for (int q = 0; q < kLfBlock; ++q)
+      if (i0 + q < m) {
+        y = fma(-ll[q], y, cc[q]);
+        z[rb + i0 + q] = y;
+      }
+  };
+  load(1, la, ca);
+  for (int i0 = 1; i0 < m; i0 += 2 * kLfBlock) {
+    load(i0 + kLfBlock, lb, cb);
+    step(i0, la, ca);
+    load(i0 + 2 * kLfBlock, la, ca);
+    step(i0 + kLfBlock, lb, cb);
+  }
+}
+
+// The backward step's products z_i winv_i, i < m (z_{m-1} winv_{m-1} is also
+// the first value of the backward substitution).
+__global__ void k_lf_products(int nlon, int nlat, const double* __restrict__ winv, double* z) {
+  const long long N = (long long)nlon * nlat;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N; g += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(g % nlon);
+    if (i < nlon - 1) z[g] = z[g] * winv[g];
+  }
+}
+
+// Chain 3: backward substitution z_i = fma(-u_i, z_{i+1}, z_i winv_i),
+// i = m-2 .. 0, then delta = d_{n-1} + Tx_{n-1} z_0 + Tx_{n-2} z_{m-1} and the
+// row constants (FP64: delta; FP32: 1/delta, Tx_{n-1}/delta, Tx_{n-2}/delta).
+__global__ void k_lf_chain_bwd(int nlon, int nlat, const double* __restrict__ Tx, const double* __restrict__ Ty,
+                               const double* __restrict__ muA, const double* __restrict__ u, double* __restrict__ z,
+                               double* lrow64, float* lrow32) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nlat) return;
+  const int n = nlon, m = n - 1;
+  const long long rb = (long long)j * n;
+  double y = z[rb + m - 1];
+  double ua[kLfBlock], pa[kLfBlock], ub[kLfBlock], pb[kLfBlock];
+  auto load = [&](int i1, double* uu, double* pp) {  // elements i1, i1 - 1, ...
+#pragma unroll
+    for (int q = 0; q < kLfBlock; ++q)
+      if (i1 - q >= 0) {
+        uu[q] = u[rb + i1 - q];
+        pp[q] = z[rb + i1 - q];
+      }
+  };
+  auto step = [&](int i1, const double* uu, const double* pp) {
+#pragma unroll
+    for (int q = 0; q < kLfBlock; ++q)
+      if (i1 - q >= 0) {
+        y = fma(-uu[q], y, pp[q]);
+        z[rb + i1 - q] = y;
+      }
+  };
+  load(m - 2, ua, pa);
+  for (int i1 = m - 2; i1 >= 0; i1 -= 2 * kLfBlock) {
+    load(i1 - kLfBlock, ub, pb);
+    step(i1, ua, pa);
+    load(i1 - 2 * kLfBlock, ua, pa);
+    step(i1 - kLfBlock, ub, pb);
+  }
+  const double* tx = Tx + rb;
+  double s = 0.0;
+  if (j < nlat - 1) s = s + Ty[rb + n - 1];
+  if (j > 0) s = s + Ty[rb + n - 1 - n];
+  s = s + muA[j];
+  const double d_last = tx[n - 1] + tx[n - 2] + s;
+  const double delta = d_last + tx[n - 1] * z[rb] + tx[n - 2] * z[rb + m - 1];
+  lrow64[(long long)j * 4 + 0] = delta;
+  lrow64[(long long)j * 4 + 1] = 0.0;
+  lrow64[(long long)j * 4 + 2] = 0.0;
+  lrow64[(long long)j * 4 + 3] = 0.0;
+  if (lrow32) {
+    const double dinv = 1.0 / delta;
+    lrow32[(long long)j * 4 + 0] = (float)dinv;
+    lrow32[(long long)j * 4 + 1] = (float)(tx[n - 1] * dinv);
+    lrow32[(long long)j * 4 + 2] = (float)(tx[n - 2] * dinv);
+    lrow32[(long long)j * 4 + 3] = 0.f;
+  }
+}
+
+// FP32 constants in the per-lane chunk layout: position k*32 + lane of row j
+// holds element i = lane*C + k (c = -u, winv, z; zero past the block).
+__global__ void k_lf_chunks(int nlon, int nlat, int C, const double* __restrict__ u, const double* __restrict__ winv,
+                            const double* __restrict__ z, float* lc32, float* lw32, float* lz32) {
+  const long long per = 32LL * C, total = per * nlat;
+  const int m = nlon - 1;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total; q += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(q / per);
+    const int pos = (int)(q - (long long)j * per), k = pos >> 5, lane = pos & 31;
+    const int i = lane * C + k;
+    const bool in = i < m;
+    const long long g = (long long)j * nlon + i;
+    lc32[q] = in ? (float)(-u[g]) : 0.f;
+    lw32[q] = in ? (float)winv[g] : 0.f;
+    lz32[q] = in ? (float)z[g] : 0.f;
+  }
+}
+
+// The line preconditioner's factorisation (Jacobi: its diagonal), enqueued
+// on st.  FP64 outputs l, winv, u, z (z doubles as scratch for the diagonal)
+// and the row constants; FP32 chunk-layout constants when lc32 is given.
+int launch_line_factor(int nlon, int nlat, int C, int precond, const double* Tx, const double* Ty,
+                       const double* muA, double* l64, double* w64, double* u64, double* z64, double* r64,
+                       float* lc32, float* lw32, float* lz32, float* lrow32, cudaStream_t st) {
+  if (precond != PC_LINE) {
+    k_line_factor<<<(nlat + 63) / 64, 64, 0, st>>>(nlon, nlat, C, precond, Tx, Ty, muA, l64, w64, u64, z64, r64, lc32,
+                                                   lw32, lz32, lrow32);
+    return cudaGetLastError() == cudaSuccess ? FTGCR_OK : FTGCR_ERR_CUDA;
+  }
+  const long long N = (long long)nlon * nlat;
+  const int eb = 256, eg = (int)std::min<long long>((N + eb - 1) / eb, 8192);
+  const int rg = (nlat + 31) / 32;  // one lane per row, one warp per block
+  k_lf_diag<<<eg, eb, 0, st>>>(nlon, nlat, Tx, Ty, muA, z64);
+  k_lf_chain_lw<<<rg, 32, 0, st>>>(nlon, nlat, Tx, z64, l64, w64);
+  k_lf_recip<<<eg, eb, 0, st>>>(nlon, nlat, Tx, l64, w64, u64, z64);
+  k_lf_chain_fwd<<<rg, 32, 0, st>>>(nlon, nlat, l64, z64);
+  k_lf_products<<<eg, eb, 0, st>>>(nlon, nlat, w64, z64);
+  k_lf_chain_bwd<<<rg, 32, 0, st>>>(nlon, nlat, Tx, Ty, muA, u64, z64, r64, lrow32);
+  if (lc32) {
+    const long long nc = 32LL * C * nlat;
+    k_lf_chunks<<<(int)std::min<long long>((nc + eb - 1) / eb, 8192), eb, 0, st>>>(nlon, nlat, C, u64, w64, z64, lc32,
+                                                                                 lw32, lz32);
+  }
+  return cudaGetLastError() == cudaSuccess ? FTGCR_OK : FTGCR_ERR_CUDA;
+}
+
 // out = L(in), FP64, one thread per element.
 __global__ void k_apply_operator(const double* in, double* out, const double* Tx, const double* Ty, const double* muA,
                                  int nlon, int nlat) {
@@ -561,11 +798,10 @@ int setup_coefficients(ftgcr_handle* h, const SolveDev<T>& sd, const double* Dd,
     z64 = tmp + 3 * h->N;
     r64 = tmp + 4 * h->N;
   }
-  k_line_factor<<<(h->nlat + 63) / 64, 64, 0, st>>>(h->nlon, h->nlat, h->C, h->precond, h->Tx64, h->Ty64, h->muA64,
-                                                    l64, w64, u64, z64, r64, mixed ? (float*)sd.lc : nullptr,
-                                                    mixed ? (float*)sd.lw : nullptr, mixed ? (float*)sd.lz : nullptr,
-                                                    mixed ? (float*)sd.lrow : nullptr);
-  CK(cudaGetLastError());
+  const int frc = launch_line_factor(h->nlon, h->nlat, h->C, h->precond, h->Tx64, h->Ty64, h->muA64, l64, w64, u64,
+                                     z64, r64, mixed ? (float*)sd.lc : nullptr, mixed ? (float*)sd.lw : nullptr,
+                                     mixed ? (float*)sd.lz : nullptr, mixed ? (float*)sd.lrow : nullptr, st);
+  if (frc) return frc;
   CK(cudaFreeAsync(scratch, st));
   return FTGCR_OK;
 }
@@ -1386,10 +1622,9 @@ extern "C" int ftgcr_solve_noalloc(const ftgcr_grid* grid, const double* D, int3
   k_face_coeffs<<<256, 256, 0, st>>>(h.nlon, h.nlat, D, dgeo, dgeo + h.nlat, dgeo + 2 * h.nlat, h.mu, h.Tx64, h.Ty64,
                                      h.muA64, nullptr, nullptr, nullptr);
   CK(cudaGetLastError());
-  k_line_factor<<<(h.nlat + 63) / 64, 64, 0, st>>>(h.nlon, h.nlat, h.C, h.precond, h.Tx64, h.Ty64, h.muA64,
-                                                   (double*)sd.lc, (double*)sd.lw, (double*)sd.lu, (double*)sd.lz,
-                                                   (double*)sd.lrow, nullptr, nullptr, nullptr, nullptr);
-  CK(cudaGetLastError());
+  rc = launch_line_factor(h.nlon, h.nlat, h.C, h.precond, h.Tx64, h.Ty64, h.muA64, (double*)sd.lc, (double*)sd.lw,
+                          (double*)sd.lu, (double*)sd.lz, (double*)sd.lrow, nullptr, nullptr, nullptr, nullptr, st);
+  if (rc) return rc;
   void* sp = h.sdev;
   CK(cudaMemcpyAsync(h.sdev, &sd, sizeof sd, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(h.sdev_arr, &sp, sizeof(void*), cudaMemcpyHostToDevice, st));
