@@ -273,56 +273,103 @@ def bench_ksweep(torch, ftgcr, dev, flush, ks=(1, 2, 4, 5, 8), reps=5):
 def bench_batch(torch, ftgcr, dev, n=128, seed=42, reps=3):
     """128 independent mixed-precision solves of sizes U{128x64, 256x128,
     512x256, 1024x512} (hills: centre, height and width drawn per solve) in
-    ONE persistent launch, against the same solves launched one by one."""
+    ONE persistent launch, against the same solves launched one by one; the
+    launch also captured into a CUDA graph and replayed.  Row bands and round
+    layout per size from the autotuner (ftgcr_tune, timed for as many solves
+    of that size as the batch holds), beside the layout ftgcr_create picks by
+    itself."""
+    import collections
+
     sizes = inputs.batch_sizes(seed, n)
-    solvers, Rs, xs = [], [], []
-    for q, (nlon, nlat) in enumerate(sizes):
-        p = inputs.hill_problem(nlon, nlat, **inputs.random_hill(seed * 1000 + q))
-        solvers.append(ftgcr.Solver(p.D, p.mu, k=K, tol=TOL, precision="mixed"))
-        Rs.append(torch.from_numpy(p.R).to(dev))
-        xs.append(torch.zeros_like(Rs[-1]))
+    probs = [inputs.hill_problem(nlon, nlat, **inputs.random_hill(seed * 1000 + q))
+             for q, (nlon, nlat) in enumerate(sizes)]
+    Rs = [torch.from_numpy(p.R).to(dev) for p in probs]
     stream = torch.cuda.current_stream()
-    alone_ms, alone_x = [], []
-    for s, R, x in zip(solvers, Rs, xs):
-        s.solve_async(R, x, stream=stream)  # warm
-        x.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        s.solve_async(R, x, stream=stream)
-        b.record(stream)
-        torch.cuda.synchronize()
-        alone_ms.append(a.elapsed_time(b))
-        alone_x.append(x.clone())
-    times = []
-    for rep in range(reps + 1):
-        for x in xs:
+    tuned = {}
+    for (nlon, nlat), cnt in sorted(collections.Counter(sizes).items()):
+        p0 = probs[sizes.index((nlon, nlat))]
+        t = ftgcr.tune(p0.D, p0.mu, k=K, tol=TOL, precision="mixed", concurrency=min(cnt, 256))
+        tuned[(nlon, nlat)] = t
+
+    def run(layout):
+        solvers = []
+        for (nlon, nlat), p in zip(sizes, probs):
+            t = layout.get((nlon, nlat)) if layout else None
+            solvers.append(ftgcr.Solver(p.D, p.mu, k=K, tol=TOL, precision="mixed", tiles=t["tiles"] if t else 0,
+                                        rounds=t["rounds"] if t else "auto"))
+        xs = [torch.zeros_like(R) for R in Rs]
+        alone_ms, alone_x = [], []
+        for s, R, x in zip(solvers, Rs, xs):
+            s.solve_async(R, x, stream=stream)  # warm
             x.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        ftgcr.solve_batch(solvers, Rs, xs, stream=stream)
-        b.record(stream)
-        torch.cuda.synchronize()
-        if rep:
-            times.append(a.elapsed_time(b))
-    same = all(bool(torch.equal(x, y)) for x, y in zip(xs, alone_x))
-    steps = sum(s.stats()["steps"] for s in solvers)
-    for s in solvers:
-        s.close()
-    ms = float(np.median(times))
-    return {"solves": n, "sizes": "U{128x64,256x128,512x256,1024x512}", "seed": seed, "precision": "mixed",
-            "launch_ms": ms, "solves_per_s": n * 1e3 / ms, "iters_per_s": steps * 1e3 / ms,
-            "sequential_ms": float(np.sum(alone_ms)), "speedup_vs_sequential": float(np.sum(alone_ms)) / ms,
-            "bitwise_equal_to_alone": same}
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s.solve_async(R, x, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            alone_ms.append(a.elapsed_time(b))
+            alone_x.append(x.clone())
+        times = []
+        for rep in range(reps + 1):
+            for x in xs:
+                x.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ftgcr.solve_batch(solvers, Rs, xs, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if rep:
+                times.append(a.elapsed_time(b))
+        same = all(bool(torch.equal(x, y)) for x, y in zip(xs, alone_x))
+        steps = sum(s.stats()["steps"] for s in solvers)
+        # the same launch captured into a CUDA graph and replayed
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            ftgcr.solve_batch(solvers, Rs, xs, stream=torch.cuda.current_stream())
+        gtimes = []
+        for rep in range(reps + 1):
+            for x in xs:
+                x.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            g.replay()
+            b.record(stream)
+            torch.cuda.synchronize()
+            if rep:
+                gtimes.append(a.elapsed_time(b))
+        gsame = all(bool(torch.equal(x, y)) for x, y in zip(xs, alone_x))
+        del g
+        for s in solvers:
+            s.close()
+        ms = float(np.median(times))
+        return {"launch_ms": ms, "solves_per_s": n * 1e3 / ms, "iters_per_s": steps * 1e3 / ms,
+                "sequential_ms": float(np.sum(alone_ms)), "speedup_vs_sequential": float(np.sum(alone_ms)) / ms,
+                "bitwise_equal_to_alone": same, "graph_replay_ms": float(np.median(gtimes)),
+                "graph_bitwise_equal_to_alone": gsame}
+
+    default = run(None)
+    auto = run(tuned)
+    out = {"solves": n, "sizes": "U{128x64,256x128,512x256,1024x512}", "seed": seed, "precision": "mixed",
+           "tiles": "autotuned (ftgcr_tune per size, concurrency = solves of that size)"}
+    out.update(auto)
+    out["autotuner"] = {f"{a}x{b}": {"tiles": t["tiles"], "rounds": t["rounds"], "default_tiles": t["default_tiles"],
+                                     "tuned_ms": t["ms"], "default_ms": t["default_ms"], "candidates": t["candidates"]}
+                        for (a, b), t in tuned.items()}
+    out["default_tiles"] = {k: default[k] for k in ("launch_ms", "solves_per_s", "graph_replay_ms",
+                                                    "bitwise_equal_to_alone")}
+    return out
 
 
-def bench_serving(torch, ftgcr, dev, n_req=2000, load=0.8, seed=7, hills_per_size=4, n_cap=300):
+def bench_serving(torch, ftgcr, dev, n_req=2000, load=0.8, seed=7, hills_per_size=4, n_cap=300,
+                  sweep_loads=(0.5, 1.0, 1.2), n_sweep=400):
     """Open-loop serving: n_req requests with Poisson arrivals at `load` x the
     measured capacity; sizes U{256x128, 512x256, 1024x512, 2048x1024}, mixed
     precision, hills drawn per problem, 1% carrying one bit flip.  Right-hand
     side and solution in pinned host memory, coefficients resident on the
     device and identified by a key (a model's operator is fixed across its time
     steps, so pooled handles keep their set-up); latency = arrival -> solution
-    on the host."""
+    on the host.  Then shorter runs at other fractions of the capacity
+    (load_sweep)."""
     import threading
 
     sizes = [(256, 128), (512, 256), (1024, 512), (2048, 1024)]
@@ -380,50 +427,60 @@ def bench_serving(torch, ftgcr, dev, n_req=2000, load=0.8, seed=7, hills_per_siz
         cap = n_cap / (time.perf_counter() - t0)
         for _, x in xs0:
             give_x(x)
-        # open loop
-        arr = inputs.poisson_arrivals(seed, n_req, load * cap)
-        sample = set(range(0, n_req, max(1, n_req // 8)))  # solutions kept for the equality check
-        t_arr, xs, kept, lat = {}, {}, {}, []
-        lock = threading.Lock()
-        start = time.perf_counter()
+        def open_loop(ld, n, seed_arr, keep_sample):
+            arr = inputs.poisson_arrivals(seed_arr, n, ld * cap)
+            sample = set(range(0, n, max(1, n // 8))) if keep_sample else set()  # kept for the equality check
+            t_arr, xs, kept, lat = {}, {}, {}, []
+            lock = threading.Lock()
+            start = time.perf_counter()
 
-        def producer():
-            for i in range(n_req):
-                d = start + arr[i] - time.perf_counter()
-                if d > 0:
-                    time.sleep(d)
-                ta = time.perf_counter()
-                t, x = submit(srv, i)
-                with lock:
-                    t_arr[t] = ta
-                    xs[t] = (i, x)
+            def producer():
+                for i in range(n):
+                    d = start + arr[i] - time.perf_counter()
+                    if d > 0:
+                        time.sleep(d)
+                    ta = time.perf_counter()
+                    t, x = submit(srv, i)
+                    with lock:
+                        t_arr[t] = ta
+                        xs[t] = (i, x)
 
-        th = threading.Thread(target=producer)
-        th.start()
-        done, results = 0, {}
-        while done < n_req:
-            r = srv.next(timeout=30)
-            if r is None:
-                break
-            now = time.perf_counter()
-            t, st, ss = r
-            with lock:
-                ta = t_arr.get(t)
-            while ta is None:  # the producer has not recorded it yet
-                time.sleep(1e-5)
+            th = threading.Thread(target=producer)
+            th.start()
+            done, results = 0, {}
+            while done < n:
+                r = srv.next(timeout=30)
+                if r is None:
+                    break
+                now = time.perf_counter()
+                t, st, ss = r
                 with lock:
                     ta = t_arr.get(t)
-            lat.append(now - ta)
-            results[t] = (st, ss)
-            with lock:
-                i, x = xs.pop(t)
-            if i in sample:
-                kept[t] = (i, x.numpy().copy())
-            give_x(x)
-            done += 1
-        th.join()
-        wall = time.perf_counter() - start
+                while ta is None:  # the producer has not recorded it yet
+                    time.sleep(1e-5)
+                    with lock:
+                        ta = t_arr.get(t)
+                lat.append(now - ta)
+                results[t] = (st, ss)
+                with lock:
+                    i, x = xs.pop(t)
+                if i in sample:
+                    kept[t] = (i, x.numpy().copy())
+                give_x(x)
+                done += 1
+            th.join()
+            wall = time.perf_counter() - start
+            return results, kept, 1e3 * np.array(lat), wall
+
+        results, kept, lat_ms, wall = open_loop(load, n_req, seed, True)
         info = srv.info()
+        # latency against offered load: shorter runs at other fractions of capacity
+        sweep = []
+        for q, ld in enumerate(sweep_loads):
+            r2, _, l2, w2 = open_loop(ld, n_sweep, seed + 1 + q, False)
+            sweep.append({"load": ld, "requests": n_sweep, "offered_per_s": ld * cap, "achieved_solves_per_s": n_sweep / w2,
+                          "completed_ok": sum(1 for st, _ in r2.values() if st == 0),
+                          "p50_ms": float(np.percentile(l2, 50)), "p99_ms": float(np.percentile(l2, 99))})
     # a sample of served results against the same request solved alone
     same = True
     for t in sorted(kept):
@@ -435,7 +492,6 @@ def bench_serving(torch, ftgcr, dev, n_req=2000, load=0.8, seed=7, hills_per_siz
             s.solve(p.R, xa, faults=faults)
         same = same and np.array_equal(x, xa)
     ok = sum(1 for st, _ in results.values() if st == 0)
-    lat_ms = 1e3 * np.array(lat)
     return {"requests": n_req, "completed_ok": ok, "load": load, "capacity_solves_per_s": cap,
             "offered_per_s": load * cap, "achieved_solves_per_s": n_req / wall,
             "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
@@ -443,7 +499,7 @@ def bench_serving(torch, ftgcr, dev, n_req=2000, load=0.8, seed=7, hills_per_siz
             "faulty_requests": sum(1 for _, f in reqs[:n_req] if f), "epochs": info["epochs"],
             "handles": info["handles"], "sizes": "U{256x128,512x256,1024x512,2048x1024}", "precision": "mixed",
             "io": "rhs and x in pinned host memory, D resident with a coefficient key",
-            "bitwise_equal_to_alone_sample": same}
+            "bitwise_equal_to_alone_sample": same, "load_sweep": sweep}
 
 
 # ------------------------------------------------------------------ GPU arm

@@ -207,7 +207,11 @@ int ftgcr_stats(ftgcr_handle* h, ftgcr_stats_t* out);
 /* Solve n independent problems in ONE persistent launch (all handles of the
  * same precision).  Each solve uses its own handle's tiling, so its result is
  * bitwise the same as when it is solved alone.  rhs[i], x[i] device memory;
- * plans may be NULL.  Enqueues only; read each status with ftgcr_stats(). */
+ * plans may be NULL.  Enqueues only; read each status with ftgcr_stats().
+ * The launch's tables are stream-ordered allocations filled by kernels from
+ * their parameters, so the whole batch can be captured into a CUDA graph
+ * (after one uncaptured call with the same handles, which configures the
+ * kernel) and replayed. */
 int ftgcr_solve_batch(ftgcr_handle* const* hs, const double* const* rhs, double* const* x,
                       const ftgcr_fault_plan* const* plans, int32_t n, void* stream);
 
@@ -233,6 +237,39 @@ int64_t ftgcr_footprint(const ftgcr_grid* grid, int32_t k);
 
 void ftgcr_destroy(ftgcr_handle* h);
 const char* ftgcr_error_string(int status);
+
+/* Tile autotuner.  The paper has no counterpart (it runs one problem per
+ * process decomposition).  Row bands and round layout trade halo
+ * recomputation against parallelism, and the best trade depends on the grid,
+ * the precision and how many solves share a launch.  ftgcr_tune times, for
+ * `concurrency` identical solves of this shape in one persistent launch, a
+ * set of band counts around the one ftgcr_create picks by itself, each in
+ * both round layouts where the mixed path's line preconditioner has two.  It
+ * returns the fastest.  Every candidate is a real handle; one whose rows do
+ * not fit on chip, or in memory, is skipped.  The problem timed is the
+ * caller's operator with a smooth manufactured right-hand side and x0 = 0:
+ * one warm launch, then the best of three.  Blocking; allocates (handles,
+ * scratch); results are cached per shape for the life of the process (a
+ * repeated call returns at once with cached = 1).
+ *  - grid: as for ftgcr_create, with tiles = 0 and neither round-layout flag
+ *    (the tuner chooses both); coeffs, k, tol as for ftgcr_create.
+ *  - concurrency: 1..FTGCR_TUNE_MAX_CONCURRENCY solves per launch.
+ *  - Use the result by setting grid.tiles = out->tiles and OR-ing out->flags
+ *    into grid.flags.
+ *  - Errors: FTGCR_ERR_ARG (arguments, or no candidate fits), FTGCR_ERR_CUDA. */
+typedef struct {
+  int32_t tiles;          /* chosen row bands */
+  int32_t flags;          /* round layout to OR into ftgcr_grid.flags: 0 (FP64, other
+                             preconditioners), FTGCR_FLAG_FUSED_ROUNDS or FTGCR_FLAG_SPLIT_ROUNDS */
+  double ms;              /* launch time of the chosen layout, ms */
+  int32_t default_tiles;  /* the band count ftgcr_create picks by itself */
+  double default_ms;      /* its launch time, ms */
+  int32_t candidates;     /* layouts timed */
+  int32_t cached;         /* 1: returned from the process cache */
+} ftgcr_tuning_t;
+#define FTGCR_TUNE_MAX_CONCURRENCY 256
+int ftgcr_tune(const ftgcr_grid* grid, const ftgcr_coeffs* coeffs, int32_t k, double tol, int32_t concurrency,
+               ftgcr_tuning_t* out);
 
 /* No-allocation FP64 solve.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory when they solve

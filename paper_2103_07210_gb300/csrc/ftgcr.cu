@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <type_traits>
 #include <vector>
@@ -420,6 +421,23 @@ struct BeginArgs {
   LossEv losses[kMaxLosses];
 };
 
+// A batch launch's solve table (descriptor pointers and tile counts), filled
+// from kernel parameters rather than a copy from host memory, so that a
+// batch captured into a CUDA graph holds its own copy of the table.
+constexpr int kTableChunk = 256;
+struct BatchTable {
+  void* sdev[kTableChunk];
+  int nt[kTableChunk];
+  int n, off;
+};
+__global__ void k_fill_table(BatchTable t, void** d_solves, int* d_nt) {
+  const int i = threadIdx.x;
+  if (i < t.n) {
+    d_solves[t.off + i] = t.sdev[i];
+    d_nt[t.off + i] = t.nt[i];
+  }
+}
+
 template <typename T>
 __global__ void k_begin_solve(SolveDev<T>* sd, BeginArgs b, int* active, int n_active, int slot, int par,
                               LaunchCtl* ctl) {
@@ -649,9 +667,22 @@ int configure_kernel(int kb, int split, size_t smem) {
   return FTGCR_OK;
 }
 
+// Resident CTAs per SM of a kernel instance at a dynamic shared memory size,
+// cached (the same answer every time; a batch launch being captured into a
+// CUDA graph then makes no query).
 template <typename T>
 int occupancy(int kb, int split, size_t smem, int* occ) {
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kernel_ptr<T>(kb, split), kThreads, smem));
+  static std::mutex mu;
+  static std::map<std::pair<const void*, size_t>, int> known;
+  const void* f = kernel_ptr<T>(kb, split);
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = known.find({f, smem});
+  if (it != known.end()) {
+    *occ = it->second;
+    return FTGCR_OK;
+  }
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, f, kThreads, smem));
+  known[{f, smem}] = *occ;
   return FTGCR_OK;
 }
 
@@ -988,7 +1019,8 @@ int solve_async_impl(ftgcr_handle* h, const double* R, const double* x0, double*
 // of a lone solve; the launch only interleaves the solves' tiles over the
 // CTAs.  The launch's own arrays (solve pointers, tile counts, active flags,
 // control block, progress record) are stream-ordered allocations freed after
-// the launch.
+// the launch, and the solve table is written by a kernel from its parameters
+// (no copy from host memory), so a batch captures into a CUDA graph.
 template <typename T>
 int solve_batch_impl(ftgcr_handle* const* hs, const double* const* rhs, double* const* x,
                      const ftgcr_fault_plan* const* plans, int n, cudaStream_t st) {
@@ -1022,14 +1054,17 @@ int solve_batch_impl(ftgcr_handle* const* hs, const double* const* rhs, double* 
   int* d_act = (int*)(buf + b_solves + b_nt);
   LaunchCtl* d_ctl = (LaunchCtl*)(buf + b_solves + b_nt + b_act);
   int* d_diag = (int*)(buf + b_solves + b_nt + b_act + b_ctl);
-  std::vector<void*> hp(n);
-  std::vector<int> hnt(n);
-  for (int i = 0; i < n; ++i) {
-    hp[i] = hs[i]->sdev;
-    hnt[i] = hs[i]->nt;
+  for (int off = 0; off < n; off += kTableChunk) {
+    BatchTable tb;
+    tb.n = std::min(kTableChunk, n - off);
+    tb.off = off;
+    for (int i = 0; i < tb.n; ++i) {
+      tb.sdev[i] = hs[off + i]->sdev;
+      tb.nt[i] = hs[off + i]->nt;
+    }
+    k_fill_table<<<1, kTableChunk, 0, st>>>(tb, d_solves, d_nt);
+    CK(cudaGetLastError());
   }
-  CK(cudaMemcpyAsync(d_solves, hp.data(), sizeof(void*) * n, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(d_nt, hnt.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(d_act, 0, sizeof(int) * 2 * n, st));
   for (int i = 0; i < n; ++i) {
     const BeginArgs b = begin_args(hs[i], rhs[i], x[i], x[i], plans ? plans[i] : nullptr);

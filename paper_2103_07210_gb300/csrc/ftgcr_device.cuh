@@ -386,6 +386,18 @@ __device__ __forceinline__ T stencil5(T v, T ve, T vw, T vn, T vs, T txc, T txw,
   return s - muA * v;
 }
 
+// The same operator with fused multiply-adds (9 FP64 operations instead of
+// 13): the mixed path's FP64 refinement residual, whose value needs FP64
+// accuracy but not the oracle's operation order.
+__device__ __forceinline__ double stencil5_fma(double v, double ve, double vw, double vn, double vs, double txc,
+                                               double txw, double tyc, double tys, double muA, bool hasN, bool hasS) {
+  double s = -muA * v;
+  if (hasS) s = fma(tys, vs - v, s);
+  if (hasN) s = fma(tyc, vn - v, s);
+  s = fma(txw, vw - v, s);
+  return fma(txc, ve - v, s);
+}
+
 // Shared-memory row layout: element i of a row lives at i + i/32 (one pad
 // word per 32), which keeps both the coalesced sweeps and the per-lane
 // contiguous chunks of the line solve free of bank conflicts.

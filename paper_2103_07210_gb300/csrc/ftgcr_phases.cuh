@@ -1635,10 +1635,10 @@ __device__ __noinline__ void phase_out(const SolveDev<T>& sd, const Ctx<T>& c, i
       const int ie = (i + 1 == nlon) ? 0 : i + 1;
       const int iw = (i == 0) ? nlon - 1 : i - 1;
       const double v = row[sk(i)];
-      const double Lx = stencil5<double>(v, row[sk(ie)], row[sk(iw)], hasN ? row[stride + sk(i)] : 0.0,
-                                         hasS ? row[-stride + sk(i)] : 0.0, __ldg(sd.Tx64 + g),
-                                         __ldg(sd.Tx64 + base + iw), hasN ? __ldg(sd.Ty64 + g) : 0.0,
-                                         hasS ? __ldg(sd.Ty64 + g - nlon) : 0.0, __ldg(sd.muA64 + j), hasN, hasS);
+      const double Lx = stencil5_fma(v, row[sk(ie)], row[sk(iw)], hasN ? row[stride + sk(i)] : 0.0,
+                                     hasS ? row[-stride + sk(i)] : 0.0, __ldg(sd.Tx64 + g), __ldg(sd.Tx64 + base + iw),
+                                     hasN ? __ldg(sd.Ty64 + g) : 0.0, hasS ? __ldg(sd.Ty64 + g - nlon) : 0.0,
+                                     __ldg(sd.muA64 + j), hasN, hasS);
       const double Rv = ldcg(sd.R + g);
       const double ro = Rv - Lx;
       sd.Rin[g] = (T)ro;

@@ -21,7 +21,7 @@ _INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libftgcr.so")
 SOURCES = ["ftgcr.cu", "ftgcr_k4.cu", "ftgcr_k8.cu", "ftgcr_k16.cu", "ftgcr_k4s.cu", "ftgcr_k8s.cu", "ftgcr_k16s.cu",
-           "ftgcr_server.cu"]
+           "ftgcr_server.cu", "ftgcr_tune.cu"]
 HEADERS = ["ftgcr_device.cuh", "ftgcr_phases.cuh", "ftgcr_instances.h", "ftgcr_serve.h"]
 # --fmad=false: device multiply-adds are fused only where the code says fma();
 # -ffp-contract=off: the same for the host-side geometry (GCC contracts by
@@ -43,8 +43,9 @@ EXPORTS = ["ftgcr_create", "ftgcr_solve", "ftgcr_solve_async", "ftgcr_stats", "f
            "ftgcr_apply_operator", "ftgcr_apply_precond", "ftgcr_footprint", "ftgcr_destroy", "ftgcr_error_string",
            "ftgcr_solve_noalloc", "ftgcr_set_coeffs", "ftgcr_server_create", "ftgcr_server_submit",
            "ftgcr_server_poll", "ftgcr_server_wait", "ftgcr_server_next", "ftgcr_server_info",
-           "ftgcr_server_destroy"]
+           "ftgcr_server_destroy", "ftgcr_tune"]
 NOALLOC_MAX_POINTS, NOALLOC_MAX_K = 16384, 4
+TUNE_MAX_CONCURRENCY = 256
 
 _lock = threading.Lock()
 _lib = None
@@ -89,6 +90,12 @@ class Stats(ctypes.Structure):
 class ServerInfo(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "queued", "running", "epochs", "handles",
                                               "bytes_in_use", "budget_bytes")]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("tiles", ctypes.c_int32), ("flags", ctypes.c_int32), ("ms", ctypes.c_double),
+                ("default_tiles", ctypes.c_int32), ("default_ms", ctypes.c_double), ("candidates", ctypes.c_int32),
+                ("cached", ctypes.c_int32)]
 
 
 class FTGCRError(RuntimeError):
@@ -156,6 +163,7 @@ def lib():
         L.ftgcr_error_string.restype = ctypes.c_char_p
         L.ftgcr_solve_noalloc.argtypes = [ctypes.POINTER(Grid), vp, i32, dbl, vp, vp, ctypes.POINTER(Stats), vp]
         L.ftgcr_set_coeffs.argtypes = [vp, ctypes.POINTER(Coeffs), vp]
+        L.ftgcr_tune.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Coeffs), i32, dbl, i32, ctypes.POINTER(Tuning)]
         L.ftgcr_server_create.argtypes = [i64, i32, i32, ctypes.POINTER(vp)]
         L.ftgcr_server_submit.argtypes = [vp, ctypes.POINTER(Grid), ctypes.POINTER(Coeffs), i32, dbl, vp, vp,
                                           ctypes.POINTER(FaultPlan), ctypes.POINTER(i64)]
@@ -338,6 +346,26 @@ def _stats_dict(s: Stats) -> dict:
                 res0=s.res0, res_final_rec=s.res_final_rec, res_final_true=s.res_final_true, norm_R=s.norm_R,
                 bytes_resident=s.bytes_resident, bytes_backup=s.bytes_backup, tiles=s.tiles, status=s.status,
                 loss_events=s.loss_events, split_rounds=bool(s.split_rounds))
+
+
+def tune(D, mu, k=4, tol=1e-10, precision="mixed", precond="line", concurrency=1, max_steps=0, inner_tol=0.0,
+         max_outer=0, protect=True) -> dict:
+    """Tile autotuner (ftgcr_tune): the fastest row-band count and round
+    layout for `concurrency` solves of this shape in one launch, by timing.
+    Returns dict(tiles, rounds, ms, default_tiles, default_ms, candidates,
+    cached); pass tiles= and rounds= to Solver (or Server.submit)."""
+    nlat, nlon = D.shape
+    g = _grid(nlon, nlat, mu, precision, precond, max_steps, 0, inner_tol, max_outer, protect)
+    dp, keep = _ptr(D)
+    t = Tuning()
+    st = lib().ftgcr_tune(ctypes.byref(g), ctypes.byref(Coeffs(dp, 0)), int(k), float(tol), int(concurrency),
+                          ctypes.byref(t))
+    del keep
+    if st != OK:
+        raise FTGCRError(st, "ftgcr_tune")
+    rounds = "split" if t.flags & FLAG_SPLIT_ROUNDS else ("fused" if t.flags & FLAG_FUSED_ROUNDS else "auto")
+    return dict(tiles=t.tiles, rounds=rounds, ms=t.ms, default_tiles=t.default_tiles, default_ms=t.default_ms,
+                candidates=t.candidates, cached=bool(t.cached))
 
 
 def solve_noalloc(D, mu, rhs, x, k=4, tol=1e-10, max_steps=0, tiles=0, stream=None):

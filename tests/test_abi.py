@@ -86,3 +86,22 @@ def test_round_layout_flags_are_validated_before_any_device_call():
     unknown = ftgcr._grid(16, 8, 1.0, "mixed", "line", 0, 0, 0.0, 0)
     unknown.flags = 8
     assert L.ftgcr_create(ctypes.byref(unknown), ctypes.byref(c), 4, 1e-10, ctypes.byref(h)) == ftgcr.ERR_ARG
+
+
+def test_tune_refuses_bad_arguments_before_any_device_call():
+    import numpy as np
+
+    L = ftgcr.lib()
+    D = np.ones((8, 16))
+    c = ftgcr.Coeffs(D.ctypes.data, 0)
+    t = ftgcr.Tuning()
+    g = ftgcr._grid(16, 8, 1.0, "mixed", "line", 0, 0, 0.0, 0)
+    for conc in (0, ftgcr.TUNE_MAX_CONCURRENCY + 1):
+        assert L.ftgcr_tune(ctypes.byref(g), ctypes.byref(c), 4, 1e-10, conc, ctypes.byref(t)) == ftgcr.ERR_ARG
+    fixed = ftgcr._grid(16, 8, 1.0, "mixed", "line", 0, 4, 0.0, 0)  # tiles given: the tuner chooses them
+    assert L.ftgcr_tune(ctypes.byref(fixed), ctypes.byref(c), 4, 1e-10, 1, ctypes.byref(t)) == ftgcr.ERR_ARG
+    forced = ftgcr._grid(16, 8, 1.0, "mixed", "line", 0, 0, 0.0, 0, rounds="split")
+    assert L.ftgcr_tune(ctypes.byref(forced), ctypes.byref(c), 4, 1e-10, 1, ctypes.byref(t)) == ftgcr.ERR_ARG
+    import torch
+    if not torch.cuda.is_available():
+        assert L.ftgcr_tune(ctypes.byref(g), ctypes.byref(c), 4, 1e-10, 1, ctypes.byref(t)) == ftgcr.ERR_CUDA
