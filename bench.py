@@ -361,7 +361,7 @@ def bench_batch(torch, ftgcr, dev, n=128, seed=42, reps=3):
 
 
 def bench_serving(torch, ftgcr, dev, n_req=2000, load=0.8, seed=7, hills_per_size=4, n_cap=300,
-                  sweep_loads=(0.5, 1.0, 1.2), n_sweep=400):
+                  sweep_loads=(0.5, 1.0, 1.2), n_sweep=400, tune_concurrency=16, n_tuned=600):
     """Open-loop serving: n_req requests with Poisson arrivals at `load` x the
     measured capacity; sizes U{256x128, 512x256, 1024x512, 2048x1024}, mixed
     precision, hills drawn per problem, 1% carrying one bit flip.  Right-hand
@@ -369,7 +369,10 @@ def bench_serving(torch, ftgcr, dev, n_req=2000, load=0.8, seed=7, hills_per_siz
     device and identified by a key (a model's operator is fixed across its time
     steps, so pooled handles keep their set-up); latency = arrival -> solution
     on the host.  Then shorter runs at other fractions of the capacity
-    (load_sweep)."""
+    (load_sweep).  Beside it, a shorter run with row bands per size from the
+    autotuner (ftgcr_tune at `tune_concurrency` solves per launch, passed with
+    each request): taller bands raise throughput a little but lengthen a lone
+    request's solve, so the default bands stay the headline."""
     import threading
 
     sizes = [(256, 128), (512, 256), (1024, 512), (2048, 1024)]
@@ -404,102 +407,128 @@ def bench_serving(torch, ftgcr, dev, n_req=2000, load=0.8, seed=7, hills_per_siz
         with pool_lock:
             xpool.setdefault(tuple(x.shape), []).append(x)
 
+    tuned = {}
+    for si, (nlon, nlat) in enumerate(sizes):
+        p0 = probs[si * hills_per_size][0]
+        tuned[(nlon, nlat)] = ftgcr.tune(p0.D, p0.mu, k=K, tol=TOL, precision="mixed", concurrency=tune_concurrency)
+    tiling = {}  # the layout the current run submits with, per shape
+
+    def layout(p):
+        t = tiling.get((p.nlon, p.nlat))
+        return (t["tiles"], t["rounds"]) if t else (0, "auto")
+
     def submit_p(srv, pi, faults=()):
         p, Dd, Rh = probs[pi]
         x = take_x(tuple(p.R.shape))
-        return srv.submit(Dd, p.mu, Rh, x, k=K, tol=TOL, precision="mixed", faults=faults, coeff_key=pi + 1), x
+        tl, rd = layout(p)
+        return srv.submit(Dd, p.mu, Rh, x, k=K, tol=TOL, precision="mixed", faults=faults, coeff_key=pi + 1,
+                          tiles=tl, rounds=rd), x
 
     def submit(srv, i):
         pi, faults = reqs[i]
         return submit_p(srv, pi, faults)
 
-    with ftgcr.Server(max_slots=64, epoch_rounds=24) as srv:
-        warm = [submit_p(srv, pi) for pi in range(len(probs))]  # a handle set up for every problem
-        for _ in warm:
-            srv.next()
-        for _, x in warm:
-            give_x(x)
-        # capacity: closed loop, everything queued at once
-        t0 = time.perf_counter()
-        xs0 = [submit(srv, i) for i in range(n_cap)]
-        for _ in range(n_cap):
-            srv.next()
-        cap = n_cap / (time.perf_counter() - t0)
-        for _, x in xs0:
-            give_x(x)
-        def open_loop(ld, n, seed_arr, keep_sample):
-            arr = inputs.poisson_arrivals(seed_arr, n, ld * cap)
-            sample = set(range(0, n, max(1, n // 8))) if keep_sample else set()  # kept for the equality check
-            t_arr, xs, kept, lat = {}, {}, {}, []
-            lock = threading.Lock()
-            start = time.perf_counter()
+    def serve(n_req, sweep_loads):
+        with ftgcr.Server(max_slots=64, epoch_rounds=24) as srv:
+            warm = [submit_p(srv, pi) for pi in range(len(probs))]  # a handle set up for every problem
+            for _ in warm:
+                srv.next()
+            for _, x in warm:
+                give_x(x)
+            # capacity: closed loop, everything queued at once
+            t0 = time.perf_counter()
+            xs0 = [submit(srv, i) for i in range(n_cap)]
+            for _ in range(n_cap):
+                srv.next()
+            cap = n_cap / (time.perf_counter() - t0)
+            for _, x in xs0:
+                give_x(x)
+            def open_loop(ld, n, seed_arr, keep_sample):
+                arr = inputs.poisson_arrivals(seed_arr, n, ld * cap)
+                sample = set(range(0, n, max(1, n // 8))) if keep_sample else set()  # kept for the equality check
+                t_arr, xs, kept, lat = {}, {}, {}, []
+                lock = threading.Lock()
+                start = time.perf_counter()
 
-            def producer():
-                for i in range(n):
-                    d = start + arr[i] - time.perf_counter()
-                    if d > 0:
-                        time.sleep(d)
-                    ta = time.perf_counter()
-                    t, x = submit(srv, i)
-                    with lock:
-                        t_arr[t] = ta
-                        xs[t] = (i, x)
+                def producer():
+                    for i in range(n):
+                        d = start + arr[i] - time.perf_counter()
+                        if d > 0:
+                            time.sleep(d)
+                        ta = time.perf_counter()
+                        t, x = submit(srv, i)
+                        with lock:
+                            t_arr[t] = ta
+                            xs[t] = (i, x)
 
-            th = threading.Thread(target=producer)
-            th.start()
-            done, results = 0, {}
-            while done < n:
-                r = srv.next(timeout=30)
-                if r is None:
-                    break
-                now = time.perf_counter()
-                t, st, ss = r
-                with lock:
-                    ta = t_arr.get(t)
-                while ta is None:  # the producer has not recorded it yet
-                    time.sleep(1e-5)
+                th = threading.Thread(target=producer)
+                th.start()
+                done, results = 0, {}
+                while done < n:
+                    r = srv.next(timeout=30)
+                    if r is None:
+                        break
+                    now = time.perf_counter()
+                    t, st, ss = r
                     with lock:
                         ta = t_arr.get(t)
-                lat.append(now - ta)
-                results[t] = (st, ss)
-                with lock:
-                    i, x = xs.pop(t)
-                if i in sample:
-                    kept[t] = (i, x.numpy().copy())
-                give_x(x)
-                done += 1
-            th.join()
-            wall = time.perf_counter() - start
-            return results, kept, 1e3 * np.array(lat), wall
+                    while ta is None:  # the producer has not recorded it yet
+                        time.sleep(1e-5)
+                        with lock:
+                            ta = t_arr.get(t)
+                    lat.append(now - ta)
+                    results[t] = (st, ss)
+                    with lock:
+                        i, x = xs.pop(t)
+                    if i in sample:
+                        kept[t] = (i, x.numpy().copy())
+                    give_x(x)
+                    done += 1
+                th.join()
+                wall = time.perf_counter() - start
+                return results, kept, 1e3 * np.array(lat), wall
 
-        results, kept, lat_ms, wall = open_loop(load, n_req, seed, True)
-        info = srv.info()
-        # latency against offered load: shorter runs at other fractions of capacity
-        sweep = []
-        for q, ld in enumerate(sweep_loads):
-            r2, _, l2, w2 = open_loop(ld, n_sweep, seed + 1 + q, False)
-            sweep.append({"load": ld, "requests": n_sweep, "offered_per_s": ld * cap, "achieved_solves_per_s": n_sweep / w2,
-                          "completed_ok": sum(1 for st, _ in r2.values() if st == 0),
-                          "p50_ms": float(np.percentile(l2, 50)), "p99_ms": float(np.percentile(l2, 99))})
-    # a sample of served results against the same request solved alone
-    same = True
-    for t in sorted(kept):
-        i, x = kept[t]
-        pi, faults = reqs[i]
-        p = probs[pi][0]
-        with ftgcr.Solver(p.D, p.mu, k=K, tol=TOL, precision="mixed") as s:
-            xa = np.zeros_like(p.R)
-            s.solve(p.R, xa, faults=faults)
-        same = same and np.array_equal(x, xa)
-    ok = sum(1 for st, _ in results.values() if st == 0)
-    return {"requests": n_req, "completed_ok": ok, "load": load, "capacity_solves_per_s": cap,
-            "offered_per_s": load * cap, "achieved_solves_per_s": n_req / wall,
-            "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
-                           "max": float(lat_ms.max())},
-            "faulty_requests": sum(1 for _, f in reqs[:n_req] if f), "epochs": info["epochs"],
-            "handles": info["handles"], "sizes": "U{256x128,512x256,1024x512,2048x1024}", "precision": "mixed",
-            "io": "rhs and x in pinned host memory, D resident with a coefficient key",
-            "bitwise_equal_to_alone_sample": same, "load_sweep": sweep}
+            results, kept, lat_ms, wall = open_loop(load, n_req, seed, True)
+            info = srv.info()
+            # latency against offered load: shorter runs at other fractions of capacity
+            sweep = []
+            for q, ld in enumerate(sweep_loads):
+                r2, _, l2, w2 = open_loop(ld, n_sweep, seed + 1 + q, False)
+                sweep.append({"load": ld, "requests": n_sweep, "offered_per_s": ld * cap, "achieved_solves_per_s": n_sweep / w2,
+                              "completed_ok": sum(1 for st, _ in r2.values() if st == 0),
+                              "p50_ms": float(np.percentile(l2, 50)), "p99_ms": float(np.percentile(l2, 99))})
+        # a sample of served results against the same request solved alone
+        same = True
+        for t in sorted(kept):
+            i, x = kept[t]
+            pi, faults = reqs[i]
+            p = probs[pi][0]
+            tl, rd = layout(p)
+            with ftgcr.Solver(p.D, p.mu, k=K, tol=TOL, precision="mixed", tiles=tl, rounds=rd) as s:
+                xa = np.zeros_like(p.R)
+                s.solve(p.R, xa, faults=faults)
+            same = same and np.array_equal(x, xa)
+        ok = sum(1 for st, _ in results.values() if st == 0)
+        return {"requests": n_req, "completed_ok": ok, "load": load, "capacity_solves_per_s": cap,
+                "offered_per_s": load * cap, "achieved_solves_per_s": n_req / wall,
+                "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
+                               "max": float(lat_ms.max())},
+                "faulty_requests": sum(1 for _, f in reqs[:n_req] if f), "epochs": info["epochs"],
+                "handles": info["handles"], "sizes": "U{256x128,512x256,1024x512,2048x1024}", "precision": "mixed",
+                "io": "rhs and x in pinned host memory, D resident with a coefficient key",
+                "bitwise_equal_to_alone_sample": same, "load_sweep": sweep}
+
+    out = serve(n_req, sweep_loads)
+    out["tiles"] = "default (ftgcr_create's own choice)"
+    tiling.update(tuned)
+    d = serve(n_tuned, ())
+    out["autotuned_tiles"] = {k: d[k] for k in ("requests", "completed_ok", "capacity_solves_per_s",
+                                                "achieved_solves_per_s", "latency_ms",
+                                                "bitwise_equal_to_alone_sample")}
+    out["autotuned_tiles"]["tiles"] = {f"{a}x{b}": {"tiles": t["tiles"], "rounds": t["rounds"],
+                                                    "default_tiles": t["default_tiles"]} for (a, b), t in tuned.items()}
+    out["autotuned_tiles"]["tuned_for"] = f"ftgcr_tune at {tune_concurrency} solves per launch"
+    return out
 
 
 # ------------------------------------------------------------------ GPU arm
