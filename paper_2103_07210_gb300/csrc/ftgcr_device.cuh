@@ -615,6 +615,182 @@ __device__ __noinline__ void line_solve_row(const SolveDev<T>& sd, int j, T* row
   __syncwarp();
 }
 
+// The same solve of one row by a group of G warps (G = 2, 4 or 8), for tiles
+// with fewer rows than warps.  Thread (w, lane) of the group takes piece
+// p = lane * G + w of the row: elements lane * C + w * C/G + kk, kk < C/G, so
+// the pieces run in row order and the constants keep their per-lane layout.
+// Each recurrence: every piece's affine map (pass 1 / 3) into `maps`, a group
+// barrier, each lane composes the maps of its G pieces, a warp scan over the
+// lanes gives every lane's carry-in, and each piece applies its lane's earlier
+// pieces to it; then the piece is replayed from its exact carry-in (pass 2 /
+// 4).  C must be a multiple of 8 G.  `maps`: 2 * 32 * G floats of shared
+// memory per group; `bar`: the group's named barrier (1..15).
+__device__ __forceinline__ void group_sync(int bar, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nthreads) : "memory");
+}
+template <int G>
+__device__ __noinline__ void line_solve_row_group(const SolveDev<float>& sd, int j, float* row_,
+                                                  const LineConsts<float> lc, float* maps, int bar) {
+  const int lane = threadIdx.x & 31, w = (threadIdx.x >> 5) % G;
+  const int n = sd.nlon, m = n - 1, C = sd.C, Cp = C / G;
+  const int i0 = lane * C + w * Cp, k0 = w * Cp;
+  const float* lr = sd.lrow + (long long)j * 4;
+  const float lr0 = __ldg(lr + 0), lr1 = __ldg(lr + 1), lr2 = __ldg(lr + 2);
+  const unsigned rb = smem_addr(row_), cbb = smem_addr(lc.cb), cwb = smem_addr(lc.cw), czb = smem_addr(lc.cz);
+  auto R = [&](int i) { return rb + 4u * (unsigned)sk(i); };
+  auto Cb = [&](int k) { return cbb + 4u * (unsigned)(k * 32 + lane); };
+  auto Cw = [&](int k) { return cwb + 4u * (unsigned)(k * 32 + lane); };
+  auto Cz = [&](int k) { return czb + 4u * (unsigned)(k * 32 + lane); };
+  float* mF = maps;           // [G][32]
+  float* mG = maps + 32 * G;  // [G][32]
+  const float bl = -lds<float>(R(n - 1));
+  if (i0 + Cp > n)
+    for (int kk = 0; kk < Cp; ++kk)
+      if (i0 + kk >= n) sts(R(i0 + kk), 0.f);
+  // forward multiplier of the piece's first element: c of the element before
+  float a0 = 0.f;
+  if (w > 0)
+    a0 = lds<float>(Cb(k0 - 1));
+  else if (lane > 0)
+    a0 = lds<float>(cbb + 4u * (unsigned)((C - 1) * 32 + lane - 1));
+  // pass 1: the piece's map g_out = F g_in + Gm
+  float F = 1.f, Gm = 0.f;
+  {
+    float a = a0;
+    for (int kb = 0; kb < Cp; kb += kLB) {
+      float rv[kLB], cv[kLB];
+#pragma unroll
+      for (int q = 0; q < kLB; ++q) {
+        rv[q] = lds<float>(R(i0 + kb + q));
+        cv[q] = lds<float>(Cb(k0 + kb + q));
+      }
+#pragma unroll
+      for (int q = 0; q < kLB; ++q) {
+        Gm = tfma(a, Gm, -rv[q]);
+        F = F * a;
+        a = cv[q];
+      }
+    }
+  }
+  mF[w * 32 + lane] = F;
+  mG[w * 32 + lane] = Gm;
+  group_sync(bar, 32 * G);
+  float FL = 1.f, GL = 0.f, Fw[G], Gw[G];
+#pragma unroll
+  for (int q = 0; q < G; ++q) {
+    Fw[q] = mF[q * 32 + lane];
+    Gw[q] = mG[q * 32 + lane];
+    GL = tfma(Fw[q], GL, Gw[q]);
+    FL = FL * Fw[q];
+  }
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const float Fo = __shfl_up_sync(0xffffffffu, FL, d);
+    const float Go = __shfl_up_sync(0xffffffffu, GL, d);
+    if (lane >= d) {
+      GL = tfma(FL, Go, GL);
+      FL = FL * Fo;
+    }
+  }
+  float carry = __shfl_up_sync(0xffffffffu, GL, 1);
+  if (lane == 0) carry = 0.f;
+#pragma unroll
+  for (int q = 0; q < G; ++q)
+    if (q < w) carry = tfma(Fw[q], carry, Gw[q]);
+  // pass 2: g from the exact carry-in
+  {
+    float a = a0, g = carry;
+    for (int kb = 0; kb < Cp; kb += kLB) {
+      float rv[kLB], cv[kLB];
+#pragma unroll
+      for (int q = 0; q < kLB; ++q) {
+        rv[q] = lds<float>(R(i0 + kb + q));
+        cv[q] = lds<float>(Cb(k0 + kb + q));
+      }
+#pragma unroll
+      for (int q = 0; q < kLB; ++q) {
+        g = tfma(a, g, -rv[q]);
+        rv[q] = g;
+        a = cv[q];
+      }
+#pragma unroll
+      for (int q = 0; q < kLB; ++q) sts(R(i0 + kb + q), rv[q]);
+    }
+  }
+  group_sync(bar, 32 * G);  // every carry read before the maps are reused
+  // pass 3: the piece's backward map y_in = Fb y_out + Y
+  float Fb = 1.f, Y = 0.f;
+  for (int kb = Cp - kLB; kb >= 0; kb -= kLB) {
+    float gv[kLB], cv[kLB], wv[kLB];
+#pragma unroll
+    for (int q = 0; q < kLB; ++q) {
+      gv[q] = lds<float>(R(i0 + kb + q));
+      cv[q] = lds<float>(Cb(k0 + kb + q));
+      wv[q] = lds<float>(Cw(k0 + kb + q));
+    }
+#pragma unroll
+    for (int q = kLB - 1; q >= 0; --q) {
+      Y = tfma(cv[q], Y, gv[q] * wv[q]);
+      Fb = Fb * cv[q];
+    }
+  }
+  mF[w * 32 + lane] = Fb;
+  mG[w * 32 + lane] = Y;
+  group_sync(bar, 32 * G);
+  float FbL = 1.f, YL = 0.f;
+#pragma unroll
+  for (int q = G - 1; q >= 0; --q) {
+    Fw[q] = mF[q * 32 + lane];
+    Gw[q] = mG[q * 32 + lane];
+    YL = tfma(Fw[q], YL, Gw[q]);
+    FbL = FbL * Fw[q];
+  }
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const float Fo = __shfl_down_sync(0xffffffffu, FbL, d);
+    const float Yo = __shfl_down_sync(0xffffffffu, YL, d);
+    if (lane + d < 32) {
+      YL = tfma(FbL, Yo, YL);
+      FbL = FbL * Fo;
+    }
+  }
+  float carryb = __shfl_down_sync(0xffffffffu, YL, 1);
+  if (lane == 31) carryb = 0.f;
+#pragma unroll
+  for (int q = G - 1; q >= 0; --q)
+    if (q > w) carryb = tfma(Fw[q], carryb, Gw[q]);
+  // pass 4: y from the exact carry-in
+  {
+    float y = carryb;
+    for (int kb = Cp - kLB; kb >= 0; kb -= kLB) {
+      float gv[kLB], cv[kLB], wv[kLB];
+#pragma unroll
+      for (int q = 0; q < kLB; ++q) {
+        gv[q] = lds<float>(R(i0 + kb + q));
+        cv[q] = lds<float>(Cb(k0 + kb + q));
+        wv[q] = lds<float>(Cw(k0 + kb + q));
+      }
+#pragma unroll
+      for (int q = kLB - 1; q >= 0; --q) {
+        y = tfma(cv[q], y, gv[q] * wv[q]);
+        gv[q] = y;
+      }
+#pragma unroll
+      for (int q = 0; q < kLB; ++q) sts(R(i0 + kb + q), gv[q]);
+    }
+  }
+  group_sync(bar, 32 * G);
+  // bordering: x_{n-1} = (b_{n-1} + Tx_{n-1} y_0 + Tx_{n-2} y_{m-1}) / delta
+  const float y0 = lds<float>(R(0));
+  const float ym = lds<float>(R(m - 1));
+  const float xl = tfma(lr2, ym, tfma(lr1, y0, bl * lr0));
+  group_sync(bar, 32 * G);
+#pragma unroll 8
+  for (int kk = 0; kk < Cp; ++kk) sts(R(i0 + kk), tfma(-xl, lds<float>(Cz(k0 + kk)), lds<float>(R(i0 + kk))));
+  group_sync(bar, 32 * G);
+  if (lane == 0 && w == 0) sts(R(n - 1), xl);
+}
+
 // FP64 path: the row's periodic tridiagonal solve by ONE thread, operation for
 // operation the CPU oracle's Thomas substitution: forward y_0 = b_0,
 // y_i = fma(-l_i, y_{i-1}, b_i); backward y_{m-1} = y_{m-1} winv_{m-1},

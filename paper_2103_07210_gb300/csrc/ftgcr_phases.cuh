@@ -693,8 +693,14 @@ __device__ __forceinline__ LineConsts<T> staged_consts(const SolveDev<T>& sd, co
 // whatever the number of active lanes (measured: 64 cycles per dependent FMA
 // for 1 to 32 lanes of one warp, 152 with eight warps on the SM), so rows
 // side by side in lanes cost one row's instructions instead of one per row.
-template <typename T>
-__device__ __forceinline__ void precond_tile(const SolveDev<T>& sd, int h0, int nrows, T* sm, int stride, const T* cs) {
+// GROUPS (mixed path, kernel instance with split rounds) and `groups` (the
+// first pass of a split round): a tile with at most half as many rows as
+// warps solves each row with a group of 2, 4 or 8 warps.  One-pass rounds
+// keep one warp per row in every instance, so a one-pass solve gives the
+// same result in a launch with split solves as alone.
+template <typename T, bool GROUPS = false>
+__device__ __forceinline__ void precond_tile(const SolveDev<T>& sd, int h0, int nrows, T* sm, int stride, const T* cs,
+                                             bool groups = false) {
   if constexpr (sizeof(T) == 8) {
     if (sd.precond == PC_LINE) {
       const int n = sd.nlon, m = n - 1;
@@ -721,6 +727,31 @@ __device__ __forceinline__ void precond_tile(const SolveDev<T>& sd, int h0, int 
     }
   }
   const int warp = threadIdx.x >> 5;
+  if constexpr (GROUPS && sizeof(T) == 4) {
+    if (groups && sd.precond == PC_LINE && 2 * nrows <= kWarps) {
+      __shared__ float maps[kWarps * 64];  // per group: 2 x 32 x G
+      auto run = [&](auto gtag) {
+        constexpr int G = decltype(gtag)::value;
+        const int grp = warp / G;
+        if (grp < nrows)
+          line_solve_row_group<G>(sd, h0 + grp, sm + grp * stride, staged_consts(sd, cs, nrows, grp),
+                                  maps + grp * 64 * G, 1 + grp);
+      };
+      const int C = sd.C;
+      if (8 * nrows <= kWarps && C % 64 == 0) {
+        run(std::integral_constant<int, 8>());
+        return;
+      }
+      if (4 * nrows <= kWarps && C % 32 == 0) {
+        run(std::integral_constant<int, 4>());
+        return;
+      }
+      if (C % 16 == 0) {
+        run(std::integral_constant<int, 2>());
+        return;
+      }
+    }
+  }
   for (int jr = warp; jr < nrows; jr += kWarps) precond_row(sd, h0 + jr, sm + jr * stride, staged_consts(sd, cs, nrows, jr));
 }
 
@@ -1037,15 +1068,15 @@ __device__ __forceinline__ void step_axpy(const SolveDev<T>& sd, const Ctx<T>& c
 }
 // (2) e = P^-1 r' on the staged rows, then the e-site flips and data-loss
 // events of the step.
-template <typename T>
+template <typename T, bool GROUPS = false>
 __device__ __forceinline__ void step_precond(const SolveDev<T>& sd, const Ctx<T>& c, const RowTile& rt, T* sm,
-                                             const T* cs, PhaseSmem& ps) {
+                                             const T* cs, PhaseSmem& ps, bool groups = false) {
   const int nlon = sd.nlon, stride = row_stride(nlon);
   const int nrows = rt.h1 - rt.h0;
   cp_async_wait_all();
   __syncthreads();
   sub_mark(ps, 0);
-  precond_tile(sd, rt.h0, nrows, sm, stride, cs);
+  precond_tile<T, GROUPS>(sd, rt.h0, nrows, sm, stride, cs, groups);
   __syncthreads();
   sub_mark(ps, 1);
   if (threadIdx.x == 0) {
@@ -1203,7 +1234,7 @@ __device__ __noinline__ void phase_pa_any(const SolveDev<T>& sd, const Ctx<T>& c
       ps.nfl = collect_flips(sd, c.t, FUSED ? (kStateVecs | (1u << V_E)) : (1u << V_E), (long long)rt.h0 * nlon,
                              (long long)rt.h1 * nlon, ps.fl);
     step_axpy<T, KB, FUSED>(sd, c, rt, sm, ps, an);
-    step_precond<T>(sd, c, rt, sm, cs, ps);
+    step_precond<T, true>(sd, c, rt, sm, cs, ps, mode == 1);
     if (threadIdx.x == 0) {
       ps.cs_solve = sidx;
       ps.cs_tile = tau;
@@ -1555,7 +1586,7 @@ __device__ __noinline__ void phase_init_any(const SolveDev<T>& sd, const Ctx<T>&
     init_rows<T>(sd, c, rt, sm, ps, an, aR, vec);
     cp_async_wait_all();
     __syncthreads();
-    precond_tile(sd, rt.h0, rt.h1 - rt.h0, sm, stride, cs);
+    precond_tile<T, true>(sd, rt.h0, rt.h1 - rt.h0, sm, stride, cs, mode == 1);
     __syncthreads();
     if (threadIdx.x == 0) {
       ps.cs_solve = sidx;
