@@ -44,9 +44,9 @@ def algorithmic_bytes(steps: int, outer: int, k: int = K, s: int = 4, N: int = N
 
 # DRAM traffic per launch of the persistent kernel from one ncu capture, valid
 # only for the kernel sources it was taken on (sha256 of the CUDA sources).
-NCU_TRAFFIC = {"sources_sha256": "074a05eed4e41c19a5a504ebab9fe18cc21b83f70812ecfc5cbf5b5c9682a6d5",
-               "bytes_per_launch": 27844864 + 8030976,  # mixed 1024x512 (read + write)
-               "large": {"2048x1024": 2706766336 + 1349251840, "4096x2048": 15110482432 + 5188121344}}
+NCU_TRAFFIC = {"sources_sha256": "af036e32b7ef7f921abbee79a606ac7bd3c1dbda1bc1c941ca669c5a9deb2dd9",
+               "bytes_per_launch": 28047360 + 8733952,  # mixed 1024x512 (read + write)
+               "large": {"2048x1024": 2709789696 + 1348184320, "4096x2048": 15130663424 + 5215703040}}
 
 
 def sources_hash() -> str:
