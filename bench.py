@@ -162,7 +162,27 @@ def oracle_throughput(seconds_budget: float = 12.0, cores: int | None = None):
         res = pool.map(_oracle_solve, range(n), chunksize=1)
         wall = time.perf_counter() - t
     return dict(value=n / wall, steps_per_s=sum(r[1] for r in res) / wall, cores=cores,
-                latency_s=float(np.median([r[0] for r in res])), n=n, wall=wall)
+                latency_s=float(np.median([r[0] for r in res])), steps=steps, n=n, wall=wall)
+
+
+def physical_cores():
+    """Distinct (package, core) pairs of the host's online CPUs, or None."""
+    seen = set()
+    base = "/sys/devices/system/cpu"
+    try:
+        for d in os.listdir(base):
+            if not (d.startswith("cpu") and d[3:].isdigit()):
+                continue
+            t = os.path.join(base, d, "topology")
+            try:
+                pkg = open(os.path.join(t, "physical_package_id")).read().strip()
+                core = open(os.path.join(t, "core_id")).read().strip()
+            except OSError:
+                continue
+            seen.add((pkg, core))
+    except OSError:
+        return None
+    return len(seen) or None
 
 
 def run_reference(args):
@@ -657,7 +677,9 @@ def run_ours(args):
             line["cpu_baseline"] = {"value": cb["value"], "unit": "solves/s", "cores": cb["cores"], "kind": "oracle",
                                     "sample": f"{cb['n']} FP64 oracle solves of the {NLON}x{NLAT} problem, "
                                               f"one process per core, {cb['wall']:.1f} s",
-                                    "latency_s_per_solve_one_core": cb["latency_s"]}
+                                    "latency_s_per_solve_one_core": cb["latency_s"],
+                                    "latency_s_per_step_one_core": cb["latency_s"] / max(1, cb["steps"]),
+                                    "steps_per_s": cb["steps_per_s"], "physical_cores": physical_cores()}
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
