@@ -191,7 +191,10 @@ int ftgcr_create(const ftgcr_grid* grid, const ftgcr_coeffs* coeffs, int32_t k, 
 /* Solve L(x) = rhs (Algorithm 1).  rhs: [N] FP64; x: [N] FP64, in = initial
  * guess, out = solution (host or device memory).  plan: NULL or a fault plan.
  * stream: a cudaStream_t, or NULL for the legacy default stream.  Blocks
- * until done and returns FTGCR_OK, FTGCR_NOT_CONVERGED or an error. */
+ * until done and returns FTGCR_OK, FTGCR_NOT_CONVERGED or an error.  Host
+ * arrays are staged and checked on the device: a NaN or an infinity in rhs
+ * or x returns FTGCR_ERR_ARG without starting the solve, and leaves x as it
+ * was. */
 int ftgcr_solve(ftgcr_handle* h, const double* rhs, double* x, const ftgcr_fault_plan* plan, void* stream);
 
 /* Same as ftgcr_solve but only enqueues the work on `stream` and returns;

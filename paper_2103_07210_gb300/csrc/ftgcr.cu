@@ -438,9 +438,35 @@ __global__ void k_fill_table(BatchTable t, void** d_solves, int* d_nt) {
   }
 }
 
+// Flags a non-finite value of a staged input (exponent bits all ones).
+__global__ void k_nonfinite(const double* __restrict__ a, long long n, LaunchCtl* ctl) {
+  bool bad = false;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    bad |= ((__double_as_longlong(a[i]) >> 52) & 0x7FF) == 0x7FF;
+  if (__syncthreads_or(bad) && threadIdx.x == 0) ctl->nonfinite = 1;
+}
+
+// skip (host-array solves): ctl->nonfinite as set by k_nonfinite; a solve
+// whose staged input is not finite records a finished, not-converged state
+// and is not started.
 template <typename T>
 __global__ void k_begin_solve(SolveDev<T>* sd, BeginArgs b, int* active, int n_active, int slot, int par,
-                              LaunchCtl* ctl) {
+                              LaunchCtl* ctl, bool check_finite = false) {
+  if (check_finite && ctl->nonfinite) {
+    if (threadIdx.x == 0) {
+      SolveState S;
+      memset(&S, 0, sizeof S);
+      S.status = ST_NOT_CONVERGED;
+      *sd->result = S;
+      active[slot] = 0;
+      active[n_active + slot] = 0;
+      ctl->counter = 0;
+      ctl->err = 0;
+      ctl->round0 = 0;
+      ctl->round_end = 0;
+    }
+    return;
+  }
   if (threadIdx.x == 0) {
     sd->R = b.R;
     sd->x0 = b.x0;
@@ -468,6 +494,7 @@ __global__ void k_begin_solve(SolveDev<T>* sd, BeginArgs b, int* active, int n_a
       ctl->err = 0;
       ctl->round0 = p;
       ctl->round_end = p;
+      ctl->nonfinite = 0;
     }
   }
   for (int q = threadIdx.x; q < b.nfaults; q += blockDim.x) const_cast<Fault*>(sd->faults)[q] = b.faults[q];
@@ -684,12 +711,6 @@ int occupancy(int kb, int split, size_t smem, int* occ) {
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, f, kThreads, smem));
   known[{f, smem}] = *occ;
   return FTGCR_OK;
-}
-
-bool finite_array(const double* a, long long n) {
-  for (long long i = 0; i < n; ++i)
-    if (!std::isfinite(a[i])) return false;
-  return true;
 }
 
 bool is_device_ptr(const void* p) {
@@ -998,9 +1019,9 @@ BeginArgs begin_args(const ftgcr_handle* h, const double* R, const double* x0, d
 
 template <typename T>
 int solve_async_impl(ftgcr_handle* h, const double* R, const double* x0, double* xout, const ftgcr_fault_plan* plan,
-                     cudaStream_t st) {
+                     cudaStream_t st, bool check_finite = false) {
   const BeginArgs b = begin_args(h, R, x0, xout, plan);
-  k_begin_solve<T><<<1, 64, 0, st>>>((SolveDev<T>*)h->sdev, b, h->active, 1, 0, 0, h->ctl);
+  k_begin_solve<T><<<1, 64, 0, st>>>((SolveDev<T>*)h->sdev, b, h->active, 1, 0, 0, h->ctl, check_finite);
   CK(cudaGetLastError());
   // every inner step takes two rounds, every refinement sweep a few more
   const int max_rounds = (int)std::min<long long>(1 << 30, 2 * h->max_steps + 8 * ((long long)h->max_outer + 2) + 16);
@@ -1136,6 +1157,7 @@ int table_run_impl(SlotTableImpl* t, int max_rounds, cudaStream_t st) {
   t->h_ctl_in->err = 0;
   t->h_ctl_in->round0 = t->round;
   t->h_ctl_in->round_end = t->round;
+  t->h_ctl_in->nonfinite = 0;
   CK(cudaMemcpyAsync(t->d_ctl, t->h_ctl_in, sizeof(LaunchCtl), cudaMemcpyHostToDevice, st));
   rc = launch_persistent<T>(kb, (SolveDev<T>* const*)t->d_solves, t->d_nt, t->d_act, t->n, t->d_ctl, t->d_diag,
                             max_rounds, grid, smem, split, st);
@@ -1155,6 +1177,7 @@ void report_timeout(const ftgcr_handle* h) {
 }
 
 int status_from_result(const ftgcr_handle* h) {
+  if (h->h_ctl->nonfinite) return FTGCR_ERR_ARG;
   if (h->h_ctl->err) {
     report_timeout(h);
     return FTGCR_ERR_TIMEOUT;
@@ -1316,18 +1339,24 @@ int ftgcr_solve(ftgcr_handle* h, const double* rhs, double* x, const ftgcr_fault
   const bool rdev = is_device_ptr(rhs), xdev = is_device_ptr(x);
   const double* R = rhs;
   double* X = x;
+  // host arrays: staged, and checked for finite values on the device (the
+  // solve does not start if one is not; x then comes back unchanged)
+  const bool check = !rdev || !xdev;
+  const int cg = (int)std::min<long long>((h->N + 255) / 256, 1024);
+  if (check) CK(cudaMemsetAsync(&h->ctl->nonfinite, 0, sizeof(int), st));
   if (!rdev) {
-    if (!finite_array(rhs, h->N)) return FTGCR_ERR_ARG;
     CK(cudaMemcpyAsync(h->stageR, rhs, sizeof(double) * h->N, cudaMemcpyHostToDevice, st));
+    k_nonfinite<<<cg, 256, 0, st>>>(h->stageR, h->N, h->ctl);
     R = h->stageR;
   }
   if (!xdev) {
-    if (!finite_array(x, h->N)) return FTGCR_ERR_ARG;
     CK(cudaMemcpyAsync(h->stageX, x, sizeof(double) * h->N, cudaMemcpyHostToDevice, st));
+    k_nonfinite<<<cg, 256, 0, st>>>(h->stageX, h->N, h->ctl);
     X = h->stageX;
   }
-  rc = h->precision == FTGCR_MIXED ? solve_async_impl<float>(h, R, X, X, plan, st)
-                                   : solve_async_impl<double>(h, R, X, X, plan, st);
+  CK(cudaGetLastError());
+  rc = h->precision == FTGCR_MIXED ? solve_async_impl<float>(h, R, X, X, plan, st, check)
+                                   : solve_async_impl<double>(h, R, X, X, plan, st, check);
   if (rc) return rc;
   if (!xdev) CK(cudaMemcpyAsync(x, h->stageX, sizeof(double) * h->N, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));

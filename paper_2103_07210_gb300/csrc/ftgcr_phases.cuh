@@ -66,6 +66,7 @@ struct LaunchCtl {
   int err;
   long long round0;
   long long round_end;
+  int nonfinite;  // a staged host input held a NaN or an infinity (the solve did not start)
 };
 
 // Optional per-round trace: for every (round, CTA) the global timer at the

@@ -174,6 +174,34 @@ def test_invalid_arguments_are_rejected():
                 s.solve(R, x, faults=[f])
 
 
+def test_non_finite_host_inputs_are_refused_and_the_handle_stays_usable():
+    # host arrays are checked on the device after staging; the solve does not start
+    p = inputs.hill_problem(64, 32, rhs="random", seed=12)
+    for prec in ("fp64", "mixed"):
+        with ftgcr.Solver(p.D, p.mu, k=4, tol=1e-10, precision=prec) as s:
+            xref = np.zeros_like(p.R)
+            assert s.solve(np.ascontiguousarray(p.R), xref) == ftgcr.OK
+            steps = s.stats()["steps"]
+            bad_r = p.R.copy()
+            bad_r[5, 7] = np.nan
+            x = np.full_like(p.R, 0.5)
+            with pytest.raises(ftgcr.FTGCRError) as ei:
+                s.solve(bad_r, x)
+            assert ei.value.status == ftgcr.ERR_ARG and np.all(x == 0.5)  # x comes back unchanged
+            bad_x = np.zeros_like(p.R)
+            bad_x[0, 0] = np.inf
+            with pytest.raises(ftgcr.FTGCRError) as ei:
+                s.solve(np.ascontiguousarray(p.R), bad_x)
+            assert ei.value.status == ftgcr.ERR_ARG
+            # the next solves, host and device, are unaffected
+            x2 = np.zeros_like(p.R)
+            assert s.solve(np.ascontiguousarray(p.R), x2) == ftgcr.OK and np.array_equal(x2, xref)
+            assert s.stats()["steps"] == steps
+            R = cuda(p.R)
+            xd = torch.zeros_like(R)
+            assert s.solve(R, xd) == ftgcr.OK and np.array_equal(xd.cpu().numpy(), xref)
+
+
 def test_repeated_solves_on_one_handle_are_identical():
     p = inputs.hill_problem(128, 64, rhs="random", seed=9)
     with ftgcr.Solver(p.D, p.mu, k=4, tol=1e-10) as s:
