@@ -318,8 +318,9 @@ int ftgcr_solve_noalloc(const ftgcr_grid* grid, const double* D, int32_t k, doub
  *    device memory free at creation.
  *  - Pointers: D, rhs and x may be host or device memory and must stay valid,
  *    and x untouched by the caller, until poll/wait reports the result.  Host
- *    rhs and x are checked for finite values by submit itself (on the
- *    caller's thread); pinned host memory is copied asynchronously.
+ *    rhs and x are staged (pinned host memory is copied asynchronously) and
+ *    checked for finite values on the device: a request holding a NaN or an
+ *    infinity does not start and completes with FTGCR_ERR_ARG, x unchanged.
  *  - Thread safety: submit, poll, wait and info may be called from any
  *    thread; destroy must not overlap any other call on the same server. */
 typedef struct ftgcr_server ftgcr_server;

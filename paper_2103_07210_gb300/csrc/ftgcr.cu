@@ -446,13 +446,14 @@ __global__ void k_nonfinite(const double* __restrict__ a, long long n, LaunchCtl
   if (__syncthreads_or(bad) && threadIdx.x == 0) ctl->nonfinite = 1;
 }
 
-// skip (host-array solves): ctl->nonfinite as set by k_nonfinite; a solve
-// whose staged input is not finite records a finished, not-converged state
-// and is not started.
+// check (host-array solves): the control block whose `nonfinite` flag
+// k_nonfinite set over the staged inputs; a solve whose input is not finite
+// records a finished, not-converged state and is not started.  ctl: the
+// launch's control block to reset (single-solve and batch launches), or null.
 template <typename T>
 __global__ void k_begin_solve(SolveDev<T>* sd, BeginArgs b, int* active, int n_active, int slot, int par,
-                              LaunchCtl* ctl, bool check_finite = false) {
-  if (check_finite && ctl->nonfinite) {
+                              LaunchCtl* ctl, const LaunchCtl* check = nullptr) {
+  if (check && check->nonfinite) {
     if (threadIdx.x == 0) {
       SolveState S;
       memset(&S, 0, sizeof S);
@@ -460,10 +461,12 @@ __global__ void k_begin_solve(SolveDev<T>* sd, BeginArgs b, int* active, int n_a
       *sd->result = S;
       active[slot] = 0;
       active[n_active + slot] = 0;
-      ctl->counter = 0;
-      ctl->err = 0;
-      ctl->round0 = 0;
-      ctl->round_end = 0;
+      if (ctl) {
+        ctl->counter = 0;
+        ctl->err = 0;
+        ctl->round0 = 0;
+        ctl->round_end = 0;
+      }
     }
     return;
   }
@@ -1021,7 +1024,8 @@ template <typename T>
 int solve_async_impl(ftgcr_handle* h, const double* R, const double* x0, double* xout, const ftgcr_fault_plan* plan,
                      cudaStream_t st, bool check_finite = false) {
   const BeginArgs b = begin_args(h, R, x0, xout, plan);
-  k_begin_solve<T><<<1, 64, 0, st>>>((SolveDev<T>*)h->sdev, b, h->active, 1, 0, 0, h->ctl, check_finite);
+  k_begin_solve<T><<<1, 64, 0, st>>>((SolveDev<T>*)h->sdev, b, h->active, 1, 0, 0, h->ctl,
+                                     check_finite ? h->ctl : nullptr);
   CK(cudaGetLastError());
   // every inner step takes two rounds, every refinement sweep a few more
   const int max_rounds = (int)std::min<long long>(1 << 30, 2 * h->max_steps + 8 * ((long long)h->max_outer + 2) + 16);
@@ -1129,6 +1133,7 @@ struct SlotTableImpl {
   int grid_cap = 0;
   std::vector<ftgcr_handle*> slot;
   std::vector<char> launched;  // slots occupied when the last launch was enqueued
+  std::vector<char> checked;   // slots whose staged inputs were checked for finite values
 };
 
 template <typename T>
@@ -1463,6 +1468,7 @@ int table_create(int precision, int max_slots, SlotTable** out) {
   t->n = max_slots;
   t->slot.assign(max_slots, nullptr);
   t->launched.assign(max_slots, 0);
+  t->checked.assign(max_slots, 0);
   CK(cudaGetDevice(&t->dev));
   const DeviceInfo di = device_info(t->dev);
   t->grid_cap = di.sms * 4;
@@ -1501,7 +1507,7 @@ void table_destroy(SlotTable* t) {
 }
 
 int table_begin(SlotTable* t, int slot, ftgcr_handle* h, const double* rhs, double* x, const ftgcr_fault_plan* plan,
-                cudaStream_t st) {
+                cudaStream_t st, int check) {
   if (!t || !h || !rhs || !x || slot < 0 || slot >= t->n || t->slot[slot] || h->precision != t->precision)
     return FTGCR_ERR_ARG;
   for (ftgcr_handle* o : t->slot)
@@ -1510,14 +1516,22 @@ int table_begin(SlotTable* t, int slot, ftgcr_handle* h, const double* rhs, doub
   if (rc) return rc;
   CK(cudaMemcpyAsync(t->d_solves + slot, &h->sdev, sizeof(void*), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(t->d_nt + slot, &h->nt, sizeof(int), cudaMemcpyHostToDevice, st));
+  if (check) {  // the handle's own control block carries the flag
+    const int cg = (int)std::min<long long>((h->N + 255) / 256, 1024);
+    CK(cudaMemsetAsync(&h->ctl->nonfinite, 0, sizeof(int), st));
+    if (check & 1) k_nonfinite<<<cg, 256, 0, st>>>(rhs, h->N, h->ctl);
+    if (check & 2) k_nonfinite<<<cg, 256, 0, st>>>(x, h->N, h->ctl);
+  }
   const BeginArgs b = begin_args(h, rhs, x, x, plan);
   // parity -1: the begin may be enqueued behind a launch still running
+  const LaunchCtl* chk = check ? h->ctl : nullptr;
   if (t->precision == FTGCR_MIXED)
-    k_begin_solve<float><<<1, 64, 0, st>>>((SolveDev<float>*)h->sdev, b, t->d_act, t->n, slot, -1, nullptr);
+    k_begin_solve<float><<<1, 64, 0, st>>>((SolveDev<float>*)h->sdev, b, t->d_act, t->n, slot, -1, nullptr, chk);
   else
-    k_begin_solve<double><<<1, 64, 0, st>>>((SolveDev<double>*)h->sdev, b, t->d_act, t->n, slot, -1, nullptr);
+    k_begin_solve<double><<<1, 64, 0, st>>>((SolveDev<double>*)h->sdev, b, t->d_act, t->n, slot, -1, nullptr, chk);
   CK(cudaGetLastError());
   t->slot[slot] = h;
+  t->checked[slot] = check != 0;
   return FTGCR_OK;
 }
 
@@ -1544,6 +1558,8 @@ int table_collect(SlotTable* t, cudaStream_t st, int* finished) {
     if (!err && t->h_act[par * t->n + s]) continue;
     CK(cudaMemcpy(h->h_result, h->result, sizeof(SolveState), cudaMemcpyDeviceToHost));
     *h->h_ctl = *t->h_ctl_out;
+    h->h_ctl->nonfinite = 0;
+    if (t->checked[s]) CK(cudaMemcpy(&h->h_ctl->nonfinite, &h->ctl->nonfinite, sizeof(int), cudaMemcpyDeviceToHost));
     h->last_stream = st;
     h->solved = 1;
     h->last_status = err ? FTGCR_ERR_TIMEOUT : status_from_result(h);

@@ -25,8 +25,11 @@ void table_destroy(SlotTable* t);
 // Begin a solve of h in a free slot.  rhs, x: device pointers (x: initial
 // guess in, solution out), valid until the solve has finished.  Enqueued on st;
 // it may be enqueued behind a launch still in flight, and then joins the next.
+// check: bit 0 rhs, bit 1 x are staged host inputs to test for non-finite
+// values on the device first; a solve that fails the test does not start and
+// finishes in the next launch with FTGCR_ERR_ARG.
 int table_begin(SlotTable* t, int slot, ftgcr_handle* h, const double* rhs, double* x, const ftgcr_fault_plan* plan,
-                cudaStream_t st);
+                cudaStream_t st, int check = 0);
 
 // Run every occupied slot for at most max_rounds rounds (enqueued on st).
 int table_run(SlotTable* t, int max_rounds, cudaStream_t st);

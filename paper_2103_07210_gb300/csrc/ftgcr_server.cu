@@ -208,7 +208,7 @@ struct ftgcr_server {
     cudaGetLastError();
     const bool xdev = cudaPointerGetAttributes(&at, X) == cudaSuccess && at.type == cudaMemoryTypeDevice;
     cudaGetLastError();
-    // host arrays were checked for finite values at submit, by the caller's thread
+    // host arrays are staged and checked for finite values on the device
     if (!rdev) {
       if (cudaMemcpyAsync(handle_stage_rhs(h), R, sizeof(double) * N, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return FTGCR_ERR_CUDA;
@@ -222,7 +222,7 @@ struct ftgcr_server {
     r->x_host = !xdev;
     ftgcr_fault_plan plan{r->faults.data(), (int32_t)r->faults.size(), r->losses.data(), (int32_t)r->losses.size()};
     const bool any = !r->faults.empty() || !r->losses.empty();
-    return table_begin(tables[r->table], r->slot, h, R, X, any ? &plan : nullptr, st);
+    return table_begin(tables[r->table], r->slot, h, R, X, any ? &plan : nullptr, st, (rdev ? 0 : 1) | (xdev ? 0 : 2));
   }
   void complete(Request* r) {
     ftgcr_handle* h = r->entry->h;
@@ -390,21 +390,6 @@ int ftgcr_server_submit(ftgcr_server* srv, const ftgcr_grid* grid, const ftgcr_c
       }
     }
     r->faults.assign(plan->faults, plan->faults + plan->n);
-  }
-  // host arrays: reject non-finite values here, on the submitting thread, so
-  // that the scheduler thread only copies them
-  auto host_finite = [&](const double* a) {
-    cudaPointerAttributes at;
-    const bool dev = cudaPointerGetAttributes(&at, a) == cudaSuccess && at.type == cudaMemoryTypeDevice;
-    cudaGetLastError();
-    if (dev) return true;
-    for (long long i = 0; i < N; ++i)
-      if (!std::isfinite(a[i])) return false;
-    return true;
-  };
-  if (!host_finite(rhs) || !host_finite(x)) {
-    delete r;
-    return FTGCR_ERR_ARG;
   }
   r->key.grid = *grid;
   r->key.k = k;

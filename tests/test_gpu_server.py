@@ -2,7 +2,8 @@
 precisions, submitted while others run, each come back bitwise equal (solution
 and counters) to the same request solved alone; handles are reused across
 requests of the same shape with new coefficients; admission respects the
-memory budget; invalid requests are refused at submit."""
+memory budget; invalid requests are refused at submit; host inputs holding
+non-finite values complete with an argument error."""
 import time
 
 import numpy as np
@@ -161,10 +162,28 @@ def test_invalid_requests_are_refused_at_submit():
         assert ei.value.status == ftgcr.ERR_ARG
         with pytest.raises(ftgcr.FTGCRError):
             srv.submit(p.D, p.mu, p.R, np.zeros_like(p.R), k=0)
-        bad = p.R.copy()
-        bad[3, 5] = np.nan
-        with pytest.raises(ftgcr.FTGCRError) as ei:
-            srv.submit(p.D, p.mu, bad, np.zeros_like(p.R))  # non-finite host right-hand side
-        assert ei.value.status == ftgcr.ERR_ARG
         with pytest.raises(ftgcr.FTGCRError):
             srv.poll(12345)
+
+
+def test_non_finite_host_inputs_complete_with_an_argument_error():
+    # host arrays are staged and checked on the device: the request does not
+    # start, completes with ERR_ARG and leaves x as it was; the others run
+    p = inputs.hill_problem(64, 32)
+    xa, sa = _alone(p, "fp64", (), 4)
+    with ftgcr.Server(max_slots=2) as srv:
+        bad = p.R.copy()
+        bad[3, 5] = np.nan
+        x_bad = np.full_like(p.R, 0.25)
+        t_bad = srv.submit(p.D, p.mu, bad, x_bad)
+        x_inf = np.zeros_like(p.R)
+        x_inf[1, 1] = -np.inf
+        t_inf = srv.submit(p.D, p.mu, p.R, x_inf, precision="mixed")
+        x_ok = np.zeros_like(p.R)
+        t_ok = srv.submit(p.D, p.mu, p.R, x_ok)
+        st_bad, _ = srv.wait(t_bad, timeout=60)
+        st_inf, _ = srv.wait(t_inf, timeout=60)
+        st_ok, ss = srv.wait(t_ok, timeout=60)
+    assert st_bad == ftgcr.ERR_ARG and np.all(x_bad == 0.25)
+    assert st_inf == ftgcr.ERR_ARG
+    assert st_ok == ftgcr.OK and np.array_equal(x_ok, xa) and ss["steps"] == sa["steps"]
