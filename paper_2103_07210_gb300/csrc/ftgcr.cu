@@ -458,6 +458,7 @@ __global__ void k_begin_solve(SolveDev<T>* sd, BeginArgs b, int* active, int n_a
       SolveState S;
       memset(&S, 0, sizeof S);
       S.status = ST_NOT_CONVERGED;
+      S.refused = 1;
       *sd->result = S;
       active[slot] = 0;
       active[n_active + slot] = 0;
@@ -1130,11 +1131,30 @@ struct SlotTableImpl {
   LaunchCtl* h_ctl_in = nullptr;   // pinned: control block written before a launch
   LaunchCtl* h_ctl_out = nullptr;  // pinned: control block read back after it
   int* h_act = nullptr;            // pinned: active flags read back after it
+  SolveState* d_results = nullptr;  // [n] result records gathered after a launch
+  SolveState* h_results = nullptr;  // pinned: their copy
   int grid_cap = 0;
   std::vector<ftgcr_handle*> slot;
   std::vector<char> launched;  // slots occupied when the last launch was enqueued
-  std::vector<char> checked;   // slots whose staged inputs were checked for finite values
 };
+
+// The result records of the solves a table launch ran (mask bit s: slot s was
+// occupied), gathered into one array so that the scheduler reads them back
+// with a single copy.
+struct SlotMask {
+  unsigned int bits[32];  // 1024 slots
+};
+template <typename T>
+__global__ void k_gather_results(SolveDev<T>* const* solves, SlotMask mask, int n, SolveState* out) {
+  constexpr int W = sizeof(SolveState) / sizeof(int);
+  static_assert(sizeof(SolveState) % sizeof(int) == 0, "whole words");
+  for (int s = blockIdx.x; s < n; s += gridDim.x) {
+    if (!((mask.bits[s >> 5] >> (s & 31)) & 1u)) continue;
+    const int* src = reinterpret_cast<const int*>(solves[s]->result);
+    int* dst = reinterpret_cast<int*>(out + s);
+    for (int q = threadIdx.x; q < W; q += blockDim.x) dst[q] = __ldcg(src + q);
+  }
+}
 
 template <typename T>
 int table_run_impl(SlotTableImpl* t, int max_rounds, cudaStream_t st) {
@@ -1169,6 +1189,14 @@ int table_run_impl(SlotTableImpl* t, int max_rounds, cudaStream_t st) {
   if (rc) return rc;
   CK(cudaMemcpyAsync(t->h_ctl_out, t->d_ctl, sizeof(LaunchCtl), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(t->h_act, t->d_act, sizeof(int) * 2 * t->n, cudaMemcpyDeviceToHost, st));
+  SlotMask mask;
+  memset(&mask, 0, sizeof mask);
+  for (int s = 0; s < t->n; ++s)
+    if (t->launched[s]) mask.bits[s >> 5] |= 1u << (s & 31);
+  k_gather_results<T><<<std::min(t->n, 128), 128, 0, st>>>((SolveDev<T>* const*)t->d_solves, mask, t->n,
+                                                            t->d_results);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(t->h_results, t->d_results, sizeof(SolveState) * t->n, cudaMemcpyDeviceToHost, st));
   return FTGCR_OK;
 }
 
@@ -1182,7 +1210,7 @@ void report_timeout(const ftgcr_handle* h) {
 }
 
 int status_from_result(const ftgcr_handle* h) {
-  if (h->h_ctl->nonfinite) return FTGCR_ERR_ARG;
+  if (h->h_result->refused) return FTGCR_ERR_ARG;
   if (h->h_ctl->err) {
     report_timeout(h);
     return FTGCR_ERR_TIMEOUT;
@@ -1468,14 +1496,14 @@ int table_create(int precision, int max_slots, SlotTable** out) {
   t->n = max_slots;
   t->slot.assign(max_slots, nullptr);
   t->launched.assign(max_slots, 0);
-  t->checked.assign(max_slots, 0);
   CK(cudaGetDevice(&t->dev));
   const DeviceInfo di = device_info(t->dev);
   t->grid_cap = di.sms * 4;
   const size_t b_solves = align256(sizeof(void*) * max_slots), b_nt = align256(sizeof(int) * max_slots),
                b_act = align256(sizeof(int) * 2 * max_slots), b_ctl = align256(sizeof(LaunchCtl)),
-               b_diag = align256(sizeof(int) * 4 * t->grid_cap);
-  if (cudaMalloc(&t->buf, b_solves + b_nt + b_act + b_ctl + b_diag) != cudaSuccess) {
+               b_diag = align256(sizeof(int) * 4 * t->grid_cap), b_res = align256(sizeof(SolveState) * max_slots);
+  const size_t total = b_solves + b_nt + b_act + b_ctl + b_diag + b_res;
+  if (cudaMalloc(&t->buf, total) != cudaSuccess) {
     cudaGetLastError();
     delete t;
     return FTGCR_ERR_OOM;
@@ -1485,10 +1513,12 @@ int table_create(int precision, int max_slots, SlotTable** out) {
   t->d_act = (int*)(t->buf + b_solves + b_nt);
   t->d_ctl = (LaunchCtl*)(t->buf + b_solves + b_nt + b_act);
   t->d_diag = (int*)(t->buf + b_solves + b_nt + b_act + b_ctl);
-  int rc = cuda_status(cudaMemset(t->buf, 0, b_solves + b_nt + b_act + b_ctl + b_diag));
+  t->d_results = (SolveState*)(t->buf + b_solves + b_nt + b_act + b_ctl + b_diag);
+  int rc = cuda_status(cudaMemset(t->buf, 0, total));
   if (!rc) rc = cuda_status(cudaMallocHost(&t->h_ctl_in, sizeof(LaunchCtl)));
   if (!rc) rc = cuda_status(cudaMallocHost(&t->h_ctl_out, sizeof(LaunchCtl)));
   if (!rc) rc = cuda_status(cudaMallocHost(&t->h_act, sizeof(int) * 2 * max_slots));
+  if (!rc) rc = cuda_status(cudaMallocHost(&t->h_results, sizeof(SolveState) * max_slots));
   if (rc) {
     table_destroy(t);
     return rc;
@@ -1503,6 +1533,7 @@ void table_destroy(SlotTable* t) {
   if (t->h_ctl_in) cudaFreeHost(t->h_ctl_in);
   if (t->h_ctl_out) cudaFreeHost(t->h_ctl_out);
   if (t->h_act) cudaFreeHost(t->h_act);
+  if (t->h_results) cudaFreeHost(t->h_results);
   delete t;
 }
 
@@ -1531,7 +1562,6 @@ int table_begin(SlotTable* t, int slot, ftgcr_handle* h, const double* rhs, doub
     k_begin_solve<double><<<1, 64, 0, st>>>((SolveDev<double>*)h->sdev, b, t->d_act, t->n, slot, -1, nullptr, chk);
   CK(cudaGetLastError());
   t->slot[slot] = h;
-  t->checked[slot] = check != 0;
   return FTGCR_OK;
 }
 
@@ -1556,10 +1586,8 @@ int table_collect(SlotTable* t, cudaStream_t st, int* finished) {
     if (!h || !t->launched[s]) continue;  // begun after the launch: runs in the next one
     t->launched[s] = 0;
     if (!err && t->h_act[par * t->n + s]) continue;
-    CK(cudaMemcpy(h->h_result, h->result, sizeof(SolveState), cudaMemcpyDeviceToHost));
+    memcpy(h->h_result, t->h_results + s, sizeof(SolveState));  // gathered after the launch
     *h->h_ctl = *t->h_ctl_out;
-    h->h_ctl->nonfinite = 0;
-    if (t->checked[s]) CK(cudaMemcpy(&h->h_ctl->nonfinite, &h->ctl->nonfinite, sizeof(int), cudaMemcpyDeviceToHost));
     h->last_stream = st;
     h->solved = 1;
     h->last_status = err ? FTGCR_ERR_TIMEOUT : status_from_result(h);

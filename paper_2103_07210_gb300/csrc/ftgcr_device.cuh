@@ -94,6 +94,7 @@ struct SolveState {
   long long cycles, restarts, finj, fdet, lossev;
   int ndetect;
   int ecur;  // buffer of e, L(e) written by the latest PA / PF
+  int refused;  // the solve did not start: a staged host input was not finite
   long long detect_step[kMaxDetect];
   double detect_ratio[kMaxDetect];
 };

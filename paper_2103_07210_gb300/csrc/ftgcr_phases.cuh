@@ -66,7 +66,7 @@ struct LaunchCtl {
   int err;
   long long round0;
   long long round_end;
-  int nonfinite;  // a staged host input held a NaN or an infinity (the solve did not start)
+  int nonfinite;  // set by the check of staged host inputs: one held a NaN or an infinity
 };
 
 // Optional per-round trace: for every (round, CTA) the global timer at the
@@ -910,7 +910,6 @@ __device__ __forceinline__ void step_axpy(const SolveDev<T>& sd, const Ctx<T>& c
                                           PhaseSmem& ps, Acc<T>& an) {
   constexpr int W = V16<T>::W;
   constexpr int U = 2;
-  constexpr bool kMixed = sizeof(T) == 4;
   const int nlon = sd.nlon, nlat = sd.nlat, stride = row_stride(nlon);
   const int nrows = rt.h1 - rt.h0;
   const T beta = c.beta;
@@ -1101,10 +1100,8 @@ template <typename T, int KB>
 __device__ __forceinline__ void step_stencil(const SolveDev<T>& sd, const Ctx<T>& c, const RowTile& rt, const T* sm,
                                              PhaseSmem& ps, double* part_out, const Acc<T>* an, bool write_e) {
   constexpr int W = V16<T>::W;
-  constexpr int U = 2;
   constexpr bool kMixed = sizeof(T) == 4;
   const int nlon = sd.nlon, nlat = sd.nlat, stride = row_stride(nlon);
-  const int nrows = rt.h1 - rt.h0;
   Acc<T> ad[KB];
   Acc<T> ah, aq;  // mixed: <r', L(e)>, <L(e), L(e)>
   if (nlon % W == 0) {
