@@ -44,9 +44,9 @@ def algorithmic_bytes(steps: int, outer: int, k: int = K, s: int = 4, N: int = N
 
 # DRAM traffic per launch of the persistent kernel from one ncu capture, valid
 # only for the kernel sources it was taken on (sha256 of the CUDA sources).
-NCU_TRAFFIC = {"sources_sha256": "af036e32b7ef7f921abbee79a606ac7bd3c1dbda1bc1c941ca669c5a9deb2dd9",
-               "bytes_per_launch": 28047360 + 8733952,  # mixed 1024x512 (read + write)
-               "large": {"2048x1024": 2709789696 + 1348184320, "4096x2048": 15130663424 + 5215703040}}
+NCU_TRAFFIC = {"sources_sha256": "d83c7cb2a1548580ea11201981f248e148f09e5a36c1508e8f8ec4c1858ead6a",
+               "bytes_per_launch": 27692800 + 8123648,  # mixed 1024x512 (read + write)
+               "large": {"2048x1024": 2718225664 + 1348723968, "4096x2048": 15129805824 + 5215024640}}
 
 
 def sources_hash() -> str:
@@ -253,6 +253,55 @@ def bench_large(torch, ftgcr, dev, flush, sizes=((2048, 1024), (4096, 2048)), re
                                  "algorithmic_bytes": nb, "achieved_gbs": gbs, "frac": gbs / peak,
                                  "peak_kind": peak_kind, "converged": info["converged"],
                                  "residual_rel": info["res_final_true"] / info["norm_R"]}
+    return out
+
+
+# ------------------------------------------------------------------ steady state: a window of inner steps
+def bench_steady(torch, ftgcr, dev, flush, sizes=((1024, 512), (2048, 1024)), window=(100, 600), reps=3):
+    """Time per inner step away from the solve's start and end: the singular
+    mu = 0 hill problem (Section 4's pure Poisson form) needs thousands of
+    fault-free steps, so solves capped at window[0] and at window[1] executed
+    steps differ by window[1] - window[0] steps of the iteration proper
+    (whole Krylov cycles: both ends are multiples of k).  Per size and
+    precision: the event-timed difference per step, its algorithmic bytes
+    (14 + 1.5(k+1)) s N, and the bandwidth against the measured copy peak.
+    `clean` says the window held no detection and no refinement sweep."""
+    peak, peak_kind = read_peaks()
+    stream = torch.cuda.current_stream()
+    n0, n1 = window
+    assert n0 % K == 0 and n1 % K == 0
+    out = {}
+    for nlon, nlat in sizes:
+        p = inputs.hill_problem(nlon, nlat)
+        R = torch.from_numpy(p.R).to(dev)
+        N = nlon * nlat
+        for precision, s_bytes in (("mixed", 4), ("fp64", 8)):
+            t, infos = {}, {}
+            for cap in window:
+                x = torch.zeros_like(R)
+                with ftgcr.Solver(p.D, 0.0, k=K, tol=TOL, precision=precision, max_steps=cap) as s:
+                    s.solve_async(R, x, stream=stream)  # warm
+                    ms = []
+                    for _ in range(reps):
+                        x.zero_()
+                        flush.fill_(3)
+                        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        a.record(stream)
+                        s.solve_async(R, x, stream=stream)
+                        b.record(stream)
+                        torch.cuda.synchronize()
+                        ms.append(a.elapsed_time(b))
+                    t[cap], infos[cap] = float(np.median(ms)), s.stats()
+            i0, i1 = infos[n0], infos[n1]
+            per_step_us = (t[n1] - t[n0]) * 1e3 / (n1 - n0)
+            nb = (14 + 1.5 * (K + 1)) * s_bytes * N
+            gbs = nb / (per_step_us * 1e-6) / 1e9
+            clean = (i0["steps"] == n0 and i1["steps"] == n1 and not i1["detect_steps"]
+                     and i1["outer"] == i0["outer"] and not i1["converged"])
+            out[f"{precision}_{nlon}x{nlat}"] = {
+                "us_per_step": per_step_us, "algorithmic_bytes_per_step": nb, "achieved_gbs": gbs,
+                "frac": gbs / peak, "peak_kind": peak_kind, "clean": clean,
+                "ms": {str(n0): t[n0], str(n1): t[n1]}}
     return out
 
 
@@ -668,6 +717,8 @@ def run_ours(args):
             line["large_grids"] = bench_large(torch, ftgcr, dev, flush)
         if not args.no_ksweep and ws == 1:
             line["k_sweep"] = bench_ksweep(torch, ftgcr, dev, flush)
+        if not args.no_steady and ws == 1:
+            line["steady_state"] = bench_steady(torch, ftgcr, dev, flush)
         if not args.no_batch and ws == 1:
             line["batch"] = bench_batch(torch, ftgcr, dev)
         if not args.no_serving and ws == 1:
@@ -699,6 +750,7 @@ def main():
     ap.add_argument("--no-large", action="store_true", help="skip the 2048x1024 and 4096x2048 solves")
     ap.add_argument("--no-ksweep", action="store_true", help="skip the k sweep (protected vs unprotected)")
     ap.add_argument("--no-serving", action="store_true", help="skip the open-loop serving run")
+    ap.add_argument("--no-steady", action="store_true", help="skip the steady-state step window (mu = 0)")
     ap.add_argument("--serving-requests", type=int, default=2000)
     ap.add_argument("--serving-load", type=float, default=0.8, help="arrival rate / measured capacity")
     args = ap.parse_args()
