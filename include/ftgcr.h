@@ -73,11 +73,12 @@ extern "C" {
 typedef struct ftgcr_handle ftgcr_handle;
 
 typedef struct {
-  int32_t nlon;      /* >= 3; one latitude row with its two halo rows and, for the line
-                        preconditioner, their factors must fit in one SM's shared
-                        memory: nlon <= about 2150 (FTGCR_FP64) or 8500 (FTGCR_MIXED;
-                        beyond about 4350 only with split rounds, see
-                        FTGCR_FLAG_SPLIT_ROUNDS), else FTGCR_ERR_ARG */
+  int32_t nlon;      /* >= 3; one latitude row with its two halo rows (and, for the
+                        mixed path's line preconditioner, their factors) must fit in
+                        one SM's shared memory: nlon <= about 9600 (FTGCR_FP64; beyond
+                        about 2150 its line solve reads the factors from global
+                        memory) or 8500 (FTGCR_MIXED; beyond about 4350 only with
+                        split rounds, see FTGCR_FLAG_SPLIT_ROUNDS), else FTGCR_ERR_ARG */
   int32_t nlat;      /* >= 1 */
   double mu;         /* Helmholtz coefficient per unit area, >= 0 (mu > 0 makes -L definite) */
   int32_t precision; /* FTGCR_FP64 | FTGCR_MIXED */
@@ -179,6 +180,8 @@ typedef struct {
   int32_t status;          /* status of the last solve */
   int64_t loss_events;     /* data-loss events that fired */
   int32_t split_rounds;    /* 1: the solve ran split rounds (FTGCR_FLAG_SPLIT_ROUNDS) */
+  int32_t global_factors;  /* 1: FP64 line solve reading its factors from global memory
+                              (wide rows: staging them would thin the bands) */
 } ftgcr_stats_t;
 
 /* Create a solver for one grid and coefficient field.  Copies D, builds the

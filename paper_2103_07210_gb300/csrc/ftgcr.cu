@@ -554,16 +554,20 @@ struct SmemPlan {
   size_t bytes;
   long long cs_off;  // elements of the inner type
   int cs_clobber;
+  int gconsts;  // FP64 line solve: factors read from global memory, not staged
 };
-SmemPlan smem_plan(int nlon, int nlat, int nt, int mixed, size_t elem, int precond, int split, size_t limit) {
+SmemPlan smem_plan(int nlon, int nlat, int nt, int mixed, size_t elem, int precond, int split, size_t limit,
+                   int gconsts = 0) {
   const size_t h = (size_t)((nlat + nt - 1) / nt);
   const size_t st = (size_t)row_stride(nlon);
   const size_t per_row = mixed ? 32 * (size_t)chunk_len(nlon) : (size_t)nlon;  // chunk vs natural layout
   const size_t out = mixed ? (h + 2) * st * sizeof(double) : 0;
   const bool line = precond == FTGCR_PRECOND_LINE;
   SmemPlan p;
+  p.gconsts = 0;
   if (!split) {
-    const size_t consts = line ? 3 * (h + 2) * per_row * elem : 0;
+    p.gconsts = line && !mixed && gconsts;
+    const size_t consts = line && !p.gconsts ? 3 * (h + 2) * per_row * elem : 0;
     p.bytes = std::max((h + 2) * st * elem + consts, out);
     p.cs_off = (long long)((h + 2) * st);
     p.cs_clobber = 0;
@@ -591,14 +595,32 @@ SmemPlan smem_plan(int nlon, int nlat, int nt, int mixed, size_t elem, int preco
 // recompute at least twice its own rows as halo), or when one row with its
 // halo rows and their constants does not fit at all.
 void choose_tiling(int nlon, int nlat, int mixed, size_t elem, int precond, int flags, int tiles, int sms,
-                   size_t limit, int* nt_out, int* split_out) {
+                   size_t limit, int* nt_out, int* split_out, int* gconsts_out) {
   const int hpar = (nlat + sms - 1) / sms;  // band height the SM count alone gives
-  auto fit = [&](int split) {
+  auto fit = [&](int split, int gc = 0) {
     int nt = (nlat + hpar - 1) / hpar;
-    while (nt < nlat && smem_plan(nlon, nlat, nt, mixed, elem, precond, split, limit).bytes > limit)
+    while (nt < nlat && smem_plan(nlon, nlat, nt, mixed, elem, precond, split, limit, gc).bytes > limit)
       nt = std::min(nlat, nt + sms);
     return nt;
   };
+  // FP64 line solve: its factors are read from global memory when staging
+  // them would cut the bands below what the SM count gives (wide rows).  The
+  // row solves are chains of dependent FP64 operations that cost the same
+  // for all the rows of a tile side by side in lanes, so a CTA that walks
+  // several thin tiles a round pays the chains once per tile.
+  *gconsts_out = 0;
+  if (!mixed && precond == FTGCR_PRECOND_LINE) {
+    if (tiles > 0) {
+      *gconsts_out = smem_plan(nlon, nlat, std::min(tiles, nlat), mixed, elem, precond, 0, limit).bytes > limit;
+    } else {
+      const int nt0 = fit(0);
+      *gconsts_out = smem_plan(nlon, nlat, nt0, mixed, elem, precond, 0, limit).bytes > limit ||
+                     (nlat + nt0 - 1) / nt0 < hpar;
+    }
+    *split_out = 0;
+    *nt_out = tiles > 0 ? std::min(tiles, nlat) : fit(0, *gconsts_out);
+    return;
+  }
   int split = 0;
   if (mixed && precond == FTGCR_PRECOND_LINE) {
     if (flags & FTGCR_FLAG_SPLIT_ROUNDS)
@@ -891,6 +913,7 @@ int create_impl(ftgcr_handle* h, const double* D_host_or_dev, bool D_on_device) 
   sd.split = h->split;
   sd.cs_off = (int)h->plan.cs_off;
   sd.cs_clobber = h->plan.cs_clobber;
+  sd.cs_global = h->plan.gconsts;
   sd.Tx64 = h->Tx64;
   sd.Ty64 = h->Ty64;
   sd.muA64 = h->muA64;
@@ -1274,9 +1297,10 @@ static void fill_handle_params(ftgcr_handle* h, const ftgcr_grid* g, int32_t k, 
   h->flags = g->flags;
   const bool mixed = g->precision == FTGCR_MIXED;
   const size_t elem = mixed ? sizeof(float) : sizeof(double);
+  int gconsts = 0;
   choose_tiling(g->nlon, g->nlat, mixed, elem, g->precond, g->flags, g->tiles, sms, (size_t)smem_limit, &h->nt,
-                &h->split);
-  h->plan = smem_plan(h->nlon, h->nlat, h->nt, mixed, elem, h->precond, h->split, (size_t)smem_limit);
+                &h->split, &gconsts);
+  h->plan = smem_plan(h->nlon, h->nlat, h->nt, mixed, elem, h->precond, h->split, (size_t)smem_limit, gconsts);
 }
 
 int ftgcr_create(const ftgcr_grid* grid, const ftgcr_coeffs* coeffs, int32_t k, double tol, ftgcr_handle** out) {
@@ -1427,6 +1451,7 @@ int ftgcr_stats(ftgcr_handle* h, ftgcr_stats_t* out) {
   out->status = h->last_status;
   out->loss_events = S.lossev;
   out->split_rounds = h->split;
+  out->global_factors = h->plan.gconsts;
   return FTGCR_OK;
 }
 
@@ -1713,6 +1738,7 @@ extern "C" int ftgcr_solve_noalloc(const ftgcr_grid* grid, const double* D, int3
   sd.split = 0;
   sd.cs_off = (int)h.plan.cs_off;
   sd.cs_clobber = 0;
+  sd.cs_global = h.plan.gconsts;
   sd.Tx64 = h.Tx64;
   sd.Ty64 = h.Ty64;
   sd.muA64 = h.muA64;

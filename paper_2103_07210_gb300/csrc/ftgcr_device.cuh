@@ -149,6 +149,10 @@ struct SolveDev {
   // the staged line-solve constants in the dynamic shared memory (elements);
   // cs_clobber: the second pass's rows overlap them
   int split, cs_off, cs_clobber;
+  // FP64 line solve: the factors are read from global memory, not staged
+  // (wide rows, where staging them would leave bands thinner than the SM
+  // count gives)
+  int cs_global;
 };
 
 // --------------------------------------------------------------- helpers
@@ -935,6 +939,95 @@ static __device__ __noinline__ void line_solve_bwd_sh(const SolveDev<double>& sd
   }
   for (; i1 >= 0; --i1) {
     y = fma(-lds<double>(Uf(i1)), y, lds<double>(R(i1)));
+    sts(R(i1), y);
+  }
+  const double* tx = sd.Tx + (long long)j * n;
+  const double num = -lds<double>(R(n - 1)) + __ldg(tx + n - 1) * lds<double>(R(0)) + __ldg(tx + n - 2) * lds<double>(R(m - 1));
+  sts(R(n - 1), num / __ldg(sd.lrow + (long long)j * 4));
+}
+
+// The two chains with the factors l and u read from global memory (FP64 path,
+// wide rows).  The same operations on the same values as line_solve_fwd_sh and
+// line_solve_bwd_sh; the factor loads run two register blocks ahead of the
+// chain, so about 2 kLB dependent FP64 operations (64 cycles or more each)
+// cover their latency.
+static __device__ __noinline__ void line_solve_fwd_gl(int n, double* row_, const double* __restrict__ l) {
+  const int m = n - 1;
+  const unsigned rb = smem_addr(row_);
+  auto R = [&](int i) { return rb + 8u * (unsigned)sk(i); };
+  double y = -lds<double>(R(0));
+  sts(R(0), y);
+  const int nb = (m - 1) / kLB;  // whole blocks from i = 1
+  double la[kLB], lb[kLB];
+#pragma unroll
+  for (int q = 0; q < kLB; ++q) {
+    la[q] = nb > 0 ? __ldg(l + 1 + q) : 0.0;
+    lb[q] = nb > 1 ? __ldg(l + 1 + kLB + q) : 0.0;
+  }
+  for (int b = 0; b < nb; ++b) {
+    const int i0 = 1 + b * kLB;
+    double lv[kLB], bv[kLB];
+#pragma unroll
+    for (int q = 0; q < kLB; ++q) {
+      lv[q] = la[q];
+      la[q] = lb[q];
+    }
+    if (b + 2 < nb) {
+#pragma unroll
+      for (int q = 0; q < kLB; ++q) lb[q] = __ldg(l + i0 + 2 * kLB + q);
+    }
+#pragma unroll
+    for (int q = 0; q < kLB; ++q) bv[q] = -lds<double>(R(i0 + q));
+#pragma unroll
+    for (int q = 0; q < kLB; ++q) {
+      y = fma(-lv[q], y, bv[q]);
+      bv[q] = y;
+    }
+#pragma unroll
+    for (int q = 0; q < kLB; ++q) sts(R(i0 + q), bv[q]);
+  }
+  for (int i0 = 1 + nb * kLB; i0 < m; ++i0) {
+    y = fma(-__ldg(l + i0), y, -lds<double>(R(i0)));
+    sts(R(i0), y);
+  }
+}
+static __device__ __noinline__ void line_solve_bwd_gl(const SolveDev<double>& sd, int j, double* row_,
+                                                      const double* __restrict__ u) {
+  const int n = sd.nlon, m = n - 1;
+  const unsigned rb = smem_addr(row_);
+  auto R = [&](int i) { return rb + 8u * (unsigned)sk(i); };
+  double y = lds<double>(R(m - 1));
+  const int nb = (m - 1) / kLB;  // whole blocks descending from i = m - 2
+  double ua[kLB], ub[kLB];
+#pragma unroll
+  for (int q = 0; q < kLB; ++q) {
+    ua[q] = nb > 0 ? __ldg(u + m - 2 - q) : 0.0;
+    ub[q] = nb > 1 ? __ldg(u + m - 2 - kLB - q) : 0.0;
+  }
+  for (int b = 0; b < nb; ++b) {
+    const int i1 = m - 2 - b * kLB;  // block [i1 - kLB + 1, i1], descending
+    double uv[kLB], gv[kLB];
+#pragma unroll
+    for (int q = 0; q < kLB; ++q) {
+      uv[q] = ua[q];
+      ua[q] = ub[q];
+    }
+    if (b + 2 < nb) {
+#pragma unroll
+      for (int q = 0; q < kLB; ++q) ub[q] = __ldg(u + i1 - 2 * kLB - q);
+    }
+#pragma unroll
+    for (int q = 0; q < kLB; ++q) gv[q] = lds<double>(R(i1 - q));
+#pragma unroll
+    for (int q = 0; q < kLB; ++q) {
+      y = fma(-uv[q], y, gv[q]);
+      gv[q] = y;
+    }
+#pragma unroll
+    for (int q = 0; q < kLB; ++q) sts(R(i1 - q), gv[q]);
+  }
+  for (int i1 = m - 2 - nb * kLB; i1 >= 0; --i1) {
+    y = fma(-__ldg(u + i1), y, lds<double>(R(i1)));
     sts(R(i1), y);
   }
   const double* tx = sd.Tx + (long long)j * n;

@@ -648,6 +648,9 @@ __device__ __forceinline__ long long consts_per_row(const SolveDev<T>& sd) {
 template <typename T>
 __device__ __forceinline__ void stage_line_consts(const SolveDev<T>& sd, int h0, int h1, T* cs) {
   if (sd.precond != PC_LINE) return;
+  if constexpr (sizeof(T) == 8) {
+    if (sd.cs_global) return;  // read from global memory by the row solves
+  }
   const long long per = consts_per_row(sd);
   const int nrows = h1 - h0;
   const long long nel = (long long)nrows * per;
@@ -705,18 +708,27 @@ __device__ __forceinline__ void precond_tile(const SolveDev<T>& sd, int h0, int 
   if constexpr (sizeof(T) == 8) {
     if (sd.precond == PC_LINE) {
       const int n = sd.nlon, m = n - 1;
-      for (int jr = threadIdx.x; jr < nrows; jr += kThreads)
-        line_solve_fwd_sh(n, sm + jr * stride, staged_consts(sd, cs, nrows, jr).cb);
+      const bool gl = sd.cs_global;
+      for (int jr = threadIdx.x; jr < nrows; jr += kThreads) {
+        if (gl)
+          line_solve_fwd_gl(n, sm + jr * stride, sd.lc + (long long)(h0 + jr) * n);
+        else
+          line_solve_fwd_sh(n, sm + jr * stride, staged_consts(sd, cs, nrows, jr).cb);
+      }
       __syncthreads();
       // the backward step's products g_i winv_i, all rows at once
       for (int idx = threadIdx.x; idx < nrows * m; idx += kThreads) {
         const int jr = idx / m, i = idx - jr * m;
         T* row = sm + jr * stride;
-        row[sk(i)] = row[sk(i)] * staged_consts(sd, cs, nrows, jr).cw[i];
+        row[sk(i)] = row[sk(i)] * (gl ? __ldg(sd.lw + (long long)(h0 + jr) * n + i) : staged_consts(sd, cs, nrows, jr).cw[i]);
       }
       __syncthreads();
-      for (int jr = threadIdx.x; jr < nrows; jr += kThreads)
-        line_solve_bwd_sh(sd, h0 + jr, sm + jr * stride, staged_consts(sd, cs, nrows, jr).cz);
+      for (int jr = threadIdx.x; jr < nrows; jr += kThreads) {
+        if (gl)
+          line_solve_bwd_gl(sd, h0 + jr, sm + jr * stride, sd.lu + (long long)(h0 + jr) * n);
+        else
+          line_solve_bwd_sh(sd, h0 + jr, sm + jr * stride, staged_consts(sd, cs, nrows, jr).cz);
+      }
       __syncthreads();
       // bordering, x_i = y_i - x_{n-1} z_i, all rows at once
       for (int idx = threadIdx.x; idx < nrows * m; idx += kThreads) {

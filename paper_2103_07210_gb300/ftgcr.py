@@ -84,7 +84,7 @@ class Stats(ctypes.Structure):
                 ("res0", ctypes.c_double), ("res_final_rec", ctypes.c_double), ("res_final_true", ctypes.c_double),
                 ("norm_R", ctypes.c_double), ("bytes_resident", ctypes.c_int64), ("bytes_backup", ctypes.c_int64),
                 ("tiles", ctypes.c_int32), ("status", ctypes.c_int32), ("loss_events", ctypes.c_int64),
-                ("split_rounds", ctypes.c_int32)]
+                ("split_rounds", ctypes.c_int32), ("global_factors", ctypes.c_int32)]
 
 
 class ServerInfo(ctypes.Structure):
@@ -313,7 +313,7 @@ class Solver:
                     detect_ratio=[s.detect_ratio[i] for i in range(n)], res0=s.res0, res_final_rec=s.res_final_rec,
                     res_final_true=s.res_final_true, norm_R=s.norm_R, bytes_resident=s.bytes_resident,
                     bytes_backup=s.bytes_backup, tiles=s.tiles, status=s.status, loss_events=s.loss_events,
-                    split_rounds=bool(s.split_rounds))
+                    split_rounds=bool(s.split_rounds), global_factors=bool(s.global_factors))
 
     def apply_operator(self, inp, out, stream=None):
         ip, ik = _ptr(inp)
@@ -345,7 +345,8 @@ def _stats_dict(s: Stats) -> dict:
                 detect_steps=[s.detect_step[i] for i in range(n)], detect_ratio=[s.detect_ratio[i] for i in range(n)],
                 res0=s.res0, res_final_rec=s.res_final_rec, res_final_true=s.res_final_true, norm_R=s.norm_R,
                 bytes_resident=s.bytes_resident, bytes_backup=s.bytes_backup, tiles=s.tiles, status=s.status,
-                loss_events=s.loss_events, split_rounds=bool(s.split_rounds))
+                loss_events=s.loss_events, split_rounds=bool(s.split_rounds),
+                global_factors=bool(s.global_factors))
 
 
 def tune(D, mu, k=4, tol=1e-10, precision="mixed", precond="line", concurrency=1, max_steps=0, inner_tol=0.0,

@@ -4,8 +4,11 @@ row: the same results as the oracle (FP64: identical decisions, solution
 rel <= 1e-10; mixed, one-pass rounds: converged at tol 1e-10 with a true residual below it,
 solution within 1e-7 of the oracle's at tol 1e-12 -- these strongly
 anisotropic grids keep the true residual of any solve near 1e-12 relative, so
-the mixed path's FP64 refinement cannot be asked for 1e-13 here).  Rows too
-wide for one band on chip are refused at creation."""
+the mixed path's FP64 refinement cannot be asked for 1e-13 here).  FP64 solves
+whose staged factors would thin the bands below what the SM count gives (or
+not fit at all) read the factors from global memory: the same decisions and
+solution as the oracle.  Rows too wide for one band on chip are refused at
+creation."""
 import numpy as np
 import pytest
 
@@ -17,8 +20,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def _solve(p, k, tol, precision, faults=()):
-    with ftgcr.Solver(p.D, p.mu, k=k, tol=tol, precision=precision) as s:
+def _solve(p, k, tol, precision, faults=(), tiles=0):
+    with ftgcr.Solver(p.D, p.mu, k=k, tol=tol, precision=precision, tiles=tiles) as s:
         R = torch.from_numpy(p.R).cuda()
         x = torch.zeros_like(R)
         st = s.solve(R, x, faults=faults)
@@ -30,8 +33,26 @@ def test_fp64_wide_rows_match_oracle():
     faults = [(4, "r", 40000, 62)]
     o = oracle.ftgcr(p.D, p.R, p.mu, 4, 1e-10, faults=faults)
     st, x, s = _solve(p, 4, 1e-10, "fp64", faults)
-    assert s["tiles"] == 32
+    assert s["tiles"] == 32 and not s["global_factors"]
     assert s["steps"] == o["steps"] and s["detect_steps"] == o["detect_steps"] and s["converged"] == o["converged"]
+    assert rel_err(x, o["x"]) <= 1e-10
+
+
+@pytest.mark.parametrize("nlon,nlat,k,tiles,rows", [
+    (2048, 320, 4, 0, 3),   # staged factors: 1-row bands; the SM count gives 3
+    (4096, 40, 4, 0, 1),    # staged factors do not fit beside even one row
+    (1024, 64, 3, 8, 8),    # 8-row bands asked for: too tall with staged factors
+    (1000, 37, 5, 5, 8),    # ragged: nlon not a multiple of the register block, last band short
+])
+def test_fp64_global_factors_match_oracle(nlon, nlat, k, tiles, rows):
+    p = inputs.hill_problem(nlon, nlat, rhs="random", seed=nlon + nlat)
+    N = nlon * nlat
+    faults = [(3, "r", N // 3, 62), (6, "ap", N // 2, 61)]
+    o = oracle.ftgcr(p.D, p.R, p.mu, k, 1e-10, faults=faults)
+    st, x, s = _solve(p, k, 1e-10, "fp64", faults, tiles=tiles)
+    assert s["global_factors"] and -(-nlat // s["tiles"]) == rows, s
+    assert s["steps"] == o["steps"] and s["detect_steps"] == o["detect_steps"] and s["converged"] == o["converged"]
+    assert len(s["detect_steps"]) >= 1
     assert rel_err(x, o["x"]) <= 1e-10
 
 
@@ -45,8 +66,9 @@ def test_mixed_wide_rows_match_oracle():
 
 
 def test_rows_too_wide_for_one_band_are_refused():
-    # FP64 beyond about 2150 columns; mixed beyond about 8500 (split rounds)
-    for (nlon, nlat), prec in (((8192, 8), "fp64"), ((16384, 4), "mixed")):
+    # FP64 beyond about 9600 columns (factors from global memory); mixed beyond
+    # about 8500 (split rounds)
+    for (nlon, nlat), prec in (((12288, 4), "fp64"), ((16384, 4), "mixed")):
         p = inputs.hill_problem(nlon, nlat)
         with pytest.raises(ftgcr.FTGCRError) as ei:
             ftgcr.Solver(p.D, p.mu, precision=prec)
