@@ -958,11 +958,15 @@ static __device__ __noinline__ void line_solve_fwd_gl(int n, double* row_, const
   double y = -lds<double>(R(0));
   sts(R(0), y);
   const int nb = (m - 1) / kLB;  // whole blocks from i = 1
-  double la[kLB], lb[kLB];
+  double la[kLB], lb[kLB], bn[kLB];
 #pragma unroll
   for (int q = 0; q < kLB; ++q) {
     la[q] = nb > 0 ? __ldg(l + 1 + q) : 0.0;
     lb[q] = nb > 1 ? __ldg(l + 1 + kLB + q) : 0.0;
+  }
+  if (nb > 0) {
+#pragma unroll
+    for (int q = 0; q < kLB; ++q) bn[q] = -lds<double>(R(1 + q));
   }
   for (int b = 0; b < nb; ++b) {
     const int i0 = 1 + b * kLB;
@@ -971,13 +975,16 @@ static __device__ __noinline__ void line_solve_fwd_gl(int n, double* row_, const
     for (int q = 0; q < kLB; ++q) {
       lv[q] = la[q];
       la[q] = lb[q];
+      bv[q] = bn[q];
     }
     if (b + 2 < nb) {
 #pragma unroll
       for (int q = 0; q < kLB; ++q) lb[q] = __ldg(l + i0 + 2 * kLB + q);
     }
+    if (b + 1 < nb) {
 #pragma unroll
-    for (int q = 0; q < kLB; ++q) bv[q] = -lds<double>(R(i0 + q));
+      for (int q = 0; q < kLB; ++q) bn[q] = -lds<double>(R(i0 + kLB + q));
+    }
 #pragma unroll
     for (int q = 0; q < kLB; ++q) {
       y = fma(-lv[q], y, bv[q]);
@@ -998,11 +1005,15 @@ static __device__ __noinline__ void line_solve_bwd_gl(const SolveDev<double>& sd
   auto R = [&](int i) { return rb + 8u * (unsigned)sk(i); };
   double y = lds<double>(R(m - 1));
   const int nb = (m - 1) / kLB;  // whole blocks descending from i = m - 2
-  double ua[kLB], ub[kLB];
+  double ua[kLB], ub[kLB], gn[kLB];
 #pragma unroll
   for (int q = 0; q < kLB; ++q) {
     ua[q] = nb > 0 ? __ldg(u + m - 2 - q) : 0.0;
     ub[q] = nb > 1 ? __ldg(u + m - 2 - kLB - q) : 0.0;
+  }
+  if (nb > 0) {
+#pragma unroll
+    for (int q = 0; q < kLB; ++q) gn[q] = lds<double>(R(m - 2 - q));
   }
   for (int b = 0; b < nb; ++b) {
     const int i1 = m - 2 - b * kLB;  // block [i1 - kLB + 1, i1], descending
@@ -1011,13 +1022,16 @@ static __device__ __noinline__ void line_solve_bwd_gl(const SolveDev<double>& sd
     for (int q = 0; q < kLB; ++q) {
       uv[q] = ua[q];
       ua[q] = ub[q];
+      gv[q] = gn[q];
     }
     if (b + 2 < nb) {
 #pragma unroll
       for (int q = 0; q < kLB; ++q) ub[q] = __ldg(u + i1 - 2 * kLB - q);
     }
+    if (b + 1 < nb) {
 #pragma unroll
-    for (int q = 0; q < kLB; ++q) gv[q] = lds<double>(R(i1 - q));
+      for (int q = 0; q < kLB; ++q) gn[q] = lds<double>(R(i1 - kLB - q));
+    }
 #pragma unroll
     for (int q = 0; q < kLB; ++q) {
       y = fma(-uv[q], y, gv[q]);
