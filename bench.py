@@ -71,6 +71,29 @@ def read_peaks():
         return 6800.0, "fallback"
 
 
+def measure_peaks_in_run(torch, ftgcr, dev, reps=5):
+    """The two ceilings measured in this process, beside MEASURED_PEAKS.json:
+    a 2 GiB device-to-device copy (read + write bytes over the event time,
+    best of `reps`) and the library's FP64 FMA-rate probe (best of 3)."""
+    n = (1 << 31) // 4
+    a = torch.empty(n, dtype=torch.float32, device=dev).fill_(1.0)
+    b = torch.empty_like(a)
+    b.copy_(a)
+    stream = torch.cuda.current_stream()
+    best = 1e30
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.copy_(a)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    copy_gbs = 2 * 4 * n / (best * 1e-3) / 1e9
+    del a, b
+    fma = max(ftgcr.fp64_fma_rate(4096) for _ in range(3))
+    return {"copy_gbs": copy_gbs, "copy_bytes": 2 * 4 * n, "fp64_fma_tflops": fma}
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
@@ -685,6 +708,22 @@ def run_ours(args):
     achieved = bytes_launch / (kern_ms * 1e-3) / 1e9
     traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["sources_sha256"] == sources_hash() else None
 
+    # the FP64 path against the two ceilings measured in this run: its
+    # algorithmic flops, about (32 + 6m) per point and step with m = (k+1)/2
+    # directions on average (stencil 10, line solve 8, axpy and norm 6, the
+    # dots and recurrences 6m), over the FP64 FMA rate; its algorithmic bytes,
+    # 21.5 FP64 vectors per step, over the copy rate
+    peaks_run = measure_peaks_in_run(torch, ftgcr, dev) if ws == 1 else None
+    t64 = float(np.mean(ms_64)) * 1e-3
+    fl64 = info_64["steps"] * (32 + 6 * (K + 1) / 2) * NLON * NLAT
+    by64 = algorithmic_bytes(info_64["steps"], -1, s=8)
+    fp64_roof = None
+    if peaks_run:
+        fp64_roof = {"bound": "alu", "achieved": fl64 / t64 / 1e12, "peak": peaks_run["fp64_fma_tflops"],
+                     "unit": "TFLOP/s", "frac": fl64 / t64 / 1e12 / peaks_run["fp64_fma_tflops"],
+                     "peak_kind": "measured in this run (FP64 FMA probe)", "flops_per_launch": fl64,
+                     "hbm_achieved_gbs": by64 / t64 / 1e9, "hbm_frac_of_copy": by64 / t64 / 1e9 / peaks_run["copy_gbs"]}
+
     # correctness of the timed result, by a property that holds at any size
     res_rel = info_mx["res_final_true"] / info_mx["norm_R"]
 
@@ -701,7 +740,8 @@ def run_ours(args):
             "latency_ms": {"p50": float(np.percentile(ms_mx, 50)), "p99": float(np.percentile(ms_mx, 99))},
             "fp64_path": {"solves_per_s": 1e3 / float(np.mean(ms_64)),
                           "iters_per_s": info_64["steps"] * 1e3 / float(np.mean(ms_64)),
-                          "steps_per_solve": info_64["steps"]},
+                          "steps_per_solve": info_64["steps"],
+                          "roofline": fp64_roof},
             "mixed_over_fp64": float(np.mean(ms_64)) / float(np.mean(ms_mx)),
             "residual_rel": res_rel,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -711,6 +751,7 @@ def run_ours(args):
             "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": 2 * 8 * NLON * NLAT,
                     "d2h_bytes_per_step": 8 * NLON * NLAT + 2 * 4096},
             "gpu_launches": 2 * args.steps,
+            "peaks_in_run": peaks_run,
             "clocks": clocks,
         }
         if not args.no_large and ws == 1:

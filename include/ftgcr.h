@@ -369,6 +369,17 @@ int ftgcr_server_info(ftgcr_server* srv, ftgcr_server_info_t* out);
  * every handle and buffer is freed. */
 int ftgcr_server_destroy(ftgcr_server* srv);
 
+/* Measurement probe, off every solve path: the device's FP64 fused
+ * multiply-add rate in TFLOP/s (2 flops per FMA), from one launch of
+ * independent FMA chains filling every SM, timed with CUDA events on
+ * `stream` (NULL: the default stream).  It is the ceiling of the FP64 path's
+ * arithmetic: its row-solve chains and compensated dot products run on the
+ * FP64 pipe.  iters: FMAs per chain, 1 .. 2^24 (about 4096 takes a few ms on
+ * GB300).  Blocks the host until the launch ends.  Errors: FTGCR_ERR_ARG (iters
+ * out of range or tflops NULL), FTGCR_ERR_OOM, FTGCR_ERR_CUDA; *tflops is 0
+ * on error. */
+int ftgcr_fp64_fma_rate(int32_t iters, double* tflops, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,7 +21,7 @@ _INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libftgcr.so")
 SOURCES = ["ftgcr.cu", "ftgcr_k4.cu", "ftgcr_k8.cu", "ftgcr_k16.cu", "ftgcr_k4s.cu", "ftgcr_k8s.cu", "ftgcr_k16s.cu",
-           "ftgcr_server.cu", "ftgcr_tune.cu"]
+           "ftgcr_server.cu", "ftgcr_tune.cu", "ftgcr_probe.cu"]
 HEADERS = ["ftgcr_device.cuh", "ftgcr_phases.cuh", "ftgcr_instances.h", "ftgcr_serve.h"]
 # --fmad=false: device multiply-adds are fused only where the code says fma();
 # -ffp-contract=off: the same for the host-side geometry (GCC contracts by
@@ -43,7 +43,7 @@ EXPORTS = ["ftgcr_create", "ftgcr_solve", "ftgcr_solve_async", "ftgcr_stats", "f
            "ftgcr_apply_operator", "ftgcr_apply_precond", "ftgcr_footprint", "ftgcr_destroy", "ftgcr_error_string",
            "ftgcr_solve_noalloc", "ftgcr_set_coeffs", "ftgcr_server_create", "ftgcr_server_submit",
            "ftgcr_server_poll", "ftgcr_server_wait", "ftgcr_server_next", "ftgcr_server_info",
-           "ftgcr_server_destroy", "ftgcr_tune"]
+           "ftgcr_server_destroy", "ftgcr_tune", "ftgcr_fp64_fma_rate"]
 NOALLOC_MAX_POINTS, NOALLOC_MAX_K = 16384, 4
 TUNE_MAX_CONCURRENCY = 256
 
@@ -172,6 +172,7 @@ def lib():
         L.ftgcr_server_next.argtypes = [vp, dbl, ctypes.POINTER(i64), ctypes.POINTER(Stats)]
         L.ftgcr_server_info.argtypes = [vp, ctypes.POINTER(ServerInfo)]
         L.ftgcr_server_destroy.argtypes = [vp]
+        L.ftgcr_fp64_fma_rate.argtypes = [i32, ctypes.POINTER(dbl), vp]
         for f in EXPORTS:
             if not hasattr(L, f):
                 raise RuntimeError(f"libftgcr.so does not export {f}")
@@ -385,6 +386,16 @@ def solve_noalloc(D, mu, rhs, x, k=4, tol=1e-10, max_steps=0, tiles=0, stream=No
     if st < 0:
         raise FTGCRError(st, "ftgcr_solve_noalloc")
     return st, _stats_dict(s)
+
+
+def fp64_fma_rate(iters=4096, stream=None) -> float:
+    """The device's measured FP64 fused multiply-add rate in TFLOP/s
+    (ftgcr_fp64_fma_rate): the ceiling of the FP64 path's arithmetic."""
+    t = ctypes.c_double(0.0)
+    st = lib().ftgcr_fp64_fma_rate(int(iters), ctypes.byref(t), _stream_ptr(stream))
+    if st < 0:
+        raise FTGCRError(st, "ftgcr_fp64_fma_rate")
+    return t.value
 
 
 def solve_batch(solvers, rhs, xs, faults=None, stream=None, losses=None) -> None:

@@ -105,3 +105,14 @@ def test_tune_refuses_bad_arguments_before_any_device_call():
     import torch
     if not torch.cuda.is_available():
         assert L.ftgcr_tune(ctypes.byref(g), ctypes.byref(c), 4, 1e-10, 1, ctypes.byref(t)) == ftgcr.ERR_CUDA
+
+
+def test_fma_rate_probe_refuses_bad_arguments_before_any_device_call():
+    L = ftgcr.lib()
+    t = ctypes.c_double(1.0)
+    for iters in (0, -1, (1 << 24) + 1):
+        assert L.ftgcr_fp64_fma_rate(iters, ctypes.byref(t), None) == ftgcr.ERR_ARG
+    assert L.ftgcr_fp64_fma_rate(16, None, None) == ftgcr.ERR_ARG
+    import torch
+    if not torch.cuda.is_available():
+        assert L.ftgcr_fp64_fma_rate(16, ctypes.byref(t), None) == ftgcr.ERR_CUDA and t.value == 0.0
