@@ -679,6 +679,7 @@ struct ftgcr_handle {
   SolveDev<float> sd32{};
   size_t smem = 0;
   int split = 0;  // split rounds (see choose_tiling)
+  int wide = 0;   // runs in the wide-row kernel instance (split rounds, or FP64 factors from global memory)
   SmemPlan plan{};
   int grid = 0;
   cudaStream_t last_stream = nullptr;
@@ -692,11 +693,12 @@ namespace {
 int kbound(int k) { return k <= 4 ? 4 : (k <= 8 ? 8 : 16); }
 
 // The persistent kernel instances live in their own translation units
-// (ftgcr_k4.cu, ftgcr_k8.cu, ftgcr_k16.cu and their split-round twins) so that
-// they compile in parallel.
+// (ftgcr_k4.cu, ftgcr_k8.cu, ftgcr_k16.cu, their mixed split-round twins
+// ftgcr_k*s.cu and their FP64 wide-row twins ftgcr_k*w.cu) so that they
+// compile in parallel.  wide: the wide-row instance.
 template <typename T>
-const void* kernel_ptr(int kb, int split) {
-  return ftgcr::persistent_kernel_ptr(kb, sizeof(T) == 8, split != 0);
+const void* kernel_ptr(int kb, int wide) {
+  return ftgcr::persistent_kernel_ptr(kb, sizeof(T) == 8, wide != 0);
 }
 
 // The dynamic shared memory attribute of a kernel is process-wide: only ever
@@ -943,16 +945,16 @@ int create_impl(ftgcr_handle* h, const double* D_host_or_dev, bool D_on_device) 
 
   (void)mixed;
   h->smem = h->plan.bytes;
-  int rc = configure_kernel<T>(kbound(h->k), h->split, std::max<size_t>(h->smem, 1));
+  int rc = configure_kernel<T>(kbound(h->k), h->wide, std::max<size_t>(h->smem, 1));
   if (rc) return rc;
   int occ = 0;
-  rc = occupancy<T>(kbound(h->k), h->split, h->smem, &occ);
+  rc = occupancy<T>(kbound(h->k), h->wide, h->smem, &occ);
   if (rc) return rc;
   if (occ < 1) return FTGCR_ERR_ARG;
   {
     // the per-thread stack must hold the kernel's spill frame
     cudaFuncAttributes fa;
-    CK(cudaFuncGetAttributes(&fa, kernel_ptr<T>(kbound(h->k), h->split)));
+    CK(cudaFuncGetAttributes(&fa, kernel_ptr<T>(kbound(h->k), h->wide)));
     size_t cur = 0;
     CK(cudaDeviceGetLimit(&cur, cudaLimitStackSize));
     if (fa.localSizeBytes + 256 > cur) CK(cudaDeviceSetLimit(cudaLimitStackSize, fa.localSizeBytes + 256));
@@ -1054,7 +1056,7 @@ int solve_async_impl(ftgcr_handle* h, const double* R, const double* x0, double*
   // every inner step takes two rounds, every refinement sweep a few more
   const int max_rounds = (int)std::min<long long>(1 << 30, 2 * h->max_steps + 8 * ((long long)h->max_outer + 2) + 16);
   int rc = launch_persistent<T>(kbound(h->k), (SolveDev<T>* const*)h->sdev_arr, h->nt_dev, h->active, 1, h->ctl,
-                                h->diag, max_rounds, h->grid, h->smem, h->split, st);
+                                h->diag, max_rounds, h->grid, h->smem, h->wide, st);
   if (rc) return rc;
   CK(cudaMemcpyAsync(h->h_result, h->result, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(LaunchCtl), cudaMemcpyDeviceToHost, st));
@@ -1078,7 +1080,7 @@ int solve_batch_impl(ftgcr_handle* const* hs, const double* const* rhs, double* 
   long long max_steps = 0, total_tiles = 0;
   int max_outer = 0, split = 0;
   for (int i = 0; i < n; ++i) {
-    split |= hs[i]->split;
+    split |= hs[i]->wide;
     kb = std::max(kb, kbound(hs[i]->k));
     smem = std::max(smem, hs[i]->smem);
     max_steps = std::max(max_steps, hs[i]->max_steps);
@@ -1187,7 +1189,7 @@ int table_run_impl(SlotTableImpl* t, int max_rounds, cudaStream_t st) {
   int split = 0;
   for (ftgcr_handle* h : t->slot)
     if (h) {
-      split |= h->split;
+      split |= h->wide;
       kb = std::max(kb, kbound(h->k));
       smem = std::max(smem, h->smem);
       tiles += h->nt;
@@ -1301,6 +1303,7 @@ static void fill_handle_params(ftgcr_handle* h, const ftgcr_grid* g, int32_t k, 
   choose_tiling(g->nlon, g->nlat, mixed, elem, g->precond, g->flags, g->tiles, sms, (size_t)smem_limit, &h->nt,
                 &h->split, &gconsts);
   h->plan = smem_plan(h->nlon, h->nlat, h->nt, mixed, elem, h->precond, h->split, (size_t)smem_limit, gconsts);
+  h->wide = h->split || h->plan.gconsts;
 }
 
 int ftgcr_create(const ftgcr_grid* grid, const ftgcr_coeffs* coeffs, int32_t k, double tol, ftgcr_handle** out) {
@@ -1767,16 +1770,16 @@ extern "C" int ftgcr_solve_noalloc(const ftgcr_grid* grid, const double* D, int3
 
   const int kb = kbound(h.k);
   h.smem = h.plan.bytes;
-  rc = configure_kernel<double>(kb, 0, std::max<size_t>(h.smem, 1));
+  rc = configure_kernel<double>(kb, h.wide, std::max<size_t>(h.smem, 1));
   if (rc) return rc;
   int occ = 0;
-  rc = occupancy<double>(kb, 0, h.smem, &occ);
+  rc = occupancy<double>(kb, h.wide, h.smem, &occ);
   if (rc) return rc;
   if (occ < 1) return FTGCR_ERR_ARG;
   {
     // no stack resize here (it may allocate): the current limit must do
     cudaFuncAttributes fa;
-    CK(cudaFuncGetAttributes(&fa, kernel_ptr<double>(kb, 0)));
+    CK(cudaFuncGetAttributes(&fa, kernel_ptr<double>(kb, h.wide)));
     size_t cur = 0;
     CK(cudaDeviceGetLimit(&cur, cudaLimitStackSize));
     if (fa.localSizeBytes > cur) return FTGCR_ERR_ARG;
@@ -1796,7 +1799,7 @@ extern "C" int ftgcr_solve_noalloc(const ftgcr_grid* grid, const double* D, int3
   a.trace_rounds = 0;
   a.diag = h.diag;
   void* args[] = {&a};
-  CK(cudaLaunchCooperativeKernel(kernel_ptr<double>(kb, 0), dim3(grid_ctas), dim3(kThreads), args, h.smem, st));
+  CK(cudaLaunchCooperativeKernel(kernel_ptr<double>(kb, h.wide), dim3(grid_ctas), dim3(kThreads), args, h.smem, st));
   SolveState res;
   LaunchCtl ctl;
   CK(cudaMemcpyAsync(&res, h.result, sizeof res, cudaMemcpyDeviceToHost, st));

@@ -948,9 +948,13 @@ static __device__ __noinline__ void line_solve_bwd_sh(const SolveDev<double>& sd
 
 // The two chains with the factors l and u read from global memory (FP64 path,
 // wide rows).  The same operations on the same values as line_solve_fwd_sh and
-// line_solve_bwd_sh; the factor loads run two register blocks ahead of the
-// chain, so about 2 kLB dependent FP64 operations (64 cycles or more each)
-// cover their latency.
+// line_solve_bwd_sh.  The factor loads run two register blocks ahead of the
+// chain, in three buffers taken in turn (a copy between buffers would wait for
+// the load), so about 2 kLB dependent FP64 operations (64 cycles or more each)
+// cover their latency; the caller has asked L2 for the rows beforehand.
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
 static __device__ __noinline__ void line_solve_fwd_gl(int n, double* row_, const double* __restrict__ l) {
   const int m = n - 1;
   const unsigned rb = smem_addr(row_);
@@ -958,33 +962,17 @@ static __device__ __noinline__ void line_solve_fwd_gl(int n, double* row_, const
   double y = -lds<double>(R(0));
   sts(R(0), y);
   const int nb = (m - 1) / kLB;  // whole blocks from i = 1
-  double la[kLB], lb[kLB], bn[kLB];
+  auto load = [&](double(&d)[kLB], int blk) {
+    if (blk < nb) {
 #pragma unroll
-  for (int q = 0; q < kLB; ++q) {
-    la[q] = nb > 0 ? __ldg(l + 1 + q) : 0.0;
-    lb[q] = nb > 1 ? __ldg(l + 1 + kLB + q) : 0.0;
-  }
-  if (nb > 0) {
-#pragma unroll
-    for (int q = 0; q < kLB; ++q) bn[q] = -lds<double>(R(1 + q));
-  }
-  for (int b = 0; b < nb; ++b) {
-    const int i0 = 1 + b * kLB;
-    double lv[kLB], bv[kLB];
-#pragma unroll
-    for (int q = 0; q < kLB; ++q) {
-      lv[q] = la[q];
-      la[q] = lb[q];
-      bv[q] = bn[q];
+      for (int q = 0; q < kLB; ++q) d[q] = __ldg(l + 1 + blk * kLB + q);
     }
-    if (b + 2 < nb) {
+  };
+  auto block = [&](const double(&lv)[kLB], int blk) {
+    const int i0 = 1 + blk * kLB;
+    double bv[kLB];
 #pragma unroll
-      for (int q = 0; q < kLB; ++q) lb[q] = __ldg(l + i0 + 2 * kLB + q);
-    }
-    if (b + 1 < nb) {
-#pragma unroll
-      for (int q = 0; q < kLB; ++q) bn[q] = -lds<double>(R(i0 + kLB + q));
-    }
+    for (int q = 0; q < kLB; ++q) bv[q] = -lds<double>(R(i0 + q));
 #pragma unroll
     for (int q = 0; q < kLB; ++q) {
       y = fma(-lv[q], y, bv[q]);
@@ -992,7 +980,21 @@ static __device__ __noinline__ void line_solve_fwd_gl(int n, double* row_, const
     }
 #pragma unroll
     for (int q = 0; q < kLB; ++q) sts(R(i0 + q), bv[q]);
+  };
+  double A[kLB], B[kLB], C[kLB];
+  load(A, 0);
+  load(B, 1);
+  int b = 0;
+  for (; b + 3 <= nb; b += 3) {
+    load(C, b + 2);
+    block(A, b);
+    load(A, b + 3);
+    block(B, b + 1);
+    load(B, b + 4);
+    block(C, b + 2);
   }
+  if (b < nb) block(A, b);
+  if (b + 1 < nb) block(B, b + 1);
   for (int i0 = 1 + nb * kLB; i0 < m; ++i0) {
     y = fma(-__ldg(l + i0), y, -lds<double>(R(i0)));
     sts(R(i0), y);
@@ -1005,33 +1007,17 @@ static __device__ __noinline__ void line_solve_bwd_gl(const SolveDev<double>& sd
   auto R = [&](int i) { return rb + 8u * (unsigned)sk(i); };
   double y = lds<double>(R(m - 1));
   const int nb = (m - 1) / kLB;  // whole blocks descending from i = m - 2
-  double ua[kLB], ub[kLB], gn[kLB];
+  auto load = [&](double(&d)[kLB], int blk) {
+    if (blk < nb) {
 #pragma unroll
-  for (int q = 0; q < kLB; ++q) {
-    ua[q] = nb > 0 ? __ldg(u + m - 2 - q) : 0.0;
-    ub[q] = nb > 1 ? __ldg(u + m - 2 - kLB - q) : 0.0;
-  }
-  if (nb > 0) {
-#pragma unroll
-    for (int q = 0; q < kLB; ++q) gn[q] = lds<double>(R(m - 2 - q));
-  }
-  for (int b = 0; b < nb; ++b) {
-    const int i1 = m - 2 - b * kLB;  // block [i1 - kLB + 1, i1], descending
-    double uv[kLB], gv[kLB];
-#pragma unroll
-    for (int q = 0; q < kLB; ++q) {
-      uv[q] = ua[q];
-      ua[q] = ub[q];
-      gv[q] = gn[q];
+      for (int q = 0; q < kLB; ++q) d[q] = __ldg(u + m - 2 - blk * kLB - q);
     }
-    if (b + 2 < nb) {
+  };
+  auto block = [&](const double(&uv)[kLB], int blk) {
+    const int i1 = m - 2 - blk * kLB;  // block [i1 - kLB + 1, i1], descending
+    double gv[kLB];
 #pragma unroll
-      for (int q = 0; q < kLB; ++q) ub[q] = __ldg(u + i1 - 2 * kLB - q);
-    }
-    if (b + 1 < nb) {
-#pragma unroll
-      for (int q = 0; q < kLB; ++q) gn[q] = lds<double>(R(i1 - kLB - q));
-    }
+    for (int q = 0; q < kLB; ++q) gv[q] = lds<double>(R(i1 - q));
 #pragma unroll
     for (int q = 0; q < kLB; ++q) {
       y = fma(-uv[q], y, gv[q]);
@@ -1039,7 +1025,21 @@ static __device__ __noinline__ void line_solve_bwd_gl(const SolveDev<double>& sd
     }
 #pragma unroll
     for (int q = 0; q < kLB; ++q) sts(R(i1 - q), gv[q]);
+  };
+  double A[kLB], B[kLB], C[kLB];
+  load(A, 0);
+  load(B, 1);
+  int b = 0;
+  for (; b + 3 <= nb; b += 3) {
+    load(C, b + 2);
+    block(A, b);
+    load(A, b + 3);
+    block(B, b + 1);
+    load(B, b + 4);
+    block(C, b + 2);
   }
+  if (b < nb) block(A, b);
+  if (b + 1 < nb) block(B, b + 1);
   for (int i1 = m - 2 - nb * kLB; i1 >= 0; --i1) {
     y = fma(-__ldg(u + i1), y, lds<double>(R(i1)));
     sts(R(i1), y);

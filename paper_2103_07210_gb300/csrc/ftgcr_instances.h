@@ -9,12 +9,21 @@ const void* persistent_kernel_k16(bool fp64);
 const void* persistent_kernel_k4_split();
 const void* persistent_kernel_k8_split();
 const void* persistent_kernel_k16_split();
-// split: the mixed-path instance with split rounds
-inline const void* persistent_kernel_ptr(int kb, bool fp64, bool split) {
-  if (split && !fp64) {
+const void* persistent_kernel_k4_wide64();
+const void* persistent_kernel_k8_wide64();
+const void* persistent_kernel_k16_wide64();
+// wide: the instance for wide-row solves (mixed path: split rounds; FP64
+// path: line-solve factors read from global memory)
+inline const void* persistent_kernel_ptr(int kb, bool fp64, bool wide) {
+  if (wide && !fp64) {
     if (kb == 4) return persistent_kernel_k4_split();
     if (kb == 8) return persistent_kernel_k8_split();
     return persistent_kernel_k16_split();
+  }
+  if (wide) {
+    if (kb == 4) return persistent_kernel_k4_wide64();
+    if (kb == 8) return persistent_kernel_k8_wide64();
+    return persistent_kernel_k16_wide64();
   }
   if (kb == 4) return persistent_kernel_k4(fp64);
   if (kb == 8) return persistent_kernel_k8(fp64);

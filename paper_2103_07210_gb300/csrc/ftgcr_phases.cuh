@@ -645,10 +645,12 @@ __device__ __forceinline__ long long consts_per_row(const SolveDev<T>& sd) {
   else
     return 32LL * sd.C;
 }
-template <typename T>
+// GL (FP64 wide-row instance): a solve whose factors stay in global memory
+// stages none.
+template <typename T, bool GL = false>
 __device__ __forceinline__ void stage_line_consts(const SolveDev<T>& sd, int h0, int h1, T* cs) {
   if (sd.precond != PC_LINE) return;
-  if constexpr (sizeof(T) == 8) {
+  if constexpr (GL && sizeof(T) == 8) {
     if (sd.cs_global) return;  // read from global memory by the row solves
   }
   const long long per = consts_per_row(sd);
@@ -689,6 +691,39 @@ __device__ __forceinline__ LineConsts<T> staged_consts(const SolveDev<T>& sd, co
   return LineConsts<T>{cs + (long long)r * per, cs + ((long long)nrows + r) * per, cs + (2LL * nrows + r) * per};
 }
 
+// The FP64 line solve of a tile whose factors stay in global memory (wide
+// rows): the same steps as the staged form in precond_tile, with the tile's
+// factor rows first asked of L2.  Its own function, so that the staged form's
+// code is the same as without it.
+static __device__ __noinline__ void precond_tile_gl(const SolveDev<double>& sd, int h0, int nrows, double* sm,
+                                                    int stride) {
+  const int n = sd.nlon, m = n - 1;
+  const long long base = (long long)h0 * n, len = (long long)nrows * n;
+  for (long long q = 16LL * threadIdx.x; q < len; q += 16LL * kThreads) {  // 128-byte lines
+    prefetch_l2(sd.lc + base + q);
+    prefetch_l2(sd.lw + base + q);
+    prefetch_l2(sd.lu + base + q);
+  }
+  for (int jr = threadIdx.x; jr < nrows; jr += kThreads) line_solve_fwd_gl(n, sm + jr * stride, sd.lc + base + (long long)jr * n);
+  __syncthreads();
+  // the backward step's products g_i winv_i, all rows at once
+  for (int idx = threadIdx.x; idx < nrows * m; idx += kThreads) {
+    const int jr = idx / m, i = idx - jr * m;
+    double* row = sm + jr * stride;
+    row[sk(i)] = row[sk(i)] * __ldg(sd.lw + base + (long long)jr * n + i);
+  }
+  __syncthreads();
+  for (int jr = threadIdx.x; jr < nrows; jr += kThreads)
+    line_solve_bwd_gl(sd, h0 + jr, sm + jr * stride, sd.lu + base + (long long)jr * n);
+  __syncthreads();
+  // bordering, x_i = y_i - x_{n-1} z_i, all rows at once
+  for (int idx = threadIdx.x; idx < nrows * m; idx += kThreads) {
+    const int jr = idx / m, i = idx - jr * m;
+    double* row = sm + jr * stride;
+    row[sk(i)] = row[sk(i)] - row[sk(n - 1)] * __ldg(sd.lz + base + (long long)jr * n + i);
+  }
+}
+
 // The preconditioner on the nrows rows of a tile staged in shared memory.
 // FP32 line solve and the pointwise preconditioners: one warp per row.  FP64
 // line solve: one lane per row, the rows side by side in the first warp(s).
@@ -702,33 +737,30 @@ __device__ __forceinline__ LineConsts<T> staged_consts(const SolveDev<T>& sd, co
 // warps solves each row with a group of 2, 4 or 8 warps.  One-pass rounds
 // keep one warp per row in every instance, so a one-pass solve gives the
 // same result in a launch with split solves as alone.
-template <typename T, bool GROUPS = false>
+template <typename T, bool GROUPS = false, bool GL = false>
 __device__ __forceinline__ void precond_tile(const SolveDev<T>& sd, int h0, int nrows, T* sm, int stride, const T* cs,
                                              bool groups = false) {
   if constexpr (sizeof(T) == 8) {
     if (sd.precond == PC_LINE) {
-      const int n = sd.nlon, m = n - 1;
-      const bool gl = sd.cs_global;
-      for (int jr = threadIdx.x; jr < nrows; jr += kThreads) {
-        if (gl)
-          line_solve_fwd_gl(n, sm + jr * stride, sd.lc + (long long)(h0 + jr) * n);
-        else
-          line_solve_fwd_sh(n, sm + jr * stride, staged_consts(sd, cs, nrows, jr).cb);
+      if constexpr (GL) {
+        if (sd.cs_global) {
+          precond_tile_gl(sd, h0, nrows, sm, stride);
+          return;
+        }
       }
+      const int n = sd.nlon, m = n - 1;
+      for (int jr = threadIdx.x; jr < nrows; jr += kThreads)
+        line_solve_fwd_sh(n, sm + jr * stride, staged_consts(sd, cs, nrows, jr).cb);
       __syncthreads();
       // the backward step's products g_i winv_i, all rows at once
       for (int idx = threadIdx.x; idx < nrows * m; idx += kThreads) {
         const int jr = idx / m, i = idx - jr * m;
         T* row = sm + jr * stride;
-        row[sk(i)] = row[sk(i)] * (gl ? __ldg(sd.lw + (long long)(h0 + jr) * n + i) : staged_consts(sd, cs, nrows, jr).cw[i]);
+        row[sk(i)] = row[sk(i)] * staged_consts(sd, cs, nrows, jr).cw[i];
       }
       __syncthreads();
-      for (int jr = threadIdx.x; jr < nrows; jr += kThreads) {
-        if (gl)
-          line_solve_bwd_gl(sd, h0 + jr, sm + jr * stride, sd.lu + (long long)(h0 + jr) * n);
-        else
-          line_solve_bwd_sh(sd, h0 + jr, sm + jr * stride, staged_consts(sd, cs, nrows, jr).cz);
-      }
+      for (int jr = threadIdx.x; jr < nrows; jr += kThreads)
+        line_solve_bwd_sh(sd, h0 + jr, sm + jr * stride, staged_consts(sd, cs, nrows, jr).cz);
       __syncthreads();
       // bordering, x_i = y_i - x_{n-1} z_i, all rows at once
       for (int idx = threadIdx.x; idx < nrows * m; idx += kThreads) {
@@ -1080,7 +1112,7 @@ __device__ __forceinline__ void step_axpy(const SolveDev<T>& sd, const Ctx<T>& c
 }
 // (2) e = P^-1 r' on the staged rows, then the e-site flips and data-loss
 // events of the step.
-template <typename T, bool GROUPS = false>
+template <typename T, bool GROUPS = false, bool GL = false>
 __device__ __forceinline__ void step_precond(const SolveDev<T>& sd, const Ctx<T>& c, const RowTile& rt, T* sm,
                                              const T* cs, PhaseSmem& ps, bool groups = false) {
   const int nlon = sd.nlon, stride = row_stride(nlon);
@@ -1088,7 +1120,7 @@ __device__ __forceinline__ void step_precond(const SolveDev<T>& sd, const Ctx<T>
   cp_async_wait_all();
   __syncthreads();
   sub_mark(ps, 0);
-  precond_tile<T, GROUPS>(sd, rt.h0, nrows, sm, stride, cs, groups);
+  precond_tile<T, GROUPS, GL>(sd, rt.h0, nrows, sm, stride, cs, groups);
   __syncthreads();
   sub_mark(ps, 1);
   if (threadIdx.x == 0) {
@@ -1195,20 +1227,20 @@ __device__ __forceinline__ void step_stencil(const SolveDev<T>& sd, const Ctx<T>
   }
 }
 
-template <typename T, int KB, bool FUSED>
+template <typename T, int KB, bool FUSED, bool GL = false>
 __device__ __noinline__ void phase_pa(const SolveDev<T>& sd, const Ctx<T>& c, int sidx, int tau, T* sm, PhaseSmem& ps,
                                       double* part_out) {
   const int nlon = sd.nlon, nlat = sd.nlat, stride = row_stride(nlon);
   const RowTile rt = row_tile(nlat, sd.nt, tau);
   T* cs = sm + sd.cs_off;
   // a CTA that keeps the same tile keeps its staged constants (single solves)
-  if (!(ps.cs_solve == sidx && ps.cs_tile == tau)) stage_line_consts(sd, rt.h0, rt.h1, cs);
+  if (!(ps.cs_solve == sidx && ps.cs_tile == tau)) stage_line_consts<T, GL>(sd, rt.h0, rt.h1, cs);
   if (threadIdx.x == 0)
     ps.nfl = collect_flips(sd, c.t, FUSED ? (kStateVecs | (1u << V_E)) : (1u << V_E), (long long)rt.h0 * nlon,
                            (long long)rt.h1 * nlon, ps.fl);
   Acc<T> an;
   step_axpy<T, KB, FUSED>(sd, c, rt, sm, ps, an);
-  step_precond<T>(sd, c, rt, sm, cs, ps);
+  step_precond<T, false, GL>(sd, c, rt, sm, cs, ps);
   step_stencil<T, KB>(sd, c, rt, sm, ps, part_out, &an, true);
   if (threadIdx.x == 0) {
     ps.cs_solve = sidx;
@@ -1542,7 +1574,7 @@ __device__ __forceinline__ void init_stencil(const SolveDev<T>& sd, const Ctx<T>
 // solve, phi0 = 0); p0 = P^-1(r0); L(p0); ||r0||^2, ||R||^2 and the first
 // beta dots.  The x/r/p/Ap flips of the first step are applied to the working
 // vectors, and their clean values kept so that the backup stays clean.
-template <typename T>
+template <typename T, bool GL = false>
 __device__ __noinline__ void phase_init(const SolveDev<T>& sd, const Ctx<T>& c, int sidx, int tau, T* sm, PhaseSmem& ps,
                            double* part_out) {
   const int nlon = sd.nlon, nlat = sd.nlat, stride = row_stride(nlon);
@@ -1550,7 +1582,7 @@ __device__ __noinline__ void phase_init(const SolveDev<T>& sd, const Ctx<T>& c, 
   if (threadIdx.x == 0)
     ps.nfl = collect_flips(sd, c.t, kStateVecs, (long long)rt.j0 * nlon, (long long)rt.j1 * nlon, ps.fl);
   T* cs = sm + sd.cs_off;
-  if (!(ps.cs_solve == sidx && ps.cs_tile == tau)) stage_line_consts(sd, rt.h0, rt.h1, cs);
+  if (!(ps.cs_solve == sidx && ps.cs_tile == tau)) stage_line_consts<T, GL>(sd, rt.h0, rt.h1, cs);
   __syncthreads();
   Acc<T> an, aR;
   constexpr int W = V16<T>::W;
@@ -1558,7 +1590,7 @@ __device__ __noinline__ void phase_init(const SolveDev<T>& sd, const Ctx<T>& c, 
   init_rows<T>(sd, c, rt, sm, ps, an, aR, vec);
   cp_async_wait_all();
   __syncthreads();
-  precond_tile(sd, rt.h0, rt.h1 - rt.h0, sm, stride, cs);
+  precond_tile<T, false, GL>(sd, rt.h0, rt.h1 - rt.h0, sm, stride, cs);
   __syncthreads();
   init_stencil<T>(sd, c, rt, sm, ps, part_out, &an, &aR, vec, true);
   if (threadIdx.x == 0) {
@@ -1822,10 +1854,10 @@ __device__ __forceinline__ void enter_solve(SolveDev<T>* const* solves, KernelSm
 // The phase of tile tau of the solve in ks.  pass 0: a one-pass round, or the
 // first pass of a split round; pass 1: the second pass of a split round (the
 // step phases of split solves only).
-template <typename T, int KB, bool SPLIT>
+template <typename T, int KB, bool WIDE>
 __device__ __forceinline__ void run_phase(KernelSmem<T>& ks, int pass, int s, int tau, T* sm, double* part_out) {
   const int kind = ks.c.kind;
-  if constexpr (SPLIT) {
+  if constexpr (WIDE && sizeof(T) == 4) {
     const int mode = ks.sd.split ? 1 + pass : 0;
     if (pass == 1 && mode == 0) return;
     switch (kind) {
@@ -1838,8 +1870,8 @@ __device__ __forceinline__ void run_phase(KernelSmem<T>& ks, int pass, int s, in
     }
   } else {
     switch (kind) {
-      case K_INIT: phase_init(ks.sd, ks.c, s, tau, sm, ks.ps, part_out); return;
-      case K_PA: phase_pa<T, KB, false>(ks.sd, ks.c, s, tau, sm, ks.ps, part_out); return;
+      case K_INIT: phase_init<T, WIDE>(ks.sd, ks.c, s, tau, sm, ks.ps, part_out); return;
+      case K_PA: phase_pa<T, KB, false, WIDE>(ks.sd, ks.c, s, tau, sm, ks.ps, part_out); return;
       case K_PF:
         if constexpr (sizeof(T) == 4) phase_pa<T, KB, true>(ks.sd, ks.c, s, tau, sm, ks.ps, part_out);
         return;
@@ -1858,12 +1890,13 @@ __device__ __forceinline__ void run_phase(KernelSmem<T>& ks, int pass, int s, in
 // Persistent cooperative kernel: every round, every CTA takes its share of
 // the tiles of all active solves, runs for each solve the state transition
 // and the decided phase, and then meets the others at one grid barrier.
-// SPLIT (mixed path): the instance for launches with split-round solves, whose
-// every round takes a second pass over the tiles after a further barrier; the
-// one-pass instance carries none of that code.
-template <typename T, int KB, bool SPLIT>
+// WIDE: the instance for launches with wide-row solves.  Mixed path: solves
+// with split rounds, whose every round takes a second pass over the tiles
+// after a further barrier.  FP64 path: solves whose line solve reads its
+// factors from global memory.  The other instance carries none of that code.
+template <typename T, int KB, bool WIDE>
 __global__ void __launch_bounds__(kThreads, 1) k_ftgcr_persistent(BatchArgs<T> a) {
-  static_assert(!SPLIT || sizeof(T) == 4, "split rounds exist on the mixed path only");
+  constexpr bool SPLIT = WIDE && sizeof(T) == 4;  // split rounds: mixed path only
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ KernelSmem<T> ks;
   T* sm = reinterpret_cast<T*>(dsm);
@@ -1956,7 +1989,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ftgcr_persistent(BatchArgs<T> a
             a.diag[blockIdx.x * 4 + 3] = tr_items;
           }
         }
-        run_phase<T, KB, SPLIT>(ks, pass, s, tau, sm, ks.sd.part + ((long long)par * ks.sd.nt + tau) * kPartStride);
+        run_phase<T, KB, WIDE>(ks, pass, s, tau, sm, ks.sd.part + ((long long)par * ks.sd.nt + tau) * kPartStride);
         __syncthreads();
         if (pass == 0 && tau == 0) {
           cta_store(ks.sd.st + (par ^ 1), &ks.N);

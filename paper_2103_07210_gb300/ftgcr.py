@@ -21,7 +21,7 @@ _INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libftgcr.so")
 SOURCES = ["ftgcr.cu", "ftgcr_k4.cu", "ftgcr_k8.cu", "ftgcr_k16.cu", "ftgcr_k4s.cu", "ftgcr_k8s.cu", "ftgcr_k16s.cu",
-           "ftgcr_server.cu", "ftgcr_tune.cu", "ftgcr_probe.cu"]
+           "ftgcr_k4w.cu", "ftgcr_k8w.cu", "ftgcr_k16w.cu", "ftgcr_server.cu", "ftgcr_tune.cu", "ftgcr_probe.cu"]
 HEADERS = ["ftgcr_device.cuh", "ftgcr_phases.cuh", "ftgcr_instances.h", "ftgcr_serve.h"]
 # --fmad=false: device multiply-adds are fused only where the code says fma();
 # -ffp-contract=off: the same for the host-side geometry (GCC contracts by
