@@ -75,7 +75,7 @@ typedef struct ftgcr_handle ftgcr_handle;
 typedef struct {
   int32_t nlon;      /* >= 3; one latitude row with its two halo rows (and, for the
                         mixed path's line preconditioner, their factors) must fit in
-                        one SM's shared memory: nlon <= about 9600 (FTGCR_FP64; beyond
+                        one SM's shared memory: nlon <= about 8190 (FTGCR_FP64; beyond
                         about 2150 its line solve reads the factors from global
                         memory) or 8500 (FTGCR_MIXED; beyond about 4350 only with
                         split rounds, see FTGCR_FLAG_SPLIT_ROUNDS), else FTGCR_ERR_ARG */

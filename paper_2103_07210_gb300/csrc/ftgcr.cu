@@ -567,7 +567,8 @@ SmemPlan smem_plan(int nlon, int nlat, int nt, int mixed, size_t elem, int preco
   p.gconsts = 0;
   if (!split) {
     p.gconsts = line && !mixed && gconsts;
-    const size_t consts = line && !p.gconsts ? 3 * (h + 2) * per_row * elem : 0;
+    // staged: three factor arrays per row; global: each row's factor ring
+    const size_t consts = !line ? 0 : p.gconsts ? (h + 2) * (size_t)kRingStride * elem : 3 * (h + 2) * per_row * elem;
     p.bytes = std::max((h + 2) * st * elem + consts, out);
     p.cs_off = (long long)((h + 2) * st);
     p.cs_clobber = 0;

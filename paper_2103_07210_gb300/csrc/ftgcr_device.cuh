@@ -340,6 +340,9 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async16_s(unsigned smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
@@ -946,33 +949,69 @@ static __device__ __noinline__ void line_solve_bwd_sh(const SolveDev<double>& sd
   sts(R(n - 1), num / __ldg(sd.lrow + (long long)j * 4));
 }
 
-// The two chains with the factors l and u read from global memory (FP64 path,
-// wide rows).  The same operations on the same values as line_solve_fwd_sh and
-// line_solve_bwd_sh.  The factor loads run two register blocks ahead of the
-// chain, in three buffers taken in turn (a copy between buffers would wait for
-// the load), so about 2 kLB dependent FP64 operations (64 cycles or more each)
-// cover their latency; the caller has asked L2 for the rows beforehand.
+// The two chains with the factors l and u kept in global memory (FP64 path,
+// wide rows): the same operations on the same values as line_solve_fwd_sh
+// and line_solve_bwd_sh.  Each chain's lane copies its row's factors into a
+// ring of kRingSlots chunks of kRingChunk elements in shared memory (ring_,
+// its own, 16-byte aligned), one chunk ahead of the chain, with cp.async
+// (16-byte copies where the row starts on a 16-byte boundary, else 8-byte
+// ones), and reads them from there: no global-memory latency and no prefetch
+// registers on the chain.  Element i sits at ring position i mod kRingElems
+// (chunk i / kRingChunk); a slot is reused once the chain has moved
+// kRingSlots - 1 chunks on.
+constexpr int kRingChunk = 64, kRingSlots = 4;
+constexpr int kRingElems = kRingChunk * kRingSlots;  // a power of two
+// rings of successive rows kRingStride doubles apart: 16 bytes more than a
+// ring, so the rows side by side in lanes read different banks
+constexpr int kRingStride = kRingElems + 2;
 __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
-static __device__ __noinline__ void line_solve_fwd_gl(int n, double* row_, const double* __restrict__ l) {
+__device__ __forceinline__ void cp_async8(unsigned smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+// Chunk c of a row's factors f (elements [c kRingChunk, ...) below lim, lim <=
+// n) into the ring at gb; always one commit group (empty for c < 0).  A
+// 16-byte copy may take the element at lim too (still inside the row).
+__device__ __forceinline__ void ring_fetch(unsigned gb, const double* f, int c, int lim, bool a16) {
+  if (c >= 0) {
+    const int i0 = c * kRingChunk, i1 = min(i0 + kRingChunk, lim);
+    if (a16) {
+      for (int i = i0; i < i1; i += 2) cp_async16_s(gb + 8u * (unsigned)(i & (kRingElems - 1)), f + i);
+    } else {
+      for (int i = i0; i < i1; ++i) cp_async8(gb + 8u * (unsigned)(i & (kRingElems - 1)), f + i);
+    }
+  }
+  cp_async_commit();
+}
+
+static __device__ __noinline__ void line_solve_fwd_gl(int n, double* row_, const double* __restrict__ l, double* ring_) {
   const int m = n - 1;
-  const unsigned rb = smem_addr(row_);
+  const unsigned rb = smem_addr(row_), gb = smem_addr(ring_);
+  const bool a16 = (reinterpret_cast<unsigned long long>(l) & 15ull) == 0;
   auto R = [&](int i) { return rb + 8u * (unsigned)sk(i); };
+  auto G = [&](int i) { return gb + 8u * (unsigned)(i & (kRingElems - 1)); };
+  ring_fetch(gb, l, 0, m, a16);
+  ring_fetch(gb, l, 1, m, a16);
+  cp_async_wait_1();
+  int ready = 0;  // chunks 0..ready have landed, ready + 1 is in flight
   double y = -lds<double>(R(0));
   sts(R(0), y);
   const int nb = (m - 1) / kLB;  // whole blocks from i = 1
-  auto load = [&](double(&d)[kLB], int blk) {
-    if (blk < nb) {
-#pragma unroll
-      for (int q = 0; q < kLB; ++q) d[q] = __ldg(l + 1 + blk * kLB + q);
+  for (int b = 0; b < nb; ++b) {
+    const int i0 = 1 + b * kLB;
+    if ((i0 + kLB - 1) / kRingChunk > ready) {  // the block reaches the next chunk
+      ++ready;
+      ring_fetch(gb, l, ready + 1, m, a16);
+      cp_async_wait_1();
     }
-  };
-  auto block = [&](const double(&lv)[kLB], int blk) {
-    const int i0 = 1 + blk * kLB;
-    double bv[kLB];
+    double bv[kLB], lv[kLB];
 #pragma unroll
-    for (int q = 0; q < kLB; ++q) bv[q] = -lds<double>(R(i0 + q));
+    for (int q = 0; q < kLB; ++q) {
+      bv[q] = -lds<double>(R(i0 + q));
+      lv[q] = lds<double>(G(i0 + q));
+    }
 #pragma unroll
     for (int q = 0; q < kLB; ++q) {
       y = fma(-lv[q], y, bv[q]);
@@ -980,44 +1019,40 @@ static __device__ __noinline__ void line_solve_fwd_gl(int n, double* row_, const
     }
 #pragma unroll
     for (int q = 0; q < kLB; ++q) sts(R(i0 + q), bv[q]);
-  };
-  double A[kLB], B[kLB], C[kLB];
-  load(A, 0);
-  load(B, 1);
-  int b = 0;
-  for (; b + 3 <= nb; b += 3) {
-    load(C, b + 2);
-    block(A, b);
-    load(A, b + 3);
-    block(B, b + 1);
-    load(B, b + 4);
-    block(C, b + 2);
   }
-  if (b < nb) block(A, b);
-  if (b + 1 < nb) block(B, b + 1);
-  for (int i0 = 1 + nb * kLB; i0 < m; ++i0) {
+  cp_async_wait_all();
+  for (int i0 = 1 + nb * kLB; i0 < m; ++i0) {  // fewer than kLB: their factors straight from global memory
     y = fma(-__ldg(l + i0), y, -lds<double>(R(i0)));
     sts(R(i0), y);
   }
 }
 static __device__ __noinline__ void line_solve_bwd_gl(const SolveDev<double>& sd, int j, double* row_,
-                                                      const double* __restrict__ u) {
+                                                      const double* __restrict__ u, double* ring_) {
   const int n = sd.nlon, m = n - 1;
-  const unsigned rb = smem_addr(row_);
+  const unsigned rb = smem_addr(row_), gb = smem_addr(ring_);
+  const bool a16 = (reinterpret_cast<unsigned long long>(u) & 15ull) == 0;
   auto R = [&](int i) { return rb + 8u * (unsigned)sk(i); };
+  auto G = [&](int i) { return gb + 8u * (unsigned)(i & (kRingElems - 1)); };
+  const int ctop = (m - 2) / kRingChunk;  // the chain runs i = m-2 .. 0, chunks ctop .. 0
+  ring_fetch(gb, u, ctop, m - 1, a16);
+  ring_fetch(gb, u, ctop - 1, m - 1, a16);
+  cp_async_wait_1();
+  int ready = ctop;  // chunks ctop..ready have landed, ready - 1 is in flight
   double y = lds<double>(R(m - 1));
   const int nb = (m - 1) / kLB;  // whole blocks descending from i = m - 2
-  auto load = [&](double(&d)[kLB], int blk) {
-    if (blk < nb) {
-#pragma unroll
-      for (int q = 0; q < kLB; ++q) d[q] = __ldg(u + m - 2 - blk * kLB - q);
+  for (int b = 0; b < nb; ++b) {
+    const int i1 = m - 2 - b * kLB;  // block [i1 - kLB + 1, i1], descending
+    if ((i1 - kLB + 1) / kRingChunk < ready) {
+      --ready;
+      ring_fetch(gb, u, ready - 1, m - 1, a16);
+      cp_async_wait_1();
     }
-  };
-  auto block = [&](const double(&uv)[kLB], int blk) {
-    const int i1 = m - 2 - blk * kLB;  // block [i1 - kLB + 1, i1], descending
-    double gv[kLB];
+    double gv[kLB], uv[kLB];
 #pragma unroll
-    for (int q = 0; q < kLB; ++q) gv[q] = lds<double>(R(i1 - q));
+    for (int q = 0; q < kLB; ++q) {
+      gv[q] = lds<double>(R(i1 - q));
+      uv[q] = lds<double>(G(i1 - q));
+    }
 #pragma unroll
     for (int q = 0; q < kLB; ++q) {
       y = fma(-uv[q], y, gv[q]);
@@ -1025,21 +1060,8 @@ static __device__ __noinline__ void line_solve_bwd_gl(const SolveDev<double>& sd
     }
 #pragma unroll
     for (int q = 0; q < kLB; ++q) sts(R(i1 - q), gv[q]);
-  };
-  double A[kLB], B[kLB], C[kLB];
-  load(A, 0);
-  load(B, 1);
-  int b = 0;
-  for (; b + 3 <= nb; b += 3) {
-    load(C, b + 2);
-    block(A, b);
-    load(A, b + 3);
-    block(B, b + 1);
-    load(B, b + 4);
-    block(C, b + 2);
   }
-  if (b < nb) block(A, b);
-  if (b + 1 < nb) block(B, b + 1);
+  cp_async_wait_all();
   for (int i1 = m - 2 - nb * kLB; i1 >= 0; --i1) {
     y = fma(-__ldg(u + i1), y, lds<double>(R(i1)));
     sts(R(i1), y);

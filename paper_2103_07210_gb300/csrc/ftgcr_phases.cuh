@@ -693,10 +693,11 @@ __device__ __forceinline__ LineConsts<T> staged_consts(const SolveDev<T>& sd, co
 
 // The FP64 line solve of a tile whose factors stay in global memory (wide
 // rows): the same steps as the staged form in precond_tile, with the tile's
-// factor rows first asked of L2.  Its own function, so that the staged form's
-// code is the same as without it.
+// factor rows first asked of L2.  ring: kRingStride doubles of shared memory
+// per row for the chains' factor rings.  Its own function, so that the staged
+// form's code is the same as without it.
 static __device__ __noinline__ void precond_tile_gl(const SolveDev<double>& sd, int h0, int nrows, double* sm,
-                                                    int stride) {
+                                                    int stride, double* ring) {
   const int n = sd.nlon, m = n - 1;
   const long long base = (long long)h0 * n, len = (long long)nrows * n;
   for (long long q = 16LL * threadIdx.x; q < len; q += 16LL * kThreads) {  // 128-byte lines
@@ -704,23 +705,54 @@ static __device__ __noinline__ void precond_tile_gl(const SolveDev<double>& sd, 
     prefetch_l2(sd.lw + base + q);
     prefetch_l2(sd.lu + base + q);
   }
-  for (int jr = threadIdx.x; jr < nrows; jr += kThreads) line_solve_fwd_gl(n, sm + jr * stride, sd.lc + base + (long long)jr * n);
+  // the rows' chains spread over up to four warps (one per SM sub-partition,
+  // each with its own FP64 unit): row w + nw q in lane q of warp w
+  const int nw = min(nrows, 4), wq = threadIdx.x >> 5, lq = threadIdx.x & 31;
+  const int jc = wq < nw ? wq + nw * lq : nrows;  // this thread's row, if any
+  if (jc < nrows) line_solve_fwd_gl(n, sm + jc * stride, sd.lc + base + (long long)jc * n, ring + jc * kRingStride);
   __syncthreads();
-  // the backward step's products g_i winv_i, all rows at once
-  for (int idx = threadIdx.x; idx < nrows * m; idx += kThreads) {
-    const int jr = idx / m, i = idx - jr * m;
-    double* row = sm + jr * stride;
-    row[sk(i)] = row[sk(i)] * __ldg(sd.lw + base + (long long)jr * n + i);
+  // the backward step's products g_i winv_i, all rows at once (row by row,
+  // each thread's loads of a group issued together)
+  constexpr int kU = 8;
+  for (int jr = 0; jr < nrows; ++jr) {
+    const unsigned rb = smem_addr(sm + jr * stride);
+    const double* w = sd.lw + base + (long long)jr * n;
+    for (int i0 = threadIdx.x; i0 < m; i0 += kU * kThreads) {
+      double wv[kU];
+#pragma unroll
+      for (int q = 0; q < kU; ++q) wv[q] = i0 + q * kThreads < m ? __ldg(w + i0 + q * kThreads) : 0.0;
+#pragma unroll
+      for (int q = 0; q < kU; ++q) {
+        const int i = i0 + q * kThreads;
+        if (i < m) {
+          const unsigned a = rb + 8u * (unsigned)sk(i);
+          sts(a, lds<double>(a) * wv[q]);
+        }
+      }
+    }
   }
   __syncthreads();
-  for (int jr = threadIdx.x; jr < nrows; jr += kThreads)
-    line_solve_bwd_gl(sd, h0 + jr, sm + jr * stride, sd.lu + base + (long long)jr * n);
+  if (jc < nrows)
+    line_solve_bwd_gl(sd, h0 + jc, sm + jc * stride, sd.lu + base + (long long)jc * n, ring + jc * kRingStride);
   __syncthreads();
   // bordering, x_i = y_i - x_{n-1} z_i, all rows at once
-  for (int idx = threadIdx.x; idx < nrows * m; idx += kThreads) {
-    const int jr = idx / m, i = idx - jr * m;
-    double* row = sm + jr * stride;
-    row[sk(i)] = row[sk(i)] - row[sk(n - 1)] * __ldg(sd.lz + base + (long long)jr * n + i);
+  for (int jr = 0; jr < nrows; ++jr) {
+    const unsigned rb = smem_addr(sm + jr * stride);
+    const double* z = sd.lz + base + (long long)jr * n;
+    const double xl = lds<double>(rb + 8u * (unsigned)sk(n - 1));
+    for (int i0 = threadIdx.x; i0 < m; i0 += kU * kThreads) {
+      double zv[kU];
+#pragma unroll
+      for (int q = 0; q < kU; ++q) zv[q] = i0 + q * kThreads < m ? __ldg(z + i0 + q * kThreads) : 0.0;
+#pragma unroll
+      for (int q = 0; q < kU; ++q) {
+        const int i = i0 + q * kThreads;
+        if (i < m) {
+          const unsigned a = rb + 8u * (unsigned)sk(i);
+          sts(a, lds<double>(a) - xl * zv[q]);
+        }
+      }
+    }
   }
 }
 
@@ -744,7 +776,7 @@ __device__ __forceinline__ void precond_tile(const SolveDev<T>& sd, int h0, int 
     if (sd.precond == PC_LINE) {
       if constexpr (GL) {
         if (sd.cs_global) {
-          precond_tile_gl(sd, h0, nrows, sm, stride);
+          precond_tile_gl(sd, h0, nrows, sm, stride, const_cast<T*>(cs));
           return;
         }
       }

@@ -43,6 +43,7 @@ def test_fp64_wide_rows_match_oracle():
     (4096, 40, 4, 0, 1),    # staged factors do not fit beside even one row
     (1024, 64, 3, 8, 8),    # 8-row bands asked for: too tall with staged factors
     (1000, 37, 5, 5, 8),    # ragged: nlon not a multiple of the register block, last band short
+    (8192, 8, 4, 0, 1),     # the widest FP64 rows that fit
 ])
 def test_fp64_global_factors_match_oracle(nlon, nlat, k, tiles, rows):
     p = inputs.hill_problem(nlon, nlat, rhs="random", seed=nlon + nlat)
@@ -66,10 +67,39 @@ def test_mixed_wide_rows_match_oracle():
 
 
 def test_rows_too_wide_for_one_band_are_refused():
-    # FP64 beyond about 9600 columns (factors from global memory); mixed beyond
+    # FP64 beyond about 8190 columns (factors from global memory); mixed beyond
     # about 8500 (split rounds)
     for (nlon, nlat), prec in (((12288, 4), "fp64"), ((16384, 4), "mixed")):
         p = inputs.hill_problem(nlon, nlat)
         with pytest.raises(ftgcr.FTGCRError) as ei:
             ftgcr.Solver(p.D, p.mu, precision=prec)
         assert ei.value.status == ftgcr.ERR_ARG
+
+
+def test_fp64_batch_of_staged_and_global_factor_solves_equals_solo():
+    # one launch holding both kinds runs the wide-row instance, which serves
+    # both; each result is bitwise the one its handle gives alone
+    probs = [inputs.hill_problem(n, m, rhs="random", seed=n + m) for n, m in ((1024, 64), (256, 128), (2000, 40))]
+    tiles = [8, 0, 0]  # 8-row bands: global factors; 256 x 128: staged; 2000 x 40: 1-row bands, staged
+    solvers = [ftgcr.Solver(p.D, p.mu, k=4, tol=1e-10, precision="fp64", tiles=t) for p, t in zip(probs, tiles)]
+    try:
+        kinds = []
+        R = [torch.from_numpy(p.R).cuda() for p in probs]
+        alone, info_alone = [], []
+        for s, r in zip(solvers, R):
+            x = torch.zeros_like(r)
+            s.solve(r, x, faults=[(4, "r", 77, 62)])
+            alone.append(x.cpu().numpy())
+            info_alone.append(s.stats())
+            kinds.append(info_alone[-1]["global_factors"])
+        assert kinds == [True, False, False], kinds
+        xs = [torch.zeros_like(r) for r in R]
+        ftgcr.solve_batch(solvers, R, xs, faults=[[(4, "r", 77, 62)]] * 3)
+        torch.cuda.synchronize()
+        for s, x, xa, ia in zip(solvers, xs, alone, info_alone):
+            ib = s.stats()
+            assert np.array_equal(x.cpu().numpy(), xa)
+            assert ib["steps"] == ia["steps"] and ib["detect_steps"] == ia["detect_steps"]
+    finally:
+        for s in solvers:
+            s.close()
