@@ -44,9 +44,9 @@ def algorithmic_bytes(steps: int, outer: int, k: int = K, s: int = 4, N: int = N
 
 # DRAM traffic per launch of the persistent kernel from one ncu capture, valid
 # only for the kernel sources it was taken on (sha256 of the CUDA sources).
-NCU_TRAFFIC = {"sources_sha256": "d83c7cb2a1548580ea11201981f248e148f09e5a36c1508e8f8ec4c1858ead6a",
-               "bytes_per_launch": 27692800 + 8123648,  # mixed 1024x512 (read + write)
-               "large": {"2048x1024": 2718225664 + 1348723968, "4096x2048": 15129805824 + 5215024640}}
+NCU_TRAFFIC = {"sources_sha256": "05b57144247d3bd16ee8e1a3c72bc95b37c1d0bcc25e8f9f1c527d6f44be1717",
+               "bytes_per_launch": 28516352 + 8707072,  # mixed 1024x512 (read + write)
+               "large": {"2048x1024": 2705236992 + 1349571840, "4096x2048": 15129706496 + 5213779200}}
 
 
 def sources_hash() -> str:
