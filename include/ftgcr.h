@@ -200,6 +200,20 @@ int ftgcr_create(const ftgcr_grid* grid, const ftgcr_coeffs* coeffs, int32_t k, 
  * was. */
 int ftgcr_solve(ftgcr_handle* h, const double* rhs, double* x, const ftgcr_fault_plan* plan, void* stream);
 
+/* Same as ftgcr_solve, host arrays included, but only enqueues the work on
+ * `stream` and returns: the copies of host arrays into the handle's staging
+ * buffers, their finiteness check, the solve and the copy of the solution
+ * back into x.  With pinned host arrays the copies run asynchronously, so
+ * solves of two handles on two streams overlap one's copies with the other's
+ * kernel.  rhs and x must stay valid, and x untouched, until the stream has
+ * passed the solve; one solve per handle may be in flight.  ftgcr_stats()
+ * (which waits for the stream) then reports its status: FTGCR_ERR_ARG in
+ * `status` for a host array holding a NaN or an infinity, x then left as it
+ * was.  Returns FTGCR_OK once enqueued, FTGCR_ERR_ARG (null pointer, invalid
+ * plan) or FTGCR_ERR_CUDA. */
+int ftgcr_solve_host_async(ftgcr_handle* h, const double* rhs, double* x, const ftgcr_fault_plan* plan,
+                           void* stream);
+
 /* Same as ftgcr_solve but only enqueues the work on `stream` and returns;
  * rhs and x must be device memory.  The status of the solve is read with
  * ftgcr_stats() once the stream has reached the end of the solve.  It

@@ -1392,11 +1392,13 @@ int ftgcr_solve_async(ftgcr_handle* h, const double* rhs, double* x, const ftgcr
                                      : solve_async_impl<double>(h, rhs, x, x, plan, st);
 }
 
-int ftgcr_solve(ftgcr_handle* h, const double* rhs, double* x, const ftgcr_fault_plan* plan, void* stream) {
+// The work of ftgcr_solve up to the copy of the solution back, enqueued on
+// the stream without waiting for it.
+static int solve_enqueue(ftgcr_handle* h, const double* rhs, double* x, const ftgcr_fault_plan* plan,
+                         cudaStream_t st) {
   if (!h || !rhs || !x) return FTGCR_ERR_ARG;
   int rc = validate_plan(h, plan);
   if (rc) return rc;
-  cudaStream_t st = (cudaStream_t)stream;
   const bool rdev = is_device_ptr(rhs), xdev = is_device_ptr(x);
   const double* R = rhs;
   double* X = x;
@@ -1420,10 +1422,22 @@ int ftgcr_solve(ftgcr_handle* h, const double* rhs, double* x, const ftgcr_fault
                                    : solve_async_impl<double>(h, R, X, X, plan, st, check);
   if (rc) return rc;
   if (!xdev) CK(cudaMemcpyAsync(x, h->stageX, sizeof(double) * h->N, cudaMemcpyDeviceToHost, st));
+  return FTGCR_OK;
+}
+
+int ftgcr_solve(ftgcr_handle* h, const double* rhs, double* x, const ftgcr_fault_plan* plan, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const int rc = solve_enqueue(h, rhs, x, plan, st);
+  if (rc) return rc;
   CK(cudaStreamSynchronize(st));
   h->last_status = status_from_result(h);
   trace_dump(h->grid);
   return h->last_status;
+}
+
+int ftgcr_solve_host_async(ftgcr_handle* h, const double* rhs, double* x, const ftgcr_fault_plan* plan,
+                           void* stream) {
+  return solve_enqueue(h, rhs, x, plan, (cudaStream_t)stream);
 }
 
 int ftgcr_stats(ftgcr_handle* h, ftgcr_stats_t* out) {

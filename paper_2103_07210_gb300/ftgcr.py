@@ -43,7 +43,7 @@ EXPORTS = ["ftgcr_create", "ftgcr_solve", "ftgcr_solve_async", "ftgcr_stats", "f
            "ftgcr_apply_operator", "ftgcr_apply_precond", "ftgcr_footprint", "ftgcr_destroy", "ftgcr_error_string",
            "ftgcr_solve_noalloc", "ftgcr_set_coeffs", "ftgcr_server_create", "ftgcr_server_submit",
            "ftgcr_server_poll", "ftgcr_server_wait", "ftgcr_server_next", "ftgcr_server_info",
-           "ftgcr_server_destroy", "ftgcr_tune", "ftgcr_fp64_fma_rate"]
+           "ftgcr_server_destroy", "ftgcr_tune", "ftgcr_fp64_fma_rate", "ftgcr_solve_host_async"]
 NOALLOC_MAX_POINTS, NOALLOC_MAX_K = 16384, 4
 TUNE_MAX_CONCURRENCY = 256
 
@@ -150,6 +150,7 @@ def lib():
         L.ftgcr_create.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Coeffs), i32, dbl, ctypes.POINTER(vp)]
         L.ftgcr_solve.argtypes = [vp, vp, vp, ctypes.POINTER(FaultPlan), vp]
         L.ftgcr_solve_async.argtypes = [vp, vp, vp, ctypes.POINTER(FaultPlan), vp]
+        L.ftgcr_solve_host_async.argtypes = [vp, vp, vp, ctypes.POINTER(FaultPlan), vp]
         L.ftgcr_stats.argtypes = [vp, ctypes.POINTER(Stats)]
         L.ftgcr_solve_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                         ctypes.POINTER(ctypes.POINTER(FaultPlan)), i32, vp]
@@ -301,6 +302,19 @@ class Solver:
         st = lib().ftgcr_solve_async(self.h, rp, xp, ctypes.byref(plan) if plan else None, _stream_ptr(stream))
         if st < 0:
             raise FTGCRError(st, "ftgcr_solve_async")
+
+    def solve_host_async(self, rhs, x, faults=(), stream=None, losses=()) -> None:
+        """Enqueue a solve whose rhs and x may be host arrays (pinned for the
+        copies to overlap other work): staging copies, finiteness check,
+        solve and the copy back into x, all on `stream`, without waiting.
+        rhs and x must stay alive until the stream has passed the solve;
+        stats()["status"] then gives its status."""
+        rp, rk = _ptr(rhs)
+        xp, xk = _ptr(x)
+        plan, keep = _plan(faults, losses)
+        st = lib().ftgcr_solve_host_async(self.h, rp, xp, ctypes.byref(plan) if plan else None, _stream_ptr(stream))
+        if st < 0:
+            raise FTGCRError(st, "ftgcr_solve_host_async")
 
     def stats(self) -> dict:
         s = Stats()

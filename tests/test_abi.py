@@ -116,3 +116,9 @@ def test_fma_rate_probe_refuses_bad_arguments_before_any_device_call():
     import torch
     if not torch.cuda.is_available():
         assert L.ftgcr_fp64_fma_rate(16, ctypes.byref(t), None) == ftgcr.ERR_CUDA and t.value == 0.0
+
+
+def test_host_async_solve_refuses_null_arguments_before_any_device_call():
+    L = ftgcr.lib()
+    buf = (ctypes.c_double * 4)()
+    assert L.ftgcr_solve_host_async(None, buf, buf, None, None) == ftgcr.ERR_ARG
