@@ -43,3 +43,17 @@ def test_fp64_tuning_keeps_the_oracle_decisions():
     assert st == ftgcr.OK and s["tiles"] == t["tiles"]
     assert s["steps"] == ref["steps"] and s["detect_steps"] == ref["detect_steps"]
     assert rel_err(x, ref["x"]) <= 1e-10
+
+
+def test_fp64_wide_rows_tuning_reaches_global_factor_layouts():
+    # 2048 columns: staged factors allow 1-row bands only; thicker bands read
+    # the factors from global memory, and the tuner times both kinds
+    p = inputs.hill_problem(2048, 48, rhs="random", seed=5)
+    t = ftgcr.tune(p.D, p.mu, k=4, tol=1e-10, precision="fp64", concurrency=1)
+    assert 0 < t["ms"] <= t["default_ms"] and t["candidates"] >= 3
+    ref = oracle.ftgcr(p.D, p.R, p.mu, 4, 1e-10)
+    st, x, s = _solve(p, 4, 1e-10, "fp64", t["tiles"], "auto")
+    assert st == ftgcr.OK and s["tiles"] == t["tiles"]
+    assert s["global_factors"] == (-(-48 // t["tiles"]) > 1)
+    assert s["steps"] == ref["steps"] and s["detect_steps"] == ref["detect_steps"]
+    assert rel_err(x, ref["x"]) <= 1e-10
