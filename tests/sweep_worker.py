@@ -8,12 +8,35 @@ def decisions(o):
     return (o["steps"], tuple(o["detect_steps"]), bool(o["converged"]), o["faults_detected"])
 
 
+def min_margin(o):
+    """Smallest |1 - ||r_t||^2 / ||r_prev||^2| over the fault tests of an oracle
+    run whose reference norm the history fixes: step 1 (against ||r^0||^2) and
+    every step after an accepted one (against that step's norm).  A step after
+    a detected fault tests against the restored backup's norm and is left out,
+    as are the exit steps (the exit test comes first) and non-finite norms
+    (their test is not close).  Returns inf when no test qualifies."""
+    h, ev = o["nrm2_hist"], o["events"]
+    best = float("inf")
+    for t in range(len(h)):
+        if ev[t] == oracle.EVENT_EXIT:
+            continue
+        if t == 0:
+            prev = o["nrm2_0"]
+        elif ev[t - 1] == oracle.EVENT_ACCEPT:
+            prev = h[t - 1]
+        else:
+            continue
+        if prev > 0 and abs(h[t]) < float("inf"):
+            best = min(best, abs(1.0 - h[t] / prev))
+    return best
+
+
 def oracle_trial(args):
     nlon, nlat, k, tol, seed, trial, nff = args
     p = inputs.hill_problem(nlon, nlat)
     f = inputs.sweep_flip(seed, trial, nff, nlon * nlat)
     o = oracle.ftgcr(p.D, p.R, p.mu, k, tol, faults=[f])
-    return trial, f, decisions(o), o["faults_injected"], o["x"]
+    return trial, f, decisions(o), o["faults_injected"], o["x"], min_margin(o)
 
 
 def fp64_bit_of_fp32_bit(b):
