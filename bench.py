@@ -149,6 +149,18 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x, device):
+    """The largest of x over the ranks of the initialised process group (x
+    itself without one): the slowest rank's time is the job's time."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -677,12 +689,7 @@ def run_ours(args):
 
     # max over ranks
     tot = float(ms_mx.sum())
-    if ws > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([tot], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot = float(t.item())
+    tot = max_over_ranks(tot, dev)
     ms_step = tot / args.steps
     value = ws * 1e3 / ms_step
 
