@@ -585,7 +585,7 @@ def bench_serving(torch, ftgcr, dev, n_req=2000, load=0.8, seed=7, hills_per_siz
                     with lock:
                         i, x = xs.pop(t)
                     if i in sample:
-                        kept[t] = (i, x.numpy().copy())
+                        kept[t] = (i, x.numpy().copy(), ss["tiles"])
                     give_x(x)
                     done += 1
                 th.join()
@@ -604,10 +604,10 @@ def bench_serving(torch, ftgcr, dev, n_req=2000, load=0.8, seed=7, hills_per_siz
         # a sample of served results against the same request solved alone
         same = True
         for t in sorted(kept):
-            i, x = kept[t]
+            i, x, tl = kept[t]  # the bands the server reported for the request
             pi, faults = reqs[i]
             p = probs[pi][0]
-            tl, rd = layout(p)
+            _, rd = layout(p)
             with ftgcr.Solver(p.D, p.mu, k=K, tol=TOL, precision="mixed", tiles=tl, rounds=rd) as s:
                 xa = np.zeros_like(p.R)
                 s.solve(p.R, xa, faults=faults)

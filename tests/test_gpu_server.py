@@ -3,7 +3,8 @@ precisions, submitted while others run, each come back bitwise equal (solution
 and counters) to the same request solved alone; handles are reused across
 requests of the same shape with new coefficients; admission respects the
 memory budget; invalid requests are refused at submit; host inputs holding
-non-finite values complete with an argument error."""
+non-finite values complete with an argument error.  Each solo run uses the
+row bands the server reported for the request."""
 import time
 
 import numpy as np
@@ -39,8 +40,9 @@ def _requests(seed):
     return out
 
 
-def _alone(p, prec, faults, k):
-    with ftgcr.Solver(p.D, p.mu, k=k, tol=1e-10, precision=prec) as s:
+def _alone(p, prec, faults, k, tiles=0):
+    # tiles: the bands the server reported for the request
+    with ftgcr.Solver(p.D, p.mu, k=k, tol=1e-10, precision=prec, tiles=tiles) as s:
         R = torch.from_numpy(p.R).cuda()
         x = torch.zeros_like(R)
         s.solve(R, x, faults=faults)
@@ -51,7 +53,6 @@ def _alone(p, prec, faults, k):
 def test_served_results_are_bitwise_the_solo_results(epoch_rounds):
     reqs = _requests(101)
     k = 4
-    alone = [_alone(p, prec, f, k) for p, prec, f in reqs]
     with ftgcr.Server(max_slots=4, epoch_rounds=epoch_rounds) as srv:
         Ds = [torch.from_numpy(p.D).cuda() for p, _, _ in reqs]
         Rs = [torch.from_numpy(p.R).cuda() for p, _, _ in reqs]
@@ -72,9 +73,11 @@ def test_served_results_are_bitwise_the_solo_results(epoch_rounds):
             results = [srv.wait(t, timeout=120) for t in tickets]
         info = srv.info()
     assert info["completed"] == len(reqs) and info["queued"] == 0 and info["running"] == 0
-    for q, (res, (xa, sa)) in enumerate(zip(results, alone)):
+    for q, res in enumerate(results):
         assert res is not None, q
         st, ss = res
+        p, prec, f = reqs[q]
+        xa, sa = _alone(p, prec, f, k, ss["tiles"])
         assert st == ftgcr.OK and sa["converged"], (q, st, sa)
         assert np.array_equal(xs[q].cpu().numpy(), xa), q
         for key in KEYS:
@@ -83,11 +86,11 @@ def test_served_results_are_bitwise_the_solo_results(epoch_rounds):
 
 def test_host_arrays_are_served_like_device_arrays():
     p = inputs.hill_problem(128, 64, **inputs.random_hill(7))
-    xa, sa = _alone(p, "mixed", (), 4)
     with ftgcr.Server(max_slots=2) as srv:
         x = np.zeros_like(p.R)
         t = srv.submit(p.D, p.mu, p.R, x, k=4, precision="mixed")
         st, ss = srv.wait(t, timeout=60)
+    xa, sa = _alone(p, "mixed", (), 4, ss["tiles"])
     assert st == ftgcr.OK
     assert np.array_equal(x, xa)
     assert ss["steps"] == sa["steps"]
@@ -107,7 +110,7 @@ def test_a_pooled_handle_takes_the_next_requests_coefficients():
             out.append((x.cpu().numpy(), ss))
         assert srv.info()["handles"] == 1
     for p, (x, ss) in zip((a, b, a), out):
-        xa, sa = _alone(p, "fp64", (), 4)
+        xa, sa = _alone(p, "fp64", (), 4, ss["tiles"])
         assert np.array_equal(x, xa) and ss["steps"] == sa["steps"]
 
 
@@ -123,7 +126,7 @@ def test_coefficient_keys_reuse_set_up_handles_correctly():
             assert st == ftgcr.OK
             out.append((p, x.cpu().numpy(), ss))
     for p, x, ss in out:
-        xa, sa = _alone(p, "fp64", (), 4)
+        xa, sa = _alone(p, "fp64", (), 4, ss["tiles"])
         assert np.array_equal(x, xa) and ss["steps"] == sa["steps"]
 
 
@@ -150,7 +153,7 @@ def test_admission_stays_within_the_budget():
     assert peak <= budget
     assert all(r[0] == ftgcr.OK for r in res)
     for p, x, (st, ss) in zip(probs, xs, res):
-        xa, sa = _alone(p, "fp64", (), 4)
+        xa, sa = _alone(p, "fp64", (), 4, ss["tiles"])
         assert np.array_equal(x.cpu().numpy(), xa) and ss["steps"] == sa["steps"]
 
 
@@ -170,7 +173,6 @@ def test_non_finite_host_inputs_complete_with_an_argument_error():
     # host arrays are staged and checked on the device: the request does not
     # start, completes with ERR_ARG and leaves x as it was; the others run
     p = inputs.hill_problem(64, 32)
-    xa, sa = _alone(p, "fp64", (), 4)
     with ftgcr.Server(max_slots=2) as srv:
         bad = p.R.copy()
         bad[3, 5] = np.nan
@@ -186,4 +188,5 @@ def test_non_finite_host_inputs_complete_with_an_argument_error():
         st_ok, ss = srv.wait(t_ok, timeout=60)
     assert st_bad == ftgcr.ERR_ARG and np.all(x_bad == 0.25)
     assert st_inf == ftgcr.ERR_ARG
+    xa, sa = _alone(p, "fp64", (), 4, ss["tiles"])
     assert st_ok == ftgcr.OK and np.array_equal(x_ok, xa) and ss["steps"] == sa["steps"]

@@ -117,11 +117,12 @@ def test_batched_split_solves_equal_alone():
 
 def test_served_split_solves_equal_alone():
     probs = [inputs.hill_problem(n, m, **inputs.random_hill(80 + n)) for n, m in ((128, 64), (256, 128), (96, 48))]
-    alone = [_solve(p, 4, 1e-10, "split") for p in probs]
     with ftgcr.Server(max_slots=4, epoch_rounds=7) as srv:
         xs = [np.zeros_like(p.R) for p in probs]
         ts = [srv.submit(p.D, p.mu, p.R, x, precision="mixed", rounds="split") for p, x in zip(probs, xs)]
         res = [srv.wait(t, timeout=60) for t in ts]
+    # solo runs with the bands the server reported
+    alone = [_solve(p, 4, 1e-10, "split", tiles=ss["tiles"]) for p, (_, ss) in zip(probs, res)]
     for q, (st, ss) in enumerate(res):
         assert st == ftgcr.OK and ss["split_rounds"]
         assert np.array_equal(xs[q], alone[q][1]) and ss["steps"] == alone[q][2]["steps"], q

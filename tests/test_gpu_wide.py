@@ -109,17 +109,17 @@ def test_served_fp64_wide_rows_equal_solo():
     # the server's FP64 table launches the wide-row instance while a
     # global-factor request is in it, staged requests alongside
     probs = [inputs.hill_problem(n, m, rhs="random", seed=n * m) for n, m in ((4096, 24), (128, 64), (2048, 160))]
-    alone = []
-    for p in probs:
-        st, x, s = _solve(p, 4, 1e-10, "fp64")
-        alone.append((x, s))
-    assert [a[1]["global_factors"] for a in alone] == [True, False, True]
     with ftgcr.Server(max_slots=4, epoch_rounds=7) as srv:
         Rs = [torch.from_numpy(p.R).cuda() for p in probs]
         xs = [torch.zeros_like(R) for R in Rs]
         tickets = [srv.submit(torch.from_numpy(p.D).cuda(), p.mu, R, x, k=4, tol=1e-10, precision="fp64")
                    for p, R, x in zip(probs, Rs, xs)]
         results = [srv.wait(t, timeout=120) for t in tickets]
+    alone = []
+    for p, (_, ss) in zip(probs, results):  # solo runs with the bands the server reported
+        st, x, s = _solve(p, 4, 1e-10, "fp64", tiles=ss["tiles"])
+        alone.append((x, s))
+    assert [a[1]["global_factors"] for a in alone] == [True, False, True]
     for q, ((st, ss), (xa, sa)) in enumerate(zip(results, alone)):
         assert st == ftgcr.OK, (q, st)
         assert np.array_equal(xs[q].cpu().numpy(), xa), q
