@@ -292,21 +292,30 @@ int ftgcr_tune(const ftgcr_grid* grid, const ftgcr_coeffs* coeffs, int32_t k, do
                ftgcr_tuning_t* out);
 
 /* No-allocation FP64 solve.  The paper has no counterpart: this entry point
- * exists for callers that cannot allocate device memory when they solve
- * (code running while a stream is being captured, where cudaMalloc is not
- * permitted; processes whose device memory belongs to another allocator;
- * code that must not fail with out-of-memory mid-run).  It solves L(x) = rhs
- * like ftgcr_solve with FTGCR_FP64 and the line preconditioner, without a
- * handle, and calls no cudaMalloc, cudaFree or other allocating routine:
- * every Krylov vector, coefficient, factor and bookkeeping record lives in
- * one static device array of FTGCR_NOALLOC_SCRATCH_BYTES that every GPU
- * loading the library holds until the process exits.
+ * exists for callers that cannot allocate device memory when they solve:
+ * processes whose device memory belongs entirely to another allocator (a
+ * framework's caching pool, a fixed arena reserved at start-up), and code that
+ * must not fail with out-of-memory in the middle of a run.  It solves
+ * L(x) = rhs like ftgcr_solve with FTGCR_FP64 and the line preconditioner,
+ * without a handle, and calls no cudaMalloc, cudaFree or other allocating
+ * routine: every Krylov vector, coefficient, factor and bookkeeping record
+ * lives in one static device array of FTGCR_NOALLOC_SCRATCH_BYTES that every
+ * GPU loading the library holds until the process exits.
  *  - Limits: nlon * nlat <= FTGCR_NOALLOC_MAX_POINTS, k <= FTGCR_NOALLOC_MAX_K;
  *    larger sizes return FTGCR_ERR_ARG.
  *  - D, rhs, x: device pointers (x: initial guess in, solution out); stats
- *    may be NULL.  Blocks until done; returns like ftgcr_solve.
- *  - The first call on a device looks up the array's device address (set-up);
- *    make that first call before any stream capture begins.
+ *    may be NULL.  Returns like ftgcr_solve.
+ *  - The call is blocking: it copies the grid geometry and the solve record
+ *    from host (stack) memory to the device, copies the result record back,
+ *    and synchronises the stream before it returns.  It is therefore not for
+ *    use while a stream is being captured into a CUDA graph
+ *    (ftgcr_solve_async is the capturable solve).
+ *  - It does not raise the per-thread stack limit (that may allocate): the
+ *    current cudaLimitStackSize must cover the solve kernel's frame plus
+ *    256 bytes, the margin ftgcr_create keeps, or the call returns
+ *    FTGCR_ERR_ARG.  The CUDA default limit covers the FP64 kernels; an
+ *    earlier ftgcr_create or the caller may also have raised it.
+ *  - The first call on a device looks up the array's device address (set-up).
  *  - All calls share the array, which keeps the last call's contents; each
  *    call clears the part it uses before it starts, so a result does not
  *    depend on earlier calls.  Calls that overlap on the GPU (other threads,

@@ -1669,13 +1669,14 @@ int handle_precision(const ftgcr_handle* h) { return h->precision; }
 }  // namespace ftgcr
 
 // ------------------------------------------------------------ no-allocation solve
-// Some callers cannot allocate device memory when they solve: code that runs
-// while a stream is being captured (cudaMalloc is not permitted then), code
-// whose device memory is owned entirely by another allocator, and code that
-// must not fail with out-of-memory in the middle of a run.  For them,
-// ftgcr_solve_noalloc keeps all of its scratch in the static device array
-// below instead of allocating a handle's pool.  Every GPU that loads the
-// library holds the array until the process exits.
+// Some callers cannot allocate device memory when they solve: processes whose
+// device memory is owned entirely by another allocator (a framework's caching
+// pool, an arena reserved at start-up), and code that must not fail with
+// out-of-memory in the middle of a run.  For them, ftgcr_solve_noalloc keeps
+// all of its scratch in the static device array below instead of allocating a
+// handle's pool.  Every GPU that loads the library holds the array until the
+// process exits.  The call blocks (it stages small records through host
+// memory and synchronises its stream), so it is not meant for stream capture.
 constexpr long long kNoAllocMaxPoints = FTGCR_NOALLOC_MAX_POINTS;
 constexpr int kNoAllocMaxK = FTGCR_NOALLOC_MAX_K;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[FTGCR_NOALLOC_SCRATCH_BYTES];
@@ -1792,12 +1793,13 @@ extern "C" int ftgcr_solve_noalloc(const ftgcr_grid* grid, const double* D, int3
   if (rc) return rc;
   if (occ < 1) return FTGCR_ERR_ARG;
   {
-    // no stack resize here (it may allocate): the current limit must do
+    // no stack resize here (it may allocate): the current limit must cover
+    // the kernel's frame with the margin ftgcr_create keeps
     cudaFuncAttributes fa;
     CK(cudaFuncGetAttributes(&fa, kernel_ptr<double>(kb, h.wide)));
     size_t cur = 0;
     CK(cudaDeviceGetLimit(&cur, cudaLimitStackSize));
-    if (fa.localSizeBytes > cur) return FTGCR_ERR_ARG;
+    if (fa.localSizeBytes + 256 > cur) return FTGCR_ERR_ARG;
   }
   const int grid_ctas = std::min(h.nt, di.sms * occ);
   const BeginArgs b = begin_args(&h, rhs, x, x, nullptr);
