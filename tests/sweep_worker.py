@@ -57,3 +57,13 @@ def oracle_mixed_counterpart(args):
     step, vec, idx, bit = inputs.sweep_flip(seed, trial, nsteps, nlon * nlat, nbits=32)
     o = oracle.ftgcr(p.D, p.R, p.mu, k, tol, faults=[(step, vec, idx, fp64_bit_of_fp32_bit(bit))])
     return trial, o["faults_detected"] > 0, o["converged"]
+
+
+def oracle_solution(args):
+    """FP64 oracle solution of a hill problem: (nlon, nlat, k, tol, rhs, seed,
+    hill seed or None for the default hill)."""
+    nlon, nlat, k, tol, rhs, seed, hill_seed = args
+    hill = inputs.random_hill(hill_seed) if hill_seed is not None else {}
+    p = inputs.hill_problem(nlon, nlat, rhs=rhs, seed=seed, **hill)
+    o = oracle.ftgcr(p.D, p.R, p.mu, k, tol)
+    return o["x"], o["converged"], o["steps"]
