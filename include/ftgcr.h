@@ -106,6 +106,17 @@ typedef struct {
  * FTGCR_ERR_ARG. */
 #define FTGCR_FLAG_SPLIT_ROUNDS 2
 #define FTGCR_FLAG_FUSED_ROUNDS 4
+/* FTGCR_MIXED with the line preconditioner: streamed step rounds, the
+ * default for solves of at least 4 Mi points (their Krylov vectors far
+ * outgrow the L2 cache).  Each CTA takes one tall band of rows (one band per
+ * SM) and walks it row by row: the step's axpy, the row's line solve and the
+ * stencil of the row below it, with every operand row brought into shared
+ * memory by bulk asynchronous copies issued ahead of the arithmetic.  Only a
+ * band's first and last rows wait for a neighbouring band's e, in a second
+ * pass.  Needs nlon a multiple of 4; with FTGCR_FLAG_SPLIT_ROUNDS or
+ * FTGCR_FLAG_FUSED_ROUNDS, another precision or preconditioner, or rows too
+ * wide for the ring of shared-memory slots a step needs: FTGCR_ERR_ARG. */
+#define FTGCR_FLAG_STREAMED_ROUNDS 8
 
 typedef struct {
   const double* D;   /* [nlat][nlon] cell-centred coefficient (column depth 1 - h), > 0 */
@@ -179,7 +190,8 @@ typedef struct {
   int32_t tiles;           /* row bands used */
   int32_t status;          /* status of the last solve */
   int64_t loss_events;     /* data-loss events that fired */
-  int32_t split_rounds;    /* 1: the solve ran split rounds (FTGCR_FLAG_SPLIT_ROUNDS) */
+  int32_t split_rounds;    /* 1: the solve ran split rounds (FTGCR_FLAG_SPLIT_ROUNDS);
+                              2: streamed step rounds (FTGCR_FLAG_STREAMED_ROUNDS) */
   int32_t global_factors;  /* 1: FP64 line solve reading its factors from global memory
                               (wide rows: staging them would thin the bands) */
 } ftgcr_stats_t;
@@ -280,7 +292,8 @@ const char* ftgcr_error_string(int status);
 typedef struct {
   int32_t tiles;          /* chosen row bands */
   int32_t flags;          /* round layout to OR into ftgcr_grid.flags: 0 (FP64, other
-                             preconditioners), FTGCR_FLAG_FUSED_ROUNDS or FTGCR_FLAG_SPLIT_ROUNDS */
+                             preconditioners), FTGCR_FLAG_FUSED_ROUNDS, FTGCR_FLAG_SPLIT_ROUNDS or
+                             FTGCR_FLAG_STREAMED_ROUNDS */
   double ms;              /* launch time of the chosen layout, ms */
   int32_t default_tiles;  /* the band count ftgcr_create picks by itself */
   double default_ms;      /* its launch time, ms */

@@ -555,7 +555,42 @@ struct SmemPlan {
   long long cs_off;  // elements of the inner type
   int cs_clobber;
   int gconsts;  // FP64 line solve: factors read from global memory, not staged
+  int sub_h;    // streamed solves: rows per sub-band of the split INIT / OUT rounds
+  int nslot;    // streamed solves: stage buffers of the step rounds (stages in flight + 1)
 };
+
+// Streamed step rounds (mixed path, line preconditioner): the shared memory
+// of a band of nlon columns.  Fixed part: three e rows and one row of line-
+// solve constants; then stage buffers of kNVS rows of kCW floats (and their
+// Tx leads): three (two stages in flight) where rows span at least two
+// chunks and memory allows, else two.  The split INIT and OUT rounds of the
+// same solve walk the band in sub-bands of sub_h rows that fit the same
+// memory.  Returns false where two stage buffers do not fit.
+bool stream_plan(int nlon, int k, size_t limit, SmemPlan* p) {
+  (void)k;  // stages of more than kNVS operand rows are taken in sub-stages
+  if (nlon % 4 != 0 || nlon < 4) return false;
+  const size_t st = (size_t)row_stride(nlon), per_row = 32 * (size_t)chunk_len(nlon);
+  const size_t fixed = (3 * st + 3 * per_row) * sizeof(float);
+  const size_t buf = (size_t)kNVS * kCW * sizeof(float) + 8 * 16;
+  int nbuf = (nlon > kCW && fixed + 3 * buf <= limit) ? 3 : 2;
+  if (fixed + nbuf * buf > limit) return false;
+  auto split_bytes = [&](size_t h) {
+    return std::max({h * st * sizeof(float) + 3 * h * per_row * sizeof(float), (h + 2) * st * sizeof(float),
+                     (h + 2) * st * sizeof(double)});
+  };
+  int sub = 0;
+  for (int h = 1; h <= kMaxStreamRows; ++h)
+    if (split_bytes((size_t)h) <= limit) sub = h;
+  if (sub < 1) return false;
+  p->bytes = std::max(fixed + (size_t)nbuf * buf, split_bytes((size_t)sub));
+  p->cs_off = (long long)((size_t)sub * st);
+  p->cs_clobber = 1;
+  p->gconsts = 0;
+  p->sub_h = sub;
+  p->nslot = nbuf;
+  return true;
+}
+
 SmemPlan smem_plan(int nlon, int nlat, int nt, int mixed, size_t elem, int precond, int split, size_t limit,
                    int gconsts = 0) {
   const size_t h = (size_t)((nlat + nt - 1) / nt);
@@ -565,6 +600,8 @@ SmemPlan smem_plan(int nlon, int nlat, int nt, int mixed, size_t elem, int preco
   const bool line = precond == FTGCR_PRECOND_LINE;
   SmemPlan p;
   p.gconsts = 0;
+  p.sub_h = 0;
+  p.nslot = 0;
   if (!split) {
     p.gconsts = line && !mixed && gconsts;
     // staged: three factor arrays per row; global: each row's factor ring
@@ -595,8 +632,22 @@ SmemPlan smem_plan(int nlon, int nlat, int nt, int mixed, size_t elem, int preco
 // SM count, cuts one-pass tiles below three rows (each tile would then
 // recompute at least twice its own rows as halo), or when one row with its
 // halo rows and their constants does not fit at all.
+// Mixed solves of at least this many points stream their step rounds by
+// default: their Krylov vectors (about 16 FP32 vectors of N) far outgrow the
+// 129 MB L2, so a round is bound by HBM rather than by L2 latency.  Smaller
+// solves run faster in one-pass rounds (measured: 2048 x 1024 83 against 122
+// us per inner step; 4096 x 2048 352 streamed against 401 split).
+constexpr long long kStreamMinPoints = 4LL * 1024 * 1024;
+
+// Streamed step rounds: one band per SM (at most kMaxStreamRows rows).
+int stream_tiles(int nlat, int tiles, int sms) {
+  int nt = tiles > 0 ? std::min(tiles, nlat) : std::min(nlat, sms);
+  if ((nlat + nt - 1) / nt > kMaxStreamRows) nt = (nlat + kMaxStreamRows - 1) / kMaxStreamRows;
+  return nt;
+}
+
 void choose_tiling(int nlon, int nlat, int mixed, size_t elem, int precond, int flags, int tiles, int sms,
-                   size_t limit, int* nt_out, int* split_out, int* gconsts_out) {
+                   size_t limit, int k, int* nt_out, int* split_out, int* gconsts_out) {
   const int hpar = (nlat + sms - 1) / sms;  // band height the SM count alone gives
   auto fit = [&](int split, int gc = 0) {
     int nt = (nlat + hpar - 1) / hpar;
@@ -624,6 +675,15 @@ void choose_tiling(int nlon, int nlat, int mixed, size_t elem, int precond, int 
   }
   int split = 0;
   if (mixed && precond == FTGCR_PRECOND_LINE) {
+    SmemPlan sp;
+    const bool can_stream = stream_plan(nlon, k, limit, &sp);
+    if ((flags & FTGCR_FLAG_STREAMED_ROUNDS) ||
+        (!(flags & (FTGCR_FLAG_SPLIT_ROUNDS | FTGCR_FLAG_FUSED_ROUNDS)) && can_stream &&
+         (long long)nlon * nlat >= kStreamMinPoints)) {
+      *split_out = can_stream ? 2 : -1;  // -1: streamed rounds asked for but impossible
+      *nt_out = stream_tiles(nlat, tiles, sms);
+      return;
+    }
     if (flags & FTGCR_FLAG_SPLIT_ROUNDS)
       split = 1;
     else if (!(flags & FTGCR_FLAG_FUSED_ROUNDS)) {
@@ -699,7 +759,7 @@ int kbound(int k) { return k <= 4 ? 4 : (k <= 8 ? 8 : 16); }
 // compile in parallel.  wide: the wide-row instance.
 template <typename T>
 const void* kernel_ptr(int kb, int wide) {
-  return ftgcr::persistent_kernel_ptr(kb, sizeof(T) == 8, wide != 0);
+  return ftgcr::persistent_kernel_ptr(kb, sizeof(T) == 8, wide);
 }
 
 // The dynamic shared memory attribute of a kernel is process-wide: only ever
@@ -917,6 +977,8 @@ int create_impl(ftgcr_handle* h, const double* D_host_or_dev, bool D_on_device) 
   sd.cs_off = (int)h->plan.cs_off;
   sd.cs_clobber = h->plan.cs_clobber;
   sd.cs_global = h->plan.gconsts;
+  sd.sub_h = h->plan.sub_h;
+  sd.nslot = h->plan.nslot;
   sd.Tx64 = h->Tx64;
   sd.Ty64 = h->Ty64;
   sd.muA64 = h->muA64;
@@ -1081,7 +1143,7 @@ int solve_batch_impl(ftgcr_handle* const* hs, const double* const* rhs, double* 
   long long max_steps = 0, total_tiles = 0;
   int max_outer = 0, split = 0;
   for (int i = 0; i < n; ++i) {
-    split |= hs[i]->wide;
+    split = std::max(split, hs[i]->wide);
     kb = std::max(kb, kbound(hs[i]->k));
     smem = std::max(smem, hs[i]->smem);
     max_steps = std::max(max_steps, hs[i]->max_steps);
@@ -1190,7 +1252,7 @@ int table_run_impl(SlotTableImpl* t, int max_rounds, cudaStream_t st) {
   int split = 0;
   for (ftgcr_handle* h : t->slot)
     if (h) {
-      split |= h->wide;
+      split = std::max(split, h->wide);
       kb = std::max(kb, kbound(h->k));
       smem = std::max(smem, h->smem);
       tiles += h->nt;
@@ -1275,9 +1337,12 @@ static int check_grid(const ftgcr_grid* g, int32_t k, double tol) {
   if (!(tol > 0.0) || !std::isfinite(tol)) return FTGCR_ERR_ARG;
   if (g->max_steps < 0 || g->tiles < 0 || g->max_outer < 0 || !(g->inner_tol >= 0.0) || g->inner_tol >= 1.0)
     return FTGCR_ERR_ARG;
-  if (g->flags & ~(FTGCR_FLAG_UNPROTECTED | FTGCR_FLAG_SPLIT_ROUNDS | FTGCR_FLAG_FUSED_ROUNDS)) return FTGCR_ERR_ARG;
-  if ((g->flags & FTGCR_FLAG_SPLIT_ROUNDS) && (g->flags & FTGCR_FLAG_FUSED_ROUNDS)) return FTGCR_ERR_ARG;
-  if ((g->flags & FTGCR_FLAG_SPLIT_ROUNDS) && (g->precision != FTGCR_MIXED || g->precond != FTGCR_PRECOND_LINE))
+  constexpr int layouts = FTGCR_FLAG_SPLIT_ROUNDS | FTGCR_FLAG_FUSED_ROUNDS | FTGCR_FLAG_STREAMED_ROUNDS;
+  if (g->flags & ~(FTGCR_FLAG_UNPROTECTED | layouts)) return FTGCR_ERR_ARG;
+  const int lf = g->flags & layouts;
+  if (lf & (lf - 1)) return FTGCR_ERR_ARG;  // at most one layout
+  if ((g->flags & (FTGCR_FLAG_SPLIT_ROUNDS | FTGCR_FLAG_STREAMED_ROUNDS)) &&
+      (g->precision != FTGCR_MIXED || g->precond != FTGCR_PRECOND_LINE))
     return FTGCR_ERR_ARG;
   // mu = 0 on a single latitude row leaves the zonal line systems singular
   if (g->mu == 0.0 && g->nlat < 2 && g->precond != FTGCR_PRECOND_IDENTITY) return FTGCR_ERR_ARG;
@@ -1301,8 +1366,19 @@ static void fill_handle_params(ftgcr_handle* h, const ftgcr_grid* g, int32_t k, 
   const bool mixed = g->precision == FTGCR_MIXED;
   const size_t elem = mixed ? sizeof(float) : sizeof(double);
   int gconsts = 0;
-  choose_tiling(g->nlon, g->nlat, mixed, elem, g->precond, g->flags, g->tiles, sms, (size_t)smem_limit, &h->nt,
+  choose_tiling(g->nlon, g->nlat, mixed, elem, g->precond, g->flags, g->tiles, sms, (size_t)smem_limit, k, &h->nt,
                 &h->split, &gconsts);
+  if (h->split == 2) {
+    stream_plan(h->nlon, k, (size_t)smem_limit, &h->plan);
+    h->wide = 2;
+    return;
+  }
+  if (h->split < 0) {  // streamed rounds asked for where they do not fit
+    h->split = 0;
+    h->plan.bytes = (size_t)smem_limit + 1;
+    h->wide = 0;
+    return;
+  }
   h->plan = smem_plan(h->nlon, h->nlat, h->nt, mixed, elem, h->precond, h->split, (size_t)smem_limit, gconsts);
   h->wide = h->split || h->plan.gconsts;
 }

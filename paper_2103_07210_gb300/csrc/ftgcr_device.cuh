@@ -148,7 +148,11 @@ struct SolveDev {
   // grid barrier between them (no recomputed halo rows); cs_off: offset of
   // the staged line-solve constants in the dynamic shared memory (elements);
   // cs_clobber: the second pass's rows overlap them
+  // split 2: streamed step rounds (one tall band per CTA, rows streamed
+  // through nslot shared-memory stage buffers); its other rounds run as
+  // split rounds over sub-bands of at most sub_h rows (0: the whole tile)
   int split, cs_off, cs_clobber;
+  int sub_h, nslot;
   // FP64 line solve: the factors are read from global memory, not staged
   // (wide rows, where staging them would leave bands thinner than the SM
   // count gives)

@@ -1530,12 +1530,10 @@ __device__ __forceinline__ void init_rows(const SolveDev<T>& sd, const Ctx<T>& c
 // and ||R||^2).
 template <typename T>
 __device__ __forceinline__ void init_stencil(const SolveDev<T>& sd, const Ctx<T>& c, const RowTile& rt, const T* sm,
-                                             PhaseSmem& ps, double* part_out, const Acc<T>* an, const Acc<T>* aR,
-                                             bool vec, bool full) {
+                                             PhaseSmem& ps, Acc<T>& a0, Acc<T>& a1, bool vec) {
   const int nlon = sd.nlon, nlat = sd.nlat, stride = row_stride(nlon);
   constexpr int W = V16<T>::W;
   const int nfl = ps.nfl;
-  Acc<T> a0, a1;
   if (vec) {
     // p0 = P^-1 r0 (in the rows), L(p0) and the first dots, 16-byte accesses
     const int nvr = nlon / W, total = (rt.j1 - rt.j0) * nvr;
@@ -1593,6 +1591,11 @@ __device__ __forceinline__ void init_stencil(const SolveDev<T>& sd, const Ctx<T>
       a1.add(lp, lp);
     }
   }
+}
+// The partial sums of INIT (full: also ||r0||^2 and ||R||^2).
+template <typename T>
+__device__ __forceinline__ void init_partials(PhaseSmem& ps, double* part_out, const Acc<T>* an, const Acc<T>* aR,
+                                              const Acc<T>& a0, const Acc<T>& a1, bool full) {
   if (full) {
     cta_red_put(ps.cr, 0, an->warp_sum());
     cta_red_put(ps.cr, 1, aR->warp_sum());
@@ -1624,7 +1627,9 @@ __device__ __noinline__ void phase_init(const SolveDev<T>& sd, const Ctx<T>& c, 
   __syncthreads();
   precond_tile<T, false, GL>(sd, rt.h0, rt.h1 - rt.h0, sm, stride, cs);
   __syncthreads();
-  init_stencil<T>(sd, c, rt, sm, ps, part_out, &an, &aR, vec, true);
+  Acc<T> a0, a1;
+  init_stencil<T>(sd, c, rt, sm, ps, a0, a1, vec);
+  init_partials<T>(ps, part_out, &an, &aR, a0, a1, true);
   if (threadIdx.x == 0) {
     ps.cs_solve = sidx;
     ps.cs_tile = tau;
@@ -1634,121 +1639,152 @@ __device__ __noinline__ void phase_init(const SolveDev<T>& sd, const Ctx<T>& c, 
 // INIT in the kernel instance with split rounds.  mode 0: as phase_init;
 // mode 1: r0 and p0 = P^-1(r0) of the own rows, p0 (unflipped) into the
 // scratch vector e[0], the two norms; mode 2: p0 with its halo rows read back
-// from e[0], L(p0), flips, dots.
+// from e[0], L(p0), flips, dots.  Modes 1 and 2 walk the tile in sub-bands of
+// at most sd.sub_h rows (the tall bands of streamed solves do not fit in
+// shared memory at once); the sums run on over the sub-bands.
 template <typename T>
 __device__ __noinline__ void phase_init_any(const SolveDev<T>& sd, const Ctx<T>& c, int sidx, int tau, T* sm,
                                             PhaseSmem& ps, double* part_out, int mode) {
   const int nlon = sd.nlon, stride = row_stride(nlon);
-  RowTile rt = row_tile(sd.nlat, sd.nt, tau);
+  const RowTile rt = row_tile(sd.nlat, sd.nt, tau);
   if (threadIdx.x == 0)
     ps.nfl = collect_flips(sd, c.t, kStateVecs, (long long)rt.j0 * nlon, (long long)rt.j1 * nlon, ps.fl);
-  Acc<T> an, aR;
+  Acc<T> an, aR, a0, a1;
   constexpr int W = V16<T>::W;
-  if (mode == 2) {
-    stage_rows(sd.e[0], rt.h0, rt.h1, nlon, sm, stride);
-    if (sd.cs_clobber && threadIdx.x == 0) ps.cs_solve = -1;
-    __syncthreads();
-  } else {
-    if (mode == 1) {
-      rt.h0 = rt.j0;
-      rt.h1 = rt.j1;
+  const int sub = (mode == 0 || sd.sub_h <= 0) ? rt.j1 - rt.j0 : sd.sub_h;
+  const bool one = sub >= rt.j1 - rt.j0;  // the whole tile at once
+  for (int a = rt.j0; a < rt.j1; a += sub) {
+    RowTile st;
+    st.j0 = a;
+    st.j1 = min(a + sub, rt.j1);
+    st.h0 = st.j0 > 0 ? st.j0 - 1 : 0;
+    st.h1 = st.j1 < sd.nlat ? st.j1 + 1 : sd.nlat;
+    if (mode == 2) {
+      if (!one) __syncthreads();  // the previous sub-band's rows are read
+      stage_rows(sd.e[0], st.h0, st.h1, nlon, sm, stride);
+      if (sd.cs_clobber && threadIdx.x == 0) ps.cs_solve = -1;
+      __syncthreads();
+    } else {
+      if (mode == 1) {
+        st.h0 = st.j0;
+        st.h1 = st.j1;
+      }
+      T* cs = sm + sd.cs_off;
+      if (!one) {
+        __syncthreads();
+        if (threadIdx.x == 0) ps.cs_solve = -1;
+      }
+      if (!(one && ps.cs_solve == sidx && ps.cs_tile == tau)) stage_line_consts(sd, st.h0, st.h1, cs);
+      __syncthreads();
+      const bool vec = c.zero_guess && ps.nfl == 0 && nlon % W == 0;
+      init_rows<T>(sd, c, st, sm, ps, an, aR, vec);
+      cp_async_wait_all();
+      __syncthreads();
+      precond_tile<T, true>(sd, st.h0, st.h1 - st.h0, sm, stride, cs, mode == 1);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        ps.cs_solve = one ? sidx : -1;
+        ps.cs_tile = tau;
+      }
+      if (mode == 1) {
+        store_rows(sd.e[0], st.h0, st.h1, nlon, sm, stride);
+        continue;
+      }
     }
-    T* cs = sm + sd.cs_off;
-    if (!(ps.cs_solve == sidx && ps.cs_tile == tau)) stage_line_consts(sd, rt.h0, rt.h1, cs);
-    __syncthreads();
     const bool vec = c.zero_guess && ps.nfl == 0 && nlon % W == 0;
-    init_rows<T>(sd, c, rt, sm, ps, an, aR, vec);
-    cp_async_wait_all();
-    __syncthreads();
-    precond_tile<T, true>(sd, rt.h0, rt.h1 - rt.h0, sm, stride, cs, mode == 1);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      ps.cs_solve = sidx;
-      ps.cs_tile = tau;
-    }
-    if (mode == 1) {
-      store_rows(sd.e[0], rt.h0, rt.h1, nlon, sm, stride);
-      cta_red_put(ps.cr, 0, an.warp_sum());
-      cta_red_put(ps.cr, 1, aR.warp_sum());
-      cta_red_finish<T>(ps.cr, 2, part_out);
-      return;
-    }
+    init_stencil<T>(sd, c, st, sm, ps, a0, a1, vec);
   }
-  const bool vec = c.zero_guess && ps.nfl == 0 && nlon % W == 0;
-  init_stencil<T>(sd, c, rt, sm, ps, part_out, &an, &aR, vec, mode == 0);
+  if (mode == 1) {
+    cta_red_put(ps.cr, 0, an.warp_sum());
+    cta_red_put(ps.cr, 1, aR.warp_sum());
+    cta_red_finish<T>(ps.cr, 2, part_out);
+    return;
+  }
+  init_partials<T>(ps, part_out, &an, &aR, a0, a1, mode == 0);
 }
 
 // OUT (mixed): x' = x + d in FP64, r_out = R - L64(x'), ||r_out||^2 (and
-// ||R||^2 the first time), inner right-hand side R_in = (float) r_out.
+// ||R||^2 the first time), inner right-hand side R_in = (float) r_out.  The
+// tile is walked in sub-bands of at most sd.sub_h rows (each staged with its
+// halo rows) when it is taller than shared memory holds.
 template <typename T>
 __device__ __noinline__ void phase_out(const SolveDev<T>& sd, const Ctx<T>& c, int tau, double* smd, PhaseSmem& ps,
                           double* part_out) {
   const int nlon = sd.nlon, nlat = sd.nlat, stride = row_stride(nlon);
-  const RowTile rt = row_tile(nlat, sd.nt, tau);
+  const RowTile rtile = row_tile(nlat, sd.nt, tau);
   if (threadIdx.x == 0) ps.cs_solve = -1;  // its FP64 rows overwrite the staged constants
-  int nz = 0;
-  {
-    // x' = x + d over the tile and its halo rows, as one flat loop so that
-    // each thread keeps several loads in flight
-    const int nrows = rt.h1 - rt.h0, total = nrows * nlon;
-    constexpr int U = 4;
-    for (int b = threadIdx.x; b < total; b += U * kThreads) {
-      double xv[U];
+  AccF64 so, sR;
+  const int sub = sd.sub_h > 0 ? sd.sub_h : rtile.j1 - rtile.j0;
+  for (int a = rtile.j0; a < rtile.j1; a += sub) {
+    RowTile rt;
+    rt.j0 = a;
+    rt.j1 = min(a + sub, rtile.j1);
+    rt.h0 = rt.j0 > 0 ? rt.j0 - 1 : 0;
+    rt.h1 = rt.j1 < nlat ? rt.j1 + 1 : nlat;
+    if (a > rtile.j0) __syncthreads();  // the previous sub-band's rows are read
+    int nz = 0;
+    {
+      // x' = x + d over the sub-band and its halo rows, as one flat loop so
+      // that each thread keeps several loads in flight
+      const int nrows = rt.h1 - rt.h0, total = nrows * nlon;
+      constexpr int U = 4;
+      for (int b = threadIdx.x; b < total; b += U * kThreads) {
+        double xv[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int idx = b + u * kThreads;
-        if (idx < total) {
-          const long long g = (long long)rt.h0 * nlon + idx;
-          xv[u] = ldcg(c.xsrc + g);
-          if (c.d) xv[u] = xv[u] + (double)ldcg(c.d + g);
+        for (int u = 0; u < U; ++u) {
+          const int idx = b + u * kThreads;
+          if (idx < total) {
+            const long long g = (long long)rt.h0 * nlon + idx;
+            xv[u] = ldcg(c.xsrc + g);
+            if (c.d) xv[u] = xv[u] + (double)ldcg(c.d + g);
+          }
         }
-      }
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int idx = b + u * kThreads;
-        if (idx < total) {
-          const int jr = idx / nlon, i = idx - jr * nlon;
-          smd[jr * stride + sk(i)] = xv[u];
-          nz |= xv[u] != 0.0;
-          const int j = rt.h0 + jr;
-          if (j >= rt.j0 && j < rt.j1) c.xdst[(long long)rt.h0 * nlon + idx] = xv[u];
+        for (int u = 0; u < U; ++u) {
+          const int idx = b + u * kThreads;
+          if (idx < total) {
+            const int jr = idx / nlon, i = idx - jr * nlon;
+            smd[jr * stride + sk(i)] = xv[u];
+            nz |= xv[u] != 0.0;
+            const int j = rt.h0 + jr;
+            if (j >= rt.j0 && j < rt.j1) c.xdst[(long long)rt.h0 * nlon + idx] = xv[u];
+          }
         }
       }
     }
-  }
-  // a tile whose x' (halo included) is all zero, as at the start of a solve
-  // from a zero guess, has L64(x') = 0: skip the FP64 stencil
-  const bool zero = !__syncthreads_or(nz);
-  AccF64 so, sR;
-  for (int j = rt.j0; j < rt.j1; ++j) {
-    const long long base = (long long)j * nlon;
-    const double* row = smd + (j - rt.h0) * stride;
-    const bool hasN = j < nlat - 1, hasS = j > 0;
-    if (zero) {
+    // a sub-band whose x' (halo included) is all zero, as at the start of a
+    // solve from a zero guess, has L64(x') = 0: skip the FP64 stencil
+    const bool zero = !__syncthreads_or(nz);
+    for (int j = rt.j0; j < rt.j1; ++j) {
+      const long long base = (long long)j * nlon;
+      const double* row = smd + (j - rt.h0) * stride;
+      const bool hasN = j < nlat - 1, hasS = j > 0;
+      if (zero) {
+        for (int i = threadIdx.x; i < nlon; i += kThreads) {
+          const long long g = base + i;
+          const double Rv = ldcg(sd.R + g);
+          const double ro = Rv - 0.0;
+          sd.Rin[g] = (T)ro;
+          so.add(ro, ro);
+          if (c.first) sR.add(Rv, Rv);
+        }
+        continue;
+      }
       for (int i = threadIdx.x; i < nlon; i += kThreads) {
         const long long g = base + i;
+        const int ie = (i + 1 == nlon) ? 0 : i + 1;
+        const int iw = (i == 0) ? nlon - 1 : i - 1;
+        const double v = row[sk(i)];
+        const double Lx = stencil5_fma(v, row[sk(ie)], row[sk(iw)], hasN ? row[stride + sk(i)] : 0.0,
+                                       hasS ? row[-stride + sk(i)] : 0.0, __ldg(sd.Tx64 + g),
+                                       __ldg(sd.Tx64 + base + iw), hasN ? __ldg(sd.Ty64 + g) : 0.0,
+                                       hasS ? __ldg(sd.Ty64 + g - nlon) : 0.0, __ldg(sd.muA64 + j), hasN, hasS);
         const double Rv = ldcg(sd.R + g);
-        const double ro = Rv - 0.0;
+        const double ro = Rv - Lx;
         sd.Rin[g] = (T)ro;
         so.add(ro, ro);
         if (c.first) sR.add(Rv, Rv);
       }
-      continue;
-    }
-    for (int i = threadIdx.x; i < nlon; i += kThreads) {
-      const long long g = base + i;
-      const int ie = (i + 1 == nlon) ? 0 : i + 1;
-      const int iw = (i == 0) ? nlon - 1 : i - 1;
-      const double v = row[sk(i)];
-      const double Lx = stencil5_fma(v, row[sk(ie)], row[sk(iw)], hasN ? row[stride + sk(i)] : 0.0,
-                                     hasS ? row[-stride + sk(i)] : 0.0, __ldg(sd.Tx64 + g), __ldg(sd.Tx64 + base + iw),
-                                     hasN ? __ldg(sd.Ty64 + g) : 0.0, hasS ? __ldg(sd.Ty64 + g - nlon) : 0.0,
-                                     __ldg(sd.muA64 + j), hasN, hasS);
-      const double Rv = ldcg(sd.R + g);
-      const double ro = Rv - Lx;
-      sd.Rin[g] = (T)ro;
-      so.add(ro, ro);
-      if (c.first) sR.add(Rv, Rv);
     }
   }
   cta_red_put(ps.cr, 0, so.warp_sum());
@@ -1800,6 +1836,10 @@ __device__ __noinline__ void phase_fin(const SolveDev<T>& sd, const Ctx<T>& c, i
   cta_red_put(ps.cr, 0, acc.warp_sum());
   cta_red_finish<T>(ps.cr, 1, part_out);
 }
+
+}  // namespace ftgcr
+#include "ftgcr_stream.cuh"
+namespace ftgcr {
 
 // ------------------------------------------------------------ the kernel
 // Block-wide copies of the per-solve records.  Records written during the
@@ -1886,12 +1926,25 @@ __device__ __forceinline__ void enter_solve(SolveDev<T>* const* solves, KernelSm
 // The phase of tile tau of the solve in ks.  pass 0: a one-pass round, or the
 // first pass of a split round; pass 1: the second pass of a split round (the
 // step phases of split solves only).
-template <typename T, int KB, bool WIDE>
-__device__ __forceinline__ void run_phase(KernelSmem<T>& ks, int pass, int s, int tau, T* sm, double* part_out) {
+template <typename T, int KB, int WIDE>
+__device__ __forceinline__ void run_phase(KernelSmem<T>& ks, int pass, int s, int tau, T* sm, double* part_out,
+                                          int* err) {
   const int kind = ks.c.kind;
-  if constexpr (WIDE && sizeof(T) == 4) {
+  if constexpr (WIDE != 0 && sizeof(T) == 4) {
     const int mode = ks.sd.split ? 1 + pass : 0;
     if (pass == 1 && mode == 0) return;
+    if constexpr (WIDE == 2) {
+      // streamed solves: the step rounds stream rows; the other rounds run as
+      // split rounds over sub-bands
+      if (ks.sd.split == 2 && kind == K_PA) {
+        phase_stream<KB, false>(ks.sd, ks.c, tau, sm, ks.ps, part_out, pass, err);
+        return;
+      }
+      if (ks.sd.split == 2 && kind == K_PF) {
+        phase_stream<KB, true>(ks.sd, ks.c, tau, sm, ks.ps, part_out, pass, err);
+        return;
+      }
+    }
     switch (kind) {
       case K_INIT: phase_init_any<T>(ks.sd, ks.c, s, tau, sm, ks.ps, part_out, mode); return;
       case K_PA: phase_pa_any<T, KB, false>(ks.sd, ks.c, s, tau, sm, ks.ps, part_out, mode); return;
@@ -1902,8 +1955,8 @@ __device__ __forceinline__ void run_phase(KernelSmem<T>& ks, int pass, int s, in
     }
   } else {
     switch (kind) {
-      case K_INIT: phase_init<T, WIDE>(ks.sd, ks.c, s, tau, sm, ks.ps, part_out); return;
-      case K_PA: phase_pa<T, KB, false, WIDE>(ks.sd, ks.c, s, tau, sm, ks.ps, part_out); return;
+      case K_INIT: phase_init<T, WIDE != 0>(ks.sd, ks.c, s, tau, sm, ks.ps, part_out); return;
+      case K_PA: phase_pa<T, KB, false, WIDE != 0>(ks.sd, ks.c, s, tau, sm, ks.ps, part_out); return;
       case K_PF:
         if constexpr (sizeof(T) == 4) phase_pa<T, KB, true>(ks.sd, ks.c, s, tau, sm, ks.ps, part_out);
         return;
@@ -1922,16 +1975,19 @@ __device__ __forceinline__ void run_phase(KernelSmem<T>& ks, int pass, int s, in
 // Persistent cooperative kernel: every round, every CTA takes its share of
 // the tiles of all active solves, runs for each solve the state transition
 // and the decided phase, and then meets the others at one grid barrier.
-// WIDE: the instance for launches with wide-row solves.  Mixed path: solves
+// WIDE 1: the instance for launches with wide-row solves.  Mixed path: solves
 // with split rounds, whose every round takes a second pass over the tiles
 // after a further barrier.  FP64 path: solves whose line solve reads its
-// factors from global memory.  The other instance carries none of that code.
-template <typename T, int KB, bool WIDE>
+// factors from global memory.  WIDE 2 (mixed path): that instance plus the
+// streamed step rounds of HBM-resident solves.  The plain instance carries
+// none of that code.
+template <typename T, int KB, int WIDE>
 __global__ void __launch_bounds__(kThreads, 1) k_ftgcr_persistent(BatchArgs<T> a) {
-  constexpr bool SPLIT = WIDE && sizeof(T) == 4;  // split rounds: mixed path only
-  extern __shared__ __align__(16) unsigned char dsm[];
+  constexpr bool SPLIT = WIDE != 0 && sizeof(T) == 4;  // split rounds: mixed path only
+  extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ KernelSmem<T> ks;
   T* sm = reinterpret_cast<T*>(dsm);
+  if constexpr (WIDE == 2 && sizeof(T) == 4) stream_init();
   const long long round0 = a.ctl->round0;
   const unsigned long long t_start = globaltimer();
   unsigned int nbar = 0;
@@ -2021,7 +2077,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_ftgcr_persistent(BatchArgs<T> a
             a.diag[blockIdx.x * 4 + 3] = tr_items;
           }
         }
-        run_phase<T, KB, WIDE>(ks, pass, s, tau, sm, ks.sd.part + ((long long)par * ks.sd.nt + tau) * kPartStride);
+        run_phase<T, KB, WIDE>(ks, pass, s, tau, sm, ks.sd.part + ((long long)par * ks.sd.nt + tau) * kPartStride,
+                               &a.ctl->err);
         __syncthreads();
         if (pass == 0 && tau == 0) {
           cta_store(ks.sd.st + (par ^ 1), &ks.N);

@@ -1,0 +1,547 @@
+// Streamed step rounds of the mixed path (FP32 inner vectors), for solves
+// whose vectors live in HBM.
+//
+// A streamed solve gives each CTA one tall band of latitude rows and walks the
+// band row by row.  For row j, the step's axpy (with the previous step's
+// direction recurrences fused in, as in the PF round) reads its operand rows
+// through a ring of shared-memory slots.  Thread 0 fills the slots ahead of
+// the consumers with bulk asynchronous copies (cp.async.bulk, one mbarrier per
+// slot), so up to the ring's size of HBM traffic is in flight per SM without
+// holding registers.  r' lands in a row buffer; the row's zonal line solve
+// (all eight warps on the one row) turns it into e, which is written out and
+// kept: three e rows stay in shared memory, so once e of row j exists the
+// stencil L(e) of row j-1 and its dots stream their own operands (face
+// coefficients, r', the L(p^l)) through the same ring.  Only the band's first
+// and last rows need an e row of a neighbouring band; their stencils run in a
+// second pass after a grid barrier.  No row is recomputed as halo and e is not
+// read back, so a step moves about its algorithmic bytes (the line solve's
+// factors, three rows per row, come on top).
+//
+// Every wait on an mbarrier is bounded; a wait that runs out raises the
+// launch's error flag, waits (bounded) for the copies still in flight, and the
+// phase returns, so that the kernel leaves at its next grid barrier.
+#pragma once
+
+namespace ftgcr {
+
+constexpr int kCW = 1024;                      // columns per chunk: one float4 per thread
+constexpr int kMaxStreamRows = 64;             // rows of a streamed band
+constexpr int kMaxRowList = 2 * kMaxStreamRows + 4;
+constexpr unsigned long long kStreamWaitNs = 2000000000ull;  // 2 s per wait
+constexpr unsigned long long kDrainNs = 500000000ull;        // 0.5 s for the copies left after a failure
+
+// Per-CTA state of the streamed phases, in static shared memory of the
+// streamed kernel instance only (no other instance refers to it).
+struct StreamSmem {
+  unsigned long long cfull;            // the line-solve constants of the next row
+  unsigned int cph;                    // the parity cfull's next completion will show
+  int bad;                             // a wait ran out
+  int nrl;                             // entries of rl
+  int rl[kMaxRowList];                 // the pass's row stages: (row << 1) | (0 axpy + line solve, 1 stencil)
+  const float* tab_ax[4 + 2 * kMaxK];  // operand rows of an axpy stage
+  const float* tab_st[4 + kMaxK];      // operand rows of a stencil stage (Ty - nlon: the south faces)
+  float* out[5];                       // p', L(p'), r', phi', L(e) of this step
+  float alpha[kMaxK];
+  float beta;
+  float muA[kMaxStreamRows];           // mu A_j of the band's rows
+  float maps[kWarps * 64];             // line-solve chunk maps
+};
+static __shared__ StreamSmem g_ss;
+
+// ---- PTX: mbarriers, bulk copies, proxy fences
+__device__ __forceinline__ void mbar_init(unsigned a, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(unsigned a, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned a, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+// Wait for the phase of parity `parity` to complete, for at most `limit_ns`.
+__device__ __forceinline__ bool mbar_wait(unsigned a, unsigned parity, unsigned long long limit_ns = kStreamWaitNs) {
+  if (mbar_try(a, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  for (unsigned it = 1;; ++it) {
+    if (mbar_try(a, parity)) return true;
+    if ((it & 31u) == 0u && globaltimer() - t0 > limit_ns) return false;
+  }
+}
+// Global -> shared bulk copy completing on an mbarrier (16-byte aligned
+// addresses, a multiple of 16 bytes).
+__device__ __forceinline__ void bulk_load(unsigned dst, const void* src, unsigned bytes, unsigned mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+// Orders this thread's generic-proxy view of global memory before its later
+// bulk copies (which read through the async proxy).
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ V16<float> lds4(unsigned a) {
+  V16<float> r;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3])
+               : "r"(a));
+  return r;
+}
+
+// 16-byte global -> shared copy of this thread's columns.  No compiler memory
+// clobber: the stage's data are read only after cp.async.wait_group, which
+// carries one, and the rows copied are never written within the same stage.
+__device__ __forceinline__ void cp_async16_nc(unsigned smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem), "l"(gmem));
+}
+__device__ __forceinline__ void sts_nc(unsigned a, float v) { asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v)); }
+
+// Once per launch of the streamed instance, before any phase: the barriers.
+__device__ __forceinline__ void stream_init() {
+  if (threadIdx.x == 0) {
+    mbar_init(smem_addr(&g_ss.cfull), 1);
+    g_ss.cph = 0u;
+    g_ss.bad = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+}
+
+// ---- the ring of stage buffers
+// A stage is one chunk of kCW columns of one row stage: an axpy stage reads
+// L(e), r, e, phi, then L(p^l), p^l for l = 0..nu_o (fused, PF) or L(p^nu),
+// r, p^nu, phi (PA); a stencil stage reads Tx, Ty (north face), Ty of the row
+// below (south face), r', then L(p^l) for l = 0..nu.  A stage with more than
+// kNVS operand rows is taken in sub-stages of kNVS.  Thread t copies, with
+// 16-byte cp.async, columns 4t .. 4t+3 of each operand row of the chunk into
+// the stage buffer and later reads exactly those, so a stage needs no
+// cross-thread synchronisation; lane 0 of each warp also copies the Tx
+// element west of its warp's columns.  sd.nslot stage buffers are used in
+// turn, sd.nslot - 1 stages ahead of the arithmetic.
+constexpr int kNVS = 12;  // operand rows per (sub-)stage
+
+__device__ __forceinline__ void cp_async_wait_n(int n) {
+  if (n <= 0)
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+  else if (n == 1)
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+  else
+    asm volatile("cp.async.wait_group 2;" ::: "memory");
+}
+
+// Operand row v of an axpy stage.
+template <bool FUSED>
+__device__ __forceinline__ const float* ax_src(const Ctx<float>& c, int v) {
+  if constexpr (FUSED) {
+    if (v == 0) return c.LeR;
+    if (v == 1) return c.rC;
+    if (v == 2) return c.eR;
+    if (v == 3) return c.phiC;
+    const int l = (v - 4) >> 1;
+    return ((v - 4) & 1) ? c.pp[l] : c.lo[l];
+  } else {
+    if (v == 0) return c.lpnu;
+    if (v == 1) return c.rC;
+    if (v == 2) return c.pnu;
+    return c.phiC;
+  }
+}
+// This thread's copies of (sub-)stage `sub` of chunk ch of a row stage into
+// stage buffer `buf` (shared address), and, for a stencil stage, lane 0's
+// copy of the Tx element west of its warp's columns into `lead`.  The
+// operand rows come from the pass's tables (tab: axpy or stencil).
+__device__ __forceinline__ void stream_copy(const float* const* tab, const float* Tx, int n, int nlat, int type,
+                                            int row, int ch, int sub, int nv, unsigned buf, unsigned lead) {
+  const int c0 = ch * kCW, i4 = 4 * (int)threadIdx.x;
+  const long long ro = (long long)row * n;
+  const int v0 = sub * kNVS;
+  if (type == 1 && sub == 0 && (threadIdx.x & 31) == 0) {
+    const int w0 = c0 + 128 * (int)(threadIdx.x >> 5);
+    if (w0 < n) cp_async16_nc(lead + 16u * (threadIdx.x >> 5), Tx + ro + (w0 >= 4 ? w0 - 4 : n - 4));
+  }
+  if (c0 + i4 >= n) return;
+  const long long off = ro + c0 + i4;
+#pragma unroll
+  for (int q = 0; q < kNVS; ++q) {
+    const int v = v0 + q;
+    // pole rows have no north (last row) or south (first row) face
+    const bool face = type == 0 || !((v == 1 && row == nlat - 1) || (v == 2 && row == 0));
+    if (v < nv && face) cp_async16_nc(buf + 4u * (unsigned)(q * kCW + i4), tab[v] + off);
+  }
+}
+
+// Registers an axpy stage carries across its sub-stages.
+struct AxRegs {
+  V16<float> ln, rr, pn, ph;
+};
+
+// Sub-stage `sub` of an axpy chunk (the same operations, in the same order, as
+// the PA / PF axpy of the other round layouts).  After the last sub-stage:
+// the flips of the step, r'' and phi'', the norm, the state vectors of the
+// row written, r'' into the row buffer.
+template <bool FUSED>
+__device__ __forceinline__ void stream_ax(int n, const PhaseSmem& ps, unsigned buf, int row, int ch, int sub, int nv,
+                                          unsigned rb, AxRegs& x, Acc<float>& an) {
+  const int c0 = ch * kCW, i4 = 4 * (int)threadIdx.x;
+  if (c0 + i4 >= n) return;
+  const int v0 = sub * kNVS;
+  auto S = [&](int q) { return lds4(buf + 4u * (unsigned)(q * kCW + i4)); };
+  if (sub == 0) {
+    x.ln = S(0);
+    x.rr = S(1);
+    x.pn = S(2);
+    x.ph = S(3);
+  }
+  if constexpr (FUSED) {
+#pragma unroll
+    for (int q = 0; q < kNVS; q += 2) {
+      const int v = v0 + q;
+      if (v >= 4 && v < nv) {
+        const float al = g_ss.alpha[(v - 4) >> 1];
+        const V16<float> ll = S(q), pl = S(q + 1);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          x.ln.v[w] = fmaf(al, ll.v[w], x.ln.v[w]);
+          x.pn.v[w] = fmaf(al, pl.v[w], x.pn.v[w]);
+        }
+      }
+    }
+  }
+  if (v0 + kNVS < nv) return;  // more sub-stages to come
+  const long long g = (long long)row * n + c0 + i4;
+  const float beta = g_ss.beta;
+  const int nfl = ps.nfl;
+  V16<float> rn, fn;
+  if constexpr (FUSED) {
+    if (nfl) {
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        x.rr.v[w] = apply_flips(x.rr.v[w], g + w, V_R, nfl, ps.fl);
+        x.ln.v[w] = apply_flips(x.ln.v[w], g + w, V_AP, nfl, ps.fl);
+        x.ph.v[w] = apply_flips(x.ph.v[w], g + w, V_X, nfl, ps.fl);
+        x.pn.v[w] = apply_flips(x.pn.v[w], g + w, V_P, nfl, ps.fl);
+      }
+    }
+  }
+  // plain (PA): ln holds L(p^nu), pn holds p^nu
+#pragma unroll
+  for (int w = 0; w < 4; ++w) {
+    rn.v[w] = fmaf(beta, x.ln.v[w], x.rr.v[w]);
+    fn.v[w] = fmaf(beta, x.pn.v[w], x.ph.v[w]);
+    an.add(rn.v[w], rn.v[w]);
+  }
+  if constexpr (FUSED) {
+    stv(g_ss.out[0] + g, x.pn);
+    stv(g_ss.out[1] + g, x.ln);
+  }
+  stv(g_ss.out[2] + g, rn);
+  stv(g_ss.out[3] + g, fn);
+#pragma unroll
+  for (int w = 0; w < 4; ++w) sts_nc(rb + 4u * (unsigned)sk(c0 + i4 + w), rn.v[w]);
+}
+
+// Registers a stencil stage carries across its sub-stages.
+struct StRegs {
+  V16<float> le;
+};
+
+// Sub-stage `sub` of a stencil chunk of row `row`: (sub-stage 0) L(e) from the
+// three e rows in shared memory (eC the row, eN north, eS south), written
+// out, <r', L(e)> and <L(e), L(e)>; (every sub-stage) the dots <L(e), L(p^l)>
+// of its operand rows.  The operations of the stencil step of the other
+// round layouts.
+template <int KB>
+__device__ __forceinline__ void stream_st(int n, int nlat, unsigned buf, unsigned lead, int row, int ch, int sub,
+                                          int nv, unsigned eC, unsigned eN, unsigned eS, float muA, StRegs& x,
+                                          Acc<float>* ad, Acc<float>& ah, Acc<float>& aq) {
+  const int c0 = ch * kCW, i4 = 4 * (int)threadIdx.x;
+  const int v0 = sub * kNVS, v1 = min(nv, v0 + kNVS);
+  const bool act = c0 + i4 < n;
+  auto S = [&](int v) { return lds4(buf + 4u * (unsigned)((v - v0) * kCW + i4)); };
+  if (sub == 0) {
+    V16<float> tx;
+    if (act) tx = S(0);
+    // the element west of this thread's columns: the previous lane's last,
+    // or for lane 0 the copy of its warp's lead
+    float txw0 = __shfl_up_sync(0xffffffffu, act ? tx.v[3] : 0.f, 1);
+    if ((threadIdx.x & 31) == 0 && act) txw0 = lds<float>(lead + 16u * (threadIdx.x >> 5) + 12u);
+    if (!act) return;
+    const bool hasN = row < nlat - 1, hasS = row > 0;
+    V16<float> ty, tys;
+    if (hasN) ty = S(1);
+    if (hasS) tys = S(2);
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const int i = c0 + i4 + w;
+      const int ie = (i + 1 == n) ? 0 : i + 1;
+      const int iw = (i == 0) ? n - 1 : i - 1;
+      const float xv = lds<float>(eC + 4u * (unsigned)sk(i));
+      const float ve = lds<float>(eC + 4u * (unsigned)sk(ie));
+      const float vw = lds<float>(eC + 4u * (unsigned)sk(iw));
+      const float vn = hasN ? lds<float>(eN + 4u * (unsigned)sk(i)) : 0.f;
+      const float vs = hasS ? lds<float>(eS + 4u * (unsigned)sk(i)) : 0.f;
+      x.le.v[w] = stencil5<float>(xv, ve, vw, vn, vs, tx.v[w], w == 0 ? txw0 : tx.v[w - 1], hasN ? ty.v[w] : 0.f,
+                                  hasS ? tys.v[w] : 0.f, muA, hasN, hasS);
+    }
+    stv(g_ss.out[4] + (long long)row * n + c0 + i4, x.le);
+  }
+  if (!act) return;
+  // the dots with the L(p^l) of this sub-stage (static indices: the
+  // accumulators stay in registers)
+#pragma unroll
+  for (int l = 0; l < KB; ++l) {
+    const int v = 4 + l;
+    if (v >= v0 && v < v1) {
+      const V16<float> lp = S(v);
+#pragma unroll
+      for (int w = 0; w < 4; ++w) ad[l].add(x.le.v[w], lp.v[w]);
+    }
+  }
+  if (sub == 0) {
+    const V16<float> rn = S(3);
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      ah.add(rn.v[w], x.le.v[w]);
+      aq.add(x.le.v[w], x.le.v[w]);
+    }
+  }
+}
+
+// Adds the CTA's sums of values [v0, nv) to the tile's partial sums already
+// in `out` (FP32 path: one double per value).
+__device__ __forceinline__ void cta_red_finish_add(CtaRed& cr, int nv, double* out, int v0) {
+  __syncthreads();
+  if (threadIdx.x >= v0 && threadIdx.x < nv) {
+    const int v = threadIdx.x;
+    double t[kWarps];
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) t[w] = cr.w[w][v].hi + cr.w[w][v].lo;
+#pragma unroll
+    for (int h = 1; h < kWarps; h <<= 1)
+#pragma unroll
+      for (int w = 0; w + h < kWarps; w += 2 * h) t[w] = t[w] + t[w + h];
+    out[2 * v] = out[2 * v] + t[0];
+  }
+}
+
+// The step round (PA, or PF with FUSED) of band tau of a streamed solve.
+// pass 0: every row's axpy, line solve and e, and the stencils of the rows
+// whose neighbours are all in the band; partial sums 0 (||r'||^2) and the
+// dots of those rows.  pass 1 (after a grid barrier): the stencils of the
+// band's edge rows, with the neighbouring band's e row read back; their dots
+// added to the partial sums.  Shared memory: three e rows (row_stride each),
+// the constants c, 1/w, z of one row (32 C each), sd.nslot stage buffers of
+// kNVS * kCW floats, then the Tx leads (sd.nslot x 8 x 16 bytes).
+template <int KB, bool FUSED>
+__device__ __noinline__ void phase_stream(const SolveDev<float>& sd, const Ctx<float>& c, int tau, float* sm,
+                                          PhaseSmem& ps, double* part_out, int pass, int* err) {
+  const int n = sd.nlon, nlat = sd.nlat, stride = row_stride(n), C = sd.C;
+  const int j0 = row_start(nlat, sd.nt, tau), j1 = row_start(nlat, sd.nt, tau + 1);
+  const int nch = (n + kCW - 1) / kCW, nbuf = sd.nslot, D = nbuf - 1;
+  const int nv_ax = FUSED ? 4 + 2 * (c.nuo + 1) : 4;
+  const int nv_st = 5 + c.nu;
+  const int ns_ax = (nv_ax + kNVS - 1) / kNVS, ns_st = (nv_st + kNVS - 1) / kNVS;
+  float* ebuf = sm;
+  float* cst = sm + 3 * stride;
+  const unsigned cst_s = smem_addr(cst);
+  float* ring = cst + 3 * 32 * C;
+  const unsigned ring_s = smem_addr(ring);
+  const unsigned lead_s = smem_addr(ring + (size_t)nbuf * kNVS * kCW);
+  const unsigned per = 128u * (unsigned)C;  // bytes of one constants row
+  auto interior = [&](int i) { return (i == 0 || i - 1 >= j0) && (i == nlat - 1 || i + 1 < j1); };
+  if (threadIdx.x == 0) {
+    ps.cs_solve = -1;  // the dynamic shared memory is laid out for this phase
+    int m = 0;
+    if (pass == 0) {
+      for (int j = j0; j < j1; ++j) {
+        g_ss.rl[m++] = j << 1;
+        if (j - 1 >= j0 && interior(j - 1)) g_ss.rl[m++] = ((j - 1) << 1) | 1;
+      }
+      if (j1 == nlat && j1 - 1 >= j0 && interior(j1 - 1)) g_ss.rl[m++] = ((j1 - 1) << 1) | 1;
+      ps.nfl = collect_flips(sd, c.t, FUSED ? (kStateVecs | (1u << V_E)) : (1u << V_E), (long long)j0 * n,
+                             (long long)j1 * n, ps.fl);
+    } else {
+      if (!interior(j0)) g_ss.rl[m++] = (j0 << 1) | 1;
+      if (j1 - 1 != j0 && !interior(j1 - 1)) g_ss.rl[m++] = ((j1 - 1) << 1) | 1;
+    }
+    g_ss.nrl = m;
+  }
+  if ((int)threadIdx.x < j1 - j0) g_ss.muA[threadIdx.x] = __ldg(sd.muA + j0 + threadIdx.x);
+  // the pass's operand tables, outputs and coefficients
+  if ((int)threadIdx.x < nv_ax) g_ss.tab_ax[threadIdx.x] = ax_src<FUSED>(c, threadIdx.x);
+  if ((int)threadIdx.x >= 64 && (int)threadIdx.x < 64 + nv_st) {
+    const int v = threadIdx.x - 64;
+    g_ss.tab_st[v] = v == 0 ? sd.Tx : v == 1 ? sd.Ty : v == 2 ? sd.Ty - n : v == 3 ? c.rW : c.lp[v - 4];
+  }
+  if ((int)threadIdx.x >= 128 && (int)threadIdx.x < 128 + kMaxK) g_ss.alpha[threadIdx.x - 128] = c.alpha[threadIdx.x - 128];
+  if (threadIdx.x == 160) {
+    g_ss.out[0] = c.pnew;
+    g_ss.out[1] = c.lpnew;
+    g_ss.out[2] = c.rW;
+    g_ss.out[3] = c.phiW;
+    g_ss.out[4] = c.LeW;
+    g_ss.beta = c.beta;
+  }
+  __syncthreads();
+  const int nrl = g_ss.nrl;
+  unsigned cph = g_ss.cph;
+  auto issue_consts = [&](int row) {  // thread 0: one row of c, 1/w, z by bulk copies
+    const unsigned mb = smem_addr(&g_ss.cfull);
+    const long long o = (long long)row * 32 * C;
+    mbar_expect(mb, 3u * per);
+    bulk_load(cst_s, sd.lc + o, per, mb);
+    bulk_load(cst_s + per, sd.lw + o, per, mb);
+    bulk_load(cst_s + 2u * per, sd.lz + o, per, mb);
+  };
+  if (threadIdx.x == 0 && pass == 0 && j0 < j1) {
+    fence_proxy_async_global();
+    issue_consts(j0);
+  }
+  // stage issue cursor (every thread the same): row stage, chunk, sub-stage
+  int pi = 0, pc = 0, psb = 0, pidx = 0;
+  auto issue_next = [&]() {
+    if (pi < nrl) {
+      const int e = g_ss.rl[pi], type = e & 1, row = e >> 1;
+      const int b = pidx % nbuf;
+      stream_copy(type ? g_ss.tab_st : g_ss.tab_ax, sd.Tx, n, nlat, type, row, pc, psb, type ? nv_st : nv_ax,
+                  ring_s + 4u * (unsigned)(b * kNVS * kCW), lead_s + 128u * (unsigned)b);
+      if (++psb == (type ? ns_st : ns_ax)) {
+        psb = 0;
+        if (++pc == nch) {
+          pc = 0;
+          ++pi;
+        }
+      }
+    }
+    cp_async_commit();  // an empty group once the pass is issued: the counts stay aligned
+    ++pidx;
+  };
+  for (int d = 0; d < D; ++d) issue_next();
+  Acc<float> an, ah, aq;
+  Acc<float> ad[KB];
+  int cidx = 0;
+  bool fail = false;
+  for (int ci = 0; ci < nrl; ++ci) {
+    const int e = g_ss.rl[ci], type = e & 1, row = e >> 1;
+    const int nv = type ? nv_st : nv_ax, ns = type ? ns_st : ns_ax;
+    unsigned eC = 0, eN = 0, eS = 0;
+    if (type == 1) {
+      if (pass == 0) {
+        eC = smem_addr(ebuf + (row % 3) * stride);
+        eN = smem_addr(ebuf + ((row + 1) % 3) * stride);
+        eS = smem_addr(ebuf + ((row + 2) % 3) * stride);
+      } else {
+        // the three e rows, the neighbour's included (plain loads; this row's
+        // stage copies are in flight meanwhile)
+        __syncthreads();  // the previous row's stencil has read them
+        if (row > 0) stage_rows(c.eW, row - 1, row, n, ebuf, stride);
+        stage_rows(c.eW, row, row + 1, n, ebuf + stride, stride);
+        if (row < nlat - 1) stage_rows(c.eW, row + 1, row + 2, n, ebuf + 2 * stride, stride);
+        __syncthreads();
+        eS = smem_addr(ebuf);
+        eC = smem_addr(ebuf + stride);
+        eN = smem_addr(ebuf + 2 * stride);
+      }
+    } else {
+      __syncthreads();  // the stencils before have read this row buffer's e
+    }
+    float* rowbuf = ebuf + (row % 3) * stride;
+    const unsigned rb = smem_addr(rowbuf);
+    const float muA = g_ss.muA[row - j0];
+    for (int ch = 0; ch < nch; ++ch) {
+      AxRegs xa;
+      StRegs xs;
+      for (int sb = 0; sb < ns; ++sb) {
+        // the next stage's copies go out before this one is waited for; a
+        // stage never reads a row this thread writes within the last D stages
+        issue_next();
+        cp_async_wait_n(D);
+        const int b = cidx % nbuf;
+        const unsigned buf = ring_s + 4u * (unsigned)(b * kNVS * kCW);
+        if (type == 0)
+          stream_ax<FUSED>(n, ps, buf, row, ch, sb, nv, rb, xa, an);
+        else
+          stream_st<KB>(n, nlat, buf, lead_s + 128u * (unsigned)b, row, ch, sb, nv, eC, eN, eS, muA, xs, ad, ah, aq);
+        ++cidx;
+      }
+    }
+    if (type == 1) continue;
+    // the row's line solve: e = P^-1 r' in place
+    __syncthreads();  // r' of every column in the row buffer
+    {
+      bool ok = true;
+      if ((threadIdx.x & 31) == 0) ok = mbar_wait(smem_addr(&g_ss.cfull), cph & 1u);
+      if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) g_ss.bad = 1;
+      __syncwarp();
+    }
+    __syncthreads();
+    if (g_ss.bad) {
+      fail = true;
+      break;
+    }
+    cph ^= 1u;
+    {
+      const LineConsts<float> lc{cst, cst + 32 * C, cst + 64 * C};
+      const int warp = threadIdx.x >> 5;
+      if (C % 64 == 0) {
+        line_solve_row_group<8>(sd, row, rowbuf, lc, g_ss.maps, 1);
+      } else if (C % 32 == 0) {
+        if (warp < 4) line_solve_row_group<4>(sd, row, rowbuf, lc, g_ss.maps, 1);
+      } else if (C % 16 == 0) {
+        if (warp < 2) line_solve_row_group<2>(sd, row, rowbuf, lc, g_ss.maps, 1);
+      } else if (warp == 0) {
+        line_solve_row(sd, row, rowbuf, lc);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      // the constants are consumed: the next row's may come in
+      if (row + 1 < j1) issue_consts(row + 1);
+      for (int q = 0; q < ps.nfl; ++q) {  // e-site flips (the paper's injection site)
+        if (ps.fl[q].vec != V_E) continue;
+        const long long g = ps.fl[q].g;
+        const int jj = (int)(g / n), i = (int)(g - (long long)jj * n);
+        if (jj != row) continue;
+        rowbuf[sk(i)] = flip_bits(rowbuf[sk(i)], ps.fl[q].bit);
+      }
+    }
+    if (sd.nlosses) {
+      __syncthreads();
+      apply_losses(sd, c.t, row, row + 1, rowbuf, stride);
+    }
+    __syncthreads();
+    store_rows(c.eW, row, row + 1, n, rowbuf, stride);
+  }
+  cp_async_wait_all();  // the groups still open are empty unless the pass failed
+  if (fail) {
+    if (threadIdx.x == 0) {
+      atomicExch(err, 3);
+      // a constants copy may still be in flight: let it land (bounded)
+      mbar_wait(smem_addr(&g_ss.cfull), cph & 1u, kDrainNs);
+    }
+    return;
+  }
+  if (pass == 0) {
+    cta_red_put(ps.cr, 0, an.warp_sum());
+#pragma unroll
+    for (int l = 0; l < KB; ++l)
+      if (l <= c.nu) cta_red_put(ps.cr, 1 + l, ad[l].warp_sum());
+    cta_red_put(ps.cr, 2 + c.nu, ah.warp_sum());
+    cta_red_put(ps.cr, 3 + c.nu, aq.warp_sum());
+    cta_red_finish<float>(ps.cr, 4 + c.nu, part_out);
+  } else {
+#pragma unroll
+    for (int l = 0; l < KB; ++l)
+      if (l <= c.nu) cta_red_put(ps.cr, 1 + l, ad[l].warp_sum());
+    cta_red_put(ps.cr, 2 + c.nu, ah.warp_sum());
+    cta_red_put(ps.cr, 3 + c.nu, aq.warp_sum());
+    cta_red_finish_add(ps.cr, 4 + c.nu, part_out, 1);
+  }
+  if (threadIdx.x == 0) g_ss.cph = cph;
+}
+
+}  // namespace ftgcr

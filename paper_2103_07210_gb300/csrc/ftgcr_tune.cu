@@ -1,5 +1,5 @@
 // Tile autotuner of libftgcr: picks, by timing, the row-band count and the
-// round layout (one-pass or split rounds) of a solve shape, for a given number
+// round layout (one-pass, split or streamed rounds) of a solve shape, for a given number
 // of solves of that shape sharing one persistent launch.
 //
 // It is a client of the public C ABI (ftgcr_create, ftgcr_solve_batch,
@@ -113,7 +113,8 @@ extern "C" int ftgcr_tune(const ftgcr_grid* grid, const ftgcr_coeffs* coeffs, in
   if (!grid || !coeffs || !coeffs->D || !out || concurrency < 1 || concurrency > FTGCR_TUNE_MAX_CONCURRENCY)
     return FTGCR_ERR_ARG;
   if (grid->tiles != 0) return FTGCR_ERR_ARG;  // the tuner chooses the bands
-  if (grid->flags & (FTGCR_FLAG_SPLIT_ROUNDS | FTGCR_FLAG_FUSED_ROUNDS)) return FTGCR_ERR_ARG;
+  if (grid->flags & (FTGCR_FLAG_SPLIT_ROUNDS | FTGCR_FLAG_FUSED_ROUNDS | FTGCR_FLAG_STREAMED_ROUNDS))
+    return FTGCR_ERR_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
@@ -173,8 +174,11 @@ extern "C" int ftgcr_tune(const ftgcr_grid* grid, const ftgcr_coeffs* coeffs, in
     if (std::find(nts.begin(), nts.end(), nt) == nts.end()) nts.push_back(nt);
   }
   std::vector<int> layouts = {0};
-  if (grid->precision == FTGCR_MIXED && grid->precond == FTGCR_PRECOND_LINE)
+  if (grid->precision == FTGCR_MIXED && grid->precond == FTGCR_PRECOND_LINE) {
     layouts = {FTGCR_FLAG_FUSED_ROUNDS, FTGCR_FLAG_SPLIT_ROUNDS};
+    // streamed step rounds: rows of at least one 1024-column chunk
+    if (grid->nlon >= 1024) layouts.push_back(FTGCR_FLAG_STREAMED_ROUNDS);
+  }
   ftgcr_tuning_t best{};
   best.ms = 1e300;
   int tried = 0;
@@ -197,7 +201,8 @@ extern "C" int ftgcr_tune(const ftgcr_grid* grid, const ftgcr_coeffs* coeffs, in
       if (ms < best.ms) {
         best.ms = ms;
         best.tiles = tiles;
-        best.flags = split ? FTGCR_FLAG_SPLIT_ROUNDS : (lay ? FTGCR_FLAG_FUSED_ROUNDS : 0);
+        best.flags = split == 2 ? FTGCR_FLAG_STREAMED_ROUNDS
+                                : (split ? FTGCR_FLAG_SPLIT_ROUNDS : (lay ? FTGCR_FLAG_FUSED_ROUNDS : 0));
       }
     }
   sc.release();

@@ -21,8 +21,9 @@ _INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libftgcr.so")
 SOURCES = ["ftgcr.cu", "ftgcr_k4.cu", "ftgcr_k8.cu", "ftgcr_k16.cu", "ftgcr_k4s.cu", "ftgcr_k8s.cu", "ftgcr_k16s.cu",
+           "ftgcr_k4t.cu", "ftgcr_k8t.cu", "ftgcr_k16t.cu",
            "ftgcr_k4w.cu", "ftgcr_k8w.cu", "ftgcr_k16w.cu", "ftgcr_server.cu", "ftgcr_tune.cu", "ftgcr_probe.cu"]
-HEADERS = ["ftgcr_device.cuh", "ftgcr_phases.cuh", "ftgcr_instances.h", "ftgcr_serve.h"]
+HEADERS = ["ftgcr_device.cuh", "ftgcr_phases.cuh", "ftgcr_stream.cuh", "ftgcr_instances.h", "ftgcr_serve.h"]
 # --fmad=false: device multiply-adds are fused only where the code says fma();
 # -ffp-contract=off: the same for the host-side geometry (GCC contracts by
 # default on aarch64)
@@ -33,7 +34,7 @@ FP64, MIXED = 0, 1
 PRECOND = {"line": 0, "jacobi": 1, "identity": 2}
 VEC = {"x": 0, "r": 1, "p": 2, "ap": 3, "e": 4}
 MAX_FAULTS, MAX_K, MAX_DETECT, MAX_LOSSES = 64, 16, 16, 16
-FLAG_UNPROTECTED, FLAG_SPLIT_ROUNDS, FLAG_FUSED_ROUNDS = 1, 2, 4
+FLAG_UNPROTECTED, FLAG_SPLIT_ROUNDS, FLAG_FUSED_ROUNDS, FLAG_STREAMED_ROUNDS = 1, 2, 4, 8
 
 OK, NOT_CONVERGED, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BUDGET, ERR_STATE = 0, 1, -1, -2, -3, -4, -5, -6
 PENDING = 2
@@ -227,7 +228,7 @@ def _plan(faults, losses=()):
     return plan, (arr, larr)
 
 
-ROUNDS = {"auto": 0, "split": FLAG_SPLIT_ROUNDS, "fused": FLAG_FUSED_ROUNDS}
+ROUNDS = {"auto": 0, "split": FLAG_SPLIT_ROUNDS, "fused": FLAG_FUSED_ROUNDS, "streamed": FLAG_STREAMED_ROUNDS}
 
 
 def _grid(nlon, nlat, mu, precision, precond, max_steps, tiles, inner_tol, max_outer, protect=True, rounds="auto"):
@@ -249,8 +250,9 @@ class Solver:
     def __init__(self, D, mu, k=4, tol=1e-10, precision="fp64", precond="line", max_steps=0, tiles=0,
                  inner_tol=0.0, max_outer=0, protect=True, rounds="auto"):
         """protect=False: plain GCR(k), the paper's unprotected baseline (no
-        fault test, no restore).  rounds: "auto", "split" or "fused"
-        (FTGCR_FLAG_SPLIT_ROUNDS / FTGCR_FLAG_FUSED_ROUNDS)."""
+        fault test, no restore).  rounds: "auto", "split", "fused" or
+        "streamed" (FTGCR_FLAG_SPLIT_ROUNDS / FTGCR_FLAG_FUSED_ROUNDS /
+        FTGCR_FLAG_STREAMED_ROUNDS)."""
         L = lib()
         nlat, nlon = D.shape
         self.nlon, self.nlat, self.k, self.tol = int(nlon), int(nlat), int(k), float(tol)
@@ -328,7 +330,8 @@ class Solver:
                     detect_ratio=[s.detect_ratio[i] for i in range(n)], res0=s.res0, res_final_rec=s.res_final_rec,
                     res_final_true=s.res_final_true, norm_R=s.norm_R, bytes_resident=s.bytes_resident,
                     bytes_backup=s.bytes_backup, tiles=s.tiles, status=s.status, loss_events=s.loss_events,
-                    split_rounds=bool(s.split_rounds), global_factors=bool(s.global_factors))
+                    split_rounds=s.split_rounds == 1, streamed_rounds=s.split_rounds == 2,
+                    global_factors=bool(s.global_factors))
 
     def apply_operator(self, inp, out, stream=None):
         ip, ik = _ptr(inp)
@@ -360,7 +363,7 @@ def _stats_dict(s: Stats) -> dict:
                 detect_steps=[s.detect_step[i] for i in range(n)], detect_ratio=[s.detect_ratio[i] for i in range(n)],
                 res0=s.res0, res_final_rec=s.res_final_rec, res_final_true=s.res_final_true, norm_R=s.norm_R,
                 bytes_resident=s.bytes_resident, bytes_backup=s.bytes_backup, tiles=s.tiles, status=s.status,
-                loss_events=s.loss_events, split_rounds=bool(s.split_rounds),
+                loss_events=s.loss_events, split_rounds=s.split_rounds == 1, streamed_rounds=s.split_rounds == 2,
                 global_factors=bool(s.global_factors))
 
 
@@ -379,7 +382,8 @@ def tune(D, mu, k=4, tol=1e-10, precision="mixed", precond="line", concurrency=1
     del keep
     if st != OK:
         raise FTGCRError(st, "ftgcr_tune")
-    rounds = "split" if t.flags & FLAG_SPLIT_ROUNDS else ("fused" if t.flags & FLAG_FUSED_ROUNDS else "auto")
+    rounds = ("split" if t.flags & FLAG_SPLIT_ROUNDS else "fused" if t.flags & FLAG_FUSED_ROUNDS else
+              "streamed" if t.flags & FLAG_STREAMED_ROUNDS else "auto")
     return dict(tiles=t.tiles, rounds=rounds, ms=t.ms, default_tiles=t.default_tiles, default_ms=t.default_ms,
                 candidates=t.candidates, cached=bool(t.cached))
 
