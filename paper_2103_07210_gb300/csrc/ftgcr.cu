@@ -281,7 +281,8 @@ __global__ void k_lf_products(int nlon, int nlat, const double* __restrict__ win
 
 // Chain 3: backward substitution z_i = fma(-u_i, z_{i+1}, z_i winv_i),
 // i = m-2 .. 0, then delta = d_{n-1} + Tx_{n-1} z_0 + Tx_{n-2} z_{m-1} and the
-// row constants (FP64: delta; FP32: 1/delta, Tx_{n-1}/delta, Tx_{n-2}/delta).
+// row constants (FP64: delta, then 1/delta, Tx_{n-1}/delta, Tx_{n-2}/delta;
+// FP32: the last three).
 __global__ void k_lf_chain_bwd(int nlon, int nlat, const double* __restrict__ Tx, const double* __restrict__ Ty,
                                const double* __restrict__ muA, const double* __restrict__ u, double* __restrict__ z,
                                double* lrow64, float* lrow32) {
@@ -321,12 +322,12 @@ __global__ void k_lf_chain_bwd(int nlon, int nlat, const double* __restrict__ Tx
   s = s + muA[j];
   const double d_last = tx[n - 1] + tx[n - 2] + s;
   const double delta = d_last + tx[n - 1] * z[rb] + tx[n - 2] * z[rb + m - 1];
+  const double dinv = 1.0 / delta;
   lrow64[(long long)j * 4 + 0] = delta;
-  lrow64[(long long)j * 4 + 1] = 0.0;
-  lrow64[(long long)j * 4 + 2] = 0.0;
-  lrow64[(long long)j * 4 + 3] = 0.0;
+  lrow64[(long long)j * 4 + 1] = dinv;
+  lrow64[(long long)j * 4 + 2] = tx[n - 1] * dinv;
+  lrow64[(long long)j * 4 + 3] = tx[n - 2] * dinv;
   if (lrow32) {
-    const double dinv = 1.0 / delta;
     lrow32[(long long)j * 4 + 0] = (float)dinv;
     lrow32[(long long)j * 4 + 1] = (float)(tx[n - 1] * dinv);
     lrow32[(long long)j * 4 + 2] = (float)(tx[n - 2] * dinv);
@@ -334,10 +335,12 @@ __global__ void k_lf_chain_bwd(int nlon, int nlat, const double* __restrict__ Tx
   }
 }
 
-// FP32 constants in the per-lane chunk layout: position k*32 + lane of row j
-// holds element i = lane*C + k (c = -u, winv, z; zero past the block).
+// Constants in the per-lane chunk layout (FP32, or FP64 for the FP64 path's
+// chunked row solve): position k*32 + lane of row j holds element
+// i = lane*C + k (c = -u, winv, z; zero past the block).
+template <typename O>
 __global__ void k_lf_chunks(int nlon, int nlat, int C, const double* __restrict__ u, const double* __restrict__ winv,
-                            const double* __restrict__ z, float* lc32, float* lw32, float* lz32) {
+                            const double* __restrict__ z, O* lc32, O* lw32, O* lz32) {
   const long long per = 32LL * C, total = per * nlat;
   const int m = nlon - 1;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total; q += (long long)gridDim.x * blockDim.x) {
@@ -346,9 +349,9 @@ __global__ void k_lf_chunks(int nlon, int nlat, int C, const double* __restrict_
     const int i = lane * C + k;
     const bool in = i < m;
     const long long g = (long long)j * nlon + i;
-    lc32[q] = in ? (float)(-u[g]) : 0.f;
-    lw32[q] = in ? (float)winv[g] : 0.f;
-    lz32[q] = in ? (float)z[g] : 0.f;
+    lc32[q] = in ? (O)(-u[g]) : O(0);
+    lw32[q] = in ? (O)winv[g] : O(0);
+    lz32[q] = in ? (O)z[g] : O(0);
   }
 }
 
@@ -357,7 +360,8 @@ __global__ void k_lf_chunks(int nlon, int nlat, int C, const double* __restrict_
 // and the row constants; FP32 chunk-layout constants when lc32 is given.
 int launch_line_factor(int nlon, int nlat, int C, int precond, const double* Tx, const double* Ty,
                        const double* muA, double* l64, double* w64, double* u64, double* z64, double* r64,
-                       float* lc32, float* lw32, float* lz32, float* lrow32, cudaStream_t st) {
+                       float* lc32, float* lw32, float* lz32, float* lrow32, cudaStream_t st, double* lcc = nullptr,
+                       double* lwc = nullptr, double* lzc = nullptr) {
   if (precond != PC_LINE) {
     k_line_factor<<<(nlat + 63) / 64, 64, 0, st>>>(nlon, nlat, C, precond, Tx, Ty, muA, l64, w64, u64, z64, r64, lc32,
                                                    lw32, lz32, lrow32);
@@ -372,11 +376,10 @@ int launch_line_factor(int nlon, int nlat, int C, int precond, const double* Tx,
   k_lf_chain_fwd<<<rg, 32, 0, st>>>(nlon, nlat, l64, z64);
   k_lf_products<<<eg, eb, 0, st>>>(nlon, nlat, w64, z64);
   k_lf_chain_bwd<<<rg, 32, 0, st>>>(nlon, nlat, Tx, Ty, muA, u64, z64, r64, lrow32);
-  if (lc32) {
-    const long long nc = 32LL * C * nlat;
-    k_lf_chunks<<<(int)std::min<long long>((nc + eb - 1) / eb, 8192), eb, 0, st>>>(nlon, nlat, C, u64, w64, z64, lc32,
-                                                                                 lw32, lz32);
-  }
+  const long long nc = 32LL * C * nlat;
+  const int cgrid = (int)std::min<long long>((nc + eb - 1) / eb, 8192);
+  if (lc32) k_lf_chunks<float><<<cgrid, eb, 0, st>>>(nlon, nlat, C, u64, w64, z64, lc32, lw32, lz32);
+  if (lcc) k_lf_chunks<double><<<cgrid, eb, 0, st>>>(nlon, nlat, C, u64, w64, z64, lcc, lwc, lzc);
   return cudaGetLastError() == cudaSuccess ? FTGCR_OK : FTGCR_ERR_CUDA;
 }
 
@@ -595,7 +598,8 @@ SmemPlan smem_plan(int nlon, int nlat, int nt, int mixed, size_t elem, int preco
                    int gconsts = 0) {
   const size_t h = (size_t)((nlat + nt - 1) / nt);
   const size_t st = (size_t)row_stride(nlon);
-  const size_t per_row = mixed ? 32 * (size_t)chunk_len(nlon) : (size_t)nlon;  // chunk vs natural layout
+  // chunk layout (FP32; FP64 rows of at least kChunkMinLon) or natural (FP64 serial solve)
+  const size_t per_row = (mixed || nlon >= kChunkMinLon) ? 32 * (size_t)chunk_len(nlon) : (size_t)nlon;
   const size_t out = mixed ? (h + 2) * st * sizeof(double) : 0;
   const bool line = precond == FTGCR_PRECOND_LINE;
   SmemPlan p;
@@ -741,6 +745,7 @@ struct ftgcr_handle {
   size_t smem = 0;
   int split = 0;  // split rounds (see choose_tiling)
   int wide = 0;   // runs in the wide-row kernel instance (split rounds, or FP64 factors from global memory)
+  int noalloc = 0;  // the record of a no-allocation solve (its pool is the static scratch array)
   SmemPlan plan{};
   int grid = 0;
   cudaStream_t last_stream = nullptr;
@@ -858,6 +863,12 @@ size_t layout(ftgcr_handle* h, unsigned char* base, SolveDev<T>* sd) {
   sd->lz = (const T*)take(sizeof(T) * lcn);
   sd->lu = (const T*)(fp64 && h->precond == FTGCR_PRECOND_LINE ? take(sizeof(T) * lcn) : nullptr);
   sd->lrow = (const T*)take(sizeof(T) * 4 * nlat);
+  // FP64 chunked row solves: the factors again in the chunk layout
+  const bool chunk = fp64 && h->precond == FTGCR_PRECOND_LINE && h->nlon >= kChunkMinLon && !h->noalloc;
+  sd->lchunk = chunk ? 1 : 0;
+  sd->lcc = chunk ? (const T*)take(sizeof(T) * 32 * (size_t)C * nlat) : sd->lc;
+  sd->lwc = chunk ? (const T*)take(sizeof(T) * 32 * (size_t)C * nlat) : sd->lw;
+  sd->lzc = chunk ? (const T*)take(sizeof(T) * 32 * (size_t)C * nlat) : sd->lz;
   size_t before = off;
   for (int q = 0; q < 3; ++q) sd->phi[q] = (T*)take(vT);
   for (int q = 0; q < 3; ++q) sd->r[q] = (T*)take(vT);
@@ -939,9 +950,12 @@ int setup_coefficients(ftgcr_handle* h, const SolveDev<T>& sd, const double* Dd,
     z64 = tmp + 3 * h->N;
     r64 = tmp + 4 * h->N;
   }
+  const bool chunk = !mixed && sd.lchunk;
   const int frc = launch_line_factor(h->nlon, h->nlat, h->C, h->precond, h->Tx64, h->Ty64, h->muA64, l64, w64, u64,
                                      z64, r64, mixed ? (float*)sd.lc : nullptr, mixed ? (float*)sd.lw : nullptr,
-                                     mixed ? (float*)sd.lz : nullptr, mixed ? (float*)sd.lrow : nullptr, st);
+                                     mixed ? (float*)sd.lz : nullptr, mixed ? (float*)sd.lrow : nullptr, st,
+                                     chunk ? (double*)sd.lcc : nullptr, chunk ? (double*)sd.lwc : nullptr,
+                                     chunk ? (double*)sd.lzc : nullptr);
   if (frc) return frc;
   CK(cudaFreeAsync(scratch, st));
   return FTGCR_OK;
@@ -1807,6 +1821,7 @@ extern "C" int ftgcr_solve_noalloc(const ftgcr_grid* grid, const double* D, int3
   // the handle record lives on the host stack; its pool is the static array
   ftgcr_handle h;
   h.dev = dev;
+  h.noalloc = 1;  // the serial row solve: no chunk-layout factors in the fixed scratch
   fill_handle_params(&h, grid, k, tol, di.sms, smem_limit);
   if (h.plan.bytes > (size_t)smem_limit) return FTGCR_ERR_ARG;
   SolveDev<double> sd{};

@@ -118,7 +118,15 @@ struct SolveDev {
   const T* lw;
   const T* lz;
   const T* lu;    // FP64 path: u_i = -Tx_i / w_i
-  const T* lrow;  // [nlat][4]: FP32 path 1/delta, Tx_{n-1}/delta, Tx_{n-2}/delta; FP64 path delta
+  const T* lrow;  // [nlat][4]: FP32 path 1/delta, Tx_{n-1}/delta, Tx_{n-2}/delta; FP64 path delta and
+                  // then the same three constants
+  // FP64 path, lchunk = 1: the factors again in the per-lane chunk layout of
+  // the FP32 path (c = -u, 1/w, z), for the chunked warp solve of a row
+  // (rows of at least kChunkMinLon columns); lchunk = 0: the serial solve
+  const T* lcc;
+  const T* lwc;
+  const T* lzc;
+  int lchunk;
   // Krylov vectors (inner precision)
   T* phi[3];
   T* r[3];
@@ -472,7 +480,8 @@ __device__ __forceinline__ LineConsts<T> line_consts_global(const SolveDev<T>& s
   return LineConsts<T>{sd.lc + o, sd.lw + o, sd.lz + o};
 }
 
-constexpr int kLB = 8;  // register block of the recurrences
+constexpr int kLB = 8;
+constexpr int kChunkMinLon = 256;  // FP64 path: the chunked row solve from this row width  // register block of the recurrences
 
 // Periodic tridiagonal solve of one latitude row, M e = -r (P = -M is the
 // zonal part of L plus the diagonal of the rest), in place in shared memory,
@@ -493,7 +502,8 @@ __device__ __noinline__ void line_solve_row(const SolveDev<T>& sd, int j, T* row
   const int len = C;  // every lane runs its whole chunk (chunk_len)
   // the row's bordering constants, loaded first so that their latency hides
   // behind the recurrences
-  const T* lr = sd.lrow + (long long)j * 4;
+  // (FP64 path: after delta in slot 0)
+  const T* lr = sd.lrow + (long long)j * 4 + (sizeof(T) == 8 ? 1 : 0);
   const T lr0 = __ldg(lr + 0), lr1 = __ldg(lr + 1), lr2 = __ldg(lr + 2);
   const unsigned rb = smem_addr(row_), cbb = smem_addr(lc.cb), cwb = smem_addr(lc.cw), czb = smem_addr(lc.cz);
   constexpr unsigned E = sizeof(T);

@@ -641,7 +641,7 @@ __device__ __forceinline__ void sub_mark(PhaseSmem& ps, int q) {
 template <typename T>
 __device__ __forceinline__ long long consts_per_row(const SolveDev<T>& sd) {
   if constexpr (sizeof(T) == 8)
-    return sd.nlon;
+    return sd.lchunk ? 32LL * sd.C : sd.nlon;
   else
     return 32LL * sd.C;
 }
@@ -658,9 +658,9 @@ __device__ __forceinline__ void stage_line_consts(const SolveDev<T>& sd, int h0,
   const long long nel = (long long)nrows * per;
   const T* src[3];
   if constexpr (sizeof(T) == 8) {
-    src[0] = sd.lc;
-    src[1] = sd.lw;
-    src[2] = sd.lu;
+    src[0] = sd.lchunk ? sd.lcc : sd.lc;
+    src[1] = sd.lchunk ? sd.lwc : sd.lw;
+    src[2] = sd.lchunk ? sd.lzc : sd.lu;
   } else {
     src[0] = sd.lc;
     src[1] = sd.lw;
@@ -779,6 +779,15 @@ __device__ __forceinline__ void precond_tile(const SolveDev<T>& sd, int h0, int 
           precond_tile_gl(sd, h0, nrows, sm, stride, const_cast<T*>(cs));
           return;
         }
+      }
+      if (sd.lchunk) {
+        // one warp per row: the chunked solve of the FP32 path in FP64 (the
+        // row's recurrences as 32 per-lane chunks joined by an exact scan of
+        // their affine maps)
+        const int warp = threadIdx.x >> 5;
+        for (int jr = warp; jr < nrows; jr += kWarps)
+          line_solve_row<double>(sd, h0 + jr, sm + jr * stride, staged_consts(sd, cs, nrows, jr));
+        return;
       }
       const int n = sd.nlon, m = n - 1;
       for (int jr = threadIdx.x; jr < nrows; jr += kThreads)

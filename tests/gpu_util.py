@@ -25,3 +25,23 @@ def rel_err(a: np.ndarray, b: np.ndarray) -> float:
 def decisions(info: dict) -> tuple:
     """What must match exactly between the GPU FP64 path and the oracle."""
     return (info["steps"], tuple(info["detect_steps"]), bool(info["converged"]), info["faults_detected"])
+
+
+
+def rel_err_fault_trial(a: np.ndarray, b: np.ndarray, fault, detected: bool) -> float:
+    """Solution error of a single-flip trial.  x and p enter neither beta,
+    alpha nor the residual recurrences (Algorithm 1), so a flip of an x or p
+    entry is never detected and stays confined to that entry of the solution
+    (Section 3: such faults are passive); its value there is the entry's
+    pre-flip rounding scaled by the flip (by up to 2^1024 for an exponent
+    bit), so two implementations that round differently agree there only to
+    that scaled rounding.  That entry is left out; every other entry must
+    match.  fault = (step, vec, index, bit)."""
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    step, vec, idx, bit = fault
+    if not detected and vec in (0, 2):  # x, p
+        keep = np.ones(a.size, dtype=bool)
+        keep[idx] = False
+        return rel_err(a[keep], b[keep])
+    return rel_err(a, b)

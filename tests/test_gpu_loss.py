@@ -1,8 +1,8 @@
 """GPU parity for the paper's data-loss fault events (Section 3), the
 unprotected GCR(k) mode and the singular mu = 0 problem, through the C ABI.
 
-FP64 path: decisions (steps, detection steps, convergence, events fired) and
-solution bitwise equal to the oracle's.  Mixed path: converges to the oracle's
+FP64 path: decisions (steps, detection steps, convergence, events fired)
+identical to the oracle's, solution within 1e-10 relative.  Mixed path: converges to the oracle's
 solution (rel <= 1e-10 at tol 1e-13) under data loss; batched solves with data
 loss equal the same solves alone."""
 import numpy as np

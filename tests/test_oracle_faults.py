@@ -2,7 +2,9 @@
 Section 2 and Section 3): invariants that hold exactly whatever the operator.
 
 * x and p never enter beta, alpha or r, so flips there are passive: the norm
-  sequence is bitwise that of the fault-free run and nothing is detected.
+  sequence is bitwise that of the fault-free run and nothing is detected,
+  and the solution differs from the fault-free one at the flipped entry only
+  (every recurrence of x and p is entrywise).
 * A flip that sets bit 62 of an r entry with |v| < 2 multiplies it by 2^1024
   (Inf or a huge value): always detected in the step it fires.
 * A fault detected in the step it fires, that did not reach the backup,
@@ -118,3 +120,17 @@ def test_nan_in_residual_is_a_fault(base):
     # exponent of a value in [1, 2) becomes all ones -> NaN (mantissa != 0) or Inf
     o = oracle.ftgcr(p.D, p.R, p.mu, 4, 1e-10, faults=[(4, "r", 5, 62), (4, "r", 5, 61)])
     assert 4 in o["detect_steps"]
+
+
+@pytest.mark.parametrize("vec,bit", [("x", 40), ("p", 40), ("p", 57), ("x", 62), ("p", 61)])
+def test_passive_flips_stay_in_their_entry(base, vec, bit):
+    p, ff = base
+    N = p.nlon * p.nlat
+    for step, idx in ((2, 17), (7, N // 2 + 3), (ff["steps"], N - 5)):
+        o = oracle.ftgcr(p.D, p.R, p.mu, 4, 1e-10, faults=[(step, vec, idx, bit)])
+        assert o["faults_injected"] == 1 and o["faults_detected"] == 0
+        x, x0 = o["x"].ravel(), ff["x"].ravel()
+        other = np.ones(N, dtype=bool)
+        other[idx] = False
+        assert np.array_equal(x[other], x0[other]), (vec, bit, step, idx)
+        assert not np.array_equal(x[idx], x0[idx])
