@@ -355,13 +355,34 @@ __global__ void k_lf_chunks(int nlon, int nlat, int C, const double* __restrict_
   }
 }
 
+// FP32 constants in the piece-major layout of the streamed rounds: position
+// L (C + 4) + kk of row j holds element i = L C + kk (c = -u, winv, z; zero
+// past the leading block and in the padding).
+__global__ void k_lf_pieces(int nlon, int nlat, int C, const double* __restrict__ u, const double* __restrict__ winv,
+                            const double* __restrict__ z, float* lc, float* lw, float* lz) {
+  const int P = C + 4;
+  const long long per = 32LL * P, total = per * nlat;
+  const int m = nlon - 1;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total; q += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(q / per);
+    const int pos = (int)(q - (long long)j * per), L = pos / P, kk = pos - L * P;
+    const int i = L * C + kk;
+    const bool in = kk < C && i < m;
+    const long long g = (long long)j * nlon + i;
+    lc[q] = in ? (float)(-u[g]) : 0.f;
+    lw[q] = in ? (float)winv[g] : 0.f;
+    lz[q] = in ? (float)z[g] : 0.f;
+  }
+}
+
 // The line preconditioner's factorisation (Jacobi: its diagonal), enqueued
 // on st.  FP64 outputs l, winv, u, z (z doubles as scratch for the diagonal)
 // and the row constants; FP32 chunk-layout constants when lc32 is given.
 int launch_line_factor(int nlon, int nlat, int C, int precond, const double* Tx, const double* Ty,
                        const double* muA, double* l64, double* w64, double* u64, double* z64, double* r64,
                        float* lc32, float* lw32, float* lz32, float* lrow32, cudaStream_t st, double* lcc = nullptr,
-                       double* lwc = nullptr, double* lzc = nullptr) {
+                       double* lwc = nullptr, double* lzc = nullptr, float* lcp = nullptr, float* lwp = nullptr,
+                       float* lzp = nullptr) {
   if (precond != PC_LINE) {
     k_line_factor<<<(nlat + 63) / 64, 64, 0, st>>>(nlon, nlat, C, precond, Tx, Ty, muA, l64, w64, u64, z64, r64, lc32,
                                                    lw32, lz32, lrow32);
@@ -380,6 +401,11 @@ int launch_line_factor(int nlon, int nlat, int C, int precond, const double* Tx,
   const int cgrid = (int)std::min<long long>((nc + eb - 1) / eb, 8192);
   if (lc32) k_lf_chunks<float><<<cgrid, eb, 0, st>>>(nlon, nlat, C, u64, w64, z64, lc32, lw32, lz32);
   if (lcc) k_lf_chunks<double><<<cgrid, eb, 0, st>>>(nlon, nlat, C, u64, w64, z64, lcc, lwc, lzc);
+  if (lcp) {
+    const long long np = 32LL * (C + 4) * nlat;
+    k_lf_pieces<<<(int)std::min<long long>((np + eb - 1) / eb, 8192), eb, 0, st>>>(nlon, nlat, C, u64, w64, z64, lcp,
+                                                                                 lwp, lzp);
+  }
   return cudaGetLastError() == cudaSuccess ? FTGCR_OK : FTGCR_ERR_CUDA;
 }
 
@@ -571,9 +597,13 @@ struct SmemPlan {
 // memory.  Returns false where two stage buffers do not fit.
 bool stream_plan(int nlon, int k, size_t limit, SmemPlan* p) {
   (void)k;  // stages of more than kNVS operand rows are taken in sub-stages
-  if (nlon % 4 != 0 || nlon < 4) return false;
-  const size_t st = (size_t)row_stride(nlon), per_row = 32 * (size_t)chunk_len(nlon);
-  const size_t fixed = (3 * st + 3 * per_row) * sizeof(float);
+  const int C = chunk_len(nlon);
+  // piece-major rows: C a power of two from 32 to 256 (the line solve's
+  // pieces are C / 8 elements in registers)
+  if (nlon % 4 != 0 || C < 32 || C > 256 || (C & (C - 1))) return false;
+  const size_t st = (size_t)row_stride(nlon), per_row = 32 * (size_t)C;
+  const size_t prow = 32 * (size_t)(C + 4);  // a piece-major row
+  const size_t fixed = 6 * prow * sizeof(float);
   const size_t buf = (size_t)kNVS * kCW * sizeof(float) + 8 * 16;
   int nbuf = (nlon > kCW && fixed + 3 * buf <= limit) ? 3 : 2;
   if (fixed + nbuf * buf > limit) return false;
@@ -869,6 +899,11 @@ size_t layout(ftgcr_handle* h, unsigned char* base, SolveDev<T>* sd) {
   sd->lcc = chunk ? (const T*)take(sizeof(T) * 32 * (size_t)C * nlat) : sd->lc;
   sd->lwc = chunk ? (const T*)take(sizeof(T) * 32 * (size_t)C * nlat) : sd->lw;
   sd->lzc = chunk ? (const T*)take(sizeof(T) * 32 * (size_t)C * nlat) : sd->lz;
+  // streamed solves: the FP32 constants again in the piece-major layout
+  const bool piece = !fp64 && h->split == 2;
+  sd->lcp = piece ? (const T*)take(sizeof(T) * 32 * (size_t)(C + 4) * nlat) : nullptr;
+  sd->lwp = piece ? (const T*)take(sizeof(T) * 32 * (size_t)(C + 4) * nlat) : nullptr;
+  sd->lzp = piece ? (const T*)take(sizeof(T) * 32 * (size_t)(C + 4) * nlat) : nullptr;
   size_t before = off;
   for (int q = 0; q < 3; ++q) sd->phi[q] = (T*)take(vT);
   for (int q = 0; q < 3; ++q) sd->r[q] = (T*)take(vT);
@@ -955,7 +990,8 @@ int setup_coefficients(ftgcr_handle* h, const SolveDev<T>& sd, const double* Dd,
                                      z64, r64, mixed ? (float*)sd.lc : nullptr, mixed ? (float*)sd.lw : nullptr,
                                      mixed ? (float*)sd.lz : nullptr, mixed ? (float*)sd.lrow : nullptr, st,
                                      chunk ? (double*)sd.lcc : nullptr, chunk ? (double*)sd.lwc : nullptr,
-                                     chunk ? (double*)sd.lzc : nullptr);
+                                     chunk ? (double*)sd.lzc : nullptr, mixed ? (float*)sd.lcp : nullptr,
+                                     mixed ? (float*)sd.lwp : nullptr, mixed ? (float*)sd.lzp : nullptr);
   if (frc) return frc;
   CK(cudaFreeAsync(scratch, st));
   return FTGCR_OK;

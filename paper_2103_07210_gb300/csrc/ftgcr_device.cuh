@@ -127,6 +127,11 @@ struct SolveDev {
   const T* lwc;
   const T* lzc;
   int lchunk;
+  // FP32 path, streamed solves: c = -u, 1/w, z in the piece-major layout of
+  // the streamed rounds ([nlat][32][C + 4], zero past the leading block)
+  const T* lcp;
+  const T* lwp;
+  const T* lzp;
   // Krylov vectors (inner precision)
   T* phi[3];
   T* r[3];

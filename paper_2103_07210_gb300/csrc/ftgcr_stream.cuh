@@ -44,7 +44,7 @@ struct StreamSmem {
   float alpha[kMaxK];
   float beta;
   float muA[kMaxStreamRows];           // mu A_j of the band's rows
-  float maps[kWarps * 64];             // line-solve chunk maps
+  float maps[kWarps * 64 + 2];         // line-solve piece maps, then y_0 and y_{m-1}
 };
 static __shared__ StreamSmem g_ss;
 
@@ -108,6 +108,176 @@ __device__ __forceinline__ void stream_init() {
     g_ss.bad = 0;
     fence_mbar_init();
   }
+  __syncthreads();
+}
+
+// ---- piece-major rows
+// The streamed rounds keep a row in shared memory piece-major: the row's 32
+// per-lane chunks of C elements (C = sd.C, a power of two, lcb = log2 C) one
+// after another with 4 floats of padding, element i at
+// (i >> lcb) * (C + 4) + (i & (C - 1)).  Four consecutive columns starting at
+// a multiple of 4 are then contiguous and 16-byte aligned, and the line
+// solve's pieces (C / 8 consecutive elements of one lane chunk per thread)
+// are read and written as float4 without bank conflicts (the chunk pitch
+// C + 4 is an odd number of float4 words).  The line-solve constants of a
+// streamed solve (c = -u, 1/w, z) come in the same layout (sd.lcp, lwp, lzp).
+__device__ __forceinline__ int pk(int i, int lcb, int P) { return (i >> lcb) * P + (i & ((1 << lcb) - 1)); }
+__device__ __forceinline__ void sts4(unsigned a, const V16<float>& v) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.v[0]), "f"(v.v[1]), "f"(v.v[2]), "f"(v.v[3]));
+}
+
+// Periodic tridiagonal solve of row j (M e = -r, the zonal line
+// preconditioner) in place in a piece-major row, by the whole block: thread
+// (w, lane) takes elements lane * C + w * CP + kk, kk < CP = C / 8, held in
+// registers.  Each recurrence of the leading block's factorisation (forward
+// g_i = b_i + c_{i-1} g_{i-1}, b = -r; backward y_i = winv_i g_i + c_i y_{i+1})
+// runs as: every piece's affine map, the maps of a lane's 8 pieces composed
+// through shared memory, a warp scan over the lanes for each lane's carry-in,
+// then each piece replayed from its exact carry-in.  The periodic coupling is
+// eliminated by bordering with z: x_{n-1} = (b_{n-1} + Tx_{n-1} y_0 +
+// Tx_{n-2} y_{m-1}) / delta, x_i = y_i - x_{n-1} z_i.  rb, cb, cw, cz: shared
+// addresses of the row and of its constants; maps: 2 * 8 * 32 + 2 floats.
+template <int CP>
+__device__ __noinline__ void line_solve_piece(const SolveDev<float>& sd, int j, unsigned rb, unsigned cb, unsigned cw,
+                                              unsigned cz, float* maps) {
+  constexpr int G = kWarps;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int n = sd.nlon, m = n - 1, C = CP * G, P = C + 4, lcb = __ffs(C) - 1;
+  const unsigned base = 4u * (unsigned)(lane * P + w * CP);
+  const int i0 = lane * C + w * CP;
+  const float* lr = sd.lrow + (long long)j * 4;
+  const float lr0 = __ldg(lr + 0), lr1 = __ldg(lr + 1), lr2 = __ldg(lr + 2);
+  float* mF = maps;
+  float* mG = maps + 32 * G;
+  const float bl = -lds<float>(rb + 4u * (unsigned)pk(n - 1, lcb, P));
+  // the forward multiplier of the piece's first element: c of the element before
+  float a0 = 0.f;
+  if (w > 0)
+    a0 = lds<float>(cb + base - 4u);
+  else if (lane > 0)
+    a0 = lds<float>(cb + 4u * (unsigned)((lane - 1) * P + C - 1));
+  float r[CP], cv[CP];
+#pragma unroll
+  for (int q = 0; q < CP; q += 4) {
+    const V16<float> x = lds4(rb + base + 4u * q), y = lds4(cb + base + 4u * q);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      // positions past the row hold no data (their factors are zero)
+      r[q + u] = i0 + q + u < n ? x.v[u] : 0.f;
+      cv[q + u] = y.v[u];
+    }
+  }
+  // forward: the piece's map g_out = F g_in + Gm
+  float F = 1.f, Gm = 0.f;
+  {
+    float a = a0;
+#pragma unroll
+    for (int q = 0; q < CP; ++q) {
+      Gm = fmaf(a, Gm, -r[q]);
+      F = F * a;
+      a = cv[q];
+    }
+  }
+  mF[w * 32 + lane] = F;
+  mG[w * 32 + lane] = Gm;
+  __syncthreads();
+  float FL = 1.f, GL = 0.f, Fw[G], Gw[G];
+#pragma unroll
+  for (int q = 0; q < G; ++q) {
+    Fw[q] = mF[q * 32 + lane];
+    Gw[q] = mG[q * 32 + lane];
+    GL = fmaf(Fw[q], GL, Gw[q]);
+    FL = FL * Fw[q];
+  }
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const float Fo = __shfl_up_sync(0xffffffffu, FL, d);
+    const float Go = __shfl_up_sync(0xffffffffu, GL, d);
+    if (lane >= d) {
+      GL = fmaf(FL, Go, GL);
+      FL = FL * Fo;
+    }
+  }
+  float carry = __shfl_up_sync(0xffffffffu, GL, 1);
+  if (lane == 0) carry = 0.f;
+#pragma unroll
+  for (int q = 0; q < G; ++q)
+    if (q < w) carry = fmaf(Fw[q], carry, Gw[q]);
+  {
+    float a = a0, g = carry;
+#pragma unroll
+    for (int q = 0; q < CP; ++q) {
+      g = fmaf(a, g, -r[q]);
+      r[q] = g;
+      a = cv[q];
+    }
+  }
+  __syncthreads();  // every carry read before the maps are reused
+  // backward: the piece's map y_in = Fb y_out + Y
+  float wv[CP];
+#pragma unroll
+  for (int q = 0; q < CP; q += 4) {
+    const V16<float> y = lds4(cw + base + 4u * q);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) wv[q + u] = y.v[u];
+  }
+  float Fb = 1.f, Y = 0.f;
+#pragma unroll
+  for (int q = CP - 1; q >= 0; --q) {
+    Y = fmaf(cv[q], Y, r[q] * wv[q]);
+    Fb = Fb * cv[q];
+  }
+  mF[w * 32 + lane] = Fb;
+  mG[w * 32 + lane] = Y;
+  __syncthreads();
+  float FbL = 1.f, YL = 0.f;
+#pragma unroll
+  for (int q = G - 1; q >= 0; --q) {
+    Fw[q] = mF[q * 32 + lane];
+    Gw[q] = mG[q * 32 + lane];
+    YL = fmaf(Fw[q], YL, Gw[q]);
+    FbL = FbL * Fw[q];
+  }
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const float Fo = __shfl_down_sync(0xffffffffu, FbL, d);
+    const float Yo = __shfl_down_sync(0xffffffffu, YL, d);
+    if (lane + d < 32) {
+      YL = fmaf(FbL, Yo, YL);
+      FbL = FbL * Fo;
+    }
+  }
+  float carryb = __shfl_down_sync(0xffffffffu, YL, 1);
+  if (lane == 31) carryb = 0.f;
+#pragma unroll
+  for (int q = G - 1; q >= 0; --q)
+    if (q > w) carryb = fmaf(Fw[q], carryb, Gw[q]);
+  {
+    float y = carryb;
+#pragma unroll
+    for (int q = CP - 1; q >= 0; --q) {
+      y = fmaf(cv[q], y, r[q] * wv[q]);
+      r[q] = y;
+    }
+  }
+  // bordering: y_0 and y_{m-1} from the threads that hold them
+  if (i0 == 0) maps[64 * G] = r[0];
+#pragma unroll
+  for (int q = 0; q < CP; ++q)
+    if (i0 + q == m - 1) maps[64 * G + 1] = r[q];
+  __syncthreads();
+  const float y0 = maps[64 * G], ym = maps[64 * G + 1];
+  const float xl = fmaf(lr2, ym, fmaf(lr1, y0, bl * lr0));
+#pragma unroll
+  for (int q = 0; q < CP; q += 4) {
+    const V16<float> z = lds4(cz + base + 4u * q);
+    V16<float> o;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) o.v[u] = fmaf(-xl, z.v[u], r[q + u]);
+    sts4(rb + base + 4u * q, o);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) sts(rb + 4u * (unsigned)pk(n - 1, lcb, P), xl);
   __syncthreads();
 }
 
@@ -184,8 +354,8 @@ struct AxRegs {
 // the flips of the step, r'' and phi'', the norm, the state vectors of the
 // row written, r'' into the row buffer.
 template <bool FUSED>
-__device__ __forceinline__ void stream_ax(int n, const PhaseSmem& ps, unsigned buf, int row, int ch, int sub, int nv,
-                                          unsigned rb, AxRegs& x, Acc<float>& an) {
+__device__ __forceinline__ void stream_ax(int n, int lcb, int P, const PhaseSmem& ps, unsigned buf, int row, int ch,
+                                          int sub, int nv, unsigned rb, AxRegs& x, Acc<float>& an) {
   const int c0 = ch * kCW, i4 = 4 * (int)threadIdx.x;
   if (c0 + i4 >= n) return;
   const int v0 = sub * kNVS;
@@ -240,8 +410,7 @@ __device__ __forceinline__ void stream_ax(int n, const PhaseSmem& ps, unsigned b
   }
   stv(g_ss.out[2] + g, rn);
   stv(g_ss.out[3] + g, fn);
-#pragma unroll
-  for (int w = 0; w < 4; ++w) sts_nc(rb + 4u * (unsigned)sk(c0 + i4 + w), rn.v[w]);
+  sts4(rb + 4u * (unsigned)pk(c0 + i4, lcb, P), rn);
 }
 
 // Registers a stencil stage carries across its sub-stages.
@@ -255,9 +424,9 @@ struct StRegs {
 // of its operand rows.  The operations of the stencil step of the other
 // round layouts.
 template <int KB>
-__device__ __forceinline__ void stream_st(int n, int nlat, unsigned buf, unsigned lead, int row, int ch, int sub,
-                                          int nv, unsigned eC, unsigned eN, unsigned eS, float muA, StRegs& x,
-                                          Acc<float>* ad, Acc<float>& ah, Acc<float>& aq) {
+__device__ __forceinline__ void stream_st(int n, int nlat, int lcb, int P, unsigned buf, unsigned lead, int row,
+                                          int ch, int sub, int nv, unsigned eC, unsigned eN, unsigned eS, float muA,
+                                          StRegs& x, Acc<float>* ad, Acc<float>& ah, Acc<float>& aq) {
   const int c0 = ch * kCW, i4 = 4 * (int)threadIdx.x;
   const int v0 = sub * kNVS, v1 = min(nv, v0 + kNVS);
   const bool act = c0 + i4 < n;
@@ -274,18 +443,23 @@ __device__ __forceinline__ void stream_st(int n, int nlat, unsigned buf, unsigne
     V16<float> ty, tys;
     if (hasN) ty = S(1);
     if (hasS) tys = S(2);
+    // e of the four columns, their north and south rows, and the columns
+    // west of the first and east of the last (periodic)
+    const int i = c0 + i4;
+    const unsigned o = 4u * (unsigned)pk(i, lcb, P);
+    const V16<float> ec = lds4(eC + o);
+    V16<float> en, es;
+    if (hasN) en = lds4(eN + o);
+    if (hasS) es = lds4(eS + o);
+    const float ew = lds<float>(eC + 4u * (unsigned)pk(i == 0 ? n - 1 : i - 1, lcb, P));
+    const float ee = lds<float>(eC + 4u * (unsigned)pk(i + 4 == n ? 0 : i + 4, lcb, P));
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
-      const int i = c0 + i4 + w;
-      const int ie = (i + 1 == n) ? 0 : i + 1;
-      const int iw = (i == 0) ? n - 1 : i - 1;
-      const float xv = lds<float>(eC + 4u * (unsigned)sk(i));
-      const float ve = lds<float>(eC + 4u * (unsigned)sk(ie));
-      const float vw = lds<float>(eC + 4u * (unsigned)sk(iw));
-      const float vn = hasN ? lds<float>(eN + 4u * (unsigned)sk(i)) : 0.f;
-      const float vs = hasS ? lds<float>(eS + 4u * (unsigned)sk(i)) : 0.f;
-      x.le.v[w] = stencil5<float>(xv, ve, vw, vn, vs, tx.v[w], w == 0 ? txw0 : tx.v[w - 1], hasN ? ty.v[w] : 0.f,
-                                  hasS ? tys.v[w] : 0.f, muA, hasN, hasS);
+      const float ve = w < 3 ? ec.v[w + 1] : ee;
+      const float vw = w > 0 ? ec.v[w - 1] : ew;
+      x.le.v[w] = stencil5<float>(ec.v[w], ve, vw, hasN ? en.v[w] : 0.f, hasS ? es.v[w] : 0.f, tx.v[w],
+                                  w == 0 ? txw0 : tx.v[w - 1], hasN ? ty.v[w] : 0.f, hasS ? tys.v[w] : 0.f, muA, hasN,
+                                  hasS);
     }
     stv(g_ss.out[4] + (long long)row * n + c0 + i4, x.le);
   }
@@ -307,6 +481,37 @@ __device__ __forceinline__ void stream_st(int n, int nlat, unsigned buf, unsigne
     for (int w = 0; w < 4; ++w) {
       ah.add(rn.v[w], x.le.v[w]);
       aq.add(x.le.v[w], x.le.v[w]);
+    }
+  }
+}
+
+// Row j of a vector into a piece-major row (float4 accesses) and back.
+__device__ __forceinline__ void stage_piece_row(const float* src, int j, int n, int lcb, int P, unsigned dst) {
+  const float* s = src + (long long)j * n;
+  for (int i = 4 * (int)threadIdx.x; i < n; i += 4 * kThreads) sts4(dst + 4u * (unsigned)pk(i, lcb, P), ldv(s + i));
+}
+__device__ __forceinline__ void store_piece_row(float* dst, int j, int n, int lcb, int P, unsigned src) {
+  float* d = dst + (long long)j * n;
+  for (int i = 4 * (int)threadIdx.x; i < n; i += 4 * kThreads) stv(d + i, lds4(src + 4u * (unsigned)pk(i, lcb, P)));
+}
+// The data-loss events of step t (Section 3) on e of row j in a piece-major
+// row buffer (the flips of apply_losses that land in the row).
+__device__ __forceinline__ void apply_losses_piece(const SolveDev<float>& sd, long long t, int j, float* row, int lcb,
+                                                   int P) {
+  const int nlon = sd.nlon;
+  const long long g0 = (long long)j * nlon, g1 = g0 + nlon;
+  for (int q = 0; q < sd.nlosses; ++q) {
+    const LossEv ev = sd.losses[q];
+    if (ev.step != t) continue;
+    const long long b0 = (long long)ev.rank * sd.N / ev.nranks, b1 = (long long)(ev.rank + 1) * sd.N / ev.nranks;
+    const long long len = b1 - b0;
+    if (len <= 0 || b1 <= g0 || b0 >= g1) continue;
+    for (long long i = 1 + threadIdx.x; i <= ev.count; i += kThreads) {
+      const unsigned long long z = splitmix64_at(ev.seed, (unsigned long long)i);
+      const long long g = b0 + (long long)(z % (unsigned long long)len);
+      if (g < g0 || g >= g1) continue;
+      unsigned int* w = reinterpret_cast<unsigned int*>(row + pk((int)(g - g0), lcb, P));
+      atomicXor(w, 1u << (unsigned)((z >> 32) % 32u));
     }
   }
 }
@@ -333,13 +538,15 @@ __device__ __forceinline__ void cta_red_finish_add(CtaRed& cr, int nv, double* o
 // whose neighbours are all in the band; partial sums 0 (||r'||^2) and the
 // dots of those rows.  pass 1 (after a grid barrier): the stencils of the
 // band's edge rows, with the neighbouring band's e row read back; their dots
-// added to the partial sums.  Shared memory: three e rows (row_stride each),
-// the constants c, 1/w, z of one row (32 C each), sd.nslot stage buffers of
+// added to the partial sums.  Shared memory: three piece-major e rows
+// (32 (C + 4) floats each), the constants c, 1/w, z of one row (the same
+// layout), sd.nslot stage buffers of
 // kNVS * kCW floats, then the Tx leads (sd.nslot x 8 x 16 bytes).
 template <int KB, bool FUSED>
 __device__ __noinline__ void phase_stream(const SolveDev<float>& sd, const Ctx<float>& c, int tau, float* sm,
                                           PhaseSmem& ps, double* part_out, int pass, int* err) {
-  const int n = sd.nlon, nlat = sd.nlat, stride = row_stride(n), C = sd.C;
+  const int n = sd.nlon, nlat = sd.nlat, C = sd.C, P = C + 4, lcb = __ffs(C) - 1;
+  const int stride = 32 * P;  // a piece-major row
   const int j0 = row_start(nlat, sd.nt, tau), j1 = row_start(nlat, sd.nt, tau + 1);
   const int nch = (n + kCW - 1) / kCW, nbuf = sd.nslot, D = nbuf - 1;
   const int nv_ax = FUSED ? 4 + 2 * (c.nuo + 1) : 4;
@@ -348,10 +555,10 @@ __device__ __noinline__ void phase_stream(const SolveDev<float>& sd, const Ctx<f
   float* ebuf = sm;
   float* cst = sm + 3 * stride;
   const unsigned cst_s = smem_addr(cst);
-  float* ring = cst + 3 * 32 * C;
+  float* ring = cst + 3 * stride;
   const unsigned ring_s = smem_addr(ring);
   const unsigned lead_s = smem_addr(ring + (size_t)nbuf * kNVS * kCW);
-  const unsigned per = 128u * (unsigned)C;  // bytes of one constants row
+  const unsigned per = 4u * (unsigned)stride;  // bytes of one constants row
   auto interior = [&](int i) { return (i == 0 || i - 1 >= j0) && (i == nlat - 1 || i + 1 < j1); };
   if (threadIdx.x == 0) {
     ps.cs_solve = -1;  // the dynamic shared memory is laid out for this phase
@@ -391,11 +598,11 @@ __device__ __noinline__ void phase_stream(const SolveDev<float>& sd, const Ctx<f
   unsigned cph = g_ss.cph;
   auto issue_consts = [&](int row) {  // thread 0: one row of c, 1/w, z by bulk copies
     const unsigned mb = smem_addr(&g_ss.cfull);
-    const long long o = (long long)row * 32 * C;
+    const long long o = (long long)row * stride;
     mbar_expect(mb, 3u * per);
-    bulk_load(cst_s, sd.lc + o, per, mb);
-    bulk_load(cst_s + per, sd.lw + o, per, mb);
-    bulk_load(cst_s + 2u * per, sd.lz + o, per, mb);
+    bulk_load(cst_s, sd.lcp + o, per, mb);
+    bulk_load(cst_s + per, sd.lwp + o, per, mb);
+    bulk_load(cst_s + 2u * per, sd.lzp + o, per, mb);
   };
   if (threadIdx.x == 0 && pass == 0 && j0 < j1) {
     fence_proxy_async_global();
@@ -438,9 +645,9 @@ __device__ __noinline__ void phase_stream(const SolveDev<float>& sd, const Ctx<f
         // the three e rows, the neighbour's included (plain loads; this row's
         // stage copies are in flight meanwhile)
         __syncthreads();  // the previous row's stencil has read them
-        if (row > 0) stage_rows(c.eW, row - 1, row, n, ebuf, stride);
-        stage_rows(c.eW, row, row + 1, n, ebuf + stride, stride);
-        if (row < nlat - 1) stage_rows(c.eW, row + 1, row + 2, n, ebuf + 2 * stride, stride);
+        if (row > 0) stage_piece_row(c.eW, row - 1, n, lcb, P, smem_addr(ebuf));
+        stage_piece_row(c.eW, row, n, lcb, P, smem_addr(ebuf + stride));
+        if (row < nlat - 1) stage_piece_row(c.eW, row + 1, n, lcb, P, smem_addr(ebuf + 2 * stride));
         __syncthreads();
         eS = smem_addr(ebuf);
         eC = smem_addr(ebuf + stride);
@@ -463,9 +670,10 @@ __device__ __noinline__ void phase_stream(const SolveDev<float>& sd, const Ctx<f
         const int b = cidx % nbuf;
         const unsigned buf = ring_s + 4u * (unsigned)(b * kNVS * kCW);
         if (type == 0)
-          stream_ax<FUSED>(n, ps, buf, row, ch, sb, nv, rb, xa, an);
+          stream_ax<FUSED>(n, lcb, P, ps, buf, row, ch, sb, nv, rb, xa, an);
         else
-          stream_st<KB>(n, nlat, buf, lead_s + 128u * (unsigned)b, row, ch, sb, nv, eC, eN, eS, muA, xs, ad, ah, aq);
+          stream_st<KB>(n, nlat, lcb, P, buf, lead_s + 128u * (unsigned)b, row, ch, sb, nv, eC, eN, eS, muA, xs, ad,
+                        ah, aq);
         ++cidx;
       }
     }
@@ -485,19 +693,16 @@ __device__ __noinline__ void phase_stream(const SolveDev<float>& sd, const Ctx<f
     }
     cph ^= 1u;
     {
-      const LineConsts<float> lc{cst, cst + 32 * C, cst + 64 * C};
-      const int warp = threadIdx.x >> 5;
-      if (C % 64 == 0) {
-        line_solve_row_group<8>(sd, row, rowbuf, lc, g_ss.maps, 1);
-      } else if (C % 32 == 0) {
-        if (warp < 4) line_solve_row_group<4>(sd, row, rowbuf, lc, g_ss.maps, 1);
-      } else if (C % 16 == 0) {
-        if (warp < 2) line_solve_row_group<2>(sd, row, rowbuf, lc, g_ss.maps, 1);
-      } else if (warp == 0) {
-        line_solve_row(sd, row, rowbuf, lc);
-      }
+      const unsigned cb = cst_s, cwb = cst_s + per, czb = cst_s + 2u * per;
+      if (C == 32)
+        line_solve_piece<4>(sd, row, rb, cb, cwb, czb, g_ss.maps);
+      else if (C == 64)
+        line_solve_piece<8>(sd, row, rb, cb, cwb, czb, g_ss.maps);
+      else if (C == 128)
+        line_solve_piece<16>(sd, row, rb, cb, cwb, czb, g_ss.maps);
+      else
+        line_solve_piece<32>(sd, row, rb, cb, cwb, czb, g_ss.maps);
     }
-    __syncthreads();
     if (threadIdx.x == 0) {
       // the constants are consumed: the next row's may come in
       if (row + 1 < j1) issue_consts(row + 1);
@@ -506,15 +711,15 @@ __device__ __noinline__ void phase_stream(const SolveDev<float>& sd, const Ctx<f
         const long long g = ps.fl[q].g;
         const int jj = (int)(g / n), i = (int)(g - (long long)jj * n);
         if (jj != row) continue;
-        rowbuf[sk(i)] = flip_bits(rowbuf[sk(i)], ps.fl[q].bit);
+        rowbuf[pk(i, lcb, P)] = flip_bits(rowbuf[pk(i, lcb, P)], ps.fl[q].bit);
       }
     }
     if (sd.nlosses) {
       __syncthreads();
-      apply_losses(sd, c.t, row, row + 1, rowbuf, stride);
+      apply_losses_piece(sd, c.t, row, rowbuf, lcb, P);
     }
     __syncthreads();
-    store_rows(c.eW, row, row + 1, n, rowbuf, stride);
+    store_piece_row(c.eW, row, n, lcb, P, rb);
   }
   cp_async_wait_all();  // the groups still open are empty unless the pass failed
   if (fail) {

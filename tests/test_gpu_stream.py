@@ -26,7 +26,7 @@ CASES = [
     (1024, 512, 4, "flow", 0),     # 152 bands of 3-4 rows
     (1024, 512, 8, "random", 0),
     (2048, 300, 2, "flow", 0),     # two chunks per row
-    (1028, 40, 3, "random", 5),    # a 4-column second chunk; 8-row bands
+    (2044, 300, 3, "flow", 40),    # a short second chunk, padded line-solve pieces; 7-8-row bands
     (1000, 33, 1, "random", 2),    # one short chunk; two tall bands
     (1024, 33, 5, "random", 1),    # one band: every row interior
     (2048, 64, 4, "flow", 64),     # two chunks per row, one-row bands
@@ -141,9 +141,12 @@ def test_batch_mixing_streamed_and_other_layouts_is_bitwise_solo():
 
 
 def test_streamed_flag_rejected_where_it_cannot_run():
-    p = inputs.hill_problem(1022, 8)  # nlon not a multiple of 4
-    with pytest.raises(ftgcr.FTGCRError):
-        ftgcr.Solver(p.D, p.mu, precision="mixed", rounds="streamed")
+    # nlon not a multiple of 4; per-lane chunks of 40 (not a power of two);
+    # chunks of 8 (rows under 993 columns)
+    for nlon in (1022, 1028, 256):
+        p = inputs.hill_problem(nlon, 8)
+        with pytest.raises(ftgcr.FTGCRError):
+            ftgcr.Solver(p.D, p.mu, precision="mixed", rounds="streamed")
     q = inputs.hill_problem(1024, 8)
     with pytest.raises(ftgcr.FTGCRError):
         ftgcr.Solver(q.D, q.mu, precision="fp64", rounds="streamed")
