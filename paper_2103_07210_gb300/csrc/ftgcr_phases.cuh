@@ -1809,9 +1809,23 @@ __device__ __noinline__ void phase_fin(const SolveDev<T>& sd, const Ctx<T>& c, i
   const RowTile rt = row_tile(nlat, sd.nt, tau);
   Acc<double> acc;
   if (sd.mixed) {
+    // the tile's rows are contiguous: a copy, four loads in flight per thread
     const double* xs = c.xsrc;
-    for (long long g = (long long)rt.j0 * nlon + threadIdx.x; g < (long long)rt.j1 * nlon; g += kThreads)
-      sd.xout[g] = ldcg(xs + g);
+    const long long g0 = (long long)rt.j0 * nlon, g1 = (long long)rt.j1 * nlon;
+    constexpr int U = 4;
+    for (long long b = g0 + threadIdx.x; b < g1; b += U * kThreads) {
+      double v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const long long g = b + (long long)u * kThreads;
+        if (g < g1) v[u] = ldcg(xs + g);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const long long g = b + (long long)u * kThreads;
+        if (g < g1) sd.xout[g] = v[u];
+      }
+    }
   } else {
     if (threadIdx.x == 0)
       ps.npt = c.patched ? collect_flips(sd, c.patch_step, 1u << V_X, 0, sd.N, ps.pt) : 0;
