@@ -507,7 +507,7 @@ def bench_batch(torch, ftgcr, dev, n=128, seed=42, reps=3):
 
 
 def bench_serving(torch, ftgcr, dev, n_req=2000, load=0.8, seed=7, hills_per_size=4, n_cap=300,
-                  sweep_loads=(0.5, 1.0, 1.2), n_sweep=400, tune_concurrency=16, n_tuned=600):
+                  sweep_loads=(0.5, 1.0, 1.2), n_sweep=400, tune_concurrency=16, n_tuned=600, n_limited=1000):
     """Open-loop serving: n_req requests with Poisson arrivals at `load` x the
     measured capacity; sizes U{256x128, 512x256, 1024x512, 2048x1024}, mixed
     precision, hills drawn per problem, 1% carrying one bit flip.  Right-hand
@@ -518,7 +518,9 @@ def bench_serving(torch, ftgcr, dev, n_req=2000, load=0.8, seed=7, hills_per_siz
     (load_sweep).  Beside it, a shorter run with row bands per size from the
     autotuner (ftgcr_tune at `tune_concurrency` solves per launch, passed with
     each request): taller bands raise throughput a little but lengthen a lone
-    request's solve, so the default bands stay the headline."""
+    request's solve, so the default bands stay the headline.  And a run with
+    the admission limit (ftgcr_server_set_max_points) at 1.1 x the largest
+    request's points, at 0.8 x its own measured capacity."""
     import threading
 
     sizes = [(256, 128), (512, 256), (1024, 512), (2048, 1024)]
@@ -574,8 +576,9 @@ def bench_serving(torch, ftgcr, dev, n_req=2000, load=0.8, seed=7, hills_per_siz
         pi, faults = reqs[i]
         return submit_p(srv, pi, faults)
 
-    def serve(n_req, sweep_loads):
+    def serve(n_req, sweep_loads, max_points=0):
         with ftgcr.Server(max_slots=64, epoch_rounds=24) as srv:
+            srv.set_max_points(max_points)
             warm = [submit_p(srv, pi) for pi in range(len(probs))]  # a handle set up for every problem
             for _ in warm:
                 srv.next()
@@ -674,6 +677,13 @@ def bench_serving(torch, ftgcr, dev, n_req=2000, load=0.8, seed=7, hills_per_siz
     out["autotuned_tiles"]["tiles"] = {f"{a}x{b}": {"tiles": t["tiles"], "rounds": t["rounds"],
                                                     "default_tiles": t["default_tiles"]} for (a, b), t in tuned.items()}
     out["autotuned_tiles"]["tuned_for"] = f"ftgcr_tune at {tune_concurrency} solves per launch"
+    tiling.clear()
+    lim = int(1.1 * max(a * b for a, b in sizes))
+    d = serve(n_limited, (), max_points=lim)
+    out["max_points_limit"] = {k: d[k] for k in ("requests", "completed_ok", "capacity_solves_per_s",
+                                                 "achieved_solves_per_s", "latency_ms",
+                                                 "bitwise_equal_to_alone_sample")}
+    out["max_points_limit"]["max_points"] = lim
     return out
 
 

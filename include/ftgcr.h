@@ -342,19 +342,24 @@ int ftgcr_solve_noalloc(const ftgcr_grid* grid, const double* D, int32_t k, doub
 /* ---- serving: continuous batching of independent solves ----
  * The paper solves one elliptic problem per model time step (Section 2); a
  * server runs many such requests at once.  It owns a scheduler thread, a
- * CUDA stream, a pool of solver handles and two tables of max_slots solve
- * slots (one per precision).  Each epoch it admits queued requests (first
- * come, first served) while a slot of the request's precision is free and its
- * handle fits the budget, then runs every running solve for at most
- * epoch_rounds rounds of one persistent launch, and hands back the solves
- * that finished.  Unfinished solves resume in the next epoch beside the newly
- * admitted ones.  Every result, statistics included, is bitwise the result
- * of the same request solved alone with ftgcr_solve.
+ * preparation thread, CUDA streams for launches, copies and set-up, a pool of
+ * solver handles and two tables of max_slots solve slots (one per precision).
+ * A queued request first gets a handle (first come, first served, within the
+ * budget); a handle that must be created or rebuilt from the request's
+ * coefficients is prepared on the preparation thread, so set-up never holds
+ * up the running solves.  Each epoch the scheduler admits ready requests, in
+ * submission order, while a slot of their precision is free, runs every
+ * running solve for at most epoch_rounds rounds of one persistent launch, and
+ * hands back the solves that finished.  Unfinished solves resume in the next
+ * epoch beside the newly admitted ones.  Every result, statistics included,
+ * is bitwise the result of the same request solved alone with ftgcr_solve.
  *  - Memory: a request is charged ftgcr_footprint(grid, k) while its handle is
- *    held; idle handles are pooled by shape (grid, k, tol) and reused (their
- *    coefficients are rebuilt from the new D), and evicted least recently used
- *    first when a new shape does not fit.  budget_bytes = 0 means half of the
- *    device memory free at creation.
+ *    held; idle handles are pooled by shape (grid, k, tol).  A request takes an
+ *    idle handle already set up from the same (D, key) as is; otherwise a new
+ *    handle is made while the budget allows (a keyless request rebuilds an
+ *    idle handle of its shape first), then an idle handle of the shape is
+ *    rebuilt, then idle handles are evicted least recently used first.
+ *    budget_bytes = 0 means half of the device memory free at creation.
  *  - Pointers: D, rhs and x may be host or device memory and must stay valid,
  *    and x untouched by the caller, until poll/wait reports the result.  Host
  *    rhs and x are staged (pinned host memory is copied asynchronously) and
@@ -364,7 +369,9 @@ int ftgcr_solve_noalloc(const ftgcr_grid* grid, const double* D, int32_t k, doub
  *    thread; destroy must not overlap any other call on the same server. */
 typedef struct ftgcr_server ftgcr_server;
 typedef struct {
-  int64_t submitted, completed, queued, running;
+  int64_t submitted, completed;
+  int64_t queued;       /* waiting for a handle, in preparation or for a slot */
+  int64_t running;
   int64_t epochs;       /* persistent launches made */
   int64_t handles;      /* handles held (running and pooled) */
   int64_t bytes_in_use; /* their footprint */
@@ -400,6 +407,15 @@ int ftgcr_server_wait(ftgcr_server* srv, int64_t ticket, double timeout_s, ftgcr
 int ftgcr_server_next(ftgcr_server* srv, double timeout_s, int64_t* ticket, ftgcr_stats_t* stats);
 
 int ftgcr_server_info(ftgcr_server* srv, ftgcr_server_info_t* out);
+
+/* Admission limit: at most max_points grid points (nlon * nlat summed over
+ * the running solves) per precision at once; 0 (the default) means no limit.
+ * Every running solve advances one round per round of the shared launch, and
+ * a round's time grows with the points in it, so the limit trades throughput
+ * for shorter rounds: the request that would cross it waits, in submission
+ * order, and so do the requests behind it; a request alone in its precision
+ * always runs.  Takes effect from the next epoch.  Errors: FTGCR_ERR_ARG. */
+int ftgcr_server_set_max_points(ftgcr_server* srv, int64_t max_points);
 
 /* Stop: queued requests end with FTGCR_ERR_STATE, running ones finish; then
  * every handle and buffer is freed. */

@@ -669,8 +669,9 @@ SmemPlan smem_plan(int nlon, int nlat, int nt, int mixed, size_t elem, int preco
 // Mixed solves of at least this many points stream their step rounds by
 // default: their Krylov vectors (about 16 FP32 vectors of N) far outgrow the
 // 129 MB L2, so a round is bound by HBM rather than by L2 latency.  Smaller
-// solves run faster in one-pass rounds (measured: 2048 x 1024 83 against 122
-// us per inner step; 4096 x 2048 352 streamed against 401 split).
+// solves run faster in one-pass rounds (measured per inner step: 2048 x 1024
+// 83 us in one-pass rounds against 94 streamed; 4096 x 2048 247 streamed
+// against 401 in split rounds).
 constexpr long long kStreamMinPoints = 4LL * 1024 * 1024;
 
 // Streamed step rounds: one band per SM (at most kMaxStreamRows rows).
@@ -1706,6 +1707,11 @@ void table_destroy(SlotTable* t) {
   delete t;
 }
 
+__global__ void k_table_place(void** solves, int* nt, int slot, void* sdev, int tiles) {
+  solves[slot] = sdev;
+  nt[slot] = tiles;
+}
+
 int table_begin(SlotTable* t, int slot, ftgcr_handle* h, const double* rhs, double* x, const ftgcr_fault_plan* plan,
                 cudaStream_t st, int check) {
   if (!t || !h || !rhs || !x || slot < 0 || slot >= t->n || t->slot[slot] || h->precision != t->precision)
@@ -1714,8 +1720,10 @@ int table_begin(SlotTable* t, int slot, ftgcr_handle* h, const double* rhs, doub
     if (o == h) return FTGCR_ERR_ARG;  // one running solve per handle
   int rc = validate_plan(h, plan);
   if (rc) return rc;
-  CK(cudaMemcpyAsync(t->d_solves + slot, &h->sdev, sizeof(void*), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(t->d_nt + slot, &h->nt, sizeof(int), cudaMemcpyHostToDevice, st));
+  // written by a kernel, not copied from pageable host memory: such a copy
+  // may wait for the launch still running on the stream
+  k_table_place<<<1, 1, 0, st>>>(t->d_solves, t->d_nt, slot, h->sdev, h->nt);
+  CK(cudaGetLastError());
   if (check) {  // the handle's own control block carries the flag
     const int cg = (int)std::min<long long>((h->N + 255) / 256, 1024);
     CK(cudaMemsetAsync(&h->ctl->nonfinite, 0, sizeof(int), st));

@@ -1,22 +1,26 @@
 // Request scheduler of libftgcr: continuous batching of independent FT-GCR(k)
 // solves (Algorithm 1) over resumable persistent launches.
 //
-// One scheduler thread per server owns a CUDA stream, two slot tables (FP64
-// and mixed precision: a launch runs one precision) and a pool of solver
-// handles.  It repeats an epoch:
-//   1. admit queued requests, first come first served, while a slot of their
-//      precision is free and their handle fits the device-memory budget
-//      (an idle pooled handle of the same shape is reused: its coefficients
-//      are rebuilt from the request's D; otherwise idle handles are evicted,
-//      least recently used first, until a new one fits);
-//   2. stage host inputs and begin each admitted solve in its slot;
-//   3. run each occupied table for at most `epoch_rounds` rounds;
-//   4. hand finished solves back (host solutions copied out, statistics
-//      filled) and free their slots and handles.
-// A request admitted in epoch e joins the solves already running at the start
-// of epoch e + 1's launch, so arrival-to-start latency is bounded by one
-// epoch.  Each solve's arithmetic depends only on its own handle, so a served
-// result is bitwise the result of the same solve run alone.
+// One scheduler thread per server owns the launch stream, two slot tables
+// (FP64 and mixed precision: a launch runs one precision) and a pool of solver
+// handles.  A request passes through three queues:
+//   queued  -> a handle is bound to it, first come first served, within the
+//              device-memory budget: an idle handle already set up from the
+//              request's coefficients (same D and key) is ready at once;
+//              otherwise a new handle is made while the budget allows, else
+//              an idle handle of the shape is rebuilt, else idle handles are
+//              evicted, least recently used first;
+//   prep    -> a second thread creates or rebuilds the handle on its own
+//              stream (and destroys evicted ones), so set-up never stalls the
+//              launches of the solves already running;
+//   ready   -> in ticket order into free slots of its precision.
+// The scheduler repeats an epoch: admit ready requests, stage their host
+// inputs on a copy stream and begin them behind the running launch, collect
+// that launch, start the next one for at most `epoch_rounds` rounds, and hand
+// back the finished solves (host solutions copied out on the copy stream
+// while the next launch runs).  A request made ready in epoch e joins epoch
+// e + 1's launch.  Each solve's arithmetic depends only on its own handle, so
+// a served result is bitwise the result of the same solve run alone.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -52,7 +56,7 @@ struct HandleKey {
 
 struct PoolEntry {
   HandleKey key;
-  ftgcr_handle* h = nullptr;  // created by the scheduler thread on first use
+  ftgcr_handle* h = nullptr;  // created by the preparation thread on first use
   const double* setup_D = nullptr;  // coefficients the handle was last set up from
   uint64_t setup_key = 0;           // with their caller-given identity (0: none)
   int64_t bytes = 0;
@@ -82,26 +86,40 @@ struct Request {
 
 int table_of(int precision) { return precision == FTGCR_MIXED ? 1 : 0; }
 
+bool same_coeffs(const PoolEntry& e, const Request* r) { return r->ckey && e.setup_key == r->ckey && e.setup_D == r->D; }
+
+int64_t points(const Request* r) { return (int64_t)r->key.grid.nlon * r->key.grid.nlat; }
+
 }  // namespace
 
 struct ftgcr_server {
   int dev = 0;
-  cudaStream_t st = nullptr;
+  cudaStream_t st = nullptr;   // persistent launches, begin kernels
+  cudaStream_t cst = nullptr;  // staging copies of host arrays, both ways
+  cudaStream_t pst = nullptr;  // coefficient rebuilds (preparation thread)
+  cudaEvent_t staged = nullptr;
   int64_t budget = 0, in_use = 0;
   int max_slots = 0, epoch_rounds = 0;
+  int64_t max_points = 0;            // grid points running at once per table (0: no limit)
+  int64_t run_points[2] = {0, 0};
   SlotTable* tables[2] = {nullptr, nullptr};
   std::vector<Request*> slot_req[2];
   std::list<PoolEntry> pool;
-  std::deque<Request*> queue;
+  std::deque<Request*> queue;     // submitted, no handle yet (arrival order)
+  std::deque<Request*> prep;      // handle being created or rebuilt
+  std::deque<Request*> ready;     // handle set up, waiting for a slot (ticket order)
+  std::vector<ftgcr_handle*> doomed;  // evicted handles, destroyed by the preparation thread
   std::deque<int64_t> finished;  // tickets in order of completion, not yet collected
   std::unordered_map<int64_t, Request*> reqs;
   int64_t next_ticket = 1;
   uint64_t tick = 0;
   int64_t submitted = 0, completed = 0, running = 0, epochs = 0;
+  int preparing = 0;  // requests taken by the preparation thread, not yet ready
+  bool blocked = false;  // the queue's head waits for memory held by running or preparing solves
   bool stop = false;
   std::mutex mu;
-  std::condition_variable cv_work, cv_done;
-  std::thread worker;
+  std::condition_variable cv_work, cv_done, cv_prep;
+  std::thread worker, preparer;
 
   // ---- under mu
   int free_slot(int t) const {
@@ -109,133 +127,253 @@ struct ftgcr_server {
       if (!slot_req[t][s]) return s;
     return -1;
   }
-  // An idle handle of the request's shape, preferably one already set up
-  // from the same coefficients.
-  PoolEntry* idle_entry(const Request* r) {
-    PoolEntry* any = nullptr;
+  // An idle handle of the request's shape: with `same`, only one already set
+  // up from the request's coefficients.
+  PoolEntry* idle_entry(const Request* r, bool same) {
     for (PoolEntry& e : pool) {
       if (e.busy || !e.h || !(e.key == r->key)) continue;
-      if (r->ckey && e.setup_key == r->ckey && e.setup_D == r->D) return &e;
-      if (!any) any = &e;
+      if (!same || same_coeffs(e, r)) return &e;
     }
-    return any;
+    return nullptr;
   }
   // Evict idle handles (least recently used first) until `need` more bytes
-  // fit; the evicted handles are destroyed by the caller, outside the lock.
-  bool make_room(int64_t need, std::vector<ftgcr_handle*>& victims) {
+  // fit; the preparation thread destroys the evicted handles.
+  bool make_room(int64_t need) {
     while (in_use + need > budget) {
       auto best = pool.end();
       for (auto it = pool.begin(); it != pool.end(); ++it)
         if (!it->busy && (best == pool.end() || it->last_used < best->last_used)) best = it;
       if (best == pool.end()) return false;
       in_use -= best->bytes;
-      if (best->h) victims.push_back(best->h);
+      if (best->h) doomed.push_back(best->h);
       pool.erase(best);
     }
     return true;
   }
-  void admit(std::vector<Request*>& adm, std::vector<ftgcr_handle*>& victims) {
-    while (!queue.empty() && !stop) {
+  PoolEntry* new_entry(const Request* r) {
+    pool.emplace_back();
+    PoolEntry* e = &pool.back();
+    e->key = r->key;
+    e->bytes = r->footprint;
+    in_use += r->footprint;
+    return e;
+  }
+  void to_ready(Request* r) {
+    auto it = ready.begin();
+    while (it != ready.end() && (*it)->ticket < r->ticket) ++it;
+    ready.insert(it, r);
+  }
+  // Give queued requests handles, first come first served, at most
+  // max_slots of them waiting for a slot or in preparation.  A request whose
+  // coefficients an idle handle already holds is ready at once.  Otherwise a
+  // new handle is made while the budget allows (so the pool grows towards a
+  // handle per coefficient set in use), else an idle handle of the shape is
+  // rebuilt, else idle handles are evicted; preparation runs on its own
+  // thread and stream, so it never holds up a launch.
+  void bind() {
+    while (!queue.empty() && !stop && (int)(ready.size() + preparing) < max_slots) {
       Request* r = queue.front();
-      const int t = table_of(r->key.grid.precision);
-      const int slot = free_slot(t);
-      if (slot < 0) break;
-      PoolEntry* e = idle_entry(r);
+      PoolEntry* e = idle_entry(r, true);
+      bool setup = false;
       if (!e) {
-        if (!make_room(r->footprint, victims)) break;  // wait for running solves to free memory
-        pool.emplace_back();
-        e = &pool.back();
-        e->key = r->key;
-        e->bytes = r->footprint;
-        in_use += r->footprint;
+        setup = true;
+        PoolEntry* any = idle_entry(r, false);
+        if (any && (!r->ckey || in_use + r->footprint > budget)) {
+          e = any;  // rebuilt from the request's coefficients
+        } else {
+          if (!make_room(r->footprint)) {  // wait for running solves to free memory
+            blocked = true;
+            break;
+          }
+          e = new_entry(r);
+        }
       }
       e->busy = true;
       r->entry = e;
+      queue.pop_front();
+      if (setup) {
+        prep.push_back(r);
+        ++preparing;
+      } else {
+        to_ready(r);
+      }
+    }
+    if (!prep.empty() || !doomed.empty()) cv_prep.notify_one();
+  }
+  // Ready requests into free slots, in ticket order.  With max_points, a
+  // table takes no request past the first that would push its running grid
+  // points over the limit (a request alone in its table always runs).
+  void admit(std::vector<Request*>& adm) {
+    bool held[2] = {false, false};
+    for (auto it = ready.begin(); it != ready.end() && !stop;) {
+      Request* r = *it;
+      const int t = table_of(r->key.grid.precision);
+      const int slot = held[t] ? -1 : free_slot(t);
+      if (slot >= 0 && max_points > 0 && run_points[t] > 0 && run_points[t] + points(r) > max_points) {
+        held[t] = true;
+        ++it;
+        continue;
+      }
+      if (slot < 0) {
+        ++it;
+        continue;
+      }
+      run_points[t] += points(r);
       r->table = t;
       r->slot = slot;
       slot_req[t][slot] = r;
-      queue.pop_front();
+      it = ready.erase(it);
       ++running;
       adm.push_back(r);
     }
   }
-  void finish_locked(Request* r, int status) {
-    if (r->slot >= 0) slot_req[r->table][r->slot] = nullptr;
-    if (r->entry) {
-      r->entry->busy = false;
-      r->entry->last_used = ++tick;
-      if (!r->entry->h) {  // creation failed: drop the reservation
-        in_use -= r->entry->bytes;
-        for (auto it = pool.begin(); it != pool.end(); ++it)
-          if (&*it == r->entry) {
-            pool.erase(it);
-            break;
-          }
-      }
-      r->entry = nullptr;
+  void release_entry(Request* r) {
+    if (!r->entry) return;
+    blocked = false;
+    r->entry->busy = false;
+    r->entry->last_used = ++tick;
+    if (!r->entry->h) {  // creation failed or never ran: drop the reservation
+      in_use -= r->entry->bytes;
+      for (auto it = pool.begin(); it != pool.end(); ++it)
+        if (&*it == r->entry) {
+          pool.erase(it);
+          break;
+        }
     }
+    r->entry = nullptr;
+  }
+  void free_slot_of(Request* r) {
+    slot_req[r->table][r->slot] = nullptr;
+    run_points[r->table] -= points(r);
+    r->slot = -1;
+    --running;
+  }
+  void finish_locked(Request* r, int status) {
+    const bool was_running = r->slot >= 0;
+    if (was_running) free_slot_of(r);
+    release_entry(r);
     r->status = status;
     r->done = true;
     finished.push_back(r->ticket);
-    --running;
     ++completed;
   }
 
-  // ---- scheduler thread, outside the lock
-  int start(Request* r) {
-    PoolEntry* e = r->entry;
-    ftgcr_coeffs co{r->D, r->ckey};
-    int rc;
-    if (!e->h) {
-      ftgcr_handle* h = nullptr;
-      rc = ftgcr_create(&r->key.grid, &co, r->key.k, r->key.tol, &h);
-      if (rc) return rc;
+  // ---- preparation thread: handle creation, coefficient rebuilds, eviction
+  void prepare_loop() {
+    cudaSetDevice(dev);
+    for (;;) {
+      Request* r = nullptr;
+      std::vector<ftgcr_handle*> kill;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv_prep.wait(lk, [&] { return stop || !prep.empty() || !doomed.empty(); });
+        kill.swap(doomed);
+        if (!prep.empty() && !stop) {
+          r = prep.front();
+          prep.pop_front();
+        }
+        if (!r && kill.empty()) {
+          if (stop) break;
+          continue;
+        }
+      }
+      for (ftgcr_handle* h : kill) ftgcr_destroy(h);
+      if (!r) continue;
+      PoolEntry* e = r->entry;
+      ftgcr_coeffs co{r->D, r->ckey};
+      int rc = FTGCR_OK;
+      if (!e->h) {
+        ftgcr_handle* h = nullptr;
+        rc = ftgcr_create(&r->key.grid, &co, r->key.k, r->key.tol, &h);
+        if (!rc) {
+          std::lock_guard<std::mutex> lk(mu);
+          e->h = h;
+        }
+      } else {
+        rc = ftgcr_set_coeffs(e->h, &co, pst);
+        if (!rc && cudaStreamSynchronize(pst) != cudaSuccess) rc = FTGCR_ERR_CUDA;
+      }
       std::lock_guard<std::mutex> lk(mu);
-      e->h = h;
-    } else if (!(r->ckey && e->setup_key == r->ckey && e->setup_D == r->D)) {
-      e->setup_key = 0;  // invalid until the rebuild is enqueued
-      rc = ftgcr_set_coeffs(e->h, &co, st);
-      if (rc) return rc;
+      --preparing;
+      if (rc) {
+        e->setup_key = 0;
+        e->setup_D = nullptr;
+        finish_locked(r, rc);
+        cv_done.notify_all();
+      } else {
+        e->setup_D = r->D;
+        e->setup_key = r->ckey;
+        to_ready(r);
+      }
+      cv_work.notify_one();
     }
-    e->setup_D = r->D;
-    e->setup_key = r->ckey;
-    ftgcr_handle* h = e->h;
+  }
+
+  // ---- scheduler thread, outside the lock
+  // Stage host arrays (copy stream) for a request whose handle is set up.
+  int stage(Request* r, const double** R, double** X, int* check) {
+    ftgcr_handle* h = r->entry->h;
     const long long N = handle_points(h);
-    const double* R = r->rhs;
-    double* X = r->x;
+    *R = r->rhs;
+    *X = r->x;
     cudaPointerAttributes at;
-    const bool rdev = cudaPointerGetAttributes(&at, R) == cudaSuccess && at.type == cudaMemoryTypeDevice;
+    const bool rdev = cudaPointerGetAttributes(&at, *R) == cudaSuccess && at.type == cudaMemoryTypeDevice;
     cudaGetLastError();
-    const bool xdev = cudaPointerGetAttributes(&at, X) == cudaSuccess && at.type == cudaMemoryTypeDevice;
+    const bool xdev = cudaPointerGetAttributes(&at, *X) == cudaSuccess && at.type == cudaMemoryTypeDevice;
     cudaGetLastError();
     // host arrays are staged and checked for finite values on the device
     if (!rdev) {
-      if (cudaMemcpyAsync(handle_stage_rhs(h), R, sizeof(double) * N, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      if (cudaMemcpyAsync(handle_stage_rhs(h), *R, sizeof(double) * N, cudaMemcpyHostToDevice, cst) != cudaSuccess)
         return FTGCR_ERR_CUDA;
-      R = handle_stage_rhs(h);
+      *R = handle_stage_rhs(h);
     }
     if (!xdev) {
-      if (cudaMemcpyAsync(handle_stage_x(h), X, sizeof(double) * N, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      if (cudaMemcpyAsync(handle_stage_x(h), *X, sizeof(double) * N, cudaMemcpyHostToDevice, cst) != cudaSuccess)
         return FTGCR_ERR_CUDA;
-      X = handle_stage_x(h);
+      *X = handle_stage_x(h);
     }
     r->x_host = !xdev;
-    ftgcr_fault_plan plan{r->faults.data(), (int32_t)r->faults.size(), r->losses.data(), (int32_t)r->losses.size()};
-    const bool any = !r->faults.empty() || !r->losses.empty();
-    return table_begin(tables[r->table], r->slot, h, R, X, any ? &plan : nullptr, st, (rdev ? 0 : 1) | (xdev ? 0 : 2));
+    *check = (rdev ? 0 : 1) | (xdev ? 0 : 2);
+    return FTGCR_OK;
   }
-  void complete(Request* r) {
+  // Stage every admitted request on the copy stream, make the launch stream
+  // wait for the copies, then begin each solve in its slot.
+  void start_all(const std::vector<Request*>& adm) {
+    std::vector<int> rc(adm.size()), check(adm.size());
+    std::vector<const double*> R(adm.size());
+    std::vector<double*> X(adm.size());
+    for (size_t i = 0; i < adm.size(); ++i) rc[i] = stage(adm[i], &R[i], &X[i], &check[i]);
+    if (!adm.empty() && (cudaEventRecord(staged, cst) != cudaSuccess || cudaStreamWaitEvent(st, staged, 0) != cudaSuccess))
+      for (int& c : rc)
+        if (!c) c = FTGCR_ERR_CUDA;
+    for (size_t i = 0; i < adm.size(); ++i) {
+      Request* r = adm[i];
+      if (!rc[i]) {
+        ftgcr_fault_plan plan{r->faults.data(), (int32_t)r->faults.size(), r->losses.data(),
+                              (int32_t)r->losses.size()};
+        const bool any = !r->faults.empty() || !r->losses.empty();
+        rc[i] = table_begin(tables[r->table], r->slot, r->entry->h, R[i], X[i], any ? &plan : nullptr, st, check[i]);
+      }
+      if (rc[i]) {  // table_begin failed or never ran: the slot is still free
+        std::lock_guard<std::mutex> lk(mu);
+        finish_locked(r, rc[i]);
+        cv_done.notify_all();
+      }
+    }
+  }
+  // Statistics of a finished solve (its launch has completed); a host
+  // solution is copied out on the copy stream, overlapping the next launch.
+  bool take_stats(Request* r, int* status) {
     ftgcr_handle* h = r->entry->h;
-    int status = FTGCR_OK;
-    if (r->x_host &&
-        cudaMemcpy(r->x, handle_stage_x(h), sizeof(double) * handle_points(h), cudaMemcpyDeviceToHost) != cudaSuccess)
-      status = FTGCR_ERR_CUDA;
     ftgcr_stats_t s{};
     const int rc = ftgcr_stats(h, &s);
-    if (!status) status = rc ? rc : s.status;
-    std::lock_guard<std::mutex> lk(mu);
     r->stats = s;
-    finish_locked(r, status);
+    *status = rc ? rc : s.status;
+    if (!r->x_host) return false;
+    if (cudaMemcpyAsync(r->x, handle_stage_x(h), sizeof(double) * handle_points(h), cudaMemcpyDeviceToHost, cst) !=
+        cudaSuccess && !*status)
+      *status = FTGCR_ERR_CUDA;
+    return true;
   }
   void fail_table(int t, int status) {
     std::vector<Request*> lost;
@@ -249,8 +387,10 @@ struct ftgcr_server {
     for (Request* r : lost) finish_locked(r, status);
   }
 
-  // Collect the launches in flight: hand back their finished solves.
-  void collect(bool* inflight, std::vector<int>& fin) {
+  // Collect the launches in flight.  Solves whose solution stays on the
+  // device are handed back at once; the others go to `out` with their
+  // status, to be handed back once their copy has landed.
+  void collect(bool* inflight, std::vector<int>& fin, std::vector<std::pair<Request*, int>>& out) {
     for (int t = 0; t < 2; ++t) {
       if (!inflight[t]) continue;
       inflight[t] = false;
@@ -266,38 +406,56 @@ struct ftgcr_server {
         for (int s = 0; s < max_slots; ++s)
           if (fin[s] && slot_req[t][s]) done.push_back(slot_req[t][s]);
       }
-      for (Request* r : done) complete(r);
-      if (!done.empty()) cv_done.notify_all();
+      bool any = false;
+      for (Request* r : done) {
+        int status = FTGCR_OK;
+        if (take_stats(r, &status)) {
+          std::lock_guard<std::mutex> lk(mu);  // the slot is free; the handle stays busy until the copy lands
+          free_slot_of(r);
+          out.emplace_back(r, status);
+        } else {
+          std::lock_guard<std::mutex> lk(mu);
+          finish_locked(r, status);
+          any = true;
+        }
+      }
+      if (any) cv_done.notify_all();
     }
+  }
+  void hand_back(std::vector<std::pair<Request*, int>>& out) {
+    if (out.empty()) return;
+    const bool ok = cudaStreamSynchronize(cst) == cudaSuccess;
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto& ro : out) finish_locked(ro.first, ok ? ro.second : (ro.second ? ro.second : FTGCR_ERR_CUDA));
+    out.clear();
+    cv_done.notify_all();
   }
 
   // One epoch per iteration, pipelined: while launch e runs on the GPU the
-  // thread admits and prepares new requests (host checks, copies and begin
-  // kernels queued behind launch e), then collects launch e and enqueues
-  // launch e + 1, which the prepared requests join.
+  // thread binds handles, admits ready requests and stages them (copies on
+  // the copy stream, begin kernels queued behind launch e), then collects
+  // launch e, enqueues launch e + 1, which the staged requests join, and
+  // hands back launch e's host solutions while e + 1 runs.
   void loop() {
     cudaSetDevice(dev);
     std::vector<int> fin(max_slots);
+    std::vector<std::pair<Request*, int>> out;
     bool inflight[2] = {false, false};
     for (;;) {
       std::vector<Request*> adm;
-      std::vector<ftgcr_handle*> victims;
       {
         std::unique_lock<std::mutex> lk(mu);
-        if (!inflight[0] && !inflight[1]) cv_work.wait(lk, [&] { return stop || running > 0 || !queue.empty(); });
+        if (!inflight[0] && !inflight[1])
+          cv_work.wait(lk, [&] {
+            return stop || running > 0 || !ready.empty() ||
+                   (!queue.empty() && !blocked && (int)(ready.size() + preparing) < max_slots);
+          });
         if (stop && running == 0) break;
-        admit(adm, victims);
+        bind();
+        admit(adm);
       }
-      for (ftgcr_handle* h : victims) ftgcr_destroy(h);
-      for (Request* r : adm) {
-        const int rc = start(r);
-        if (rc) {  // table_begin failed or never ran: the slot is still free
-          std::lock_guard<std::mutex> lk(mu);
-          finish_locked(r, rc);
-          cv_done.notify_all();
-        }
-      }
-      collect(inflight, fin);
+      start_all(adm);
+      collect(inflight, fin, out);
       for (int t = 0; t < 2; ++t) {
         if (table_occupied(tables[t]) == 0) continue;
         const int rc = table_run(tables[t], epoch_rounds, st);
@@ -310,9 +468,10 @@ struct ftgcr_server {
         std::lock_guard<std::mutex> lk(mu);
         ++epochs;
       }
+      hand_back(out);
     }
+    hand_back(out);
   }
-
 };
 
 extern "C" {
@@ -337,18 +496,26 @@ int ftgcr_server_create(int64_t budget_bytes, int32_t max_slots, int32_t epoch_r
   s->budget = budget_bytes;
   s->max_slots = max_slots;
   s->epoch_rounds = epoch_rounds;
-  int rc = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) == cudaSuccess ? FTGCR_OK : FTGCR_ERR_CUDA;
+  int rc = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) == cudaSuccess &&
+                   cudaStreamCreateWithFlags(&s->cst, cudaStreamNonBlocking) == cudaSuccess &&
+                   cudaStreamCreateWithFlags(&s->pst, cudaStreamNonBlocking) == cudaSuccess &&
+                   cudaEventCreateWithFlags(&s->staged, cudaEventDisableTiming) == cudaSuccess
+               ? FTGCR_OK
+               : FTGCR_ERR_CUDA;
   for (int t = 0; t < 2 && !rc; ++t) {
     rc = table_create(t == 1 ? FTGCR_MIXED : FTGCR_FP64, max_slots, &s->tables[t]);
     s->slot_req[t].assign(max_slots, nullptr);
   }
   if (rc) {
     for (SlotTable* t : s->tables) table_destroy(t);
-    if (s->st) cudaStreamDestroy(s->st);
+    for (cudaStream_t q : {s->st, s->cst, s->pst})
+      if (q) cudaStreamDestroy(q);
+    if (s->staged) cudaEventDestroy(s->staged);
     delete s;
     return rc;
   }
   s->worker = std::thread([s] { s->loop(); });
+  s->preparer = std::thread([s] { s->prepare_loop(); });
   *out = s;
   return FTGCR_OK;
 }
@@ -466,12 +633,20 @@ int ftgcr_server_next(ftgcr_server* srv, double timeout_s, int64_t* ticket, ftgc
   return take_result(srv, srv->reqs.find(*ticket), stats);
 }
 
+int ftgcr_server_set_max_points(ftgcr_server* srv, int64_t max_points) {
+  if (!srv || max_points < 0) return FTGCR_ERR_ARG;
+  std::lock_guard<std::mutex> lk(srv->mu);
+  srv->max_points = max_points;
+  srv->cv_work.notify_one();
+  return FTGCR_OK;
+}
+
 int ftgcr_server_info(ftgcr_server* srv, ftgcr_server_info_t* out) {
   if (!srv || !out) return FTGCR_ERR_ARG;
   std::lock_guard<std::mutex> lk(srv->mu);
   out->submitted = srv->submitted;
   out->completed = srv->completed;
-  out->queued = (int64_t)srv->queue.size();
+  out->queued = (int64_t)(srv->queue.size() + srv->ready.size()) + srv->preparing;
   out->running = srv->running;
   out->epochs = srv->epochs;
   out->handles = (int64_t)srv->pool.size();
@@ -491,13 +666,20 @@ int ftgcr_server_destroy(ftgcr_server* srv) {
     }
     srv->queue.clear();
     srv->cv_work.notify_all();
+    srv->cv_prep.notify_all();
     srv->cv_done.notify_all();
   }
-  if (srv->worker.joinable()) srv->worker.join();  // running solves finish first
+  if (srv->preparer.joinable()) srv->preparer.join();  // ends after the preparation in progress
+  if (srv->worker.joinable()) srv->worker.join();      // running solves finish first
+  for (Request* r : srv->prep) r->done = true, r->status = FTGCR_ERR_STATE;  // never started
+  for (Request* r : srv->ready) r->done = true, r->status = FTGCR_ERR_STATE;
+  for (ftgcr_handle* h : srv->doomed) ftgcr_destroy(h);
   for (PoolEntry& e : srv->pool)
     if (e.h) ftgcr_destroy(e.h);
   for (SlotTable* t : srv->tables) table_destroy(t);
-  if (srv->st) cudaStreamDestroy(srv->st);
+  for (cudaStream_t q : {srv->st, srv->cst, srv->pst})
+    if (q) cudaStreamDestroy(q);
+  if (srv->staged) cudaEventDestroy(srv->staged);
   for (auto& kv : srv->reqs) delete kv.second;
   delete srv;
   return FTGCR_OK;

@@ -1,21 +1,26 @@
 // Streamed step rounds of the mixed path (FP32 inner vectors), for solves
 // whose vectors live in HBM.
 //
-// A streamed solve gives each CTA one tall band of latitude rows and walks the
-// band row by row.  For row j, the step's axpy (with the previous step's
-// direction recurrences fused in, as in the PF round) reads its operand rows
-// through a ring of shared-memory slots.  Thread 0 fills the slots ahead of
-// the consumers with bulk asynchronous copies (cp.async.bulk, one mbarrier per
-// slot), so up to the ring's size of HBM traffic is in flight per SM without
-// holding registers.  r' lands in a row buffer; the row's zonal line solve
-// (all eight warps on the one row) turns it into e, which is written out and
-// kept: three e rows stay in shared memory, so once e of row j exists the
-// stencil L(e) of row j-1 and its dots stream their own operands (face
-// coefficients, r', the L(p^l)) through the same ring.  Only the band's first
-// and last rows need an e row of a neighbouring band; their stencils run in a
-// second pass after a grid barrier.  No row is recomputed as halo and e is not
-// read back, so a step moves about its algorithmic bytes (the line solve's
-// factors, three rows per row, come on top).
+// A streamed solve gives each CTA one tall band of latitude rows (at most 64)
+// and walks the band row by row.  For row j, the step's axpy (with the
+// previous step's direction recurrences fused in, as in the PF round) reads
+// its operand rows in chunks of 1024 columns through a ring of two or three
+// shared-memory stage buffers: every thread copies its own four columns of
+// each operand row with 16-byte cp.async, one or two stages ahead of the
+// arithmetic, and later reads exactly those, so HBM traffic stays in flight
+// without holding registers and a stage needs no barrier of its own.  r'
+// lands in a row buffer; the row's zonal line solve (all eight warps on the
+// one row, each lane on a contiguous piece; its constants arrive by bulk
+// copies on an mbarrier while the axpy runs) turns it into e, which is
+// written out and kept: three e rows stay in shared memory, so once e of row
+// j exists the stencil L(e) of row j-1 and its dots stream their own operands
+// (face coefficients, r', the L(p^l)) through the same ring.  Only the band's
+// first and last rows need an e row of a neighbouring band; their stencils
+// run in a second pass after a grid barrier.  No row is recomputed as halo
+// and e is read back only at band edges, so a step moves about its
+// algorithmic bytes (the line solve's constants, three rows per row, come on
+// top).  Rows in shared memory are piece-major: lane l's C-element piece of
+// the row is contiguous, padded to a pitch of C + 4 floats.
 //
 // Every wait on an mbarrier is bounded; a wait that runs out raises the
 // launch's error flag, waits (bounded) for the copies still in flight, and the

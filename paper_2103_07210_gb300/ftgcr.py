@@ -44,7 +44,8 @@ EXPORTS = ["ftgcr_create", "ftgcr_solve", "ftgcr_solve_async", "ftgcr_stats", "f
            "ftgcr_apply_operator", "ftgcr_apply_precond", "ftgcr_footprint", "ftgcr_destroy", "ftgcr_error_string",
            "ftgcr_solve_noalloc", "ftgcr_set_coeffs", "ftgcr_server_create", "ftgcr_server_submit",
            "ftgcr_server_poll", "ftgcr_server_wait", "ftgcr_server_next", "ftgcr_server_info",
-           "ftgcr_server_destroy", "ftgcr_tune", "ftgcr_fp64_fma_rate", "ftgcr_solve_host_async"]
+           "ftgcr_server_destroy", "ftgcr_server_set_max_points", "ftgcr_tune", "ftgcr_fp64_fma_rate",
+           "ftgcr_solve_host_async"]
 NOALLOC_MAX_POINTS, NOALLOC_MAX_K = 16384, 4
 TUNE_MAX_CONCURRENCY = 256
 
@@ -174,6 +175,7 @@ def lib():
         L.ftgcr_server_next.argtypes = [vp, dbl, ctypes.POINTER(i64), ctypes.POINTER(Stats)]
         L.ftgcr_server_info.argtypes = [vp, ctypes.POINTER(ServerInfo)]
         L.ftgcr_server_destroy.argtypes = [vp]
+        L.ftgcr_server_set_max_points.argtypes = [vp, i64]
         L.ftgcr_fp64_fma_rate.argtypes = [i32, ctypes.POINTER(dbl), vp]
         for f in EXPORTS:
             if not hasattr(L, f):
@@ -513,6 +515,13 @@ class Server:
             raise FTGCRError(st, "no request outstanding")
         self._keep.pop(t.value, None)
         return t.value, st, _stats_dict(s)
+
+    def set_max_points(self, max_points: int):
+        """Admission limit on the grid points running at once per precision
+        (0: none); see ftgcr_server_set_max_points."""
+        st = lib().ftgcr_server_set_max_points(self.srv, int(max_points))
+        if st != OK:
+            raise FTGCRError(st, "ftgcr_server_set_max_points")
 
     def info(self) -> dict:
         i = ServerInfo()

@@ -190,3 +190,60 @@ def test_non_finite_host_inputs_complete_with_an_argument_error():
     assert st_inf == ftgcr.ERR_ARG
     xa, sa = _alone(p, "fp64", (), 4, ss["tiles"])
     assert st_ok == ftgcr.OK and np.array_equal(x_ok, xa) and ss["steps"] == sa["steps"]
+
+
+def test_max_points_limits_the_running_solves_and_keeps_results():
+    """With a limit of one 256x128 grid per table, at most one mixed solve
+    runs at a time (a larger request runs alone), FP64 solves are limited
+    separately, and every result is still the solo result."""
+    shapes = [(256, 128, "mixed"), (256, 128, "mixed"), (512, 256, "mixed"), (256, 128, "fp64"), (256, 128, "mixed"),
+              (128, 64, "fp64"), (256, 128, "mixed")]
+    probs = [(inputs.hill_problem(n, m, **inputs.random_hill(300 + q)), prec) for q, (n, m, prec) in enumerate(shapes)]
+    with ftgcr.Server(max_slots=8, epoch_rounds=6) as srv:
+        srv.set_max_points(256 * 128)
+        Rs = [torch.from_numpy(p.R).cuda() for p, _ in probs]
+        xs = [torch.zeros_like(R) for R in Rs]
+        ts = [srv.submit(torch.from_numpy(p.D).cuda(), p.mu, R, x, precision=prec)
+              for (p, prec), R, x in zip(probs, Rs, xs)]
+        peak = 0
+        while srv.info()["completed"] < len(ts):
+            peak = max(peak, srv.info()["running"])
+            time.sleep(0.0002)
+        res = [srv.wait(t, timeout=60) for t in ts]
+    assert peak <= 2  # one per precision table
+    assert all(r[0] == ftgcr.OK for r in res)
+    for (p, prec), x, (st, ss) in zip(probs, xs, res):
+        xa, sa = _alone(p, prec, (), 4, ss["tiles"])
+        assert np.array_equal(x.cpu().numpy(), xa) and ss["steps"] == sa["steps"]
+    with ftgcr.Server() as srv:
+        with pytest.raises(ftgcr.FTGCRError):
+            srv.set_max_points(-1)
+
+
+def test_requests_whose_handles_are_prepared_beside_a_running_launch_match_solo():
+    """Requests of one shape with eight different coefficient keys, submitted
+    while a long solve runs: handles are created or rebuilt beside the
+    running launch, and every result is the solo result."""
+    big = inputs.hill_problem(1024, 512, **inputs.random_hill(400))
+    probs = [inputs.hill_problem(256, 128, **inputs.random_hill(410 + q)) for q in range(8)]
+    with ftgcr.Server(max_slots=16, epoch_rounds=4) as srv:
+        Rb = torch.from_numpy(big.R).cuda()
+        xb = torch.zeros_like(Rb)
+        tb = srv.submit(torch.from_numpy(big.D).cuda(), big.mu, Rb, xb, precision="mixed", coeff_key=1)
+        Ds = [torch.from_numpy(p.D).cuda() for p in probs]
+        Rs = [torch.from_numpy(p.R).pin_memory() for p in probs]
+        xs = [torch.zeros(p.R.shape, dtype=torch.float64).pin_memory() for p in probs]
+        ts = [srv.submit(D, p.mu, R, x, precision="mixed", coeff_key=10 + q)
+              for q, (p, D, R, x) in enumerate(zip(probs, Ds, Rs, xs))]
+        # the same keys again: pooled handles already set up from them
+        xs2 = [torch.zeros(p.R.shape, dtype=torch.float64).pin_memory() for p in probs]
+        ts2 = [srv.submit(D, p.mu, R, x, precision="mixed", coeff_key=10 + q)
+               for q, (p, D, R, x) in enumerate(zip(probs, Ds, Rs, xs2))]
+        res = [srv.wait(t, timeout=60) for t in ts + ts2]
+        rb = srv.wait(tb, timeout=60)
+    assert rb[0] == ftgcr.OK and all(r[0] == ftgcr.OK for r in res)
+    xa, _ = _alone(big, "mixed", (), 4, rb[1]["tiles"])
+    assert np.array_equal(xb.cpu().numpy(), xa)
+    for q, p in enumerate(probs):
+        xa, sa = _alone(p, "mixed", (), 4, res[q][1]["tiles"])
+        assert np.array_equal(xs[q].numpy(), xa) and np.array_equal(xs2[q].numpy(), xa)

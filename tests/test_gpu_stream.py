@@ -1,7 +1,7 @@
 """Streamed step rounds (FTGCR_FLAG_STREAMED_ROUNDS): every CTA walks one
-tall band row by row, its operand rows brought into shared memory by bulk
-asynchronous copies, and the band's edge rows take their stencil in a second
-pass.  Forced here on grids the oracle solves in seconds: one-row and
+tall band row by row, its operand rows staged into shared memory by
+per-thread asynchronous copies, and the band's edge rows take their stencil in
+a second pass.  Forced here on grids the oracle solves in seconds: one-row and
 multi-row bands, rows of one, two and a ragged second chunk of columns,
 k = 1..8, flips of every vector, data-loss events, and batches that mix
 streamed solves with solves of the other layouts.  Every solution matches the
