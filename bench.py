@@ -44,9 +44,9 @@ def algorithmic_bytes(steps: int, outer: int, k: int = K, s: int = 4, N: int = N
 
 # DRAM traffic per launch of the persistent kernel from one ncu capture, valid
 # only for the kernel sources it was taken on (sha256 of the CUDA sources).
-NCU_TRAFFIC = {"sources_sha256": "05b57144247d3bd16ee8e1a3c72bc95b37c1d0bcc25e8f9f1c527d6f44be1717",
-               "bytes_per_launch": 28516352 + 8707072,  # mixed 1024x512 (read + write)
-               "large": {"2048x1024": 2705236992 + 1349571840, "4096x2048": 15129706496 + 5213779200}}
+NCU_TRAFFIC = {"sources_sha256": "0216fc33ca446b7f65a2151501db1e17a31ba09bec2eadc5aa5962b931169294",
+               "bytes_per_launch": 27851008 + 7156992,  # mixed 1024x512 (read + write)
+               "large": {"2048x1024": 2677366528 + 1348097024, "4096x2048": 12607077632 + 5222849536}}
 
 
 def sources_hash() -> str:
@@ -56,7 +56,7 @@ def sources_hash() -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2103_07210_gb300", "csrc")
     for f in sorted(os.listdir(d)):
-        if f in ("ftgcr_device.cuh", "ftgcr_phases.cuh", "ftgcr_instances.h") or \
+        if f in ("ftgcr_device.cuh", "ftgcr_phases.cuh", "ftgcr_stream.cuh", "ftgcr_instances.h") or \
                 (f.startswith("ftgcr_k") and f.endswith(".cu")):
             h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()

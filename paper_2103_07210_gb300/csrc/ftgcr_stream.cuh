@@ -425,13 +425,13 @@ struct StRegs {
 
 // Sub-stage `sub` of a stencil chunk of row `row`: (sub-stage 0) L(e) from the
 // three e rows in shared memory (eC the row, eN north, eS south), written
-// out, <r', L(e)> and <L(e), L(e)>; (every sub-stage) the dots <L(e), L(p^l)>
-// of its operand rows.  The operations of the stencil step of the other
+// out, <r', L(e)> and <L(e), L(e)>, and e of the row written to eout unless
+// it is null; (every sub-stage) the dots <L(e), L(p^l)> of its operand rows.  The operations of the stencil step of the other
 // round layouts.
 template <int KB>
 __device__ __forceinline__ void stream_st(int n, int nlat, int lcb, int P, unsigned buf, unsigned lead, int row,
                                           int ch, int sub, int nv, unsigned eC, unsigned eN, unsigned eS, float muA,
-                                          StRegs& x, Acc<float>* ad, Acc<float>& ah, Acc<float>& aq) {
+                                          StRegs& x, Acc<float>* ad, Acc<float>& ah, Acc<float>& aq, float* eout) {
   const int c0 = ch * kCW, i4 = 4 * (int)threadIdx.x;
   const int v0 = sub * kNVS, v1 = min(nv, v0 + kNVS);
   const bool act = c0 + i4 < n;
@@ -453,6 +453,7 @@ __device__ __forceinline__ void stream_st(int n, int nlat, int lcb, int P, unsig
     const int i = c0 + i4;
     const unsigned o = 4u * (unsigned)pk(i, lcb, P);
     const V16<float> ec = lds4(eC + o);
+    if (eout) stv(eout + (long long)row * n + i, ec);
     V16<float> en, es;
     if (hasN) en = lds4(eN + o);
     if (hasS) es = lds4(eS + o);
@@ -658,9 +659,10 @@ __device__ __noinline__ void phase_stream(const SolveDev<float>& sd, const Ctx<f
         eC = smem_addr(ebuf + stride);
         eN = smem_addr(ebuf + 2 * stride);
       }
-    } else {
-      __syncthreads();  // the stencils before have read this row buffer's e
     }
+    // An axpy row needs no barrier here: it writes r' only at this thread's
+    // columns of the buffer, whose last reader (the stencil two rows back, its
+    // south row) read only this thread's columns.
     float* rowbuf = ebuf + (row % 3) * stride;
     const unsigned rb = smem_addr(rowbuf);
     const float muA = g_ss.muA[row - j0];
@@ -678,7 +680,7 @@ __device__ __noinline__ void phase_stream(const SolveDev<float>& sd, const Ctx<f
           stream_ax<FUSED>(n, lcb, P, ps, buf, row, ch, sb, nv, rb, xa, an);
         else
           stream_st<KB>(n, nlat, lcb, P, buf, lead_s + 128u * (unsigned)b, row, ch, sb, nv, eC, eN, eS, muA, xs, ad,
-                        ah, aq);
+                        ah, aq, pass == 0 ? c.eW : nullptr);
         ++cidx;
       }
     }
@@ -723,8 +725,8 @@ __device__ __noinline__ void phase_stream(const SolveDev<float>& sd, const Ctx<f
       __syncthreads();
       apply_losses_piece(sd, c.t, row, rowbuf, lcb, P);
     }
-    __syncthreads();
-    store_piece_row(c.eW, row, n, lcb, P, rb);
+    if (ps.nfl || sd.nlosses) __syncthreads();  // thread 0's flips before any reader
+    if (!interior(row)) store_piece_row(c.eW, row, n, lcb, P, rb);  // else stored by its stencil
   }
   cp_async_wait_all();  // the groups still open are empty unless the pass failed
   if (fail) {
