@@ -497,9 +497,9 @@ constexpr int kChunkMinLon = 256;  // FP64 path: the chunked row solve from this
 // scan composes the maps into each chunk's carry-in, and a second pass
 // replays the chunk from its exact carry-in.  The periodic coupling of the
 // last unknown is eliminated by bordering with the precomputed
-// z = A0^-1 (-Tx_{n-1} e_0 - Tx_{n-2} e_{n-2}).  row and the constants must be
-// in shared memory.
-template <typename T>
+// z = A0^-1 (-Tx_{n-1} e_0 - Tx_{n-2} e_{n-2}).  row must be in shared
+// memory; the constants too, or (GC) in global memory in the same layout.
+template <typename T, bool GC = false>
 __device__ __noinline__ void line_solve_row(const SolveDev<T>& sd, int j, T* row_, const LineConsts<T> lc) {
   const int lane = threadIdx.x & 31;
   const int n = sd.nlon, m = n - 1, C = sd.C;
@@ -516,6 +516,10 @@ __device__ __noinline__ void line_solve_row(const SolveDev<T>& sd, int j, T* row
   auto Cb = [&](int k) { return cbb + E * (unsigned)(k * 32 + lane); };
   auto Cw = [&](int k) { return cwb + E * (unsigned)(k * 32 + lane); };
   auto Cz = [&](int k) { return czb + E * (unsigned)(k * 32 + lane); };
+  // the constants: shared memory, or (GC) global memory in the same layout
+  auto cB = [&](int k) { return GC ? __ldg(lc.cb + k * 32 + lane) : lds<T>(Cb(k)); };
+  auto cW = [&](int k) { return GC ? __ldg(lc.cw + k * 32 + lane) : lds<T>(Cw(k)); };
+  auto cZ = [&](int k) { return GC ? __ldg(lc.cz + k * 32 + lane) : lds<T>(Cz(k)); };
   // b_{n-1}, read before the passes: its slot may lie in the last lane's chunk
   const T bl = -lds<T>(R(n - 1));
   // positions past the row hold no data: make them finite (their factors are zero)
@@ -524,7 +528,7 @@ __device__ __noinline__ void line_solve_row(const SolveDev<T>& sd, int j, T* row
       if (i0 + k >= n) sts(R(i0 + k), T(0));
   __syncwarp();
   // forward multiplier of chunk element 0 is c_{i0-1}, the last c of the previous lane
-  const T mylast = lds<T>(Cb(C - 1));
+  const T mylast = cB(C - 1);
   T a0 = __shfl_up_sync(0xffffffffu, mylast, 1);
   if (lane == 0) a0 = T(0);
   // pass 1: affine map g_out = F g_in + G of the chunk
@@ -536,7 +540,7 @@ __device__ __noinline__ void line_solve_row(const SolveDev<T>& sd, int j, T* row
 #pragma unroll
       for (int q = 0; q < kLB; ++q) {
         rv[q] = lds<T>(R(i0 + kb + q));
-        cv[q] = lds<T>(Cb(kb + q));
+        cv[q] = cB(kb + q);
       }
 #pragma unroll
       for (int q = 0; q < kLB; ++q) {
@@ -566,7 +570,7 @@ __device__ __noinline__ void line_solve_row(const SolveDev<T>& sd, int j, T* row
 #pragma unroll
       for (int q = 0; q < kLB; ++q) {
         rv[q] = lds<T>(R(i0 + kb + q));
-        cv[q] = lds<T>(Cb(kb + q));
+        cv[q] = cB(kb + q);
       }
 #pragma unroll
       for (int q = 0; q < kLB; ++q) {
@@ -587,8 +591,8 @@ __device__ __noinline__ void line_solve_row(const SolveDev<T>& sd, int j, T* row
 #pragma unroll
     for (int q = 0; q < kLB; ++q) {
       gv[q] = lds<T>(R(i0 + kb + q));
-      cv[q] = lds<T>(Cb(kb + q));
-      wv[q] = lds<T>(Cw(kb + q));
+      cv[q] = cB(kb + q);
+      wv[q] = cW(kb + q);
     }
 #pragma unroll
     for (int q = kLB - 1; q >= 0; --q) {
@@ -616,8 +620,8 @@ __device__ __noinline__ void line_solve_row(const SolveDev<T>& sd, int j, T* row
 #pragma unroll
       for (int q = 0; q < kLB; ++q) {
         gv[q] = lds<T>(R(i0 + kb + q));
-        cv[q] = lds<T>(Cb(kb + q));
-        wv[q] = lds<T>(Cw(kb + q));
+        cv[q] = cB(kb + q);
+        wv[q] = cW(kb + q);
       }
 #pragma unroll
       for (int q = kLB - 1; q >= 0; --q) {
@@ -636,7 +640,7 @@ __device__ __noinline__ void line_solve_row(const SolveDev<T>& sd, int j, T* row
   const T xl = tfma(lr2, ym, tfma(lr1, y0, bl * lr0));
   __syncwarp();
 #pragma unroll 8
-  for (int k = 0; k < len; ++k) sts(R(i0 + k), tfma(-xl, lds<T>(Cz(k)), lds<T>(R(i0 + k))));
+  for (int k = 0; k < len; ++k) sts(R(i0 + k), tfma(-xl, cZ(k), lds<T>(R(i0 + k))));
   __syncwarp();
   if (lane == 0) sts(R(n - 1), xl);
   __syncwarp();

@@ -693,12 +693,28 @@ __device__ __forceinline__ LineConsts<T> staged_consts(const SolveDev<T>& sd, co
 
 // The FP64 line solve of a tile whose factors stay in global memory (wide
 // rows): the same steps as the staged form in precond_tile, with the tile's
-// factor rows first asked of L2.  ring: kRingStride doubles of shared memory
+// factor rows first asked of L2 (rows of 256+ columns: the chunked solve,
+// one warp per row, reading the chunk-layout factors from global memory).  ring: kRingStride doubles of shared memory
 // per row for the chains' factor rings.  Its own function, so that the staged
 // form's code is the same as without it.
 static __device__ __noinline__ void precond_tile_gl(const SolveDev<double>& sd, int h0, int nrows, double* sm,
                                                     int stride, double* ring) {
   const int n = sd.nlon, m = n - 1;
+  if (sd.lchunk) {
+    // rows of 256+ columns: the chunked solve, one warp per row, its factors
+    // read from global memory in the chunk layout (first asked of L2)
+    const long long per = 32LL * sd.C, b0 = (long long)h0 * per, l0 = (long long)nrows * per;
+    for (long long q = 16LL * threadIdx.x; q < l0; q += 16LL * kThreads) {
+      prefetch_l2(sd.lcc + b0 + q);
+      prefetch_l2(sd.lwc + b0 + q);
+      prefetch_l2(sd.lzc + b0 + q);
+    }
+    for (int jr = threadIdx.x >> 5; jr < nrows; jr += kWarps)
+      line_solve_row<double, true>(sd, h0 + jr, sm + jr * stride,
+                                   LineConsts<double>{sd.lcc + b0 + jr * per, sd.lwc + b0 + jr * per,
+                                                      sd.lzc + b0 + jr * per});
+    return;
+  }
   const long long base = (long long)h0 * n, len = (long long)nrows * n;
   for (long long q = 16LL * threadIdx.x; q < len; q += 16LL * kThreads) {  // 128-byte lines
     prefetch_l2(sd.lc + base + q);
@@ -757,8 +773,9 @@ static __device__ __noinline__ void precond_tile_gl(const SolveDev<double>& sd, 
 }
 
 // The preconditioner on the nrows rows of a tile staged in shared memory.
-// FP32 line solve and the pointwise preconditioners: one warp per row.  FP64
-// line solve: one lane per row, the rows side by side in the first warp(s).
+// FP32 line solve, FP64 line solve on rows of 256+ columns and the pointwise
+// preconditioners: one warp per row.  FP64 line solve on narrower rows: one
+// lane per row, the rows side by side in the first warp(s).
 // Each row's solve is the oracle's serial elimination, a chain of dependent
 // FP64 operations, and GB300 issues an FP64 warp instruction at the same cost
 // whatever the number of active lanes (measured: 64 cycles per dependent FMA
