@@ -44,9 +44,9 @@ def algorithmic_bytes(steps: int, outer: int, k: int = K, s: int = 4, N: int = N
 
 # DRAM traffic per launch of the persistent kernel from one ncu capture, valid
 # only for the kernel sources it was taken on (sha256 of the CUDA sources).
-NCU_TRAFFIC = {"sources_sha256": "0216fc33ca446b7f65a2151501db1e17a31ba09bec2eadc5aa5962b931169294",
-               "bytes_per_launch": 27851008 + 7156992,  # mixed 1024x512 (read + write)
-               "large": {"2048x1024": 2677366528 + 1348097024, "4096x2048": 12607077632 + 5222849536}}
+NCU_TRAFFIC = {"sources_sha256": "429f513e358b66c7802e997146097f40ca463c3ab4b69082e793e4c821eba683",
+               "bytes_per_launch": 27847424 + 6946304,  # mixed 1024x512 (read + write)
+               "large": {"2048x1024": 2676232192 + 1348171520, "4096x2048": 12606965248 + 5222618624}}
 
 
 def sources_hash() -> str:
