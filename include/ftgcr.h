@@ -110,13 +110,24 @@ typedef struct {
  * default for solves of at least 4 Mi points (their Krylov vectors far
  * outgrow the L2 cache).  Each CTA takes one tall band of rows (one band per
  * SM) and walks it row by row: the step's axpy, the row's line solve and the
- * stencil of the row below it, with every operand row brought into shared
- * memory by bulk asynchronous copies issued ahead of the arithmetic.  Only a
+ * stencil of the row below it, with every operand row staged into shared
+ * memory by asynchronous copies issued ahead of the arithmetic.  Only a
  * band's first and last rows wait for a neighbouring band's e, in a second
  * pass.  Needs nlon a multiple of 4; with FTGCR_FLAG_SPLIT_ROUNDS or
  * FTGCR_FLAG_FUSED_ROUNDS, another precision or preconditioner, or rows too
  * wide for the ring of shared-memory slots a step needs: FTGCR_ERR_ARG. */
 #define FTGCR_FLAG_STREAMED_ROUNDS 8
+/* FTGCR_FP64 with the line preconditioner: solve every latitude row in the
+ * oracle's operation order (Thomas elimination, one lane per row) at every
+ * row width.  By default rows of 256 or more columns take a chunked scan
+ * (one warp per row, 32 chunks joined by their exact affine maps), which is
+ * the same elimination rounded differently: the fault decisions of
+ * Algorithm 1 stay the oracle's, but in long, slowly converging solves (the
+ * singular mu = 0 problem, hundreds of steps) the exit can come some steps
+ * earlier or later.  With this flag the preconditioned vectors are bitwise
+ * the oracle's at every width, at the cost of the serial chains on wide rows.
+ * Another precision or preconditioner: FTGCR_ERR_ARG. */
+#define FTGCR_FLAG_ORACLE_ORDER 16
 
 typedef struct {
   const double* D;   /* [nlat][nlon] cell-centred coefficient (column depth 1 - h), > 0 */

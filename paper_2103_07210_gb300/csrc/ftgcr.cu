@@ -895,7 +895,10 @@ size_t layout(ftgcr_handle* h, unsigned char* base, SolveDev<T>* sd) {
   sd->lu = (const T*)(fp64 && h->precond == FTGCR_PRECOND_LINE ? take(sizeof(T) * lcn) : nullptr);
   sd->lrow = (const T*)take(sizeof(T) * 4 * nlat);
   // FP64 chunked row solves: the factors again in the chunk layout
-  const bool chunk = fp64 && h->precond == FTGCR_PRECOND_LINE && h->nlon >= kChunkMinLon && !h->noalloc;
+  // (not with FTGCR_FLAG_ORACLE_ORDER: the oracle's serial order on every row;
+  // the shared-memory plan was sized for the larger chunk layout)
+  const bool chunk = fp64 && h->precond == FTGCR_PRECOND_LINE && h->nlon >= kChunkMinLon && !h->noalloc &&
+                     !(h->flags & FTGCR_FLAG_ORACLE_ORDER);
   sd->lchunk = chunk ? 1 : 0;
   sd->lcc = chunk ? (const T*)take(sizeof(T) * 32 * (size_t)C * nlat) : sd->lc;
   sd->lwc = chunk ? (const T*)take(sizeof(T) * 32 * (size_t)C * nlat) : sd->lw;
@@ -1389,7 +1392,9 @@ static int check_grid(const ftgcr_grid* g, int32_t k, double tol) {
   if (g->max_steps < 0 || g->tiles < 0 || g->max_outer < 0 || !(g->inner_tol >= 0.0) || g->inner_tol >= 1.0)
     return FTGCR_ERR_ARG;
   constexpr int layouts = FTGCR_FLAG_SPLIT_ROUNDS | FTGCR_FLAG_FUSED_ROUNDS | FTGCR_FLAG_STREAMED_ROUNDS;
-  if (g->flags & ~(FTGCR_FLAG_UNPROTECTED | layouts)) return FTGCR_ERR_ARG;
+  if (g->flags & ~(FTGCR_FLAG_UNPROTECTED | FTGCR_FLAG_ORACLE_ORDER | layouts)) return FTGCR_ERR_ARG;
+  if ((g->flags & FTGCR_FLAG_ORACLE_ORDER) && (g->precision != FTGCR_FP64 || g->precond != FTGCR_PRECOND_LINE))
+    return FTGCR_ERR_ARG;
   const int lf = g->flags & layouts;
   if (lf & (lf - 1)) return FTGCR_ERR_ARG;  // at most one layout
   if ((g->flags & (FTGCR_FLAG_SPLIT_ROUNDS | FTGCR_FLAG_STREAMED_ROUNDS)) &&

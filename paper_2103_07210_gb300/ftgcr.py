@@ -34,7 +34,7 @@ FP64, MIXED = 0, 1
 PRECOND = {"line": 0, "jacobi": 1, "identity": 2}
 VEC = {"x": 0, "r": 1, "p": 2, "ap": 3, "e": 4}
 MAX_FAULTS, MAX_K, MAX_DETECT, MAX_LOSSES = 64, 16, 16, 16
-FLAG_UNPROTECTED, FLAG_SPLIT_ROUNDS, FLAG_FUSED_ROUNDS, FLAG_STREAMED_ROUNDS = 1, 2, 4, 8
+FLAG_UNPROTECTED, FLAG_SPLIT_ROUNDS, FLAG_FUSED_ROUNDS, FLAG_STREAMED_ROUNDS, FLAG_ORACLE_ORDER = 1, 2, 4, 8, 16
 
 OK, NOT_CONVERGED, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BUDGET, ERR_STATE = 0, 1, -1, -2, -3, -4, -5, -6
 PENDING = 2
@@ -233,10 +233,11 @@ def _plan(faults, losses=()):
 ROUNDS = {"auto": 0, "split": FLAG_SPLIT_ROUNDS, "fused": FLAG_FUSED_ROUNDS, "streamed": FLAG_STREAMED_ROUNDS}
 
 
-def _grid(nlon, nlat, mu, precision, precond, max_steps, tiles, inner_tol, max_outer, protect=True, rounds="auto"):
+def _grid(nlon, nlat, mu, precision, precond, max_steps, tiles, inner_tol, max_outer, protect=True, rounds="auto",
+          oracle_order=False):
     prec = {"fp64": FP64, "mixed": MIXED}.get(precision, precision)
     pc = PRECOND.get(precond, precond)
-    flags = (0 if protect else FLAG_UNPROTECTED) | ROUNDS[rounds]
+    flags = (0 if protect else FLAG_UNPROTECTED) | ROUNDS[rounds] | (FLAG_ORACLE_ORDER if oracle_order else 0)
     return Grid(int(nlon), int(nlat), float(mu), int(prec), int(pc), int(max_steps), int(tiles), float(inner_tol),
                 int(max_outer), flags)
 
@@ -250,16 +251,18 @@ class Solver:
     """One FT-GCR(k) problem resident on the GPU (ftgcr_create)."""
 
     def __init__(self, D, mu, k=4, tol=1e-10, precision="fp64", precond="line", max_steps=0, tiles=0,
-                 inner_tol=0.0, max_outer=0, protect=True, rounds="auto"):
+                 inner_tol=0.0, max_outer=0, protect=True, rounds="auto", oracle_order=False):
         """protect=False: plain GCR(k), the paper's unprotected baseline (no
         fault test, no restore).  rounds: "auto", "split", "fused" or
         "streamed" (FTGCR_FLAG_SPLIT_ROUNDS / FTGCR_FLAG_FUSED_ROUNDS /
-        FTGCR_FLAG_STREAMED_ROUNDS)."""
+        FTGCR_FLAG_STREAMED_ROUNDS).  oracle_order (FP64, line
+        preconditioner): FTGCR_FLAG_ORACLE_ORDER."""
         L = lib()
         nlat, nlon = D.shape
         self.nlon, self.nlat, self.k, self.tol = int(nlon), int(nlat), int(k), float(tol)
         self.precision = precision
-        g = _grid(nlon, nlat, mu, precision, precond, max_steps, tiles, inner_tol, max_outer, protect, rounds)
+        g = _grid(nlon, nlat, mu, precision, precond, max_steps, tiles, inner_tol, max_outer, protect, rounds,
+                  oracle_order)
         dp, keep = _ptr(D)
         c = Coeffs(dp, 0)
         h = ctypes.c_void_p()

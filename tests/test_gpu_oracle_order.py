@@ -1,0 +1,74 @@
+"""Long, slowly converging FP64 solves on rows of 256+ columns: the singular
+mu = 0 hill problem (Section 3's pure Poisson form) takes hundreds of steps.
+
+- With FTGCR_FLAG_ORACLE_ORDER every row is solved in the oracle's operation
+  order, and the solve takes the oracle's decisions exactly: the same step
+  count, no detections, the same solution (rel <= 1e-10, bitwise in practice).
+- By default such rows take the chunked scan, the same elimination rounded
+  differently: the solution still matches the oracle to 1e-10 and nothing is
+  detected, but the exit may come a few percent of the steps earlier or later
+  (measured: 484 against 470 steps for k = 6 at 256 x 128).
+- Fault decisions under single flips stay the oracle's in either mode."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_07210_gb300 import ftgcr, inputs
+from tests.gpu_util import rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _mu0(nlon, nlat):
+    p = inputs.hill_problem(nlon, nlat, rhs="flow", mu_hat=0.0)
+    return p, p.R - p.R.mean()
+
+
+def _gpu(p, R, mu, k, oracle_order, faults=(), max_steps=20000, tiles=0):
+    with ftgcr.Solver(p.D, mu, k=k, tol=1e-10, precision="fp64", max_steps=max_steps, tiles=tiles,
+                      oracle_order=oracle_order) as s:
+        Rt = torch.from_numpy(np.ascontiguousarray(R)).cuda()
+        x = torch.zeros_like(Rt)
+        s.solve(Rt, x, faults=faults)
+        return x.cpu().numpy(), s.stats()
+
+
+@pytest.mark.parametrize("nlon,nlat,k", [(256, 128, 6), (256, 128, 4), (320, 64, 4)])
+def test_oracle_order_takes_the_oracles_decisions_in_long_singular_solves(nlon, nlat, k):
+    p, R = _mu0(nlon, nlat)
+    o = oracle.ftgcr(p.D, R, 0.0, k, 1e-10, max_steps=20000)
+    x, s = _gpu(p, R, 0.0, k, True)
+    assert o["converged"] and s["converged"]
+    assert s["steps"] == o["steps"] and s["detect_steps"] == o["detect_steps"] == []
+    assert rel_err(x - x.mean(), o["x"] - o["x"].mean()) <= 1e-10
+
+
+def test_chunked_rows_keep_the_solution_and_no_detection_in_long_singular_solves():
+    p, R = _mu0(256, 128)
+    o = oracle.ftgcr(p.D, R, 0.0, 6, 1e-10, max_steps=20000)
+    x, s = _gpu(p, R, 0.0, 6, False)
+    assert o["converged"] and s["converged"] and s["detect_steps"] == []
+    assert abs(s["steps"] - o["steps"]) <= 0.05 * o["steps"]
+    assert rel_err(x - x.mean(), o["x"] - o["x"].mean()) <= 1e-10
+
+
+@pytest.mark.parametrize("oracle_order", [True, False])
+@pytest.mark.parametrize("nlon,nlat,tiles", [(512, 256, 0), (2048, 48, 6)])  # staged; factors in global memory
+def test_fault_decisions_match_in_either_mode(nlon, nlat, tiles, oracle_order):
+    p = inputs.hill_problem(nlon, nlat, rhs="random", seed=44)
+    N = p.R.size
+    faults = [(4, "r", N // 3 + 7, 62), (9, "ap", N // 2 + 1, 61)]
+    o = oracle.ftgcr(p.D, p.R, p.mu, 4, 1e-10, faults=faults)
+    x, s = _gpu(p, p.R, p.mu, 4, oracle_order, faults=faults, max_steps=0, tiles=tiles)
+    assert s["global_factors"] == (tiles > 0)
+    assert s["steps"] == o["steps"] and s["detect_steps"] == o["detect_steps"]
+    assert s["faults_detected"] == o["faults_detected"] and s["converged"] == o["converged"]
+    assert rel_err(x, o["x"]) <= 1e-10
+
+
+def test_oracle_order_is_refused_outside_the_fp64_line_solve():
+    p = inputs.hill_problem(64, 32)
+    for kw in (dict(precision="mixed"), dict(precision="fp64", precond="jacobi")):
+        with pytest.raises(ftgcr.FTGCRError):
+            ftgcr.Solver(p.D, p.mu, oracle_order=True, **kw)
