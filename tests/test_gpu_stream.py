@@ -140,6 +140,29 @@ def test_batch_mixing_streamed_and_other_layouts_is_bitwise_solo():
             s.close()
 
 
+def test_server_mixing_streamed_and_other_layouts_is_bitwise_solo():
+    """Served requests in every layout, streamed among them (the launch then runs the
+    streamed instance for all), host arrays, each result bitwise the solo one."""
+    shapes = [(1024, 96, "streamed"), (256, 128, "auto"), (2048, 40, "streamed"), (4096, 24, "split"),
+              (128, 64, "fused"), (1024, 64, "streamed")]
+    probs = [inputs.hill_problem(n, m, **inputs.random_hill(90 + q)) for q, (n, m, _) in enumerate(shapes)]
+    alone = []
+    for p, (_, _, r) in zip(probs, shapes):
+        with ftgcr.Solver(p.D, p.mu, k=4, tol=1e-10, precision="mixed", rounds=r) as s:
+            x = np.zeros_like(p.R)
+            s.solve(p.R, x)
+            alone.append((x, s.stats()))
+    with ftgcr.Server(max_slots=4, epoch_rounds=7) as srv:
+        xs = [np.zeros_like(p.R) for p in probs]
+        ts = [srv.submit(torch.from_numpy(p.D).cuda(), p.mu, p.R, x, precision="mixed", rounds=r, coeff_key=q + 1)
+              for q, (p, x, (_, _, r)) in enumerate(zip(probs, xs, shapes))]
+        res = [srv.wait(t, timeout=120) for t in ts]
+    for q, (st, ss) in enumerate(res):
+        assert st == ftgcr.OK, q
+        assert np.array_equal(xs[q], alone[q][0]), q
+        assert ss["steps"] == alone[q][1]["steps"] and ss["streamed_rounds"] == alone[q][1]["streamed_rounds"]
+
+
 def test_streamed_flag_rejected_where_it_cannot_run():
     # nlon not a multiple of 4; per-lane chunks of 40 (not a power of two);
     # chunks of 8 (rows under 993 columns)
