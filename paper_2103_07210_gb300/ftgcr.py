@@ -373,13 +373,14 @@ def _stats_dict(s: Stats) -> dict:
 
 
 def tune(D, mu, k=4, tol=1e-10, precision="mixed", precond="line", concurrency=1, max_steps=0, inner_tol=0.0,
-         max_outer=0, protect=True) -> dict:
+         max_outer=0, protect=True, oracle_order=False) -> dict:
     """Tile autotuner (ftgcr_tune): the fastest row-band count and round
     layout for `concurrency` solves of this shape in one launch, by timing.
     Returns dict(tiles, rounds, ms, default_tiles, default_ms, candidates,
     cached); pass tiles= and rounds= to Solver (or Server.submit)."""
     nlat, nlon = D.shape
-    g = _grid(nlon, nlat, mu, precision, precond, max_steps, 0, inner_tol, max_outer, protect)
+    g = _grid(nlon, nlat, mu, precision, precond, max_steps, 0, inner_tol, max_outer, protect,
+              oracle_order=oracle_order)
     dp, keep = _ptr(D)
     t = Tuning()
     st = lib().ftgcr_tune(ctypes.byref(g), ctypes.byref(Coeffs(dp, 0)), int(k), float(tol), int(concurrency),
@@ -463,11 +464,13 @@ class Server:
         self._keep = {}
 
     def submit(self, D, mu, rhs, x, k=4, tol=1e-10, precision="fp64", precond="line", faults=(), max_steps=0,
-               tiles=0, inner_tol=0.0, max_outer=0, losses=(), protect=True, coeff_key=0, rounds="auto") -> int:
+               tiles=0, inner_tol=0.0, max_outer=0, losses=(), protect=True, coeff_key=0, rounds="auto",
+               oracle_order=False) -> int:
         """coeff_key: 0, or an identity of D's contents; the same (D, key) pair
         lets a pooled handle already set up from it skip the set-up."""
         nlat, nlon = D.shape
-        g = _grid(nlon, nlat, mu, precision, precond, max_steps, tiles, inner_tol, max_outer, protect, rounds)
+        g = _grid(nlon, nlat, mu, precision, precond, max_steps, tiles, inner_tol, max_outer, protect, rounds,
+                  oracle_order)
         dp, dk = _ptr(D)
         rp, rk = _ptr(rhs)
         xp, xk = _ptr(x)
