@@ -128,6 +128,13 @@ typedef struct {
  * the oracle's at every width, at the cost of the serial chains on wide rows.
  * Another precision or preconditioner: FTGCR_ERR_ARG. */
 #define FTGCR_FLAG_ORACLE_ORDER 16
+/* Every solve of the handle starts from x = 0: x is output only, and its
+ * contents on entry are neither read nor checked (host arrays are not copied
+ * in).  The results are those of the same solve from a zeroed x (FP64:
+ * bitwise); the mixed path also saves the refinement round that would form
+ * the first outer residual r_out = R - L(0) = R, taking R for the first inner
+ * solve directly. */
+#define FTGCR_FLAG_ZERO_GUESS 32
 
 typedef struct {
   const double* D;   /* [nlat][nlon] cell-centred coefficient (column depth 1 - h), > 0 */

@@ -1027,6 +1027,7 @@ int create_impl(ftgcr_handle* h, const double* D_host_or_dev, bool D_on_device) 
   sd.tol2 = h->tol * h->tol;
   sd.inner_tol2 = h->inner_tol * h->inner_tol;
   sd.protect = (h->flags & FTGCR_FLAG_UNPROTECTED) ? 0 : 1;
+  sd.zero_guess = (h->flags & FTGCR_FLAG_ZERO_GUESS) ? 1 : 0;
   sd.split = h->split;
   sd.cs_off = (int)h->plan.cs_off;
   sd.cs_clobber = h->plan.cs_clobber;
@@ -1392,7 +1393,8 @@ static int check_grid(const ftgcr_grid* g, int32_t k, double tol) {
   if (g->max_steps < 0 || g->tiles < 0 || g->max_outer < 0 || !(g->inner_tol >= 0.0) || g->inner_tol >= 1.0)
     return FTGCR_ERR_ARG;
   constexpr int layouts = FTGCR_FLAG_SPLIT_ROUNDS | FTGCR_FLAG_FUSED_ROUNDS | FTGCR_FLAG_STREAMED_ROUNDS;
-  if (g->flags & ~(FTGCR_FLAG_UNPROTECTED | FTGCR_FLAG_ORACLE_ORDER | layouts)) return FTGCR_ERR_ARG;
+  if (g->flags & ~(FTGCR_FLAG_UNPROTECTED | FTGCR_FLAG_ORACLE_ORDER | FTGCR_FLAG_ZERO_GUESS | layouts))
+    return FTGCR_ERR_ARG;
   if ((g->flags & FTGCR_FLAG_ORACLE_ORDER) && (g->precision != FTGCR_FP64 || g->precond != FTGCR_PRECOND_LINE))
     return FTGCR_ERR_ARG;
   const int lf = g->flags & layouts;
@@ -1535,8 +1537,11 @@ static int solve_enqueue(ftgcr_handle* h, const double* rhs, double* x, const ft
   const double* R = rhs;
   double* X = x;
   // host arrays: staged, and checked for finite values on the device (the
-  // solve does not start if one is not; x then comes back unchanged)
-  const bool check = !rdev || !xdev;
+  // solve does not start if one is not; x then comes back unchanged).  With
+  // FTGCR_FLAG_ZERO_GUESS x is output only: not copied in nor checked (its
+  // staging buffer is zeroed, which a refused solve returns)
+  const bool zg = (h->flags & FTGCR_FLAG_ZERO_GUESS) != 0;
+  const bool check = !rdev || (!xdev && !zg);
   const int cg = (int)std::min<long long>((h->N + 255) / 256, 1024);
   if (check) CK(cudaMemsetAsync(&h->ctl->nonfinite, 0, sizeof(int), st));
   if (!rdev) {
@@ -1545,8 +1550,12 @@ static int solve_enqueue(ftgcr_handle* h, const double* rhs, double* x, const ft
     R = h->stageR;
   }
   if (!xdev) {
-    CK(cudaMemcpyAsync(h->stageX, x, sizeof(double) * h->N, cudaMemcpyHostToDevice, st));
-    k_nonfinite<<<cg, 256, 0, st>>>(h->stageX, h->N, h->ctl);
+    if (zg) {
+      CK(cudaMemsetAsync(h->stageX, 0, sizeof(double) * h->N, st));
+    } else {
+      CK(cudaMemcpyAsync(h->stageX, x, sizeof(double) * h->N, cudaMemcpyHostToDevice, st));
+      k_nonfinite<<<cg, 256, 0, st>>>(h->stageX, h->N, h->ctl);
+    }
     X = h->stageX;
   }
   CK(cudaGetLastError());
@@ -1894,6 +1903,7 @@ extern "C" int ftgcr_solve_noalloc(const ftgcr_grid* grid, const double* D, int3
   sd.tol2 = h.tol * h.tol;
   sd.inner_tol2 = h.inner_tol * h.inner_tol;
   sd.protect = (h.flags & FTGCR_FLAG_UNPROTECTED) ? 0 : 1;
+  sd.zero_guess = (h.flags & FTGCR_FLAG_ZERO_GUESS) ? 1 : 0;
   sd.split = 0;
   sd.cs_off = (int)h.plan.cs_off;
   sd.cs_clobber = 0;

@@ -84,6 +84,7 @@ struct SolveState {
   int finbuf;   // phi buffer of the final iterate (FIN) / inner solution (OUT)
   int finzero;  // FIN writes x = 0 (R = 0)
   int first_out;
+  int xzero;    // mixed: x is zero and in no buffer yet (a zero-guess solve before its first OUT)
   int stag;     // mixed: detections since the last accepted step
   int out_redo; // mixed: this OUT recomputes r_out for the kept x (no test)
   int out_rej;  // mixed: consecutive rejected refinement updates
@@ -103,6 +104,7 @@ struct SolveState {
 template <typename T>
 struct SolveDev {
   int nlon, nlat, k, nt, C, precond, mixed, nfaults;
+  int zero_guess;  // every solve starts from x = 0 (x not read)
   int nt_hmax;  // rows of the tallest row tile
   long long N, max_steps;
   int max_outer;

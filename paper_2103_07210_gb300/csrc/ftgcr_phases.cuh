@@ -25,6 +25,7 @@ struct FlipEnt {
 template <typename T>
 struct Ctx {
   int kind, nu, zero_guess, xsrc_user, finzero, patched, first;
+  int rin_R;  // INIT: r0 = -R (zero initial guess; mixed: the first inner solve), ||R||^2 in FP64
   long long t;           // PA: executed step; INIT/PB/RESTORE: step whose x/r/p/Ap flips are applied
   long long patch_step;  // step of the flips whose clean values the backup carries
   T beta;
@@ -295,12 +296,22 @@ __device__ __noinline__ void transition(const SolveDev<T>& sd, const SolveState&
   bool to_fin = false;
   switch (S.pending) {
     case K_NONE:
-      if (sd.mixed) {
+      if (sd.mixed && sd.zero_guess) {
+        // x0 = 0: r_out = R, so the first inner solve takes R as it is
+        c.kind = K_INIT;
+        c.zero_guess = 1;
+        c.rin_R = 1;
+        N.xzero = 1;
+      } else if (sd.mixed) {
         c.kind = K_OUT;
         c.xsrc_user = 1;
         c.first = 1;
       } else {
         c.kind = K_INIT;
+        if (sd.zero_guess) {
+          c.zero_guess = 1;
+          c.rin_R = 1;
+        }
       }
       break;
     case K_OUT: {
@@ -337,13 +348,14 @@ __device__ __noinline__ void transition(const SolveDev<T>& sd, const SolveState&
           N.out_redo = 1;
           c.kind = K_OUT;
           c.d = nullptr;
-          c.xsrc = sd.xbuf[S.xcur];
+          c.xsrc = S.xzero ? nullptr : sd.xbuf[S.xcur];
           c.xdst = sd.xbuf[S.xcur ^ 1];
         }
         break;
       }
       N.out_rej = 0;
       N.xcur = S.xcur ^ 1;
+      N.xzero = 0;
       N.nrm2_out = nrm2_out;
       if (N.nrm2_R == 0.0) {
         N.status = ST_CONVERGED;
@@ -374,6 +386,23 @@ __device__ __noinline__ void transition(const SolveDev<T>& sd, const SolveState&
         N.thr2 = sd.tol2 * N.nrm2_R;
         N.nrm2_0 = red[0];
         thr2 = N.thr2;
+      } else if (S.first_out) {
+        // zero initial guess: this INIT took R itself, and its FP64 ||R||^2
+        // stands for the first OUT's (r_out = R)
+        N.nrm2_R = red[1];
+        N.thr2 = sd.tol2 * N.nrm2_R;
+        N.first_out = 0;
+        N.nrm2_0 = N.nrm2_R;
+        N.nrm2_out = N.nrm2_R;
+        N.outer = S.outer + 1;
+        const double a = sd.inner_tol2 * N.nrm2_R, b = 0.25 * N.thr2;
+        N.thr2_in = a > b ? a : b;
+        thr2 = N.thr2_in;
+        if (N.nrm2_R == 0.0) {  // R = 0: x = 0 is the solution
+          N.status = ST_CONVERGED;
+          to_fin = true;
+          break;
+        }
       } else {
         thr2 = S.thr2_in;
       }
@@ -589,10 +618,10 @@ __device__ __noinline__ void transition(const SolveDev<T>& sd, const SolveState&
     c.pnew = sd.p[N.slot[0]];
     c.lpnew = sd.Lp[N.slot[0]];
   } else if (c.kind == K_OUT && !N.out_redo) {
-    c.xsrc = c.xsrc_user ? sd.x0 : sd.xbuf[S.xcur];
+    c.xsrc = c.xsrc_user ? sd.x0 : (N.xzero ? nullptr : sd.xbuf[S.xcur]);
     c.xdst = sd.xbuf[S.xcur ^ 1];
   } else if (c.kind == K_FIN) {
-    if (sd.mixed) c.xsrc = sd.xbuf[N.xcur];
+    if (sd.mixed) c.xsrc = N.xzero ? nullptr : sd.xbuf[N.xcur];
   }
   N.pending = c.kind;
   if (c.kind == K_NONE) N.active = 0;
@@ -1488,21 +1517,42 @@ __device__ __noinline__ void phase_restore(const SolveDev<T>& sd, const Ctx<T>& 
 // x0, r0 written (with the step's x / r flips and their clean values kept).
 template <typename T>
 __device__ __forceinline__ void init_rows(const SolveDev<T>& sd, const Ctx<T>& c, const RowTile& rt, T* sm,
-                                          PhaseSmem& ps, Acc<T>& an, Acc<T>& aR, bool vec) {
+                                          PhaseSmem& ps, Acc<T>& an, Acc<T>& aR, AccF64& aR64, bool vec) {
   const int nlon = sd.nlon, nlat = sd.nlat, stride = row_stride(nlon);
   constexpr int W = V16<T>::W;
   const int nfl = ps.nfl;
   if (vec) {
-    // r0 = -R_in (zero guess), x0 = 0
+    // r0 = -R_in (zero guess), x0 = 0; rin_R: r0 = -R (the caller's FP64 R,
+    // 16-byte aligned here) and ||R||^2 in FP64
     const int nvr = nlon / W, total = (rt.h1 - rt.h0) * nvr;
     for (int idx = threadIdx.x; idx < total; idx += kThreads) {
       const RowVec v = row_vec(idx, nvr, rt.h0, nlon, W);
-      const V16<T> rin = ldv(sd.Rin + v.g);
+      V16<T> rin;
+      if (c.rin_R) {
+        constexpr int D2 = V16<double>::W;
+#pragma unroll
+        for (int h = 0; h < W; h += D2) {
+          const V16<double> rr = ldv(sd.R + v.g + h);
+#pragma unroll
+          for (int w = 0; w < D2; ++w) {
+            rin.v[h + w] = (T)rr.v[w];
+            if (v.j >= rt.j0 && v.j < rt.j1) {
+              if constexpr (sizeof(T) == 8)
+                aR.add(rr.v[w], rr.v[w]);  // FP64 path: the compensated sum, as with x0 read
+              else
+                aR64.add(rr.v[w], rr.v[w]);
+            }
+          }
+        }
+      } else {
+        rin = ldv(sd.Rin + v.g);
+      }
       V16<T> rv, zv;
       T* row = sm + (v.j - rt.h0) * stride;
 #pragma unroll
       for (int w = 0; w < W; ++w) {
-        rv.v[w] = -rin.v[w];
+        // FP64 path from R: L(0) - R, whose zero entries are +0 (as with x0 read)
+        rv.v[w] = (sizeof(T) == 8 && c.rin_R) ? T(0) - rin.v[w] : -rin.v[w];
         zv.v[w] = T(0);
         row[sk(v.i + w)] = rv.v[w];
       }
@@ -1521,7 +1571,17 @@ __device__ __forceinline__ void init_rows(const SolveDev<T>& sd, const Ctx<T>& c
     for (int i = threadIdx.x; i < nlon; i += kThreads) {
       const long long g = base + i;
       T rv, xv;
-      if (c.zero_guess) {
+      if (c.rin_R) {
+        const double Rg = ldcg(sd.R + g);
+        rv = sizeof(T) == 8 ? T(0) - (T)Rg : -(T)Rg;  // FP64: L(0) - R; mixed: -(float)(R - 0)
+        xv = T(0);
+        if (own) {
+          if constexpr (sizeof(T) == 8)
+            aR.add(Rg, Rg);  // FP64 path: the compensated sum, as with x0 read
+          else
+            aR64.add(Rg, Rg);
+        }
+      } else if (c.zero_guess) {
         rv = -ldcg(sd.Rin + g);
         xv = T(0);
       } else {
@@ -1621,10 +1681,10 @@ __device__ __forceinline__ void init_stencil(const SolveDev<T>& sd, const Ctx<T>
 // The partial sums of INIT (full: also ||r0||^2 and ||R||^2).
 template <typename T>
 __device__ __forceinline__ void init_partials(PhaseSmem& ps, double* part_out, const Acc<T>* an, const Acc<T>* aR,
-                                              const Acc<T>& a0, const Acc<T>& a1, bool full) {
+                                              const Acc<T>& a0, const Acc<T>& a1, bool full, const AccF64* aR64 = nullptr) {
   if (full) {
     cta_red_put(ps.cr, 0, an->warp_sum());
-    cta_red_put(ps.cr, 1, aR->warp_sum());
+    cta_red_put(ps.cr, 1, aR64 ? aR64->warp_sum() : aR->warp_sum());
   }
   cta_red_put(ps.cr, 2, a0.warp_sum());
   cta_red_put(ps.cr, 3, a1.warp_sum());
@@ -1646,16 +1706,19 @@ __device__ __noinline__ void phase_init(const SolveDev<T>& sd, const Ctx<T>& c, 
   if (!(ps.cs_solve == sidx && ps.cs_tile == tau)) stage_line_consts<T, GL>(sd, rt.h0, rt.h1, cs);
   __syncthreads();
   Acc<T> an, aR;
+  AccF64 aR64;
   constexpr int W = V16<T>::W;
-  const bool vec = c.zero_guess && ps.nfl == 0 && nlon % W == 0;  // the common case, 16-byte accesses
-  init_rows<T>(sd, c, rt, sm, ps, an, aR, vec);
+  // the common case, 16-byte accesses (the caller's R must be aligned for them)
+  const bool vec = c.zero_guess && ps.nfl == 0 && nlon % W == 0 &&
+                   (!c.rin_R || (reinterpret_cast<unsigned long long>(sd.R) & 15ull) == 0ull);
+  init_rows<T>(sd, c, rt, sm, ps, an, aR, aR64, vec);
   cp_async_wait_all();
   __syncthreads();
   precond_tile<T, false, GL>(sd, rt.h0, rt.h1 - rt.h0, sm, stride, cs);
   __syncthreads();
   Acc<T> a0, a1;
   init_stencil<T>(sd, c, rt, sm, ps, a0, a1, vec);
-  init_partials<T>(ps, part_out, &an, &aR, a0, a1, true);
+  init_partials<T>(ps, part_out, &an, &aR, a0, a1, true, c.rin_R && sizeof(T) == 4 ? &aR64 : nullptr);
   if (threadIdx.x == 0) {
     ps.cs_solve = sidx;
     ps.cs_tile = tau;
@@ -1676,7 +1739,9 @@ __device__ __noinline__ void phase_init_any(const SolveDev<T>& sd, const Ctx<T>&
   if (threadIdx.x == 0)
     ps.nfl = collect_flips(sd, c.t, kStateVecs, (long long)rt.j0 * nlon, (long long)rt.j1 * nlon, ps.fl);
   Acc<T> an, aR, a0, a1;
+  AccF64 aR64;
   constexpr int W = V16<T>::W;
+  const bool ralign = !c.rin_R || (reinterpret_cast<unsigned long long>(sd.R) & 15ull) == 0ull;
   const int sub = (mode == 0 || sd.sub_h <= 0) ? rt.j1 - rt.j0 : sd.sub_h;
   const bool one = sub >= rt.j1 - rt.j0;  // the whole tile at once
   for (int a = rt.j0; a < rt.j1; a += sub) {
@@ -1702,8 +1767,8 @@ __device__ __noinline__ void phase_init_any(const SolveDev<T>& sd, const Ctx<T>&
       }
       if (!(one && ps.cs_solve == sidx && ps.cs_tile == tau)) stage_line_consts(sd, st.h0, st.h1, cs);
       __syncthreads();
-      const bool vec = c.zero_guess && ps.nfl == 0 && nlon % W == 0;
-      init_rows<T>(sd, c, st, sm, ps, an, aR, vec);
+      const bool vec = c.zero_guess && ps.nfl == 0 && nlon % W == 0 && ralign;
+      init_rows<T>(sd, c, st, sm, ps, an, aR, aR64, vec);
       cp_async_wait_all();
       __syncthreads();
       precond_tile<T, true>(sd, st.h0, st.h1 - st.h0, sm, stride, cs, mode == 1);
@@ -1722,11 +1787,11 @@ __device__ __noinline__ void phase_init_any(const SolveDev<T>& sd, const Ctx<T>&
   }
   if (mode == 1) {
     cta_red_put(ps.cr, 0, an.warp_sum());
-    cta_red_put(ps.cr, 1, aR.warp_sum());
+    cta_red_put(ps.cr, 1, c.rin_R && sizeof(T) == 4 ? aR64.warp_sum() : aR.warp_sum());
     cta_red_finish<T>(ps.cr, 2, part_out);
     return;
   }
-  init_partials<T>(ps, part_out, &an, &aR, a0, a1, mode == 0);
+  init_partials<T>(ps, part_out, &an, &aR, a0, a1, mode == 0, c.rin_R && sizeof(T) == 4 ? &aR64 : nullptr);
 }
 
 // OUT (mixed): x' = x + d in FP64, r_out = R - L64(x'), ||r_out||^2 (and
@@ -1761,7 +1826,7 @@ __device__ __noinline__ void phase_out(const SolveDev<T>& sd, const Ctx<T>& c, i
           const int idx = b + u * kThreads;
           if (idx < total) {
             const long long g = (long long)rt.h0 * nlon + idx;
-            xv[u] = ldcg(c.xsrc + g);
+            xv[u] = c.xsrc ? ldcg(c.xsrc + g) : 0.0;  // x = 0 before a zero-guess solve's first OUT
             if (c.d) xv[u] = xv[u] + (double)ldcg(c.d + g);
           }
         }
@@ -1835,7 +1900,7 @@ __device__ __noinline__ void phase_fin(const SolveDev<T>& sd, const Ctx<T>& c, i
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const long long g = b + (long long)u * kThreads;
-        if (g < g1) v[u] = ldcg(xs + g);
+        if (g < g1) v[u] = xs ? ldcg(xs + g) : 0.0;  // no x buffer yet: x = 0
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {

@@ -327,13 +327,17 @@ struct ftgcr_server {
         return FTGCR_ERR_CUDA;
       *R = handle_stage_rhs(h);
     }
+    // FTGCR_FLAG_ZERO_GUESS: x is output only (its staging buffer zeroed, not
+    // copied in nor checked)
+    const bool zg = (r->key.grid.flags & FTGCR_FLAG_ZERO_GUESS) != 0;
     if (!xdev) {
-      if (cudaMemcpyAsync(handle_stage_x(h), *X, sizeof(double) * N, cudaMemcpyHostToDevice, cst) != cudaSuccess)
-        return FTGCR_ERR_CUDA;
+      const cudaError_t e = zg ? cudaMemsetAsync(handle_stage_x(h), 0, sizeof(double) * N, cst)
+                               : cudaMemcpyAsync(handle_stage_x(h), *X, sizeof(double) * N, cudaMemcpyHostToDevice, cst);
+      if (e != cudaSuccess) return FTGCR_ERR_CUDA;
       *X = handle_stage_x(h);
     }
     r->x_host = !xdev;
-    *check = (rdev ? 0 : 1) | (xdev ? 0 : 2);
+    *check = (rdev ? 0 : 1) | (xdev || zg ? 0 : 2);
     return FTGCR_OK;
   }
   // Stage every admitted request on the copy stream, make the launch stream

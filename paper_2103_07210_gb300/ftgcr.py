@@ -35,6 +35,7 @@ PRECOND = {"line": 0, "jacobi": 1, "identity": 2}
 VEC = {"x": 0, "r": 1, "p": 2, "ap": 3, "e": 4}
 MAX_FAULTS, MAX_K, MAX_DETECT, MAX_LOSSES = 64, 16, 16, 16
 FLAG_UNPROTECTED, FLAG_SPLIT_ROUNDS, FLAG_FUSED_ROUNDS, FLAG_STREAMED_ROUNDS, FLAG_ORACLE_ORDER = 1, 2, 4, 8, 16
+FLAG_ZERO_GUESS = 32
 
 OK, NOT_CONVERGED, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BUDGET, ERR_STATE = 0, 1, -1, -2, -3, -4, -5, -6
 PENDING = 2
@@ -234,10 +235,11 @@ ROUNDS = {"auto": 0, "split": FLAG_SPLIT_ROUNDS, "fused": FLAG_FUSED_ROUNDS, "st
 
 
 def _grid(nlon, nlat, mu, precision, precond, max_steps, tiles, inner_tol, max_outer, protect=True, rounds="auto",
-          oracle_order=False):
+          oracle_order=False, zero_guess=False):
     prec = {"fp64": FP64, "mixed": MIXED}.get(precision, precision)
     pc = PRECOND.get(precond, precond)
     flags = (0 if protect else FLAG_UNPROTECTED) | ROUNDS[rounds] | (FLAG_ORACLE_ORDER if oracle_order else 0)
+    flags |= FLAG_ZERO_GUESS if zero_guess else 0
     return Grid(int(nlon), int(nlat), float(mu), int(prec), int(pc), int(max_steps), int(tiles), float(inner_tol),
                 int(max_outer), flags)
 
@@ -251,18 +253,19 @@ class Solver:
     """One FT-GCR(k) problem resident on the GPU (ftgcr_create)."""
 
     def __init__(self, D, mu, k=4, tol=1e-10, precision="fp64", precond="line", max_steps=0, tiles=0,
-                 inner_tol=0.0, max_outer=0, protect=True, rounds="auto", oracle_order=False):
+                 inner_tol=0.0, max_outer=0, protect=True, rounds="auto", oracle_order=False, zero_guess=False):
         """protect=False: plain GCR(k), the paper's unprotected baseline (no
         fault test, no restore).  rounds: "auto", "split", "fused" or
         "streamed" (FTGCR_FLAG_SPLIT_ROUNDS / FTGCR_FLAG_FUSED_ROUNDS /
         FTGCR_FLAG_STREAMED_ROUNDS).  oracle_order (FP64, line
-        preconditioner): FTGCR_FLAG_ORACLE_ORDER."""
+        preconditioner): FTGCR_FLAG_ORACLE_ORDER.  zero_guess: every solve
+        starts from x = 0 and x is output only (FTGCR_FLAG_ZERO_GUESS)."""
         L = lib()
         nlat, nlon = D.shape
         self.nlon, self.nlat, self.k, self.tol = int(nlon), int(nlat), int(k), float(tol)
         self.precision = precision
         g = _grid(nlon, nlat, mu, precision, precond, max_steps, tiles, inner_tol, max_outer, protect, rounds,
-                  oracle_order)
+                  oracle_order, zero_guess)
         dp, keep = _ptr(D)
         c = Coeffs(dp, 0)
         h = ctypes.c_void_p()
@@ -373,14 +376,14 @@ def _stats_dict(s: Stats) -> dict:
 
 
 def tune(D, mu, k=4, tol=1e-10, precision="mixed", precond="line", concurrency=1, max_steps=0, inner_tol=0.0,
-         max_outer=0, protect=True, oracle_order=False) -> dict:
+         max_outer=0, protect=True, oracle_order=False, zero_guess=False) -> dict:
     """Tile autotuner (ftgcr_tune): the fastest row-band count and round
     layout for `concurrency` solves of this shape in one launch, by timing.
     Returns dict(tiles, rounds, ms, default_tiles, default_ms, candidates,
     cached); pass tiles= and rounds= to Solver (or Server.submit)."""
     nlat, nlon = D.shape
     g = _grid(nlon, nlat, mu, precision, precond, max_steps, 0, inner_tol, max_outer, protect,
-              oracle_order=oracle_order)
+              oracle_order=oracle_order, zero_guess=zero_guess)
     dp, keep = _ptr(D)
     t = Tuning()
     st = lib().ftgcr_tune(ctypes.byref(g), ctypes.byref(Coeffs(dp, 0)), int(k), float(tol), int(concurrency),
@@ -465,12 +468,12 @@ class Server:
 
     def submit(self, D, mu, rhs, x, k=4, tol=1e-10, precision="fp64", precond="line", faults=(), max_steps=0,
                tiles=0, inner_tol=0.0, max_outer=0, losses=(), protect=True, coeff_key=0, rounds="auto",
-               oracle_order=False) -> int:
+               oracle_order=False, zero_guess=False) -> int:
         """coeff_key: 0, or an identity of D's contents; the same (D, key) pair
         lets a pooled handle already set up from it skip the set-up."""
         nlat, nlon = D.shape
         g = _grid(nlon, nlat, mu, precision, precond, max_steps, tiles, inner_tol, max_outer, protect, rounds,
-                  oracle_order)
+                  oracle_order, zero_guess)
         dp, dk = _ptr(D)
         rp, rk = _ptr(rhs)
         xp, xk = _ptr(x)

@@ -90,7 +90,7 @@ def test_round_layout_flags_are_validated_before_any_device_call():
     for g in bad:
         assert L.ftgcr_create(ctypes.byref(g), ctypes.byref(c), 4, 1e-10, ctypes.byref(h)) == ftgcr.ERR_ARG
     unknown = ftgcr._grid(16, 8, 1.0, "mixed", "line", 0, 0, 0.0, 0)
-    unknown.flags = 32
+    unknown.flags = 64
     assert L.ftgcr_create(ctypes.byref(unknown), ctypes.byref(c), 4, 1e-10, ctypes.byref(h)) == ftgcr.ERR_ARG
 
 
