@@ -133,7 +133,8 @@ typedef struct {
  * in).  The results are those of the same solve from a zeroed x (FP64:
  * bitwise); the mixed path also saves the refinement round that would form
  * the first outer residual r_out = R - L(0) = R, taking R for the first inner
- * solve directly. */
+ * solve directly.  A host-array solve refused for a non-finite rhs returns
+ * x = 0. */
 #define FTGCR_FLAG_ZERO_GUESS 32
 
 typedef struct {
