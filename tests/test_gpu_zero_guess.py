@@ -101,3 +101,16 @@ def test_batch_and_server_mix_flagged_and_unflagged_solves():
     for q, (st, ss) in enumerate(res):
         assert st == ftgcr.OK
         assert np.array_equal(xh[q], alone[q][0]), q
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_refused_zero_guess_host_solve_returns_zero(precision):
+    p = inputs.hill_problem(64, 32)
+    R = p.R.copy()
+    R[3, 5] = np.nan
+    x = np.full(p.R.shape, 7.0)
+    with ftgcr.Solver(p.D, p.mu, precision=precision, zero_guess=True) as s:
+        with pytest.raises(ftgcr.FTGCRError) as ei:
+            s.solve(R, x)
+    assert ei.value.status == ftgcr.ERR_ARG
+    assert np.array_equal(x, np.zeros_like(x))
