@@ -117,16 +117,19 @@ typedef struct {
  * FTGCR_FLAG_FUSED_ROUNDS, another precision or preconditioner, or rows too
  * wide for the ring of shared-memory slots a step needs: FTGCR_ERR_ARG. */
 #define FTGCR_FLAG_STREAMED_ROUNDS 8
-/* FTGCR_FP64 with the line preconditioner: solve every latitude row in the
- * oracle's operation order (Thomas elimination, one lane per row) at every
- * row width.  By default rows of 256 or more columns take a chunked scan
- * (one warp per row, 32 chunks joined by their exact affine maps), which is
- * the same elimination rounded differently: the fault decisions of
- * Algorithm 1 stay the oracle's, but in long, slowly converging solves (the
+/* FTGCR_FP64: take the oracle's operation order where the default takes a
+ * faster one that rounds differently.  (1) Inner products: by default each
+ * thread sums its products with one fma per element (double-double from the
+ * warp up); with this flag every product and partial sum is compensated
+ * (Dot2, Ogita-Rump-Oishi), as in the oracle.  (2) Line preconditioner:
+ * rows of 256 or more columns take a chunked scan by default (one warp per
+ * row, 32 chunks joined by their exact affine maps); with this flag every
+ * row takes the oracle's Thomas elimination (one lane per row).  Either
+ * default keeps the fault decisions of Algorithm 1 and the solution within
+ * rounding of the oracle's, but in long, slowly converging solves (the
  * singular mu = 0 problem, hundreds of steps) the exit can come some steps
- * earlier or later.  With this flag the preconditioned vectors are bitwise
- * the oracle's at every width, at the cost of the serial chains on wide rows.
- * Another precision or preconditioner: FTGCR_ERR_ARG. */
+ * earlier or later; with this flag the exit steps are the oracle's.
+ * FTGCR_MIXED: FTGCR_ERR_ARG. */
 #define FTGCR_FLAG_ORACLE_ORDER 16
 /* Every solve of the handle starts from x = 0: x is output only, and its
  * contents on entry are neither read nor checked (host arrays are not copied

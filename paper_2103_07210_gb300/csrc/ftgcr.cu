@@ -1028,6 +1028,7 @@ int create_impl(ftgcr_handle* h, const double* D_host_or_dev, bool D_on_device) 
   sd.inner_tol2 = h->inner_tol * h->inner_tol;
   sd.protect = (h->flags & FTGCR_FLAG_UNPROTECTED) ? 0 : 1;
   sd.zero_guess = (h->flags & FTGCR_FLAG_ZERO_GUESS) ? 1 : 0;
+  sd.dot2 = (h->flags & FTGCR_FLAG_ORACLE_ORDER) ? 1 : 0;
   sd.split = h->split;
   sd.cs_off = (int)h->plan.cs_off;
   sd.cs_clobber = h->plan.cs_clobber;
@@ -1395,8 +1396,7 @@ static int check_grid(const ftgcr_grid* g, int32_t k, double tol) {
   constexpr int layouts = FTGCR_FLAG_SPLIT_ROUNDS | FTGCR_FLAG_FUSED_ROUNDS | FTGCR_FLAG_STREAMED_ROUNDS;
   if (g->flags & ~(FTGCR_FLAG_UNPROTECTED | FTGCR_FLAG_ORACLE_ORDER | FTGCR_FLAG_ZERO_GUESS | layouts))
     return FTGCR_ERR_ARG;
-  if ((g->flags & FTGCR_FLAG_ORACLE_ORDER) && (g->precision != FTGCR_FP64 || g->precond != FTGCR_PRECOND_LINE))
-    return FTGCR_ERR_ARG;
+  if ((g->flags & FTGCR_FLAG_ORACLE_ORDER) && g->precision != FTGCR_FP64) return FTGCR_ERR_ARG;
   const int lf = g->flags & layouts;
   if (lf & (lf - 1)) return FTGCR_ERR_ARG;  // at most one layout
   if ((g->flags & (FTGCR_FLAG_SPLIT_ROUNDS | FTGCR_FLAG_STREAMED_ROUNDS)) &&
@@ -1904,6 +1904,7 @@ extern "C" int ftgcr_solve_noalloc(const ftgcr_grid* grid, const double* D, int3
   sd.inner_tol2 = h.inner_tol * h.inner_tol;
   sd.protect = (h.flags & FTGCR_FLAG_UNPROTECTED) ? 0 : 1;
   sd.zero_guess = (h.flags & FTGCR_FLAG_ZERO_GUESS) ? 1 : 0;
+  sd.dot2 = (h.flags & FTGCR_FLAG_ORACLE_ORDER) ? 1 : 0;
   sd.split = 0;
   sd.cs_off = (int)h.plan.cs_off;
   sd.cs_clobber = 0;

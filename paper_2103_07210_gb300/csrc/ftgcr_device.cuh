@@ -108,6 +108,7 @@ struct SolveDev {
   int nt_hmax;  // rows of the tallest row tile
   long long N, max_steps;
   int max_outer;
+  int dot2;  // FP64 inner products: each thread's products summed compensated (Dot2), else by fma
   double tol2, inner_tol2;
   // operator (inner precision)
   const T* Tx;
@@ -204,10 +205,14 @@ __device__ __forceinline__ DD dd_add(DD a, DD b) {
   return DD{t, (a.lo + b.lo) + q};
 }
 
-// Inner-product accumulators.  FP64 vectors: Dot2 (Ogita, Rump and Oishi):
-// exact products by fma (TwoProduct), running sum by TwoSum, low parts
-// collected; the same algorithm as the CPU oracle's inner product, so both
-// round (p + s) of nearly the same double-double value.  FP32 vectors: the
+// Inner-product accumulators.  FP64 vectors, with mode(1) (the solve's
+// oracle order): Dot2 (Ogita, Rump and Oishi): exact products by fma
+// (TwoProduct), running sum by TwoSum, low parts collected; the same
+// algorithm as the CPU oracle's inner product, so both round (p + s) of
+// nearly the same double-double value.  With mode(0), the default: one fma
+// per element within the thread, double-double from the warp up; the sum then
+// differs from Dot2's by about the rounding of a few hundred terms (relative
+// 1e-14 at most), far below the margins of the fault test.  FP32 vectors: the
 // product of two floats is exact as a float pair (TwoProduct with fmaf) and is
 // accumulated in a float-float pair; warps combine float-float pairs in FP32
 // and only per-warp sums reach FP64 (GB300's FP64 pipe is ~60x slower than
@@ -217,8 +222,18 @@ struct Acc;
 template <>
 struct Acc<double> {
   double p, s;
-  __device__ __forceinline__ Acc() : p(0.0), s(0.0) {}
+  bool ex;  // Dot2 within the thread, else one fma per element
+  __device__ __forceinline__ Acc() : p(0.0), s(0.0), ex(true) {}
+  __device__ __forceinline__ void mode(int dot2) { ex = dot2 != 0; }
   __device__ __forceinline__ void add(double a, double b) {
+    if (!ex) {
+      // each thread's few hundred products by fma; the sums above the thread
+      // stay double-double.  GB300 issues about two FP64 operations per SM
+      // and clock, so the eight of TwoProduct + TwoSum per element cost more
+      // than the rest of a step together.
+      p = fma(a, b, p);
+      return;
+    }
     const double h = a * b;
     const double r = fma(a, b, -h);
     const double t = p + h;
@@ -256,6 +271,7 @@ template <>
 struct Acc<float> {
   float hi, lo;
   __device__ __forceinline__ Acc() : hi(0.f), lo(0.f) {}
+  __device__ __forceinline__ void mode(int) {}  // always compensated (FP32 pipe)
   __device__ __forceinline__ void add(float a, float b) {
     const float p = a * b;
     const float pe = fmaf(a, b, -p);

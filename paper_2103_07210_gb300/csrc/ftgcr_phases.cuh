@@ -1235,6 +1235,9 @@ __device__ __forceinline__ void step_stencil(const SolveDev<T>& sd, const Ctx<T>
   const int nlon = sd.nlon, nlat = sd.nlat, stride = row_stride(nlon);
   Acc<T> ad[KB];
   Acc<T> ah, aq;  // mixed: <r', L(e)>, <L(e), L(e)>
+  ah.mode(sd.dot2), aq.mode(sd.dot2);
+#pragma unroll
+  for (int l = 0; l < KB; ++l) ad[l].mode(sd.dot2);
   if (nlon % W == 0) {
     const int nvr = nlon / W, total = (rt.j1 - rt.j0) * nvr;
     for (int idx = threadIdx.x; idx < total; idx += kThreads) {
@@ -1326,6 +1329,7 @@ __device__ __noinline__ void phase_pa(const SolveDev<T>& sd, const Ctx<T>& c, in
     ps.nfl = collect_flips(sd, c.t, FUSED ? (kStateVecs | (1u << V_E)) : (1u << V_E), (long long)rt.h0 * nlon,
                            (long long)rt.h1 * nlon, ps.fl);
   Acc<T> an;
+  an.mode(sd.dot2);
   step_axpy<T, KB, FUSED>(sd, c, rt, sm, ps, an);
   step_precond<T, false, GL>(sd, c, rt, sm, cs, ps);
   step_stencil<T, KB>(sd, c, rt, sm, ps, part_out, &an, true);
@@ -1348,6 +1352,7 @@ __device__ __noinline__ void phase_pa_any(const SolveDev<T>& sd, const Ctx<T>& c
   const int nlon = sd.nlon, stride = row_stride(nlon);
   RowTile rt = row_tile(sd.nlat, sd.nt, tau);
   Acc<T> an;
+  an.mode(sd.dot2);
   if (mode == 2) {
     stage_rows(c.eW, rt.h0, rt.h1, nlon, sm, stride);
     if (sd.cs_clobber && threadIdx.x == 0) ps.cs_solve = -1;  // the rows overwrote staged constants
@@ -1388,6 +1393,7 @@ __device__ __noinline__ void phase_pb(const SolveDev<T>& sd, const Ctx<T>& c, in
   __syncthreads();
   const int nfl = ps.nfl;
   Acc<T> a0, a1;
+  a0.mode(sd.dot2), a1.mode(sd.dot2);
   auto finish = [&](long long g, T pa, T la, T rv) {
     if (nfl) {
       pa = apply_flips(pa, g, V_P, nfl, ps.fl);
@@ -1486,6 +1492,7 @@ __device__ __noinline__ void phase_restore(const SolveDev<T>& sd, const Ctx<T>& 
   __syncthreads();
   const int nfl = ps.nfl, npt = ps.npt;
   Acc<T> a0, a1;
+  a0.mode(sd.dot2), a1.mode(sd.dot2);
   for (long long g = e0 + threadIdx.x; g < e1; g += kThreads) {
     T ph = ldcg(c.phiS + g), rr = ldcg(c.rS + g), pp = ldcg(c.pS + g), ll = ldcg(c.lpS + g);
     if (npt) {
@@ -1706,6 +1713,7 @@ __device__ __noinline__ void phase_init(const SolveDev<T>& sd, const Ctx<T>& c, 
   if (!(ps.cs_solve == sidx && ps.cs_tile == tau)) stage_line_consts<T, GL>(sd, rt.h0, rt.h1, cs);
   __syncthreads();
   Acc<T> an, aR;
+  an.mode(sd.dot2), aR.mode(sd.dot2);
   AccF64 aR64;
   constexpr int W = V16<T>::W;
   // the common case, 16-byte accesses (the caller's R must be aligned for them)
@@ -1717,6 +1725,7 @@ __device__ __noinline__ void phase_init(const SolveDev<T>& sd, const Ctx<T>& c, 
   precond_tile<T, false, GL>(sd, rt.h0, rt.h1 - rt.h0, sm, stride, cs);
   __syncthreads();
   Acc<T> a0, a1;
+  a0.mode(sd.dot2), a1.mode(sd.dot2);
   init_stencil<T>(sd, c, rt, sm, ps, a0, a1, vec);
   init_partials<T>(ps, part_out, &an, &aR, a0, a1, true, c.rin_R && sizeof(T) == 4 ? &aR64 : nullptr);
   if (threadIdx.x == 0) {
@@ -1739,6 +1748,7 @@ __device__ __noinline__ void phase_init_any(const SolveDev<T>& sd, const Ctx<T>&
   if (threadIdx.x == 0)
     ps.nfl = collect_flips(sd, c.t, kStateVecs, (long long)rt.j0 * nlon, (long long)rt.j1 * nlon, ps.fl);
   Acc<T> an, aR, a0, a1;
+  an.mode(sd.dot2), aR.mode(sd.dot2), a0.mode(sd.dot2), a1.mode(sd.dot2);
   AccF64 aR64;
   constexpr int W = V16<T>::W;
   const bool ralign = !c.rin_R || (reinterpret_cast<unsigned long long>(sd.R) & 15ull) == 0ull;
@@ -1890,6 +1900,7 @@ __device__ __noinline__ void phase_fin(const SolveDev<T>& sd, const Ctx<T>& c, i
   const int nlon = sd.nlon, nlat = sd.nlat;
   const RowTile rt = row_tile(nlat, sd.nt, tau);
   Acc<double> acc;
+  acc.mode(sd.dot2);
   if (sd.mixed) {
     // the tile's rows are contiguous: a copy, four loads in flight per thread
     const double* xs = c.xsrc;

@@ -257,8 +257,9 @@ class Solver:
         """protect=False: plain GCR(k), the paper's unprotected baseline (no
         fault test, no restore).  rounds: "auto", "split", "fused" or
         "streamed" (FTGCR_FLAG_SPLIT_ROUNDS / FTGCR_FLAG_FUSED_ROUNDS /
-        FTGCR_FLAG_STREAMED_ROUNDS).  oracle_order (FP64, line
-        preconditioner): FTGCR_FLAG_ORACLE_ORDER.  zero_guess: every solve
+        FTGCR_FLAG_STREAMED_ROUNDS).  oracle_order (FP64):
+        FTGCR_FLAG_ORACLE_ORDER, the oracle's compensated inner products and
+        serial row solves.  zero_guess: every solve
         starts from x = 0 and x is output only (FTGCR_FLAG_ZERO_GUESS)."""
         L = lib()
         nlat, nlon = D.shape

@@ -84,7 +84,7 @@ def test_round_layout_flags_are_validated_before_any_device_call():
            ftgcr._grid(16, 8, 1.0, "mixed", "identity", 0, 0, 0.0, 0, rounds="streamed"),
            ftgcr._grid(16, 8, 1.0, "mixed", "line", 0, 0, 0.0, 0, rounds="streamed"),
            ftgcr._grid(16, 8, 1.0, "mixed", "line", 0, 0, 0.0, 0, oracle_order=True),  # FP64 path only
-           ftgcr._grid(16, 8, 1.0, "fp64", "jacobi", 0, 0, 0.0, 0, oracle_order=True)]  # line solve only
+           ftgcr._grid(16, 8, 1.0, "mixed", "jacobi", 0, 0, 0.0, 0, oracle_order=True)]
     bad[0].flags |= ftgcr.FLAG_FUSED_ROUNDS  # both layouts at once
     bad[5].flags |= ftgcr.FLAG_SPLIT_ROUNDS
     for g in bad:

@@ -2,7 +2,8 @@
 unprotected GCR(k) mode and the singular mu = 0 problem, through the C ABI.
 
 FP64 path: decisions (steps, detection steps, convergence, events fired)
-identical to the oracle's, solution within 1e-10 relative.  Mixed path: converges to the oracle's
+identical to the oracle's (the exit step of the long singular solves: in the
+oracle's operation order), solution within 1e-10 relative.  Mixed path: converges to the oracle's
 solution (rel <= 1e-10 at tol 1e-13) under data loss; batched solves with data
 loss equal the same solves alone."""
 import numpy as np
@@ -25,9 +26,9 @@ def _events(seed, N, fracs, steps, nranks=12):
     return [(int(t), g.below(nranks), nranks, max(1, int(round(f * N))), g.next()) for t, f in zip(steps, fracs)]
 
 
-def _gpu(p, k, tol, faults=(), losses=(), protect=True, precision="fp64", max_steps=0, mu=None):
+def _gpu(p, k, tol, faults=(), losses=(), protect=True, precision="fp64", max_steps=0, mu=None, oracle_order=False):
     with ftgcr.Solver(p.D, p.mu if mu is None else mu, k=k, tol=tol, precision=precision, protect=protect,
-                      max_steps=max_steps) as s:
+                      max_steps=max_steps, oracle_order=oracle_order) as s:
         R = cuda(p.R)
         x = torch.zeros_like(R)
         st = s.solve(R, x, faults=faults, losses=losses)
@@ -71,14 +72,23 @@ def test_fp64_unprotected_matches_oracle():
 
 
 @pytest.mark.parametrize("nlon,nlat,k", [(64, 32, 4), (128, 64, 6)])
-def test_fp64_mu_zero_matches_oracle(nlon, nlat, k):
+@pytest.mark.parametrize("oracle_order", [True, False])
+def test_fp64_mu_zero_matches_oracle(nlon, nlat, k, oracle_order):
+    """Hundreds of slowly converging steps: in the oracle's operation order the
+    exit step is the oracle's; by default (inner products summed by fma within
+    each thread) it may move by a few percent (measured: 260 against 259 steps
+    at 128 x 64, k = 6), with no detection and the same solution."""
     p = inputs.hill_problem(nlon, nlat, rhs="flow", mu_hat=0.0)
     R = p.R - p.R.mean()
     p.R = R
     o = oracle.ftgcr(p.D, R, 0.0, k, 1e-10)
-    st, x, s = _gpu(p, k, 1e-10, mu=0.0)
+    st, x, s = _gpu(p, k, 1e-10, mu=0.0, oracle_order=oracle_order)
     assert o["converged"] and s["converged"]
-    assert s["steps"] == o["steps"] and s["detect_steps"] == o["detect_steps"]
+    assert s["detect_steps"] == o["detect_steps"] == []
+    if oracle_order:
+        assert s["steps"] == o["steps"]
+    else:
+        assert abs(s["steps"] - o["steps"]) <= 0.05 * o["steps"]
     assert rel_err(x - x.mean(), o["x"] - o["x"].mean()) <= 1e-10
 
 

@@ -1,13 +1,15 @@
-"""Long, slowly converging FP64 solves on rows of 256+ columns: the singular
-mu = 0 hill problem (Section 3's pure Poisson form) takes hundreds of steps.
+"""Long, slowly converging FP64 solves: the singular mu = 0 hill problem
+(Section 3's pure Poisson form) takes hundreds of steps.
 
-- With FTGCR_FLAG_ORACLE_ORDER every row is solved in the oracle's operation
-  order, and the solve takes the oracle's decisions exactly: the same step
-  count, no detections, the same solution (rel <= 1e-10, bitwise in practice).
-- By default such rows take the chunked scan, the same elimination rounded
-  differently: the solution still matches the oracle to 1e-10 and nothing is
-  detected, but the exit may come a few percent of the steps earlier or later
-  (measured: 484 against 470 steps for k = 6 at 256 x 128).
+- With FTGCR_FLAG_ORACLE_ORDER every inner product is summed compensated and
+  every row solved in the oracle's operation order, and the solve takes the
+  oracle's decisions exactly: the same step count, no detections, the same
+  solution (rel <= 1e-10, bitwise in practice).
+- By default each thread sums its products by fma and rows of 256+ columns
+  take the chunked scan: the same arithmetic rounded differently.  The
+  solution still matches the oracle to 1e-10 and nothing is detected, but the
+  exit may come a few percent of the steps earlier or later (measured with
+  the chunked scan alone: 484 against 470 steps for k = 6 at 256 x 128).
 - Fault decisions under single flips stay the oracle's in either mode."""
 import numpy as np
 import pytest
@@ -34,7 +36,7 @@ def _gpu(p, R, mu, k, oracle_order, faults=(), max_steps=20000, tiles=0):
         return x.cpu().numpy(), s.stats()
 
 
-@pytest.mark.parametrize("nlon,nlat,k", [(256, 128, 6), (256, 128, 4), (320, 64, 4)])
+@pytest.mark.parametrize("nlon,nlat,k", [(256, 128, 6), (256, 128, 4), (320, 64, 4), (128, 64, 4)])
 def test_oracle_order_takes_the_oracles_decisions_in_long_singular_solves(nlon, nlat, k):
     p, R = _mu0(nlon, nlat)
     o = oracle.ftgcr(p.D, R, 0.0, k, 1e-10, max_steps=20000)
@@ -44,10 +46,11 @@ def test_oracle_order_takes_the_oracles_decisions_in_long_singular_solves(nlon, 
     assert rel_err(x - x.mean(), o["x"] - o["x"].mean()) <= 1e-10
 
 
-def test_chunked_rows_keep_the_solution_and_no_detection_in_long_singular_solves():
-    p, R = _mu0(256, 128)
-    o = oracle.ftgcr(p.D, R, 0.0, 6, 1e-10, max_steps=20000)
-    x, s = _gpu(p, R, 0.0, 6, False)
+@pytest.mark.parametrize("nlon,nlat,k", [(256, 128, 6), (128, 64, 4)])
+def test_default_order_keeps_the_solution_and_no_detection_in_long_singular_solves(nlon, nlat, k):
+    p, R = _mu0(nlon, nlat)
+    o = oracle.ftgcr(p.D, R, 0.0, k, 1e-10, max_steps=20000)
+    x, s = _gpu(p, R, 0.0, k, False)
     assert o["converged"] and s["converged"] and s["detect_steps"] == []
     assert abs(s["steps"] - o["steps"]) <= 0.05 * o["steps"]
     assert rel_err(x - x.mean(), o["x"] - o["x"].mean()) <= 1e-10
@@ -67,8 +70,22 @@ def test_fault_decisions_match_in_either_mode(nlon, nlat, tiles, oracle_order):
     assert rel_err(x, o["x"]) <= 1e-10
 
 
-def test_oracle_order_is_refused_outside_the_fp64_line_solve():
+def test_oracle_order_is_refused_on_the_mixed_path():
     p = inputs.hill_problem(64, 32)
-    for kw in (dict(precision="mixed"), dict(precision="fp64", precond="jacobi")):
+    for pc in ("line", "jacobi"):
         with pytest.raises(ftgcr.FTGCRError):
-            ftgcr.Solver(p.D, p.mu, oracle_order=True, **kw)
+            ftgcr.Solver(p.D, p.mu, precision="mixed", precond=pc, oracle_order=True)
+
+
+@pytest.mark.parametrize("precond", ["jacobi", "identity"])
+def test_oracle_order_with_other_preconditioners_takes_the_oracles_steps(precond):
+    p = inputs.hill_problem(96, 48, rhs="random", seed=5)
+    pc = {"jacobi": oracle.PRECOND_JACOBI, "identity": oracle.PRECOND_IDENTITY}[precond]
+    o = oracle.ftgcr(p.D, p.R, p.mu, 4, 1e-10, precond=pc, max_steps=20000)
+    with ftgcr.Solver(p.D, p.mu, k=4, tol=1e-10, precision="fp64", precond=precond, oracle_order=True) as s:
+        Rt = torch.from_numpy(p.R).cuda()
+        x = torch.zeros_like(Rt)
+        s.solve(Rt, x)
+        st = s.stats()
+    assert o["converged"] and st["converged"] and st["steps"] == o["steps"]
+    assert rel_err(x.cpu().numpy(), o["x"]) <= 1e-10
