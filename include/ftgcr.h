@@ -124,11 +124,14 @@ typedef struct {
  * (Dot2, Ogita-Rump-Oishi), as in the oracle.  (2) Line preconditioner:
  * rows of 256 or more columns take a chunked scan by default (one warp per
  * row, 32 chunks joined by their exact affine maps); with this flag every
- * row takes the oracle's Thomas elimination (one lane per row).  Either
- * default keeps the fault decisions of Algorithm 1 and the solution within
- * rounding of the oracle's, but in long, slowly converging solves (the
- * singular mu = 0 problem, hundreds of steps) the exit can come some steps
- * earlier or later; with this flag the exit steps are the oracle's.
+ * row takes the oracle's Thomas elimination (one lane per row).  (3) The
+ * operator inside the solve: fused multiply-adds by default (9 FP64
+ * operations a point instead of 13), the oracle's form with this flag
+ * (ftgcr_apply_operator always takes the oracle's form).  The defaults keep
+ * the fault decisions of Algorithm 1 and the solution within rounding of the
+ * oracle's, but in long, slowly converging solves (the singular mu = 0
+ * problem, hundreds of steps) the exit can come some steps earlier or later;
+ * with this flag the exit steps are the oracle's.
  * FTGCR_MIXED: FTGCR_ERR_ARG. */
 #define FTGCR_FLAG_ORACLE_ORDER 16
 /* Every solve of the handle starts from x = 0: x is output only, and its

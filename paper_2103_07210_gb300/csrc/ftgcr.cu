@@ -1028,7 +1028,7 @@ int create_impl(ftgcr_handle* h, const double* D_host_or_dev, bool D_on_device) 
   sd.inner_tol2 = h->inner_tol * h->inner_tol;
   sd.protect = (h->flags & FTGCR_FLAG_UNPROTECTED) ? 0 : 1;
   sd.zero_guess = (h->flags & FTGCR_FLAG_ZERO_GUESS) ? 1 : 0;
-  sd.dot2 = (h->flags & FTGCR_FLAG_ORACLE_ORDER) ? 1 : 0;
+  sd.oracle_order = (h->flags & FTGCR_FLAG_ORACLE_ORDER) ? 1 : 0;
   sd.split = h->split;
   sd.cs_off = (int)h->plan.cs_off;
   sd.cs_clobber = h->plan.cs_clobber;
@@ -1904,7 +1904,7 @@ extern "C" int ftgcr_solve_noalloc(const ftgcr_grid* grid, const double* D, int3
   sd.inner_tol2 = h.inner_tol * h.inner_tol;
   sd.protect = (h.flags & FTGCR_FLAG_UNPROTECTED) ? 0 : 1;
   sd.zero_guess = (h.flags & FTGCR_FLAG_ZERO_GUESS) ? 1 : 0;
-  sd.dot2 = (h.flags & FTGCR_FLAG_ORACLE_ORDER) ? 1 : 0;
+  sd.oracle_order = (h.flags & FTGCR_FLAG_ORACLE_ORDER) ? 1 : 0;
   sd.split = 0;
   sd.cs_off = (int)h.plan.cs_off;
   sd.cs_clobber = 0;

@@ -108,7 +108,7 @@ struct SolveDev {
   int nt_hmax;  // rows of the tallest row tile
   long long N, max_steps;
   int max_outer;
-  int dot2;  // FP64 inner products: each thread's products summed compensated (Dot2), else by fma
+  int oracle_order;  // FP64: Dot2 sums and the oracle's stencil form (else fma forms)
   double tol2, inner_tol2;
   // operator (inner precision)
   const T* Tx;
@@ -439,6 +439,17 @@ __device__ __forceinline__ double stencil5_fma(double v, double ve, double vw, d
   if (hasN) s = fma(tyc, vn - v, s);
   s = fma(txw, vw - v, s);
   return fma(txc, ve - v, s);
+}
+
+// The solve's operator: FP32 vectors in the oracle's form; FP64 vectors in it
+// only in the oracle's operation order, else with fused multiply-adds.
+template <typename T>
+__device__ __forceinline__ T stencil_op(int oracle_order, T v, T ve, T vw, T vn, T vs, T txc, T txw, T tyc, T tys,
+                                        T muA, bool hasN, bool hasS) {
+  if constexpr (sizeof(T) == 8) {
+    if (!oracle_order) return stencil5_fma(v, ve, vw, vn, vs, txc, txw, tyc, tys, muA, hasN, hasS);
+  }
+  return stencil5<T>(v, ve, vw, vn, vs, txc, txw, tyc, tys, muA, hasN, hasS);
 }
 
 // Shared-memory row layout: element i of a row lives at i + i/32 (one pad

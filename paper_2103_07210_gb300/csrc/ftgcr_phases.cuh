@@ -913,15 +913,16 @@ __device__ __forceinline__ T stencil_smem(const SolveDev<T>& sd, const T* sm, in
   const T v = row[sk(i)];
   const T vn = hasN ? row[stride + sk(i)] : T(0);
   const T vs = hasS ? row[-stride + sk(i)] : T(0);
-  return stencil5<T>(v, row[sk(ie)], row[sk(iw)], vn, vs, __ldg(sd.Tx + g), __ldg(sd.Tx + (long long)j * nlon + iw),
-                     hasN ? __ldg(sd.Ty + g) : T(0), hasS ? __ldg(sd.Ty + g - nlon) : T(0), __ldg(sd.muA + j), hasN,
-                     hasS);
+  return stencil_op<T>(sd.oracle_order, v, row[sk(ie)], row[sk(iw)], vn, vs, __ldg(sd.Tx + g),
+                       __ldg(sd.Tx + (long long)j * nlon + iw), hasN ? __ldg(sd.Ty + g) : T(0),
+                       hasS ? __ldg(sd.Ty + g - nlon) : T(0), __ldg(sd.muA + j), hasN, hasS);
 }
 
-// Stencil on a global-memory field (initialisation / final residual).
+// Stencil on a global-memory field (initialisation / final residual; the
+// operator entry point, always in the oracle's form).
 template <typename V>
 __device__ __forceinline__ V stencil_global(const V* x, const V* Tx, const V* Ty, const V* muA, int nlon, int nlat,
-                                            int j, int i) {
+                                            int j, int i, int oracle_order = 1) {
   const int ie = (i + 1 == nlon) ? 0 : i + 1;
   const int iw = (i == 0) ? nlon - 1 : i - 1;
   const long long g = (long long)j * nlon + i;
@@ -929,9 +930,9 @@ __device__ __forceinline__ V stencil_global(const V* x, const V* Tx, const V* Ty
   const V v = ldcg(x + g);
   const V vn = hasN ? ldcg(x + g + nlon) : V(0);
   const V vs = hasS ? ldcg(x + g - nlon) : V(0);
-  return stencil5<V>(v, ldcg(x + (long long)j * nlon + ie), ldcg(x + (long long)j * nlon + iw), vn, vs, __ldg(Tx + g),
-                     __ldg(Tx + (long long)j * nlon + iw), hasN ? __ldg(Ty + g) : V(0), hasS ? __ldg(Ty + g - nlon) : V(0),
-                     __ldg(muA + j), hasN, hasS);
+  return stencil_op<V>(oracle_order, v, ldcg(x + (long long)j * nlon + ie), ldcg(x + (long long)j * nlon + iw), vn,
+                       vs, __ldg(Tx + g), __ldg(Tx + (long long)j * nlon + iw), hasN ? __ldg(Ty + g) : V(0),
+                       hasS ? __ldg(Ty + g - nlon) : V(0), __ldg(muA + j), hasN, hasS);
 }
 
 // Element (j, i) of a row-tile loop over 16-byte vectors: flat index ->
@@ -1235,9 +1236,9 @@ __device__ __forceinline__ void step_stencil(const SolveDev<T>& sd, const Ctx<T>
   const int nlon = sd.nlon, nlat = sd.nlat, stride = row_stride(nlon);
   Acc<T> ad[KB];
   Acc<T> ah, aq;  // mixed: <r', L(e)>, <L(e), L(e)>
-  ah.mode(sd.dot2), aq.mode(sd.dot2);
+  ah.mode(sd.oracle_order), aq.mode(sd.oracle_order);
 #pragma unroll
-  for (int l = 0; l < KB; ++l) ad[l].mode(sd.dot2);
+  for (int l = 0; l < KB; ++l) ad[l].mode(sd.oracle_order);
   if (nlon % W == 0) {
     const int nvr = nlon / W, total = (rt.j1 - rt.j0) * nvr;
     for (int idx = threadIdx.x; idx < total; idx += kThreads) {
@@ -1264,9 +1265,9 @@ __device__ __forceinline__ void step_stencil(const SolveDev<T>& sd, const Ctx<T>
         const int iw = (i == 0) ? nlon - 1 : i - 1;
         const T x = row[sk(i)];
         ev.v[w] = x;
-        le.v[w] = stencil5<T>(x, row[sk(ie)], row[sk(iw)], hasN ? row[stride + sk(i)] : T(0),
-                              hasS ? row[-stride + sk(i)] : T(0), tx.v[w], w == 0 ? txw0 : tx.v[w - 1],
-                              hasN ? ty.v[w] : T(0), hasS ? tys.v[w] : T(0), muA, hasN, hasS);
+        le.v[w] = stencil_op<T>(sd.oracle_order, x, row[sk(ie)], row[sk(iw)], hasN ? row[stride + sk(i)] : T(0),
+                                hasS ? row[-stride + sk(i)] : T(0), tx.v[w], w == 0 ? txw0 : tx.v[w - 1],
+                                hasN ? ty.v[w] : T(0), hasS ? tys.v[w] : T(0), muA, hasN, hasS);
       }
       if (write_e) stv(c.eW + v.g, ev);
       stv(c.LeW + v.g, le);
@@ -1329,7 +1330,7 @@ __device__ __noinline__ void phase_pa(const SolveDev<T>& sd, const Ctx<T>& c, in
     ps.nfl = collect_flips(sd, c.t, FUSED ? (kStateVecs | (1u << V_E)) : (1u << V_E), (long long)rt.h0 * nlon,
                            (long long)rt.h1 * nlon, ps.fl);
   Acc<T> an;
-  an.mode(sd.dot2);
+  an.mode(sd.oracle_order);
   step_axpy<T, KB, FUSED>(sd, c, rt, sm, ps, an);
   step_precond<T, false, GL>(sd, c, rt, sm, cs, ps);
   step_stencil<T, KB>(sd, c, rt, sm, ps, part_out, &an, true);
@@ -1352,7 +1353,7 @@ __device__ __noinline__ void phase_pa_any(const SolveDev<T>& sd, const Ctx<T>& c
   const int nlon = sd.nlon, stride = row_stride(nlon);
   RowTile rt = row_tile(sd.nlat, sd.nt, tau);
   Acc<T> an;
-  an.mode(sd.dot2);
+  an.mode(sd.oracle_order);
   if (mode == 2) {
     stage_rows(c.eW, rt.h0, rt.h1, nlon, sm, stride);
     if (sd.cs_clobber && threadIdx.x == 0) ps.cs_solve = -1;  // the rows overwrote staged constants
@@ -1393,7 +1394,7 @@ __device__ __noinline__ void phase_pb(const SolveDev<T>& sd, const Ctx<T>& c, in
   __syncthreads();
   const int nfl = ps.nfl;
   Acc<T> a0, a1;
-  a0.mode(sd.dot2), a1.mode(sd.dot2);
+  a0.mode(sd.oracle_order), a1.mode(sd.oracle_order);
   auto finish = [&](long long g, T pa, T la, T rv) {
     if (nfl) {
       pa = apply_flips(pa, g, V_P, nfl, ps.fl);
@@ -1492,7 +1493,7 @@ __device__ __noinline__ void phase_restore(const SolveDev<T>& sd, const Ctx<T>& 
   __syncthreads();
   const int nfl = ps.nfl, npt = ps.npt;
   Acc<T> a0, a1;
-  a0.mode(sd.dot2), a1.mode(sd.dot2);
+  a0.mode(sd.oracle_order), a1.mode(sd.oracle_order);
   for (long long g = e0 + threadIdx.x; g < e1; g += kThreads) {
     T ph = ldcg(c.phiS + g), rr = ldcg(c.rS + g), pp = ldcg(c.pS + g), ll = ldcg(c.lpS + g);
     if (npt) {
@@ -1593,7 +1594,7 @@ __device__ __forceinline__ void init_rows(const SolveDev<T>& sd, const Ctx<T>& c
         xv = T(0);
       } else {
         // FP64 path only (T = double): r0 = L(x0) - R
-        const T Lx = (T)stencil_global<double>(sd.x0, sd.Tx64, sd.Ty64, sd.muA64, nlon, nlat, j, i);
+        const T Lx = (T)stencil_global<double>(sd.x0, sd.Tx64, sd.Ty64, sd.muA64, nlon, nlat, j, i, sd.oracle_order);
         rv = Lx - (T)ldcg(sd.R + g);
         xv = (T)ldcg(sd.x0 + g);
         if (own) aR.add((T)ldcg(sd.R + g), (T)ldcg(sd.R + g));
@@ -1649,9 +1650,9 @@ __device__ __forceinline__ void init_stencil(const SolveDev<T>& sd, const Ctx<T>
         const int iw = (i == 0) ? nlon - 1 : i - 1;
         const T x = row[sk(i)];
         pv.v[w] = x;
-        lv.v[w] = stencil5<T>(x, row[sk(ie)], row[sk(iw)], hasN ? row[stride + sk(i)] : T(0),
-                              hasS ? row[-stride + sk(i)] : T(0), tx.v[w], w == 0 ? txw0 : tx.v[w - 1],
-                              hasN ? ty.v[w] : T(0), hasS ? tys.v[w] : T(0), muA, hasN, hasS);
+        lv.v[w] = stencil_op<T>(sd.oracle_order, x, row[sk(ie)], row[sk(iw)], hasN ? row[stride + sk(i)] : T(0),
+                                hasS ? row[-stride + sk(i)] : T(0), tx.v[w], w == 0 ? txw0 : tx.v[w - 1],
+                                hasN ? ty.v[w] : T(0), hasS ? tys.v[w] : T(0), muA, hasN, hasS);
         a0.add(rr.v[w], lv.v[w]);
         a1.add(lv.v[w], lv.v[w]);
       }
@@ -1713,7 +1714,7 @@ __device__ __noinline__ void phase_init(const SolveDev<T>& sd, const Ctx<T>& c, 
   if (!(ps.cs_solve == sidx && ps.cs_tile == tau)) stage_line_consts<T, GL>(sd, rt.h0, rt.h1, cs);
   __syncthreads();
   Acc<T> an, aR;
-  an.mode(sd.dot2), aR.mode(sd.dot2);
+  an.mode(sd.oracle_order), aR.mode(sd.oracle_order);
   AccF64 aR64;
   constexpr int W = V16<T>::W;
   // the common case, 16-byte accesses (the caller's R must be aligned for them)
@@ -1725,7 +1726,7 @@ __device__ __noinline__ void phase_init(const SolveDev<T>& sd, const Ctx<T>& c, 
   precond_tile<T, false, GL>(sd, rt.h0, rt.h1 - rt.h0, sm, stride, cs);
   __syncthreads();
   Acc<T> a0, a1;
-  a0.mode(sd.dot2), a1.mode(sd.dot2);
+  a0.mode(sd.oracle_order), a1.mode(sd.oracle_order);
   init_stencil<T>(sd, c, rt, sm, ps, a0, a1, vec);
   init_partials<T>(ps, part_out, &an, &aR, a0, a1, true, c.rin_R && sizeof(T) == 4 ? &aR64 : nullptr);
   if (threadIdx.x == 0) {
@@ -1748,7 +1749,7 @@ __device__ __noinline__ void phase_init_any(const SolveDev<T>& sd, const Ctx<T>&
   if (threadIdx.x == 0)
     ps.nfl = collect_flips(sd, c.t, kStateVecs, (long long)rt.j0 * nlon, (long long)rt.j1 * nlon, ps.fl);
   Acc<T> an, aR, a0, a1;
-  an.mode(sd.dot2), aR.mode(sd.dot2), a0.mode(sd.dot2), a1.mode(sd.dot2);
+  an.mode(sd.oracle_order), aR.mode(sd.oracle_order), a0.mode(sd.oracle_order), a1.mode(sd.oracle_order);
   AccF64 aR64;
   constexpr int W = V16<T>::W;
   const bool ralign = !c.rin_R || (reinterpret_cast<unsigned long long>(sd.R) & 15ull) == 0ull;
@@ -1900,7 +1901,7 @@ __device__ __noinline__ void phase_fin(const SolveDev<T>& sd, const Ctx<T>& c, i
   const int nlon = sd.nlon, nlat = sd.nlat;
   const RowTile rt = row_tile(nlat, sd.nt, tau);
   Acc<double> acc;
-  acc.mode(sd.dot2);
+  acc.mode(sd.oracle_order);
   if (sd.mixed) {
     // the tile's rows are contiguous: a copy, four loads in flight per thread
     const double* xs = c.xsrc;
@@ -1939,10 +1940,10 @@ __device__ __noinline__ void phase_fin(const SolveDev<T>& sd, const Ctx<T>& c, i
           return v;
         };
         const double v = val(g);
-        const double Lx = stencil5<double>(v, val(base + ie), val(base + iw), hasN ? val(g + nlon) : 0.0,
-                                           hasS ? val(g - nlon) : 0.0, __ldg(sd.Tx64 + g), __ldg(sd.Tx64 + base + iw),
-                                           hasN ? __ldg(sd.Ty64 + g) : 0.0, hasS ? __ldg(sd.Ty64 + g - nlon) : 0.0,
-                                           __ldg(sd.muA64 + j), hasN, hasS);
+        const double Lx = stencil_op<double>(sd.oracle_order, v, val(base + ie), val(base + iw),
+                                             hasN ? val(g + nlon) : 0.0, hasS ? val(g - nlon) : 0.0, __ldg(sd.Tx64 + g),
+                                             __ldg(sd.Tx64 + base + iw), hasN ? __ldg(sd.Ty64 + g) : 0.0,
+                                             hasS ? __ldg(sd.Ty64 + g - nlon) : 0.0, __ldg(sd.muA64 + j), hasN, hasS);
         const double res = Lx - ldcg(sd.R + g);
         sd.xout[g] = v;
         acc.add(res, res);
