@@ -51,9 +51,9 @@ def algorithmic_bytes(steps: int, outer: int, k: int = K, s: int = 4, N: int = N
 
 # DRAM traffic per launch of the persistent kernel from one ncu capture, valid
 # only for the kernel sources it was taken on (sha256 of the CUDA sources).
-NCU_TRAFFIC = {"sources_sha256": "59b68c8d7e54b60ce1c1a40f1142e779542c57d2eb10eb76a4fc1aa21e6d3871",
-               "bytes_per_launch": 23566592 + 6683136,  # mixed 1024x512 (read + write)
-               "large": {"2048x1024": 2652711936 + 1323554816, "4096x2048": 12415260160 + 5120877568}}
+NCU_TRAFFIC = {"sources_sha256": "d168926416590449a9521c4fa8c62e64a664158f6af5e4915f54f5654b670522",
+               "bytes_per_launch": 23570688 + 6663936,  # mixed 1024x512 (read + write)
+               "large": {"2048x1024": 2652937728 + 1323485440, "4096x2048": 12415849472 + 5120951552}}
 
 
 def sources_hash() -> str:
