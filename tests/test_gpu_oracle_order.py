@@ -89,3 +89,18 @@ def test_oracle_order_with_other_preconditioners_takes_the_oracles_steps(precond
         st = s.stats()
     assert o["converged"] and st["converged"] and st["steps"] == o["steps"]
     assert rel_err(x.cpu().numpy(), o["x"]) <= 1e-10
+
+
+@pytest.mark.parametrize("nlon,nlat,k,flip", [(128, 64, 4, None), (100, 37, 3, (5, "r", 1234, 60)),
+                                              (64, 32, 8, (3, "p", 700, 52))])
+def test_oracle_order_is_bitwise_the_oracle_on_rows_under_256_columns(nlon, nlat, k, flip):
+    """In the oracle's operation order (compensated sums, the oracle's stencil
+    form, serial row solves) an FP64 solve on rows under 256 columns takes the
+    oracle's arithmetic step by step: the same decisions and the same solution
+    bit for bit, with or without a flip."""
+    p = inputs.hill_problem(nlon, nlat, rhs="random", seed=17)
+    faults = [flip] if flip else []
+    o = oracle.ftgcr(p.D, p.R, p.mu, k, 1e-10, faults=faults)
+    x, s = _gpu(p, p.R, p.mu, k, True, faults=faults, max_steps=0)
+    assert s["steps"] == o["steps"] and s["detect_steps"] == o["detect_steps"]
+    assert np.array_equal(x, o["x"])
