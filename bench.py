@@ -514,7 +514,8 @@ def bench_batch(torch, ftgcr, dev, n=128, seed=42, reps=3):
 
 
 def bench_serving(torch, ftgcr, dev, n_req=2000, load=0.8, seed=7, hills_per_size=4, n_cap=300,
-                  sweep_loads=(0.5, 1.0, 1.2), n_sweep=400, tune_concurrency=16, n_tuned=600, n_limited=1000):
+                  sweep_loads=(0.5, 1.0, 1.2), n_sweep=400, tune_concurrency=16, n_tuned=600, n_limited=1000,
+                  n_isolated=400):
     """Open-loop serving: n_req requests with Poisson arrivals at `load` x the
     measured capacity; sizes U{256x128, 512x256, 1024x512, 2048x1024}, mixed
     precision, hills drawn per problem, 1% carrying one bit flip.  Right-hand
@@ -527,7 +528,9 @@ def bench_serving(torch, ftgcr, dev, n_req=2000, load=0.8, seed=7, hills_per_siz
     each request): taller bands raise throughput a little but lengthen a lone
     request's solve, so the default bands stay the headline.  And a run with
     the admission limit (ftgcr_server_set_max_points) at 1.1 x the largest
-    request's points, at 0.8 x its own measured capacity."""
+    request's points, at 0.8 x its own measured capacity.  And `isolated`: the
+    first n_isolated requests served one at a time, whose p99 / p50 is what
+    the size mix alone gives with no contention."""
     import threading
 
     sizes = [(256, 128), (512, 256), (1024, 512), (2048, 1024)]
@@ -584,7 +587,28 @@ def bench_serving(torch, ftgcr, dev, n_req=2000, load=0.8, seed=7, hills_per_siz
         pi, faults = reqs[i]
         return submit_p(srv, pi, faults)
 
-    def serve(n_req, sweep_loads, max_points=0):
+    def isolated(srv, n):
+        """The same request stream served one request at a time (each waits
+        for the previous to finish): latency with no contention at all, the
+        floor the size mix itself sets under p50 and p99."""
+        lat, by = [], {}
+        for i in range(n):
+            t0 = time.perf_counter()
+            t, x = submit(srv, i)
+            r = srv.next(timeout=30)
+            dt = 1e3 * (time.perf_counter() - t0)
+            give_x(x)
+            if r is None or r[0] != t:
+                return None
+            p = probs[reqs[i][0]][0]
+            lat.append(dt)
+            by.setdefault(f"{p.nlon}x{p.nlat}", []).append(dt)
+        lat = np.array(lat)
+        p50, p99 = float(np.percentile(lat, 50)), float(np.percentile(lat, 99))
+        return {"requests": n, "p50_ms": p50, "p99_ms": p99, "p99_over_p50": p99 / p50,
+                "median_ms_by_size": {k: float(np.median(v)) for k, v in sorted(by.items())}}
+
+    def serve(n_req, sweep_loads, max_points=0, n_isolated=0):
         with ftgcr.Server(max_slots=64, epoch_rounds=24) as srv:
             srv.set_max_points(max_points)
             warm = [submit_p(srv, pi) for pi in range(len(probs))]  # a handle set up for every problem
@@ -645,6 +669,7 @@ def bench_serving(torch, ftgcr, dev, n_req=2000, load=0.8, seed=7, hills_per_siz
                 wall = time.perf_counter() - start
                 return results, kept, 1e3 * np.array(lat), wall
 
+            iso = isolated(srv, n_isolated) if n_isolated else None
             results, kept, lat_ms, wall = open_loop(load, n_req, seed, True)
             info = srv.info()
             # latency against offered load: shorter runs at other fractions of capacity
@@ -673,9 +698,10 @@ def bench_serving(torch, ftgcr, dev, n_req=2000, load=0.8, seed=7, hills_per_siz
                 "faulty_requests": sum(1 for _, f in reqs[:n_req] if f), "epochs": info["epochs"],
                 "handles": info["handles"], "sizes": "U{256x128,512x256,1024x512,2048x1024}", "precision": "mixed",
                 "io": "rhs and x in pinned host memory, D resident with a coefficient key",
-                "bitwise_equal_to_alone_sample": same, "load_sweep": sweep}
+                "bitwise_equal_to_alone_sample": same, "load_sweep": sweep,
+                **({"isolated": iso} if n_isolated else {})}
 
-    out = serve(n_req, sweep_loads)
+    out = serve(n_req, sweep_loads, n_isolated=n_isolated)
     out["tiles"] = "default (ftgcr_create's own choice)"
     tiling.update(tuned)
     d = serve(n_tuned, ())
