@@ -23,12 +23,15 @@ def main(argv=None):
     ap.add_argument("--rounds", choices=list(ftgcr.ROUNDS), default="auto")
     ap.add_argument("--rhs", choices=["flow", "random"], default="flow")
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--zero-guess", action="store_true",
+                    help="declare x = 0 on entry (FTGCR_FLAG_ZERO_GUESS), as the benchmark's solves do")
     a = ap.parse_args(argv)
     import torch
 
     p = inputs.hill_problem(a.nlon, a.nlat, rhs=a.rhs)
     R = torch.from_numpy(p.R).cuda()
-    with ftgcr.Solver(p.D, p.mu, k=a.k, tol=a.tol, precision=a.precision, rounds=a.rounds) as s:
+    with ftgcr.Solver(p.D, p.mu, k=a.k, tol=a.tol, precision=a.precision, rounds=a.rounds,
+                      zero_guess=a.zero_guess) as s:
         times = []
         for _ in range(max(1, a.repeat)):
             x = torch.zeros_like(R)

@@ -12,7 +12,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 @pytest.mark.parametrize("args", [["--nlon", "64", "--nlat", "32", "--precision", "fp64"],
-                                  ["--nlon", "256", "--nlat", "128", "--repeat", "2"]])
+                                  ["--nlon", "256", "--nlat", "128", "--repeat", "2"],
+                                  ["--nlon", "256", "--nlat", "128", "--zero-guess"]])
 def test_command_line_solves_and_reports(args):
     r = subprocess.run([sys.executable, "-m", "paper_2103_07210_gb300"] + args, cwd=ROOT, capture_output=True,
                        text=True, timeout=600)
