@@ -1,8 +1,9 @@
 """Streamed step rounds (FTGCR_FLAG_STREAMED_ROUNDS): every CTA walks one
 tall band row by row, its operand rows staged into shared memory by
 per-thread asynchronous copies, and the band's edge rows take their stencil in
-a second pass.  Forced here on grids the oracle solves in seconds: one-row and
-multi-row bands, rows of one, two and a ragged second chunk of columns,
+a second pass.  Forced here on grids the oracle solves in seconds: one-row to
+64-row bands (the tallest allowed), more bands than SMs, rows of one, two and
+a ragged second chunk of columns,
 k = 1..8, flips of every vector, data-loss events, and batches that mix
 streamed solves with solves of the other layouts.  Every solution matches the
 FP64 oracle to 1e-10 at tol 1e-13; batched results equal solo results
@@ -30,6 +31,9 @@ CASES = [
     (1000, 33, 1, "random", 2),    # one short chunk; two tall bands
     (1024, 33, 5, "random", 1),    # one band: every row interior
     (2048, 64, 4, "flow", 64),     # two chunks per row, one-row bands
+    (1024, 128, 4, "flow", 2),     # 64-row bands, the tallest a streamed band may be
+    (1024, 130, 3, "flow", 2),     # 65-row bands asked for: raised to three bands of 43-44 rows
+    (1024, 512, 4, "random", 256), # 2-row bands, more bands than SMs: a CTA walks two a round
 ]
 
 
@@ -63,6 +67,19 @@ def test_streamed_matches_oracle(oracle_x, case):
     xref, conv, _ = oracle_x[case[:4]]
     assert conv
     assert rel_err(x, xref) <= 1e-10
+
+
+def test_streamed_bands_stay_within_64_rows():
+    """A tiling whose bands would pass 64 rows is raised to the fewest bands
+    of at most 64 rows (at 1024 x 9729, one band more than there are SMs);
+    a tiling of 64-row bands is kept.  The 10 M-point solve is checked by its
+    own true residual."""
+    for nlat, tiles, want in ((130, 2, 3), (128, 2, 2), (9729, 0, 153)):
+        p = inputs.hill_problem(1024, nlat)
+        st, x, info = _solve(p, 4, tiles, tol=1e-10)
+        assert info["tiles"] == want and info["streamed_rounds"], (nlat, tiles, info["tiles"])
+        assert st == ftgcr.OK and info["converged"]
+        assert info["res_final_true"] <= 1e-10 * info["norm_R"]
 
 
 def test_streamed_is_deterministic_and_close_to_fused():
