@@ -104,3 +104,33 @@ def test_oracle_order_is_bitwise_the_oracle_on_rows_under_256_columns(nlon, nlat
     x, s = _gpu(p, p.R, p.mu, k, True, faults=faults, max_steps=0)
     assert s["steps"] == o["steps"] and s["detect_steps"] == o["detect_steps"]
     assert np.array_equal(x, o["x"])
+
+
+def test_batch_mixing_both_orders_equals_each_solve_alone():
+    """One launch over FP64 solves in the default order and in the oracle's
+    order (each solve carries its own flag): every result, the step count
+    included, is bitwise the same solve alone, and those in the oracle's
+    order are bitwise the oracle's."""
+    probs = [inputs.hill_problem(n, m, rhs="random", seed=60 + i) for i, (n, m) in
+             enumerate([(128, 64), (96, 48), (300, 40), (128, 64)])]
+    orders = [True, False, True, False]
+    solvers = [ftgcr.Solver(p.D, p.mu, k=4, tol=1e-10, precision="fp64", oracle_order=o) for p, o in zip(probs, orders)]
+    try:
+        R = [torch.from_numpy(p.R).cuda() for p in probs]
+        alone, steps = [], []
+        for s, r in zip(solvers, R):
+            x = torch.zeros_like(r)
+            s.solve(r, x)
+            alone.append(x.cpu().numpy())
+            steps.append(s.stats()["steps"])
+        xs = [torch.zeros_like(r) for r in R]
+        ftgcr.solve_batch(solvers, R, xs)
+        torch.cuda.synchronize()
+        for s, x, a, st in zip(solvers, xs, alone, steps):
+            assert np.array_equal(x.cpu().numpy(), a) and s.stats()["steps"] == st
+    finally:
+        for s in solvers:
+            s.close()
+    for p, o, a in zip(probs, orders, alone):
+        if o and p.nlon < 256:
+            assert np.array_equal(a, oracle.ftgcr(p.D, p.R, p.mu, 4, 1e-10)["x"])
