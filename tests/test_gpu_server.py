@@ -20,8 +20,10 @@ KEYS = ("steps", "cycles", "restarts", "faults_injected", "faults_detected", "ou
 
 
 def _requests(seed):
-    """(problem, precision, faults) of a small mix; shapes repeat with new hills
-    so that pooled handles get new coefficients."""
+    """(problem, precision, faults, oracle_order) of a small mix; shapes repeat
+    with new hills so that pooled handles get new coefficients, and some FP64
+    requests of a shape ask for the oracle's operation order (a handle of
+    their own: pooled handles match on the flags too)."""
     shapes = [(128, 64), (64, 32), (256, 128), (128, 64), (40, 21), (512, 256), (256, 128), (64, 32), (1024, 512),
               (128, 64), (100, 7), (256, 128)]
     out = []
@@ -36,13 +38,13 @@ def _requests(seed):
             faults = [(5, "ap", 777, nb - 2), (9, "e", 12345, 20)]
         if q == 7:
             faults = [(4, "r", 33, nb - 2)]
-        out.append((p, prec, faults))
+        out.append((p, prec, faults, prec == "fp64" and q in (3, 9, 10)))
     return out
 
 
-def _alone(p, prec, faults, k, tiles=0):
+def _alone(p, prec, faults, k, tiles=0, oracle_order=False):
     # tiles: the bands the server reported for the request
-    with ftgcr.Solver(p.D, p.mu, k=k, tol=1e-10, precision=prec, tiles=tiles) as s:
+    with ftgcr.Solver(p.D, p.mu, k=k, tol=1e-10, precision=prec, tiles=tiles, oracle_order=oracle_order) as s:
         R = torch.from_numpy(p.R).cuda()
         x = torch.zeros_like(R)
         s.solve(R, x, faults=faults)
@@ -54,12 +56,13 @@ def test_served_results_are_bitwise_the_solo_results(epoch_rounds):
     reqs = _requests(101)
     k = 4
     with ftgcr.Server(max_slots=4, epoch_rounds=epoch_rounds) as srv:
-        Ds = [torch.from_numpy(p.D).cuda() for p, _, _ in reqs]
-        Rs = [torch.from_numpy(p.R).cuda() for p, _, _ in reqs]
+        Ds = [torch.from_numpy(p.D).cuda() for p, _, _, _ in reqs]
+        Rs = [torch.from_numpy(p.R).cuda() for p, _, _, _ in reqs]
         xs = [torch.zeros_like(R) for R in Rs]
         tickets = []
-        for q, (p, prec, f) in enumerate(reqs):
-            tickets.append(srv.submit(Ds[q], p.mu, Rs[q], xs[q], k=k, tol=1e-10, precision=prec, faults=f))
+        for q, (p, prec, f, oo) in enumerate(reqs):
+            tickets.append(srv.submit(Ds[q], p.mu, Rs[q], xs[q], k=k, tol=1e-10, precision=prec, faults=f,
+                                      oracle_order=oo))
             if q % 4 == 3:
                 time.sleep(0.002)  # later requests arrive while earlier ones run
         if epoch_rounds == 5:  # completion queue
@@ -76,8 +79,8 @@ def test_served_results_are_bitwise_the_solo_results(epoch_rounds):
     for q, res in enumerate(results):
         assert res is not None, q
         st, ss = res
-        p, prec, f = reqs[q]
-        xa, sa = _alone(p, prec, f, k, ss["tiles"])
+        p, prec, f, oo = reqs[q]
+        xa, sa = _alone(p, prec, f, k, ss["tiles"], oo)
         assert st == ftgcr.OK and sa["converged"], (q, st, sa)
         assert np.array_equal(xs[q].cpu().numpy(), xa), q
         for key in KEYS:
